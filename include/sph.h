@@ -1,0 +1,208 @@
+/*
+ * sph.h - C ABI of the GB300 (sm_103a) solid-body SPH right-hand-side library.
+ *
+ * The library evaluates, on one GPU, the per-time-step right-hand side of the
+ * SPH method of Schaefer et al. (2016), "A smooth particle hydrodynamics code
+ * to model collisions between solid, self-gravitating objects":
+ *   octree over Morton-sorted particles (Sect. 3.5.1), interaction partners
+ *   (Sect. 3.5.2), kernel sums for continuity, momentum with the full stress
+ *   tensor and internal energy (Sect. 3.1.2, Eqs. continuity_equation_sph,
+ *   accel_artvisc, energy_sph), equations of state (Sect. 2.5), Hooke's law
+ *   with Jaumann rotation (Sect. 2.4, Eqs. stresstensor_evolution,
+ *   rotation_terms), von Mises yield (Sect. 2.6), Grady-Kipp damage
+ *   (Sects. 2.7, 3.2), artificial viscosity and stress (Sects. 3.1.3, 3.1.4),
+ *   XSPH (Sect. 3.1.5), the linear-consistency tensor (Sect. 3.1.6, Eq.
+ *   ext_sph), Barnes-Hut self-gravity (Sect. 3.3, Eq. gravitational_force)
+ *   and the predictor-corrector integrator (Sect. 3.4.1).
+ *
+ * Conventions shared by every entry point
+ *  - All particle arrays are caller-owned DEVICE memory; the library never
+ *    frees or reallocates them.  Host pointers are only the sph_material
+ *    array, sph_params, sph_state/sph_derivs structs themselves (their
+ *    fields point to device memory) and the ctx handle.
+ *  - Particle data is structure-of-arrays, FP64 unless stated.  Symmetric
+ *    tensors are stored component-major: 3D (xx, yy, zz, xy, xz, yz), 2D
+ *    (xx, yy, xy); component k of particle a is at S[k*n + a].
+ *  - h is the kernel's support radius: W(r; h) = 0 for r > h (Sect. 3.1.1).
+ *    Pairs use h_ab = (h_a + h_b) / 2 (Sect. 4.2).
+ *  - A context (sph_ctx) owns all scratch, sized once by sph_create; no
+ *    other call allocates device memory.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *    NULL = legacy default stream).  Argument errors are reported at once
+ *    (SPH_ERR_INVALID); errors found by kernels (capacity exceeded,
+ *    non-finite input) set a device error word that sph_sync_status reads,
+ *    and that blocking calls (params.check = 1) read before returning.
+ *  - No call traps, asserts or spins without a bound on the device.
+ *  - Not thread-safe per context; different contexts are independent.
+ */
+#ifndef SPH_GB300_H
+#define SPH_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SPH_OK = 0,
+  SPH_ERR_INVALID = 1,   /* bad argument (checked on the host)                 */
+  SPH_ERR_CAPACITY = 2,  /* a list or node capacity of the context was exceeded */
+  SPH_ERR_NONFINITE = 3, /* NaN/Inf in the input, or h <= 0, rho <= 0           */
+  SPH_ERR_TIMEOUT = 4,   /* a bounded device loop reached its iteration limit  */
+  SPH_ERR_CUDA = 5       /* a CUDA runtime call failed; see sph_last_error     */
+} sph_status;
+
+enum { SPH_EOS_LINEAR = 0, SPH_EOS_MURNAGHAN = 1, SPH_EOS_TILLOTSON = 2, SPH_EOS_ISOTHERMAL = 3 };
+enum { SPH_FP64 = 0, SPH_MIXED = 1 };
+enum { SPH_MAX_MATERIALS = 8 };
+
+/* Material (Sect. 2.5-2.7).  K0 is the bulk modulus used in Young's modulus
+ * E = 9 K mu / (3K + mu) and the crack speed c_g (Sect. 3.2, 2.7). */
+typedef struct {
+  int32_t eos;       /* SPH_EOS_*                                           */
+  int32_t strength;  /* 1: evolve deviatoric stress S                       */
+  int32_t damage;    /* 1: Grady-Kipp damage (needs state.dmg and flaws)     */
+  int32_t pad;
+  double rho0, cs;   /* reference density; sound speed (linear, isothermal) */
+  double K0, n_M;    /* bulk modulus; Murnaghan exponent                    */
+  double A_T, B_T, E0, E_iv, E_cv, a_T, b_T, alpha_T, beta_T; /* Tillotson  */
+  double rho_cut;    /* linear EOS: p = 0 below rho/rho0 < rho_cut (0: off)  */
+  double mu, Y0;     /* shear modulus; von Mises yield stress (<= 0: none)   */
+} sph_material;
+
+/* Run parameters. */
+typedef struct {
+  int32_t dim;          /* 2 or 3                                              */
+  int32_t density_sum;  /* 1: rho = sum m W (Eq. density_by_kernel_sum)        */
+  int32_t consistency;  /* 1: velocity gradient with C = L^-1 (Eq. ext_sph)     */
+  int32_t gravity;      /* 1: add Barnes-Hut self-gravity to dv/dt             */
+  int32_t leaf_size;    /* tree leaves hold at most this many particles (<=32) */
+  int32_t max_depth;    /* octree depth B: cell index bits per axis (<= 21)     */
+  int32_t precision;    /* SPH_FP64 or SPH_MIXED                                */
+  int32_t check;        /* 1: synchronise and report device errors per call    */
+  double alpha, beta, eps_v;      /* artificial viscosity (Sect. 3.1.3)          */
+  double eps_s, n_as, dmpd;       /* artificial stress eps_s (0: off), n, Delta mpd */
+  double xsph;                    /* XSPH factor (0: off)                          */
+  double G, theta, eps_grav;      /* gravity constant; opening angle; softening/h  */
+  double c_courant, c_accel, c_quantity;          /* time step factors (Sect. 3.4.1) */
+  double u_floor, S_floor, dmg_floor, dt_max, dt_fixed;
+} sph_params;
+
+/* Particle state (device pointers).  S and dmg may be NULL.  Flaw thresholds
+ * of particle a are flaw_eps[flaw_off[id[a]] .. flaw_off[id[a]+1]) (FP32,
+ * ascending; Sect. 3.2), so flaws need not move when particles are reordered.
+ * Instances: ninst >= 1; when ninst > 1, inst_off[0..ninst] (device, int64)
+ * delimits independent problems that never interact; they must be listed in
+ * particle order and stay contiguous (reordering keeps them so). */
+typedef struct {
+  int32_t dim;
+  int32_t ninst;
+  int64_t n;
+  double *x[3];
+  double *v[3];
+  double *rho, *u, *m, *h;
+  double *S, *dmg;
+  int32_t *mat, *id;
+  const int64_t *flaw_off;
+  const float *flaw_eps;
+  const int64_t *inst_off;
+} sph_state;
+
+/* Time derivatives (device pointers; optional ones may be NULL). */
+typedef struct {
+  double *dx[3];     /* dx/dt: v plus the XSPH term                        */
+  double *dv[3];     /* dv/dt, gravity included                             */
+  double *drho;      /* d rho/dt (0 in density-sum mode)                     */
+  double *du;        /* du/dt                                                */
+  double *dS;        /* dS/dt, component-major like S                        */
+  double *ddmg;      /* d(d^1/3)/dt                                          */
+  double *cs;        /* optional: sound speed                               */
+  double *p;         /* optional: pressure                                  */
+  int32_t *n_act;    /* optional: activated flaws                           */
+  int32_t *nnb;      /* optional: number of interaction partners            */
+} sph_derivs;
+
+typedef struct sph_ctx sph_ctx;
+
+/* Creates a context for up to max_particles particles in up to
+ * max_instances instances, max_neighbours partners per particle and tree
+ * leaves of up to leaf_size (1..32) particles; allocates all scratch on the
+ * current device.  Returns SPH_ERR_INVALID for bad sizes, SPH_ERR_CUDA when
+ * the allocation fails (ctx is then NULL). */
+sph_status sph_create(sph_ctx **ctx, int32_t dim, int64_t max_particles, int32_t max_instances,
+                      int32_t max_neighbours, int32_t leaf_size, void *stream);
+void sph_destroy(sph_ctx *ctx);
+/* Text of the last error on this context (static storage of the context). */
+const char *sph_last_error(const sph_ctx *ctx);
+/* Waits for `stream`, reads and clears the device error word. */
+sph_status sph_sync_status(sph_ctx *ctx, void *stream);
+/* Bytes of device memory the context holds. */
+int64_t sph_ctx_bytes(const sph_ctx *ctx);
+
+/* Octree of Sect. 3.5.1 over the state: root cube per instance (lower corner
+ * at the per-axis minimum, edge s0 = max extent * (1 + 2^-20)), particles
+ * ordered by Morton key of the cell index floor((x - min)/s0 * 2^B), nodes
+ * = every cell whose parent holds more than leaf_size particles (leaves: at
+ * most leaf_size particles, or depth B).  Node mass and centre of mass.
+ * reorder = 1 permutes every state array in place into that order (the
+ * flaws stay indexed by id).  perm (device int32[n], may be NULL) receives,
+ * for each sorted slot, the state index (before any reorder). */
+sph_status sph_build_tree(sph_ctx *ctx, sph_state *state, int32_t leaf_size, int32_t max_depth, int32_t reorder,
+                          int32_t *perm, void *stream);
+
+/* Copies the tree of the last sph_build_tree out (device buffers, capacity
+ * `cap` nodes, pre-order): level, cell index at that level (3 int64 per node,
+ * instance bits stripped), particle count, mass, centre of mass (3 per node).
+ * *nnodes (host) receives the node count; returns SPH_ERR_CAPACITY if > cap.
+ * Blocks on `stream`. */
+sph_status sph_tree_nodes(sph_ctx *ctx, int64_t cap, int32_t *level, int64_t *cell, int64_t *count, double *mass,
+                          double *com, int64_t *nnodes, void *stream);
+
+/* Interaction partners (Sect. 3.5.2): N(a) = {b != a, same instance :
+ * ((dx^2 + dy^2) + dz^2) < h_ab^2} evaluated exactly in FP64 (no fused
+ * multiply-add).  Builds the tree itself (no reorder).  Writes CSR lists in
+ * state order, ascending within a particle: nb_offset (device int64[n+1]),
+ * nb_index (device int32[nb_capacity]).  Returns SPH_ERR_CAPACITY if a
+ * particle has more than max_neighbours partners or the total exceeds
+ * nb_capacity (checked by blocking on `stream`). */
+sph_status sph_neighbours(sph_ctx *ctx, const sph_state *state, int32_t leaf_size, int32_t max_depth,
+                          int64_t *nb_offset, int32_t *nb_index, int64_t nb_capacity, void *stream);
+
+/* One right-hand side: tree, partners, (density sum), the neighbour pass for
+ * continuity / velocity gradient / XSPH, the per-particle constitutive update
+ * (EOS, Hooke + Jaumann, yield, damage, artificial stress), the momentum and
+ * energy pass, and gravity if params->gravity.  In density-sum mode rho is
+ * overwritten with the kernel sum.  mats: host array of nmat materials
+ * indexed by state->mat. */
+sph_status sph_rhs(sph_ctx *ctx, sph_state *state, const sph_material *mats, int32_t nmat, const sph_params *params,
+                   sph_derivs *out, void *stream);
+
+/* Barnes-Hut self-gravity alone (Sect. 3.3): a_a = -G sum m_p (x_a - x_p) /
+ * (r^2 + eps_a^2)^1.5, eps_a = eps_grav h_a; a node is a pseudo-particle when
+ * s/r < theta and its cube does not contain a.  theta = 0 gives the direct
+ * sum.  Builds the tree itself (no reorder).  Writes ax, ay, az (device; az
+ * ignored in 2D). */
+sph_status sph_gravity(sph_ctx *ctx, const sph_state *state, const sph_params *params, double *ax, double *ay,
+                       double *az, void *stream);
+
+/* nsteps predictor-corrector steps (Sect. 3.4.1) in place:
+ *   q^p = q + dt/2 dq/dt(q),  q^c = q + dt dq/dt(q^p)
+ * for x, v, rho (continuity mode), u, S, d^1/3, then S <- f_Y S and the
+ * damage cap.  dt per instance = params->dt_fixed if > 0, else the minimum of
+ * the Courant, acceleration and quantity limits, computed on the device.
+ * dt (device double[ninst], may be NULL) receives the last step's time
+ * steps.  At the start of every step the state is reordered along the
+ * octree, so particle order changes; id follows the particles. */
+sph_status sph_step(sph_ctx *ctx, sph_state *state, const sph_material *mats, int32_t nmat, const sph_params *params,
+                    double *dt, int32_t nsteps, void *stream);
+
+/* Peak FMA throughput of this device, measured by a register-resident loop
+ * (precision SPH_FP64 or SPH_MIXED = FP32); returns FLOP/s (2 per FMA) in
+ * *flops.  Blocks. */
+sph_status sph_measure_fma_peak(int32_t precision, double *flops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

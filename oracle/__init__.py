@@ -76,7 +76,8 @@ class Derivs(C.Structure):
     _fields_ = [("dxdt", _dp), ("dydt", _dp), ("dzdt", _dp), ("dvx", _dp), ("dvy", _dp), ("dvz", _dp),
                 ("drho", _dp), ("du", _dp), ("dS", _dp), ("ddmg", _dp), ("p", _dp), ("cs", _dp),
                 ("n_act", _ip), ("nnb", _ip), ("mag_drho", _dp), ("mag_dv", _dp), ("mag_du", _dp),
-                ("mag_gradv", _dp), ("gradv", _dp), ("agx", _dp), ("agy", _dp), ("agz", _dp)]
+                ("mag_gradv", _dp), ("mag1_drho", _dp), ("mag1_dv", _dp), ("mag1_du", _dp), ("mag1_gradv", _dp),
+                ("mag_rho", _dp), ("mag1_rho", _dp), ("gradv", _dp), ("agx", _dp), ("agy", _dp), ("agz", _dp)]
 
 
 def lib():
@@ -190,7 +191,9 @@ def _derivs(dim, n, ns):
         "dS": np.zeros((ns, n)), "ddmg": np.zeros(n), "p": np.zeros(n), "cs": np.zeros(n),
         "n_act": np.zeros(n, np.int32), "nnb": np.zeros(n, np.int32), "mag_drho": np.zeros(n),
         "mag_dv": np.zeros(n), "mag_du": np.zeros(n), "mag_gradv": np.zeros(n),
-        "gradv": np.zeros((dim * dim, n)), "ag": np.zeros((dim, n)),
+        "gradv": np.zeros((dim * dim, n)), "ag": np.zeros((dim, n)), "mag1_drho": np.zeros(n),
+        "mag1_dv": np.zeros(n), "mag1_du": np.zeros(n), "mag1_gradv": np.zeros(n), "mag_rho": np.zeros(n),
+        "mag1_rho": np.zeros(n),
     }
     d = Derivs()
     d.dxdt, d.dydt = _p(out["dxdt"][0]), _p(out["dxdt"][1])
@@ -202,6 +205,8 @@ def _derivs(dim, n, ns):
     d.n_act, d.nnb = _p(out["n_act"], _ip), _p(out["nnb"], _ip)
     d.mag_drho, d.mag_dv, d.mag_du = _p(out["mag_drho"]), _p(out["mag_dv"]), _p(out["mag_du"])
     d.mag_gradv, d.gradv = _p(out["mag_gradv"]), _p(out["gradv"])
+    d.mag1_drho, d.mag1_dv, d.mag1_du = _p(out["mag1_drho"]), _p(out["mag1_dv"]), _p(out["mag1_du"])
+    d.mag1_gradv, d.mag_rho, d.mag1_rho = _p(out["mag1_gradv"]), _p(out["mag_rho"]), _p(out["mag1_rho"])
     d.agx, d.agy = _p(out["ag"][0]), _p(out["ag"][1])
     d.agz = _p(out["ag"][2]) if dim == 3 else _p(None)
     return d, out

@@ -79,6 +79,10 @@ typedef struct {
   int32_t *nnb;            /* neighbour count                                 */
   /* Per-particle magnitude sums sum_b |term_b| used as error scales:        */
   double *mag_drho, *mag_dv, *mag_du, *mag_gradv;
+  /* The same sums with each term weighted by its conditioning at the       */
+  /* kernel's support edge, kappa = q/(1-q) for q >= 1/2 (else 1): a       */
+  /* relative error e in q changes a term by about 2 e kappa |term|.       */
+  double *mag1_drho, *mag1_dv, *mag1_du, *mag1_gradv, *mag_rho, *mag1_rho;
   double *gradv;           /* corrected velocity gradient, D*D per particle,  component-major */
   double *agx, *agy, *agz; /* gravitational acceleration alone               */
 } orc_derivs;

@@ -785,6 +785,9 @@ static int flaw_count_below(const float *eps, int64_t n, double e) {
   return c;
 }
 
+/* Conditioning of a kernel term at the support edge (see oracle.h). */
+static double edge_kappa(double q) { return q >= 0.5 ? q / (1.0 - q) : 1.0; }
+
 static int rhs_instance(orc_state *s, const orc_material *mats, int nmat, const orc_params *P, orc_derivs *d) {
   const int dim = P->dim;
   const int64_t n = s->n;
@@ -808,7 +811,7 @@ static int rhs_instance(orc_state *s, const orc_material *mats, int nmat, const 
   if (P->density_sum) {
 #pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int64_t a = 0; a < n; ++a) {
-      double sum = s->m[a] * orc_W(0.0, s->h[a], dim);
+      double sum = s->m[a] * orc_W(0.0, s->h[a], dim), m1 = 0.0;
       for (int64_t k = off[a]; k < off[a + 1]; ++k) {
         int64_t b = nb[k];
         double r2 = 0.0;
@@ -816,9 +819,14 @@ static int rhs_instance(orc_state *s, const orc_material *mats, int nmat, const 
           double dd = X[ax][a] - X[ax][b];
           r2 = r2 + dd * dd;
         }
-        sum += s->m[b] * orc_W(sqrt(r2), 0.5 * (s->h[a] + s->h[b]), dim);
+        double hab = 0.5 * (s->h[a] + s->h[b]);
+        double t = s->m[b] * orc_W(sqrt(r2), hab, dim);
+        sum += t;
+        m1 += t * edge_kappa(sqrt(r2) / hab);
       }
       s->rho[a] = sum;
+      if (d->mag_rho) d->mag_rho[a] = sum;
+      if (d->mag1_rho) d->mag1_rho[a] = m1;
     }
   }
 
@@ -830,7 +838,7 @@ static int rhs_instance(orc_state *s, const orc_material *mats, int nmat, const 
 #pragma omp parallel for num_threads(g_threads) schedule(static)
   for (int64_t a = 0; a < n; ++a) {
     const orc_material *M = mat_of(s, mats, nmat, a);
-    double drho = 0.0, magdrho = 0.0, maggv = 0.0;
+    double drho = 0.0, magdrho = 0.0, maggv = 0.0, m1drho = 0.0, m1gv = 0.0;
     double L[3][3] = {{0}}, Gt[3][3] = {{0}}, xs[3] = {0, 0, 0};
     for (int64_t k = off[a]; k < off[a + 1]; ++k) {
       int64_t b = nb[k];
@@ -853,8 +861,10 @@ static int rhs_instance(orc_state *s, const orc_material *mats, int nmat, const 
         vg += dv[ax] * g[ax];
         vga += fabs(dv[ax] * g[ax]);
       }
+      double kap = edge_kappa(r / hab);
       drho += vol * vg;
       magdrho += vol * vga;
+      m1drho += vol * vga * kap;
       /* Sect. 3.1.6: L^{ag} = sum vol (x_b - x_a)^a d_g W, same with v for G */
       double sdv = 0.0, sg = 0.0;
       for (int i = 0; i < dim; ++i) {
@@ -866,6 +876,7 @@ static int rhs_instance(orc_state *s, const orc_material *mats, int nmat, const 
         }
       }
       maggv += vol * sdv * sg;
+      m1gv += vol * sdv * sg * kap;
       /* Sect. 3.1.5: XSPH with the mean density (rho_a + rho_b)/2 */
       if (P->xsph != 0.0) {
         double w = orc_W(r, hab, dim);
@@ -875,6 +886,7 @@ static int rhs_instance(orc_state *s, const orc_material *mats, int nmat, const 
     }
     drho = s->rho[a] * drho;
     magdrho = fabs(s->rho[a]) * magdrho;
+    m1drho = fabs(s->rho[a]) * m1drho;
 
     /* Linear consistency, Eq. (ext_sph): grad v = G C with C = L^-1, or I */
     double C[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
@@ -891,6 +903,7 @@ static int rhs_instance(orc_state *s, const orc_material *mats, int nmat, const 
         for (int k = 0; k < dim; ++k) gv[i][j] += Gt[i][k] * C[k][j];
       }
     maggv = maggv * cmax * dim;
+    m1gv = m1gv * cmax * dim;
 
     /* Equation of state, Sect. 2.5 */
     double p, cs;
@@ -986,6 +999,8 @@ static int rhs_instance(orc_state *s, const orc_material *mats, int nmat, const 
     if (d->drho) d->drho[a] = P->density_sum ? 0.0 : drho;
     if (d->mag_drho) d->mag_drho[a] = magdrho;
     if (d->mag_gradv) d->mag_gradv[a] = maggv;
+    if (d->mag1_drho) d->mag1_drho[a] = m1drho;
+    if (d->mag1_gradv) d->mag1_gradv[a] = m1gv;
     if (d->gradv)
       for (int i = 0; i < dim; ++i)
         for (int j = 0; j < dim; ++j) d->gradv[(int64_t)(i * dim + j) * n + a] = gv[i][j];
@@ -1006,7 +1021,7 @@ static int rhs_instance(orc_state *s, const orc_material *mats, int nmat, const 
   /*   du_a/dt = -1/2 sum_b m_b (v_a - v_b) . [T_a + T_b - Pi* I] grad_a W   */
 #pragma omp parallel for num_threads(g_threads) schedule(static)
   for (int64_t a = 0; a < n; ++a) {
-    double acc[3] = {0, 0, 0}, du = 0.0, magdv = 0.0, magdu = 0.0;
+    double acc[3] = {0, 0, 0}, du = 0.0, magdv = 0.0, magdu = 0.0, m1dv = 0.0, m1du = 0.0;
     for (int64_t k = off[a]; k < off[a + 1]; ++k) {
       int64_t b = nb[k];
       double dx[3] = {0, 0, 0}, dv[3] = {0, 0, 0}, r2 = 0.0;
@@ -1046,10 +1061,13 @@ static int rhs_instance(orc_state *s, const orc_material *mats, int nmat, const 
           su += Bij * g[j];
           sua += fabs(dv[i] * Bij * g[j]);
         }
+        double kap = edge_kappa(r / hab);
         acc[i] += s->m[b] * sv;
         magdv += s->m[b] * sva;
+        m1dv += s->m[b] * sva * kap;
         du += -0.5 * s->m[b] * dv[i] * su;
         magdu += 0.5 * s->m[b] * sua;
+        m1du += 0.5 * s->m[b] * sua * kap;
       }
     }
     double *DV[3] = {d->dvx, d->dvy, d->dvz};
@@ -1058,6 +1076,8 @@ static int rhs_instance(orc_state *s, const orc_material *mats, int nmat, const 
     if (d->du) d->du[a] = du;
     if (d->mag_dv) d->mag_dv[a] = magdv;
     if (d->mag_du) d->mag_du[a] = magdu;
+    if (d->mag1_dv) d->mag1_dv[a] = m1dv;
+    if (d->mag1_du) d->mag1_du[a] = m1du;
   }
 
   /* Self-gravity, Sect. 3.3 */
@@ -1126,6 +1146,12 @@ static orc_derivs derivs_view(const orc_derivs *d, int64_t lo) {
   v.mag_dv = SHIFT(d->mag_dv, lo);
   v.mag_du = SHIFT(d->mag_du, lo);
   v.mag_gradv = SHIFT(d->mag_gradv, lo);
+  v.mag1_drho = SHIFT(d->mag1_drho, lo);
+  v.mag1_dv = SHIFT(d->mag1_dv, lo);
+  v.mag1_du = SHIFT(d->mag1_du, lo);
+  v.mag1_gradv = SHIFT(d->mag1_gradv, lo);
+  v.mag_rho = SHIFT(d->mag_rho, lo);
+  v.mag1_rho = SHIFT(d->mag1_rho, lo);
   v.agx = SHIFT(d->agx, lo);
   v.agy = SHIFT(d->agy, lo);
   v.agz = SHIFT(d->agz, lo);

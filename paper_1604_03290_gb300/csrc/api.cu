@@ -1,0 +1,462 @@
+// C ABI entry points of include/sph.h: argument checks, context allocation
+// and the sequencing of the device passes.
+#include <string.h>
+
+#include <algorithm>
+
+#include "sph_internal.cuh"
+
+namespace sph {
+void scan_counts(sph_ctx *c, const int32_t *in, int32_t *out, int64_t m, cudaStream_t st);
+void export_nodes(sph_ctx *c, int64_t cap, int32_t *level, int64_t *cell, int64_t *count, double *mass, double *com,
+                  cudaStream_t st);
+}  // namespace sph
+
+using namespace sph;
+
+static sph_status fail(sph_ctx *c, sph_status s, const char *msg) {
+  if (c) snprintf(c->err, sizeof(c->err), "%s", msg);
+  return s;
+}
+
+static sph_status cuda_check(sph_ctx *c, const char *where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    if (c) snprintf(c->err, sizeof(c->err), "%s: %s", where, cudaGetErrorString(e));
+    return SPH_ERR_CUDA;
+  }
+  return SPH_OK;
+}
+
+template <class T>
+static T *ctx_alloc(sph_ctx *c, int64_t count, bool &ok) {
+  if (!ok) return nullptr;
+  void *p = nullptr;
+  size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
+  if (cudaMalloc(&p, bytes) != cudaSuccess || c->nallocs >= 128) {
+    ok = false;
+    return nullptr;
+  }
+  c->allocs[c->nallocs++] = p;
+  c->bytes += (int64_t)bytes;
+  return (T *)p;
+}
+
+extern "C" {
+
+sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t max_instances,
+                      int32_t max_neighbours, int32_t leaf_size, void *stream) {
+  (void)stream;
+  if (!out) return SPH_ERR_INVALID;
+  *out = nullptr;
+  if ((dim != 2 && dim != 3) || max_particles < 1 || max_particles > ((int64_t)1 << 31) - 64 ||
+      max_instances < 1 || max_neighbours < 1 || leaf_size < 1 || leaf_size > kMaxLeaf)
+    return SPH_ERR_INVALID;
+  sph_ctx *c = new sph_ctx();
+  memset(c, 0, sizeof(*c));
+  cudaGetDevice(&c->device);
+  c->dim = dim;
+  c->cap_n = max_particles;
+  c->cap_inst = max_instances;
+  c->kmax = max_neighbours;
+  c->leaf_default = leaf_size;
+  const int64_t N = max_particles;
+  bool ok = true;
+  c->d_err = ctx_alloc<int32_t>(c, 1, ok);
+  if (cudaMallocHost(&c->h_err, sizeof(int32_t)) != cudaSuccess) ok = false;
+  Tree &T = c->tree;
+  for (int k = 0; k < 2; ++k) {
+    T.keys[k] = ctx_alloc<unsigned long long>(c, N, ok);
+    T.vals[k] = ctx_alloc<int32_t>(c, N, ok);
+  }
+  T.hist_cap = (int64_t)256 * ((N + 4095) / 4096 + 1);
+  T.hist = ctx_alloc<uint32_t>(c, T.hist_cap, ok);
+  T.ncount = ctx_alloc<int32_t>(c, N + 1, ok);
+  T.nstart = ctx_alloc<int32_t>(c, N + 1, ok);
+  T.scan_tmp = ctx_alloc<int32_t>(c, (N + 1) / 4096 + 2, ok);
+  T.cap_nodes = std::max<int64_t>(4096, leaf_size <= 2 ? 4 * N : 2 * N);
+  const int64_t cn = T.cap_nodes;
+  T.nnodes = ctx_alloc<int32_t>(c, 1, ok);
+  T.first = ctx_alloc<int32_t>(c, cn, ok);
+  T.end = ctx_alloc<int32_t>(c, cn, ok);
+  T.skip = ctx_alloc<int32_t>(c, cn, ok);
+  T.parent = ctx_alloc<int32_t>(c, cn, ok);
+  T.nchild = ctx_alloc<int32_t>(c, cn, ok);
+  T.arrived = ctx_alloc<int32_t>(c, cn, ok);
+  T.level = ctx_alloc<int32_t>(c, cn, ok);
+  T.cell = ctx_alloc<unsigned long long>(c, cn, ok);
+  T.mass = ctx_alloc<double>(c, cn, ok);
+  T.com = ctx_alloc<double>(c, 3 * cn, ok);
+  T.bblo = ctx_alloc<double>(c, 3 * cn, ok);
+  T.bbhi = ctx_alloc<double>(c, 3 * cn, ok);
+  T.hmax = ctx_alloc<double>(c, cn, ok);
+  T.fbox_lo = ctx_alloc<float4>(c, cn, ok);
+  T.fbox_hi = ctx_alloc<float4>(c, cn, ok);
+  T.fcom_hi = ctx_alloc<float4>(c, cn, ok);
+  T.fcom_lo = ctx_alloc<float4>(c, cn, ok);
+  const int64_t ci = max_instances;
+  T.inst_bb = ctx_alloc<unsigned long long>(c, 6 * ci, ok);
+  T.inst_lo = ctx_alloc<double>(c, 3 * ci, ok);
+  T.inst_s0 = ctx_alloc<double>(c, ci, ok);
+  T.inst_root = ctx_alloc<int32_t>(c, ci, ok);
+  T.inst_goff = ctx_alloc<int32_t>(c, ci + 1, ok);
+  T.cap_groups = N / kWarp + ci + 1;
+  T.grp_start = ctx_alloc<int32_t>(c, T.cap_groups, ok);
+  T.grp_end = ctx_alloc<int32_t>(c, T.cap_groups, ok);
+  T.grp_inst = ctx_alloc<int32_t>(c, T.cap_groups, ok);
+  T.ngroups = ctx_alloc<int32_t>(c, 1, ok);
+  c->pk.px = ctx_alloc<float4>(c, N, ok);
+  c->pk.pxl = ctx_alloc<float4>(c, N, ok);
+  c->pk.pv = ctx_alloc<float4>(c, N, ok);
+  c->pk.pvl = ctx_alloc<float4>(c, N, ok);
+  c->nb_idx = ctx_alloc<int32_t>(c, (int64_t)max_neighbours * N, ok);
+  c->nb_cnt = ctx_alloc<int32_t>(c, N, ok);
+  c->csr_total = ctx_alloc<int64_t>(c, 1, ok);
+  c->T = ctx_alloc<double>(c, 8 * N, ok);
+  c->zeta = ctx_alloc<double>(c, 8 * N, ok);
+  c->cs = ctx_alloc<double>(c, N, ok);
+  c->p = ctx_alloc<double>(c, N, ok);
+  c->ag = ctx_alloc<double>(c, 3 * N, ok);
+  c->units = ctx_alloc<Units>(c, 1, ok);
+  c->vscale = 1.0;
+  StepBufs &S = c->st;
+  for (int k = 0; k < 3; ++k) {
+    S.x[k] = ctx_alloc<double>(c, N, ok);
+    S.v[k] = ctx_alloc<double>(c, N, ok);
+  }
+  S.rho = ctx_alloc<double>(c, N, ok);
+  S.u = ctx_alloc<double>(c, N, ok);
+  S.S = ctx_alloc<double>(c, 6 * N, ok);
+  S.dmg = ctx_alloc<double>(c, N, ok);
+  for (int s = 0; s < 2; ++s) {
+    for (int k = 0; k < 3; ++k) {
+      S.d_x[s][k] = ctx_alloc<double>(c, N, ok);
+      S.d_v[s][k] = ctx_alloc<double>(c, N, ok);
+    }
+    S.d_rho[s] = ctx_alloc<double>(c, N, ok);
+    S.d_u[s] = ctx_alloc<double>(c, N, ok);
+    S.d_S[s] = ctx_alloc<double>(c, 6 * N, ok);
+    S.d_dmg[s] = ctx_alloc<double>(c, N, ok);
+    S.d_cs[s] = ctx_alloc<double>(c, N, ok);
+    S.d_nact[s] = ctx_alloc<int32_t>(c, N, ok);
+  }
+  S.dt_enc = ctx_alloc<unsigned long long>(c, ci, ok);
+  S.dt = ctx_alloc<double>(c, ci, ok);
+  S.gather = ctx_alloc<double>(c, N, ok);
+  S.gather_i = ctx_alloc<int32_t>(c, N, ok);
+  if (ok) ok = cudaMemset(c->d_err, 0, sizeof(int32_t)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    sph_destroy(c);
+    return SPH_ERR_CUDA;
+  }
+  *out = c;
+  return SPH_OK;
+}
+
+void sph_destroy(sph_ctx *c) {
+  if (!c) return;
+  for (int i = 0; i < c->nallocs; ++i) cudaFree(c->allocs[i]);
+  if (c->h_err) cudaFreeHost(c->h_err);
+  delete c;
+}
+
+const char *sph_last_error(const sph_ctx *c) { return c ? c->err : "no context"; }
+
+int64_t sph_ctx_bytes(const sph_ctx *c) { return c ? c->bytes : 0; }
+
+sph_status sph_sync_status(sph_ctx *c, void *stream) {
+  if (!c) return SPH_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(c, SPH_ERR_CUDA, cudaGetErrorString(e));
+  int32_t w = *c->h_err;
+  cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), st);
+  if (w & ERR_NONFINITE) return fail(c, SPH_ERR_NONFINITE, "non-finite input, or h <= 0 or rho <= 0");
+  if (w & (ERR_NB_OVERFLOW | ERR_NODE_OVERFLOW | ERR_CSR_OVERFLOW))
+    return fail(c, SPH_ERR_CAPACITY,
+                (w & ERR_NB_OVERFLOW) ? "a particle has more partners than max_neighbours"
+                : (w & ERR_NODE_OVERFLOW) ? "octree node capacity exceeded"
+                                          : "partner list longer than nb_capacity");
+  if (w & ERR_TIMEOUT) return fail(c, SPH_ERR_TIMEOUT, "a bounded device loop hit its iteration limit");
+  return SPH_OK;
+}
+
+}  // extern "C"
+
+static sph_status check_state(sph_ctx *c, const sph_state *s) {
+  if (!c || !s) return SPH_ERR_INVALID;
+  if (s->dim != c->dim) return fail(c, SPH_ERR_INVALID, "state dim differs from the context's");
+  if (s->n < 0 || s->n > c->cap_n) return fail(c, SPH_ERR_INVALID, "n exceeds the context capacity");
+  int ninst = s->ninst > 0 ? s->ninst : 1;
+  if (ninst > c->cap_inst) return fail(c, SPH_ERR_INVALID, "ninst exceeds the context capacity");
+  if (ninst > 1 && !s->inst_off) return fail(c, SPH_ERR_INVALID, "inst_off is required when ninst > 1");
+  if (s->n > 0) {
+    for (int ax = 0; ax < s->dim; ++ax)
+      if (!s->x[ax] || !s->v[ax]) return fail(c, SPH_ERR_INVALID, "missing position or velocity array");
+    if (!s->rho || !s->u || !s->m || !s->h) return fail(c, SPH_ERR_INVALID, "missing rho, u, m or h");
+  }
+  return SPH_OK;
+}
+
+static sph_status check_tree_args(sph_ctx *c, const sph_state *s, int leaf, int depth) {
+  if (leaf < 1 || leaf > kMaxLeaf) return fail(c, SPH_ERR_INVALID, "leaf_size must be in 1..32");
+  int ninst = s->ninst > 0 ? s->ninst : 1;
+  int ibits = 0;
+  while ((1 << ibits) < ninst) ++ibits;
+  if (depth < 1 || depth > 21 || s->dim * depth + ibits > 64)
+    return fail(c, SPH_ERR_INVALID, "max_depth must be in 1..21 with dim * max_depth + log2(ninst) <= 64");
+  return SPH_OK;
+}
+
+static sph_status check_params(sph_ctx *c, const sph_state *s, const sph_material *mats, int nmat,
+                               const sph_params *p, MatTable &mt) {
+  if (!p || !mats || nmat < 1 || nmat > SPH_MAX_MATERIALS)
+    return fail(c, SPH_ERR_INVALID, "params and 1..8 materials are required");
+  if (p->dim != s->dim) return fail(c, SPH_ERR_INVALID, "params.dim differs from the state's");
+  if (p->precision != SPH_FP64 && p->precision != SPH_MIXED) return fail(c, SPH_ERR_INVALID, "bad precision");
+  if (p->eps_s > 0.0 && !(p->dmpd > 0.0)) return fail(c, SPH_ERR_INVALID, "artificial stress needs dmpd > 0");
+  memset(&mt, 0, sizeof(mt));
+  for (int i = 0; i < nmat; ++i) {
+    mt.m[i] = mats[i];
+    if (mats[i].damage && (!s->flaw_off || !s->flaw_eps) && s->dmg)
+      return fail(c, SPH_ERR_INVALID, "damage needs flaw_off and flaw_eps");
+    if (!(mats[i].rho0 > 0.0)) return fail(c, SPH_ERR_INVALID, "material rho0 must be positive");
+  }
+  mt.nmat = nmat;
+  return check_tree_args(c, s, p->leaf_size, p->max_depth);
+}
+
+namespace sph {
+// Velocity scale of the materials (sound speed, or sqrt(K / rho0)), for the
+// time unit of the FP32 views.
+double velocity_scale(const MatTable &mt) {
+  double v = 0.0;
+  for (int i = 0; i < mt.nmat; ++i) {
+    const sph_material &m = mt.m[i];
+    double c = m.cs;
+    double K = std::max(m.K0, std::max(m.A_T, m.B_T));
+    if (!(c > 0.0) && K > 0.0 && m.rho0 > 0.0) c = sqrt(K / m.rho0);
+    if (c > v) v = c;
+  }
+  return v > 0.0 ? v : 1.0;
+}
+}  // namespace sph
+
+static void set_materials(sph_ctx *c, const MatTable *mt) {
+  if (mt) {
+    c->mt = *mt;
+    c->vscale = velocity_scale(*mt);
+  } else {
+    memset(&c->mt, 0, sizeof(c->mt));
+    c->vscale = 1.0;
+  }
+}
+
+static sph_status finish(sph_ctx *c, const sph_params *p, cudaStream_t st, const char *where) {
+  sph_status r = cuda_check(c, where);
+  if (r != SPH_OK) return r;
+  if (p && p->check) return sph_sync_status(c, st);
+  return SPH_OK;
+}
+
+// One full right-hand side on state s into out (tree + partners + passes).
+static void rhs_all(sph_ctx *c, sph_state *s, const MatTable &mt, const sph_params &p, const sph_derivs &out,
+                    cudaStream_t st) {
+  tree_build(c, s, p.leaf_size, p.max_depth, st);
+  find_partners(c, s, st);
+  if (p.gravity) gravity_walk(c, s, p, c->ag, c->ag + c->cap_n, c->ag + 2 * c->cap_n, st);
+  rhs_passes(c, s, mt, p, out, st);
+}
+
+extern "C" {
+
+sph_status sph_build_tree(sph_ctx *c, sph_state *s, int32_t leaf_size, int32_t max_depth, int32_t reorder,
+                          int32_t *perm, void *stream) {
+  sph_status r = check_state(c, s);
+  if (r != SPH_OK) return r;
+  if ((r = check_tree_args(c, s, leaf_size, max_depth)) != SPH_OK) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  set_materials(c, nullptr);
+  tree_build(c, s, leaf_size, max_depth, st);
+  if (perm && s->n > 0)
+    cudaMemcpyAsync(perm, c->tree.perm, sizeof(int32_t) * s->n, cudaMemcpyDeviceToDevice, st);
+  if (reorder) tree_reorder_state(c, s, st);
+  return cuda_check(c, "sph_build_tree");
+}
+
+sph_status sph_tree_nodes(sph_ctx *c, int64_t cap, int32_t *level, int64_t *cell, int64_t *count, double *mass,
+                          double *com, int64_t *nnodes, void *stream) {
+  if (!c || !nnodes) return SPH_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  int32_t nn = 0;
+  cudaMemcpyAsync(&nn, c->tree.nnodes, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check(c, "sph_tree_nodes");
+  *nnodes = nn;
+  if (nn > cap) return fail(c, SPH_ERR_CAPACITY, "node list longer than cap");
+  if (nn > 0) export_nodes(c, nn, level, cell, count, mass, com, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check(c, "sph_tree_nodes");
+  return sph_sync_status(c, stream);
+}
+
+sph_status sph_neighbours(sph_ctx *c, const sph_state *s, int32_t leaf_size, int32_t max_depth, int64_t *nb_offset,
+                          int32_t *nb_index, int64_t nb_capacity, void *stream) {
+  sph_status r = check_state(c, s);
+  if (r != SPH_OK) return r;
+  if ((r = check_tree_args(c, s, leaf_size, max_depth)) != SPH_OK) return r;
+  if (!nb_offset || (!nb_index && nb_capacity > 0)) return fail(c, SPH_ERR_INVALID, "null output");
+  cudaStream_t st = (cudaStream_t)stream;
+  set_materials(c, nullptr);
+  tree_build(c, s, leaf_size, max_depth, st);
+  find_partners(c, s, st);
+  partners_to_csr(c, s, nb_offset, nb_index, nb_capacity, st);
+  if ((r = cuda_check(c, "sph_neighbours")) != SPH_OK) return r;
+  return sph_sync_status(c, stream);
+}
+
+sph_status sph_rhs(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t nmat, const sph_params *p,
+                   sph_derivs *out, void *stream) {
+  sph_status r = check_state(c, s);
+  if (r != SPH_OK) return r;
+  MatTable mt;
+  if ((r = check_params(c, s, mats, nmat, p, mt)) != SPH_OK) return r;
+  if (!out) return fail(c, SPH_ERR_INVALID, "null derivs");
+  for (int ax = 0; ax < s->dim && s->n > 0; ++ax)
+    if (!out->dx[ax] || !out->dv[ax]) return fail(c, SPH_ERR_INVALID, "dx and dv outputs are required");
+  if (s->n > 0 && (!out->drho || !out->du)) return fail(c, SPH_ERR_INVALID, "drho and du outputs are required");
+  if (s->n > 0 && s->S && !out->dS) return fail(c, SPH_ERR_INVALID, "dS output required when S is given");
+  if (s->n > 0 && s->dmg && !out->ddmg) return fail(c, SPH_ERR_INVALID, "ddmg output required when dmg is given");
+  cudaStream_t st = (cudaStream_t)stream;
+  set_materials(c, &mt);
+  rhs_all(c, s, mt, *p, *out, st);
+  return finish(c, p, st, "sph_rhs");
+}
+
+sph_status sph_gravity(sph_ctx *c, const sph_state *s, const sph_params *p, double *ax, double *ay, double *az,
+                       void *stream) {
+  sph_status r = check_state(c, s);
+  if (r != SPH_OK) return r;
+  if (!p) return fail(c, SPH_ERR_INVALID, "null params");
+  if ((r = check_tree_args(c, s, p->leaf_size, p->max_depth)) != SPH_OK) return r;
+  if (!ax || !ay || (s->dim == 3 && !az)) return fail(c, SPH_ERR_INVALID, "null output");
+  cudaStream_t st = (cudaStream_t)stream;
+  set_materials(c, nullptr);
+  tree_build(c, s, p->leaf_size, p->max_depth, st);
+  gravity_walk(c, s, *p, ax, ay, az, st);
+  return finish(c, p, st, "sph_gravity");
+}
+
+sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t nmat, const sph_params *p, double *dt,
+                    int32_t nsteps, void *stream) {
+  sph_status r = check_state(c, s);
+  if (r != SPH_OK) return r;
+  MatTable mt;
+  if ((r = check_params(c, s, mats, nmat, p, mt)) != SPH_OK) return r;
+  if (nsteps < 0) return fail(c, SPH_ERR_INVALID, "nsteps < 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  set_materials(c, &mt);
+  StepBufs &B = c->st;
+  const int ninst = s->ninst > 0 ? s->ninst : 1;
+  // predicted state shares m, h, mat, id, flaws and instances with s
+  sph_state q = *s;
+  for (int k = 0; k < 3; ++k) {
+    q.x[k] = s->x[k] ? B.x[k] : nullptr;
+    q.v[k] = s->v[k] ? B.v[k] : nullptr;
+  }
+  q.rho = B.rho;
+  q.u = B.u;
+  q.S = s->S ? B.S : nullptr;
+  q.dmg = s->dmg ? B.dmg : nullptr;
+  sph_derivs d[2];
+  for (int j = 0; j < 2; ++j) {
+    memset(&d[j], 0, sizeof(sph_derivs));
+    for (int k = 0; k < 3; ++k) {
+      d[j].dx[k] = B.d_x[j][k];
+      d[j].dv[k] = B.d_v[j][k];
+    }
+    d[j].drho = B.d_rho[j];
+    d[j].du = B.d_u[j];
+    d[j].dS = B.d_S[j];
+    d[j].ddmg = B.d_dmg[j];
+    d[j].cs = B.d_cs[j];
+    d[j].n_act = B.d_nact[j];
+  }
+  for (int it = 0; it < nsteps; ++it) {
+    // order the state along the tree once per step (coalesced partner gathers)
+    tree_build(c, s, p->leaf_size, p->max_depth, st);
+    tree_reorder_state(c, s, st);
+    find_partners(c, s, st);
+    if (p->gravity) gravity_walk(c, s, *p, c->ag, c->ag + c->cap_n, c->ag + 2 * c->cap_n, st);
+    rhs_passes(c, s, mt, *p, d[0], st);
+    timestep_reduce(c, s, *p, d[0], st);
+    pc_update(c, s, &q, d[0], 0.5, mt, *p, st);
+    rhs_all(c, &q, mt, *p, d[1], st);
+    pc_update(c, s, s, d[1], 1.0, mt, *p, st);
+  }
+  if (dt && nsteps > 0) cudaMemcpyAsync(dt, B.dt, sizeof(double) * ninst, cudaMemcpyDeviceToDevice, st);
+  return finish(c, p, st, "sph_step");
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// FMA throughput probe
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_fma_loop(T *out, int iters, T a, T b) {
+  T x0 = threadIdx.x * (T)1e-3, x1 = x0 + (T)1, x2 = x0 + (T)2, x3 = x0 + (T)3;
+  T x4 = x0 + (T)4, x5 = x0 + (T)5, x6 = x0 + (T)6, x7 = x0 + (T)7;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      x0 = fma(x0, a, b);
+      x1 = fma(x1, a, b);
+      x2 = fma(x2, a, b);
+      x3 = fma(x3, a, b);
+      x4 = fma(x4, a, b);
+      x5 = fma(x5, a, b);
+      x6 = fma(x6, a, b);
+      x7 = fma(x7, a, b);
+    }
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+template <typename T>
+static double fma_rate(int iters) {
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = sms * 8, threads = 256;
+  T *out = nullptr;
+  if (cudaMalloc(&out, sizeof(T) * blocks * threads) != cudaSuccess) return -1.0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_fma_loop<T><<<blocks, threads>>>(out, 8, (T)0.999999, (T)1e-7);
+  double best = 0.0;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0);
+    k_fma_loop<T><<<blocks, threads>>>(out, iters, (T)0.999999, (T)1e-7);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    double flops = 2.0 * 8 * 16 * (double)iters * blocks * threads;
+    best = std::max(best, flops / (ms * 1e-3));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  return best;
+}
+
+extern "C" sph_status sph_measure_fma_peak(int32_t precision, double *flops) {
+  if (!flops) return SPH_ERR_INVALID;
+  double r = precision == SPH_FP64 ? fma_rate<double>(100) : fma_rate<float>(4000);
+  *flops = r;
+  return (r > 0 && cudaGetLastError() == cudaSuccess) ? SPH_OK : SPH_ERR_CUDA;
+}
+
+

@@ -1,0 +1,201 @@
+// Barnes-Hut self-gravity (Sect. 3.3), GB300 form.
+//
+// A warp walks the pre-order tree for 32 consecutive sorted particles.
+// Acceptance stays per particle, exactly as in a per-particle walk: a lane
+// that uses node n as a pseudo-particle ignores the rest of n's subtree
+// (ids below skip[n]); the warp enters n's children if any lane rejected
+// n.  Leaves rejected by a lane are summed particle by particle (self
+// skipped), staged through shared memory.  The accepted set of every
+// particle - hence the sum - is the one of the per-particle definition:
+//   node used iff its cube does not contain a and s / r < theta
+//   (s = s0 / 2^level, r = |x_a - com|, evaluated as s < theta * r);
+//   a_a = -G sum m_p (x_a - x_p) / (r^2 + eps_a^2)^1.5, eps_a = eps_grav h_a
+// (the paper's Eq. gravitational_force read as attractive, with Plummer
+// softening).
+//
+// Mixed precision: distances from hi/lo split coordinates in FP32, the
+// acceptance test in FP32 with a relative band of 1e-4 around the threshold
+// inside which the FP64 expression decides, FP32 monopole terms summed with
+// Kahan compensation.
+#include <type_traits>
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+constexpr int kGrWarps = 4;
+constexpr float kMacBand = 1e-4f;
+
+struct GravArgs {
+  Tree T;
+  PackedF32 pk;
+  const double *x[3], *m, *h;
+  int dim;
+  double G, theta, eps;
+  double *out[3];
+  const Units *U;
+  int32_t *err;
+};
+
+__device__ __forceinline__ double r2_fp64(int dim, const double xa[3], const double c[3]) {
+  double dx = __dsub_rn(xa[0], c[0]);
+  double dy = __dsub_rn(xa[1], c[1]);
+  double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+  if (dim == 3) {
+    double dz = __dsub_rn(xa[2], c[2]);
+    r2 = __dadd_rn(r2, __dmul_rn(dz, dz));
+  }
+  return r2;
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kGrWarps * 32) k_gravity(GravArgs A) {
+  using R = typename std::conditional<MIXED, float, double>::type;
+  __shared__ float4 sh_hi[kGrWarps][kMaxLeaf];
+  __shared__ float4 sh_lo[kGrWarps][kMaxLeaf];
+  __shared__ int32_t sh_b[kGrWarps][kMaxLeaf];
+  const Tree &T = A.T;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ngroups = *T.ngroups;
+  const int L = T.leaf_size, B = T.max_depth, dim = A.dim;
+  const int nnodes = *T.nnodes;
+  const int64_t cap = T.cap_nodes;
+  const double Gs = MIXED ? A.G * A.U->M * A.U->T * A.U->T * A.U->invL * A.U->invL * A.U->invL : A.G;
+  const R G = (R)Gs;
+  const double out_scale = MIXED ? A.U->acc : 1.0;
+  for (int g = blockIdx.x * kGrWarps + w; g < ngroups; g += gridDim.x * kGrWarps) {
+    const int32_t s0 = T.grp_start[g], s1 = T.grp_end[g], inst = T.grp_inst[g];
+    const int32_t slot = s0 + lane;
+    const bool act = slot < s1;
+    const int32_t a = act ? T.perm[slot] : 0;
+    const unsigned long long ka = act ? T.skey[slot] : 0ULL;
+    double xa[3] = {0, 0, 0};
+    for (int ax = 0; ax < dim; ++ax) xa[ax] = A.x[ax][a];
+    const float4 Pa = A.pk.px[a], Qa = A.pk.pxl[a];
+    const double e = MIXED ? A.eps * (double)Pa.w : A.eps * A.h[a];
+    const R eps2 = (R)(e * e);
+    const double s0r = T.inst_s0[inst];
+    const double th = A.theta;
+    const float th2f = (float)(th * th);
+    KahanT<R> acc[3];
+    int32_t skip_until = -1;
+    const int32_t root = T.inst_root[inst];
+    const int32_t stop = root >= 0 ? T.skip[root] : root;
+    int iter = 0;
+    for (int32_t nd = root; nd < stop && iter <= nnodes; ++iter) {
+      const int lev = T.level[nd];
+      const int32_t f = T.first[nd], e1 = T.end[nd], sk = T.skip[nd];
+      const bool leaf = (e1 - f <= L) || lev == B;
+      bool open = false, direct = false;
+      if (act && nd >= skip_until) {
+        const bool inside = (ka >> (dim * (B - lev))) == T.cell[nd];
+        bool accept = false;
+        float mpf = 0.f;
+        R d[3] = {R(0), R(0), R(0)}, r2 = R(0);
+        if (!inside) {
+          if constexpr (MIXED) {
+            const float4 ch = T.fcom_hi[nd], cl = T.fcom_lo[nd];
+            d[0] = (Pa.x - ch.x) + (Qa.x - cl.x);
+            d[1] = (Pa.y - ch.y) + (Qa.y - cl.y);
+            d[2] = (Pa.z - ch.z) + (Qa.z - cl.z);
+            r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            mpf = ch.w;
+            const float sf = cl.w;
+            const float lhs = sf * sf, rhs = th2f * r2;
+            if (lhs < rhs * (1.0f - kMacBand)) accept = true;
+            else if (lhs > rhs * (1.0f + kMacBand)) accept = false;
+            else {
+              double c[3] = {T.com[nd], T.com[cap + nd], dim == 3 ? T.com[2 * cap + nd] : 0.0};
+              accept = ldexp(s0r, -lev) < th * sqrt(r2_fp64(dim, xa, c));
+            }
+          } else {
+            const double s = ldexp(s0r, -lev);
+            double c[3] = {T.com[nd], T.com[cap + nd], dim == 3 ? T.com[2 * cap + nd] : 0.0};
+            for (int ax = 0; ax < 3; ++ax) d[ax] = ax < dim ? xa[ax] - c[ax] : 0.0;
+            r2 = r2_fp64(dim, xa, c);
+            accept = s < th * sqrt(r2);
+          }
+        }
+        if (accept) {
+          const R mp = MIXED ? (R)mpf : (R)T.mass[nd];
+          const R q = r2 + eps2;
+          const R inv = R(1) / (q * sqrt(q));
+          for (int ax = 0; ax < dim; ++ax) acc[ax].add(-G * mp * d[ax] * inv);
+          skip_until = sk;
+        } else if (leaf) {
+          direct = true;
+          skip_until = sk;
+        } else {
+          open = true;
+        }
+      }
+      const bool any_open = __any_sync(0xffffffffu, open);
+      if (__any_sync(0xffffffffu, direct)) {
+        for (int32_t base = f; base < e1; base += kMaxLeaf) {
+          const int c = min(e1 - base, kMaxLeaf);
+          if (lane < c) {
+            const int32_t b = T.perm[base + lane];
+            const float4 pb = A.pk.px[b], qb = A.pk.pxl[b];
+            sh_hi[w][lane] = make_float4(pb.x, pb.y, pb.z, (float)0);
+            sh_lo[w][lane] = make_float4(qb.x, qb.y, qb.z, qb.w);  // .w = m as float
+            sh_b[w][lane] = b;
+          }
+          __syncwarp();
+          if (direct) {
+            for (int k = 0; k < c; ++k) {
+              const int32_t b = sh_b[w][k];
+              if (b == a) continue;
+              R d[3], mb;
+              if constexpr (MIXED) {
+                const float4 ph = sh_hi[w][k], pl = sh_lo[w][k];
+                d[0] = (Pa.x - ph.x) + (Qa.x - pl.x);
+                d[1] = (Pa.y - ph.y) + (Qa.y - pl.y);
+                d[2] = (Pa.z - ph.z) + (Qa.z - pl.z);
+                mb = pl.w;
+              } else {
+                for (int ax = 0; ax < 3; ++ax) d[ax] = ax < dim ? xa[ax] - A.x[ax][b] : 0.0;
+                mb = A.m[b];
+              }
+              const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+              const R q = r2 + eps2;
+              if (!(q > R(0))) continue;
+              const R inv = R(1) / (q * sqrt(q));
+              for (int ax = 0; ax < dim; ++ax) acc[ax].add(-G * mb * d[ax] * inv);
+            }
+          }
+          __syncwarp();
+        }
+      }
+      nd = any_open ? nd + 1 : sk;
+    }
+    if (iter > nnodes) raise_err(A.err, ERR_TIMEOUT);
+    if (act)
+      for (int ax = 0; ax < dim; ++ax) A.out[ax][a] = acc[ax].value() * out_scale;
+  }
+}
+
+void gravity_walk(sph_ctx *c, const sph_state *s, const sph_params &p, double *ax, double *ay, double *az,
+                  cudaStream_t st) {
+  if (s->n == 0) return;
+  GravArgs A;
+  memset(&A, 0, sizeof(A));
+  A.T = c->tree;
+  A.pk = c->pk;
+  for (int k = 0; k < 3; ++k) A.x[k] = s->x[k];
+  A.m = s->m;
+  A.h = s->h;
+  A.dim = s->dim;
+  A.G = p.G;
+  A.theta = p.theta;
+  A.eps = p.eps_grav;
+  A.out[0] = ax;
+  A.out[1] = ay;
+  A.out[2] = az;
+  A.U = c->units;
+  A.err = c->d_err;
+  int blocks = 152 * 8;
+  if (p.precision == SPH_MIXED) k_gravity<true><<<blocks, kGrWarps * 32, 0, st>>>(A);
+  else k_gravity<false><<<blocks, kGrWarps * 32, 0, st>>>(A);
+}
+
+}  // namespace sph

@@ -1,0 +1,261 @@
+// Internal declarations of the GB300 SPH library: the context, device
+// helpers and the kernels' host launchers.  Not part of the public ABI
+// (include/sph.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "sph.h"
+
+namespace sph {
+
+// ---------------------------------------------------------------------------
+// Device error word bits (OR-ed by kernels, read by sph_sync_status).
+// ---------------------------------------------------------------------------
+enum : int32_t {
+  ERR_NB_OVERFLOW = 1,     // a particle has more partners than max_neighbours
+  ERR_NODE_OVERFLOW = 2,   // octree needs more nodes than the context holds
+  ERR_NONFINITE = 4,       // NaN/Inf coordinate or velocity, h <= 0, rho <= 0
+  ERR_TIMEOUT = 8,         // a bounded loop hit its iteration limit
+  ERR_CSR_OVERFLOW = 16,   // CSR output longer than the caller's capacity
+};
+
+constexpr int kWarp = 32;
+constexpr int kMaxLeaf = 32;
+
+// Per-particle FP32 views used by the walks and the mixed-precision passes.
+// Positions are split X = x - corner into hi = float(X), lo = float(X - hi)
+// so that differences of neighbours keep ~48 bits; velocities likewise.
+struct PackedF32 {
+  float4 *px;   // (x_hi, y_hi, z_hi, h)
+  float4 *pxl;  // (x_lo, y_lo, z_lo, m)
+  float4 *pv;   // (vx_hi, vy_hi, vz_hi, rho)
+  float4 *pvl;  // (vx_lo, vy_lo, vz_lo, m/rho)
+};
+
+struct Tree {
+  // sort
+  unsigned long long *keys[2];
+  int32_t *vals[2];
+  uint32_t *hist;
+  int64_t hist_cap;
+  int32_t *perm;       // sorted slot -> state index (points into vals[*])
+  unsigned long long *skey;  // sorted keys (points into keys[*])
+  // per-slot node emission counts and their exclusive scan
+  int32_t *ncount;
+  int32_t *nstart;
+  int32_t *scan_tmp;
+  // nodes (pre-order)
+  int64_t cap_nodes;
+  int32_t *nnodes;     // device scalar
+  int32_t *first, *end, *skip, *parent, *nchild, *arrived, *level;
+  unsigned long long *cell;  // level prefix of the key (instance bits included)
+  double *mass, *com;  // com: 3 * cap_nodes, component-major
+  double *bblo, *bbhi; // tight particle box, 3 * cap_nodes each
+  double *hmax;
+  float4 *fbox_lo;     // (lo xyz relative to instance corner, rounded down; hmax rounded up)
+  float4 *fbox_hi;     // (hi xyz, rounded up)
+  float4 *fcom_hi;     // (com hi xyz relative to instance corner, mass)
+  float4 *fcom_lo;     // (com lo xyz, edge s0 / 2^level)
+  // per instance
+  unsigned long long *inst_bb;  // 6 per instance: encoded min xyz, encoded max xyz
+  double *inst_lo;     // 3 per instance
+  double *inst_s0;
+  int32_t *inst_root;
+  int32_t *inst_goff;  // groups before each instance (ninst + 1)
+  // walk groups: up to 32 consecutive slots of one instance
+  int32_t *grp_start, *grp_end, *grp_inst;
+  int32_t *ngroups;    // device scalar
+  int64_t cap_groups;
+  int leaf_size, max_depth, dim, ninst;
+  int64_t n;
+};
+
+struct MatTable {
+  sph_material m[SPH_MAX_MATERIALS];
+  int32_t nmat;
+};
+
+// Code units of the FP32 views.  Every factor is a power of two, so the
+// scaling is exact and FP32 arithmetic in code units rounds exactly as it
+// would in SI, but without overflow or underflow: L from h of particle 0,
+// M from its mass, T from L over a material sound speed.
+struct Units {
+  double L, M, T;                 // base units (SI per code unit)
+  double invL, invM, invT;
+  double rho, invrho;             // M / L^D
+  double V, invV;                 // L / T
+  double sig, invsig;             // rho V^2: stress, pressure
+  double E, invE;                 // V^2: specific energy
+  double acc;                     // L / T^2
+  double Gs;                      // gravity constant in code units (set per call)
+  float matf[SPH_MAX_MATERIALS][16];  // materials in code units (see k_units)
+};
+
+struct StepBufs {
+  // predicted state
+  double *x[3], *v[3], *rho, *u, *S, *dmg;
+  // two derivative sets
+  double *d_x[2][3], *d_v[2][3], *d_rho[2], *d_u[2], *d_S[2], *d_dmg[2], *d_cs[2];
+  int32_t *d_nact[2];
+  unsigned long long *dt_enc;  // per instance, ordered encoding for atomicMin
+  double *dt;                  // per instance
+  double *gather;              // reorder scratch (n doubles)
+  int32_t *gather_i;
+};
+
+}  // namespace sph
+
+struct sph_ctx {
+  int dim;
+  int device;
+  int64_t cap_n;
+  int32_t cap_inst;
+  int32_t kmax;
+  int32_t leaf_default;
+  int64_t bytes;
+  char err[512];
+  int32_t *d_err;       // device error word
+  int32_t *h_err;       // pinned host copy
+  sph::Tree tree;
+  sph::PackedF32 pk;
+  // partners, column-major: nb_idx[k * cap_n + a]
+  int32_t *nb_idx;
+  int32_t *nb_cnt;
+  int64_t *csr_total;   // device scalar for sph_neighbours
+  // pass A -> pass B per-particle data
+  void *T;              // nsym * cap_n of double (FP64) or float (mixed)
+  void *zeta;
+  double *cs;
+  double *p;
+  double *ag;           // gravity acceleration, 3 * cap_n
+  sph::Units *units;    // device
+  double vscale;        // host: velocity scale for the time unit
+  sph::MatTable mt;     // host copy of the materials of the current call
+  sph::StepBufs st;
+  // allocation list
+  void *allocs[128];
+  int nallocs;
+};
+
+namespace sph {
+
+// ---------------------------------------------------------------------------
+// Small device helpers
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int nsym(int dim) { return dim == 3 ? 6 : 3; }
+
+// symmetric component index: 3D (xx,yy,zz,xy,xz,yz), 2D (xx,yy,xy)
+__host__ __device__ inline int symk(int dim, int a, int b) {
+  if (a == b) return a;
+  if (dim == 2) return 2;
+  int s = a + b;  // (0,1)->1, (0,2)->2, (1,2)->3
+  return s + 2;
+}
+
+// Order-preserving map of doubles to unsigned 64-bit integers, so that
+// atomicMin/atomicMax on the integers give the min/max of the doubles.
+__device__ __forceinline__ unsigned long long dbl_to_ord(double v) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b & 0x8000000000000000ULL) ? ~b : (b | 0x8000000000000000ULL);
+}
+__device__ __forceinline__ double ord_to_dbl(unsigned long long o) {
+  unsigned long long b = (o & 0x8000000000000000ULL) ? (o & 0x7fffffffffffffffULL) : ~o;
+  return __longlong_as_double((long long)b);
+}
+
+// Instance of particle i (instances are contiguous ranges).
+__device__ __forceinline__ int inst_of(const int64_t *inst_off, int ninst, int64_t i) {
+  if (ninst <= 1 || inst_off == nullptr) return 0;
+  int lo = 0, hi = ninst - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (inst_off[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void raise_err(int32_t *err, int32_t bit) { atomicOr(err, bit); }
+
+// Cubic B-spline kernel of Sect. 3.1.1 with support radius h.
+template <class R>
+__device__ __forceinline__ R kernel_sigma(int dim) {
+  return dim == 3 ? R(2.5464790894703255) : R(1.8189136353359467);  // 8/pi, 40/(7 pi)
+}
+
+template <class R>
+__device__ __forceinline__ R kern_W(R q, R norm) {  // norm = s / h^D
+  if (q < R(0.5)) return norm * (R(6) * q * q * q - R(6) * q * q + R(1));
+  if (q <= R(1)) {
+    R t = R(1) - q;
+    return norm * R(2) * t * t * t;
+  }
+  return R(0);
+}
+
+template <class R>
+__device__ __forceinline__ R kern_dW(R q, R gnorm) {  // gnorm = 6 s / h^(D+1)
+  if (q < R(0.5)) return gnorm * (R(3) * q * q - R(2) * q);
+  if (q <= R(1)) {
+    R t = R(1) - q;
+    return -gnorm * t * t;
+  }
+  return R(0);
+}
+
+template <class R>
+__device__ __forceinline__ R hpow(R h, int k) {
+  R r = h;
+  for (int i = 1; i < k; ++i) r *= h;
+  return r;
+}
+
+// Kahan-compensated accumulator (plain sum in double).
+template <class R>
+struct KahanT {
+  R s = R(0), c = R(0);
+  __device__ __forceinline__ void add(R v) {
+    R y = v - c;
+    R t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+template <>
+struct KahanT<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+// Host-side launch helpers ---------------------------------------------------
+inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+// Material constants in code units, indices into Units::matf
+enum { MF_RHO0, MF_CS, MF_K0, MF_NM, MF_AT, MF_BT, MF_E0, MF_EIV, MF_ECV, MF_AA, MF_BB, MF_ALPHA, MF_BETA,
+       MF_RHOCUT, MF_MU, MF_Y0 };
+
+double velocity_scale(const MatTable &mt);
+// tree.cu
+void tree_build(sph_ctx *c, const sph_state *s, int leaf_size, int max_depth, cudaStream_t st);
+void tree_reorder_state(sph_ctx *c, sph_state *s, cudaStream_t st);
+void pack_f32(sph_ctx *c, const sph_state *s, cudaStream_t st);
+// neighbours.cu
+void find_partners(sph_ctx *c, const sph_state *s, cudaStream_t st);
+void partners_to_csr(sph_ctx *c, const sph_state *s, int64_t *off, int32_t *idx, int64_t cap, cudaStream_t st);
+// rhs.cu
+void rhs_passes(sph_ctx *c, sph_state *s, const MatTable &mt, const sph_params &p, const sph_derivs &out,
+                cudaStream_t st);
+// gravity.cu
+void gravity_walk(sph_ctx *c, const sph_state *s, const sph_params &p, double *ax, double *ay, double *az,
+                  cudaStream_t st);
+// step.cu
+void timestep_reduce(sph_ctx *c, const sph_state *s, const sph_params &p, const sph_derivs &d, cudaStream_t st);
+void pc_update(sph_ctx *c, const sph_state *base, sph_state *out, const sph_derivs &d, double frac,
+               const MatTable &mt, const sph_params &p, cudaStream_t st);
+
+}  // namespace sph

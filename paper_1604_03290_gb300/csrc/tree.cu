@@ -1,0 +1,862 @@
+// Octree over Morton-sorted particles (Sect. 3.5.1), GB300 form.
+//
+// Instead of the paper's lock-based insertion (atomicCAS on child slots) the
+// tree is derived from sorted keys, with no locks and no waits:
+//   1. per-instance bounding box -> root cube (lower corner = per-axis min,
+//      edge s0 = max extent * (1 + 2^-20));
+//   2. key = instance bits | Morton interleave of the cell index
+//      k = floor((x - min) / s0 * 2^B) (B bits per axis);
+//   3. LSD radix sort of (key, particle) pairs, 8-bit digits, stable;
+//   4. every slot i that starts a cell at some level emits that cell as a
+//      node if its parent cell holds more than L particles; slot order then
+//      level order is exactly pre-order, so the subtree of a node is the
+//      contiguous id range [id, skip[id]) and walks need no stack;
+//   5. node mass, centre of mass and tight box bottom-up: the last child to
+//      arrive (atomic counter) combines its siblings in child order, so the
+//      result does not depend on arrival order.
+#include "sph_internal.cuh"
+
+namespace sph {
+
+// ---------------------------------------------------------------------------
+// Bounding boxes and validity
+// ---------------------------------------------------------------------------
+__global__ void k_bbox_init(unsigned long long *bb, int ninst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ninst) {
+    for (int ax = 0; ax < 3; ++ax) {
+      bb[6 * i + ax] = dbl_to_ord(__longlong_as_double(0x7ff0000000000000LL));       // +inf
+      bb[6 * i + 3 + ax] = dbl_to_ord(__longlong_as_double((long long)0xfff0000000000000ULL));  // -inf
+    }
+  }
+}
+
+__device__ __forceinline__ double warp_min(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// One block per instance when several instances are given; otherwise a
+// grid-stride pass.  Also flags non-finite positions/velocities and h, rho
+// that are not positive.
+__global__ void k_bbox(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+                       const double *__restrict__ vx, const double *__restrict__ vy, const double *__restrict__ vz,
+                       const double *__restrict__ h, const double *__restrict__ rho, int64_t n, int dim,
+                       const int64_t *__restrict__ inst_off, int ninst, unsigned long long *bb, int32_t *err) {
+  const double inf = __longlong_as_double(0x7ff0000000000000LL);
+  double lo[3] = {inf, inf, inf}, hi[3] = {-inf, -inf, -inf};
+  int64_t i0, i1, stride;
+  int inst;
+  if (ninst > 1 && inst_off) {
+    inst = blockIdx.x;
+    i0 = inst_off[inst] + threadIdx.x;
+    i1 = inst_off[inst + 1];
+    stride = blockDim.x;
+  } else {
+    inst = 0;
+    i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    i1 = n;
+    stride = (int64_t)gridDim.x * blockDim.x;
+  }
+  bool bad = false;
+  for (int64_t i = i0; i < i1; i += stride) {
+    double p[3] = {x[i], y[i], dim == 3 ? z[i] : 0.0};
+    double v2 = vx[i] + vy[i] + (dim == 3 ? vz[i] : 0.0);
+    double hh = h[i], rr = rho[i];
+    bad |= !isfinite(p[0] + p[1] + p[2]) || !isfinite(v2) || !(hh > 0.0) || !isfinite(hh) || !(rr > 0.0) ||
+           !isfinite(rr);
+    for (int ax = 0; ax < 3; ++ax) {
+      lo[ax] = fmin(lo[ax], p[ax]);
+      hi[ax] = fmax(hi[ax], p[ax]);
+    }
+  }
+  if (bad) raise_err(err, ERR_NONFINITE);
+  __shared__ double s[6][32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int ax = 0; ax < 3; ++ax) {
+    double a = warp_min(lo[ax]), b = warp_max(hi[ax]);
+    if (lane == 0) {
+      s[ax][w] = a;
+      s[3 + ax][w] = b;
+    }
+  }
+  __syncthreads();
+  if (w == 0) {
+    for (int ax = 0; ax < 3; ++ax) {
+      double a = lane < nw ? s[ax][lane] : inf;
+      double b = lane < nw ? s[3 + ax][lane] : -inf;
+      a = warp_min(a);
+      b = warp_max(b);
+      if (lane == 0) {
+        atomicMin(&bb[6 * inst + ax], dbl_to_ord(a));
+        atomicMax(&bb[6 * inst + 3 + ax], dbl_to_ord(b));
+      }
+    }
+  }
+}
+
+// Root cube per instance (Sect. 3.5.1): corner = per-axis minimum, edge
+// s0 = max over axes of the extent, enlarged by 2^-20 so that the particle
+// at the maximum falls inside; a zero extent (one particle) gives s0 = 1.
+__global__ void k_root(const unsigned long long *bb, int ninst, int dim, double *lo_out, double *s0_out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ninst) return;
+  double ext = 0.0;
+  for (int ax = 0; ax < 3; ++ax) {
+    double lo = ord_to_dbl(bb[6 * i + ax]), hi = ord_to_dbl(bb[6 * i + 3 + ax]);
+    if (ax >= dim || !(hi >= lo)) {  // unused axis or empty instance
+      lo = 0.0;
+      hi = 0.0;
+    }
+    lo_out[3 * i + ax] = lo;
+    ext = fmax(ext, __dsub_rn(hi, lo));
+  }
+  double s0 = __dmul_rn(ext, 1.0 + 0x1p-20);
+  s0_out[i] = s0 > 0.0 ? s0 : 1.0;
+}
+
+// ---------------------------------------------------------------------------
+// Morton keys
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long spread3(unsigned long long v) {
+  v &= 0x1fffffULL;
+  v = (v | (v << 32)) & 0x1f00000000ffffULL;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffULL;
+  v = (v | (v << 8)) & 0x100f00f00f00f00fULL;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ULL;
+  v = (v | (v << 2)) & 0x1249249249249249ULL;
+  return v;
+}
+__device__ __forceinline__ unsigned long long compact3(unsigned long long v) {
+  v &= 0x1249249249249249ULL;
+  v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ULL;
+  v = (v ^ (v >> 4)) & 0x100f00f00f00f00fULL;
+  v = (v ^ (v >> 8)) & 0x1f0000ff0000ffULL;
+  v = (v ^ (v >> 16)) & 0x1f00000000ffffULL;
+  v = (v ^ (v >> 32)) & 0x1fffffULL;
+  return v;
+}
+__device__ __forceinline__ unsigned long long spread2(unsigned long long v) {
+  v &= 0xffffffffULL;
+  v = (v | (v << 16)) & 0x0000ffff0000ffffULL;
+  v = (v | (v << 8)) & 0x00ff00ff00ff00ffULL;
+  v = (v | (v << 4)) & 0x0f0f0f0f0f0f0f0fULL;
+  v = (v | (v << 2)) & 0x3333333333333333ULL;
+  v = (v | (v << 1)) & 0x5555555555555555ULL;
+  return v;
+}
+__device__ __forceinline__ unsigned long long compact2(unsigned long long v) {
+  v &= 0x5555555555555555ULL;
+  v = (v ^ (v >> 1)) & 0x3333333333333333ULL;
+  v = (v ^ (v >> 2)) & 0x0f0f0f0f0f0f0f0fULL;
+  v = (v ^ (v >> 4)) & 0x00ff00ff00ff00ffULL;
+  v = (v ^ (v >> 8)) & 0x0000ffff0000ffffULL;
+  v = (v ^ (v >> 16)) & 0xffffffffULL;
+  return v;
+}
+
+// Cell index along one axis, evaluated in the same operation order as the
+// definition: floor(((x - min) / s0) * 2^B), clamped to [0, 2^B - 1].
+__device__ __forceinline__ unsigned long long cell_index(double v, double lo, double s0, int B) {
+  double t = __ddiv_rn(__dsub_rn(v, lo), s0);
+  double f = floor(__dmul_rn(t, (double)(1ULL << B)));
+  long long kmax = (1LL << B) - 1;
+  long long k = f < 0.0 ? 0 : (f > (double)kmax ? kmax : (long long)f);
+  return (unsigned long long)k;
+}
+
+__global__ void k_keys(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+                       int64_t n, int dim, int B, const int64_t *__restrict__ inst_off, int ninst,
+                       const double *__restrict__ ilo, const double *__restrict__ is0, unsigned long long *keys,
+                       int32_t *vals) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int inst = inst_of(inst_off, ninst, i);
+  double s0 = is0[inst];
+  unsigned long long kx = cell_index(x[i], ilo[3 * inst + 0], s0, B);
+  unsigned long long ky = cell_index(y[i], ilo[3 * inst + 1], s0, B);
+  unsigned long long key;
+  if (dim == 3) {
+    unsigned long long kz = cell_index(z[i], ilo[3 * inst + 2], s0, B);
+    key = spread3(kx) | (spread3(ky) << 1) | (spread3(kz) << 2);
+  } else {
+    key = spread2(kx) | (spread2(ky) << 1);
+  }
+  key |= (unsigned long long)inst << (dim * B);
+  keys[i] = key;
+  vals[i] = (int32_t)i;
+}
+
+// Code units from particle 0 (see Units).
+__device__ __forceinline__ double pow2_floor(double v) { return (v > 0.0 && isfinite(v)) ? ldexp(1.0, ilogb(v)) : 1.0; }
+
+__global__ void k_units(const double *__restrict__ h, const double *__restrict__ m, int64_t n, int dim,
+                        double vscale, MatTable mt, Units *U) {
+  if (threadIdx.x != 0) return;
+  const double L = pow2_floor(n > 0 ? h[0] : 1.0), M = pow2_floor(n > 0 ? m[0] : 1.0);
+  const double T = pow2_floor(L / (vscale > 0.0 ? vscale : 1.0));
+  Units u;
+  u.L = L;
+  u.M = M;
+  u.T = T;
+  u.invL = 1.0 / L;
+  u.invM = 1.0 / M;
+  u.invT = 1.0 / T;
+  u.rho = dim == 3 ? M / (L * L * L) : M / (L * L);  // density: mass per L^D
+  u.invrho = 1.0 / u.rho;
+  u.V = L / T;
+  u.invV = 1.0 / u.V;
+  u.sig = dim == 3 ? M / (L * T * T) : M / (T * T);  // stress: rho V^2
+  u.invsig = 1.0 / u.sig;
+  u.E = u.V * u.V;
+  u.invE = 1.0 / u.E;
+  u.acc = L / (T * T);
+  u.Gs = 0.0;
+  for (int i = 0; i < SPH_MAX_MATERIALS; ++i) {
+    const sph_material &a = mt.m[i < mt.nmat ? i : 0];
+    float *f = u.matf[i];
+    f[MF_RHO0] = (float)(a.rho0 * u.invrho);
+    f[MF_CS] = (float)(a.cs * u.invV);
+    f[MF_K0] = (float)(a.K0 * u.invsig);
+    f[MF_NM] = (float)a.n_M;
+    f[MF_AT] = (float)(a.A_T * u.invsig);
+    f[MF_BT] = (float)(a.B_T * u.invsig);
+    f[MF_E0] = (float)(a.E0 * u.invE);
+    f[MF_EIV] = (float)(a.E_iv * u.invE);
+    f[MF_ECV] = (float)(a.E_cv * u.invE);
+    f[MF_AA] = (float)a.a_T;
+    f[MF_BB] = (float)a.b_T;
+    f[MF_ALPHA] = (float)a.alpha_T;
+    f[MF_BETA] = (float)a.beta_T;
+    f[MF_RHOCUT] = (float)a.rho_cut;
+    f[MF_MU] = (float)(a.mu * u.invsig);
+    f[MF_Y0] = (float)(a.Y0 * u.invsig);
+  }
+  *U = u;
+}
+
+// FP32 views of the state (see PackedF32), in code units.
+__global__ void k_pack(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+                       const double *__restrict__ vx, const double *__restrict__ vy, const double *__restrict__ vz,
+                       const double *__restrict__ h, const double *__restrict__ m, const double *__restrict__ rho,
+                       int64_t n, int dim, const int64_t *__restrict__ inst_off, int ninst,
+                       const double *__restrict__ ilo, const Units *__restrict__ U, PackedF32 pk) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int inst = inst_of(inst_off, ninst, i);
+  const double iL = U->invL, iV = U->invV;
+  double X[3] = {(x[i] - ilo[3 * inst]) * iL, (y[i] - ilo[3 * inst + 1]) * iL,
+                 dim == 3 ? (z[i] - ilo[3 * inst + 2]) * iL : 0.0};
+  double V[3] = {vx[i] * iV, vy[i] * iV, dim == 3 ? vz[i] * iV : 0.0};
+  float xh[3], xl[3], vh[3], vl[3];
+  for (int ax = 0; ax < 3; ++ax) {
+    xh[ax] = __double2float_rn(X[ax]);
+    xl[ax] = __double2float_rn(X[ax] - (double)xh[ax]);
+    vh[ax] = __double2float_rn(V[ax]);
+    vl[ax] = __double2float_rn(V[ax] - (double)vh[ax]);
+  }
+  double r = rho[i] * U->invrho, mm = m[i] * U->invM;
+  pk.px[i] = make_float4(xh[0], xh[1], xh[2], __double2float_rn(h[i] * iL));
+  pk.pxl[i] = make_float4(xl[0], xl[1], xl[2], __double2float_rn(mm));
+  pk.pv[i] = make_float4(vh[0], vh[1], vh[2], __double2float_rn(r));
+  pk.pvl[i] = make_float4(vl[0], vl[1], vl[2], __double2float_rn(mm / r));
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort of (u64 key, i32 value), 8-bit digits, stable.
+// ---------------------------------------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const unsigned long long *__restrict__ keys, int64_t n,
+                                                             int shift, uint32_t *hist, int nblocks) {
+  __shared__ uint32_t hs[256];
+  hs[threadIdx.x] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll 4
+  for (int it = 0; it < kSortItems; ++it) {
+    int64_t i = base + it * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&hs[(keys[i] >> shift) & 255], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = hs[threadIdx.x];
+}
+
+// Exclusive scan of m unsigned ints in place, one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_scan_u32_1blk(uint32_t *d, int64_t m) {
+  __shared__ uint32_t ws[32];
+  int64_t chunk = (m + 1023) / 1024;
+  int64_t b = threadIdx.x * chunk, e = min(m, b + chunk);
+  uint32_t s = 0;
+  for (int64_t i = b; i < e; ++i) s += d[i];
+  // block exclusive scan of s
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t v = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) ws[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t t = ws[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t u = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += u;
+    }
+    ws[lane] = t;
+  }
+  __syncthreads();
+  uint32_t off = v - s + (w > 0 ? ws[w - 1] : 0);
+  for (int64_t i = b; i < e; ++i) {
+    uint32_t t = d[i];
+    d[i] = off;
+    off += t;
+  }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const unsigned long long *__restrict__ kin,
+                                                                const int32_t *__restrict__ vin,
+                                                                unsigned long long *__restrict__ kout,
+                                                                int32_t *__restrict__ vout, int64_t n, int shift,
+                                                                const uint32_t *__restrict__ hist, int nblocks) {
+  __shared__ uint32_t off[256];
+  __shared__ uint32_t wc[kSortThreads / 32][256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  off[threadIdx.x] = hist[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+  const unsigned lt = (1u << lane) - 1u;
+  int64_t base = (int64_t)blockIdx.x * kSortTile;
+  for (int it = 0; it < kSortItems; ++it) {
+    int64_t i = base + it * kSortThreads + threadIdx.x;
+    bool valid = i < n;
+    unsigned long long key = valid ? kin[i] : 0ULL;
+    int32_t val = valid ? vin[i] : 0;
+    int d = valid ? (int)((key >> shift) & 255) : 256;
+#pragma unroll
+    for (int ww = 0; ww < kSortThreads / 32; ++ww) wc[ww][threadIdx.x] = 0;
+    __syncthreads();
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    int rank = __popc(peers & lt);
+    if (valid && rank == 0) wc[w][d] = __popc(peers);
+    __syncthreads();
+    uint32_t tot = 0;
+    {
+      int dd = threadIdx.x;
+#pragma unroll
+      for (int ww = 0; ww < kSortThreads / 32; ++ww) {
+        uint32_t t = wc[ww][dd];
+        wc[ww][dd] = tot;
+        tot += t;
+      }
+    }
+    __syncthreads();
+    if (valid) {
+      uint32_t pos = off[d] + wc[w][d] + rank;
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+    __syncthreads();
+    off[threadIdx.x] += tot;
+    __syncthreads();
+  }
+}
+
+static void radix_sort(sph_ctx *c, int64_t n, int bits, cudaStream_t st) {
+  Tree &T = c->tree;
+  int nblocks = nblk(n, kSortTile);
+  int passes = (bits + 7) / 8;
+  int src = 0;
+  for (int p = 0; p < passes; ++p) {
+    int shift = 8 * p;
+    k_radix_hist<<<nblocks, kSortThreads, 0, st>>>(T.keys[src], n, shift, T.hist, nblocks);
+    k_scan_u32_1blk<<<1, 1024, 0, st>>>(T.hist, (int64_t)256 * nblocks);
+    k_radix_scatter<<<nblocks, kSortThreads, 0, st>>>(T.keys[src], T.vals[src], T.keys[src ^ 1], T.vals[src ^ 1], n,
+                                                     shift, T.hist, nblocks);
+    src ^= 1;
+  }
+  T.skey = T.keys[src];
+  T.perm = T.vals[src];
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of int32 counts (length m), three phases.
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256, kScanItems = 16, kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t *total) {
+  __shared__ int32_t ws[32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int32_t s = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int32_t t = __shfl_up_sync(0xffffffffu, s, o);
+    if (lane >= o) s += t;
+  }
+  if (lane == 31) ws[w] = s;
+  __syncthreads();
+  if (w == 0) {
+    int32_t t = lane < nw ? ws[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t u = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += u;
+    }
+    ws[lane] = t;
+  }
+  __syncthreads();
+  int32_t res = s - v + (w > 0 ? ws[w - 1] : 0);
+  *total = ws[nw - 1];
+  __syncthreads();
+  return res;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int32_t *__restrict__ in, int32_t *__restrict__ out,
+                                                             int64_t m, int32_t *tile_sums) {
+  int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int32_t v[kScanItems];
+  int32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = (base + k < m) ? in[base + k] : 0;
+    s += v[k];
+  }
+  int32_t tot;
+  int32_t off = block_excl_scan(s, &tot);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < m) out[base + k] = off;
+    off += v[k];
+  }
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tops(int32_t *t, int m) {
+  int chunk = (m + 1023) / 1024;
+  int b = threadIdx.x * chunk, e = min(m, b + chunk);
+  int32_t s = 0;
+  for (int i = b; i < e; ++i) s += t[i];
+  int32_t tot;
+  int32_t off = block_excl_scan(s, &tot);
+  for (int i = b; i < e; ++i) {
+    int32_t x = t[i];
+    t[i] = off;
+    off += x;
+  }
+}
+
+__global__ void k_scan_add(int32_t *out, int64_t m, const int32_t *tile_sums) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) out[i] += tile_sums[i / kScanTile];
+}
+
+static void scan_excl_i32(const int32_t *in, int32_t *out, int64_t m, int32_t *tmp, cudaStream_t st) {
+  int tiles = nblk(m, kScanTile);
+  k_scan_tiles<<<tiles, kScanThreads, 0, st>>>(in, out, m, tmp);
+  k_scan_tops<<<1, 1024, 0, st>>>(tmp, tiles);
+  k_scan_add<<<nblk(m, 256), 256, 0, st>>>(out, m, tmp);
+}
+
+void scan_counts(sph_ctx *c, const int32_t *in, int32_t *out, int64_t m, cudaStream_t st) {
+  scan_excl_i32(in, out, m, c->tree.scan_tmp, st);
+}
+
+// ---------------------------------------------------------------------------
+// Node emission
+// ---------------------------------------------------------------------------
+struct KeyLevels {
+  const unsigned long long *key;
+  int dim, B;
+  __device__ __forceinline__ unsigned long long prefix(int64_t i, int l) const { return key[i] >> (dim * (B - l)); }
+  // deepest level at which slots i-1 and i share a cell; -1 if they lie in
+  // different instances
+  __device__ __forceinline__ int common(int64_t i) const {
+    unsigned long long d = key[i] ^ key[i - 1];
+    if (d == 0) return B;
+    int hb = 63 - __clzll((long long)d);
+    if (hb >= dim * B) return -1;
+    return B - 1 - hb / dim;
+  }
+  // first slot in [lo, hi) whose level-l prefix exceeds p
+  __device__ __forceinline__ int64_t upper(unsigned long long p, int l, int64_t lo, int64_t hi) const {
+    while (lo < hi) {
+      int64_t mid = (lo + hi) >> 1;
+      if (prefix(mid, l) <= p) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+  }
+  // first slot in [lo, hi) whose level-l prefix is >= p
+  __device__ __forceinline__ int64_t lower(unsigned long long p, int l, int64_t lo, int64_t hi) const {
+    while (lo < hi) {
+      int64_t mid = (lo + hi) >> 1;
+      if (prefix(mid, l) < p) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+  }
+};
+
+__device__ __forceinline__ void slot_segment(const int64_t *inst_off, int ninst, int64_t n, int64_t i, int64_t &lo,
+                                             int64_t &hi) {
+  if (ninst > 1 && inst_off) {
+    int k = inst_of(inst_off, ninst, i);
+    lo = inst_off[k];
+    hi = inst_off[k + 1];
+  } else {
+    lo = 0;
+    hi = n;
+  }
+}
+
+// First level at which slot i starts a cell that is a node, or B+1 if none.
+__device__ __forceinline__ int first_node_level(const KeyLevels &K, int64_t i, int64_t seg_lo, int64_t seg_hi,
+                                                int L) {
+  int c = (i == seg_lo) ? -1 : K.common(i);
+  int l0 = c + 1;
+  if (l0 > K.B) return K.B + 1;
+  if (l0 > 0) {
+    unsigned long long pp = K.prefix(i, l0 - 1);
+    int64_t lo = K.lower(pp, l0 - 1, max(seg_lo, i - L), i);
+    int64_t hi = K.upper(pp, l0 - 1, i + 1, min(seg_hi, i + L + 1));
+    if (hi - lo <= L) return K.B + 1;  // the parent cell is a leaf (or lies below one)
+  }
+  return l0;
+}
+
+__global__ void k_node_count(KeyLevels K, int64_t n, int L, const int64_t *__restrict__ inst_off, int ninst,
+                             int32_t *cnt) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  if (i == n) {
+    cnt[n] = 0;
+    return;
+  }
+  int64_t seg_lo, seg_hi;
+  slot_segment(inst_off, ninst, n, i, seg_lo, seg_hi);
+  int l0 = first_node_level(K, i, seg_lo, seg_hi, L);
+  int k = 0;
+  int64_t e = seg_hi;
+  for (int l = l0; l <= K.B; ++l) {
+    int64_t end = K.upper(K.prefix(i, l), l, i + 1, e);
+    ++k;
+    if (end - i <= L || l == K.B) break;
+    e = end;
+  }
+  cnt[i] = k;
+}
+
+__global__ void k_node_emit(KeyLevels K, int64_t n, int L, const int64_t *__restrict__ inst_off, int ninst,
+                            const int32_t *__restrict__ nstart, Tree T, int32_t *err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  if (i == n) {
+    *T.nnodes = nstart[n] <= T.cap_nodes ? nstart[n] : (int32_t)T.cap_nodes;
+    if (nstart[n] > T.cap_nodes) raise_err(err, ERR_NODE_OVERFLOW);
+    return;
+  }
+  if (nstart[i + 1] == nstart[i]) return;
+  int64_t seg_lo, seg_hi;
+  slot_segment(inst_off, ninst, n, i, seg_lo, seg_hi);
+  int l0 = first_node_level(K, i, seg_lo, seg_hi, L);
+  int32_t parent = -1;
+  if (l0 > 0) {
+    // the parent cell starts at slot p; its node is the (l0-1 - l0(p))-th of p's chain
+    unsigned long long pp = K.prefix(i, l0 - 1);
+    int64_t p = K.lower(pp, l0 - 1, seg_lo, i);
+    int lp = (p == seg_lo) ? 0 : K.common(p) + 1;
+    parent = nstart[p] + (l0 - 1 - lp);
+  }
+  int64_t e = seg_hi;
+  int32_t id = nstart[i];
+  for (int l = l0; l <= K.B; ++l, ++id) {
+    int64_t end = K.upper(K.prefix(i, l), l, i + 1, e);
+    if (id < T.cap_nodes) {
+      T.first[id] = (int32_t)i;
+      T.end[id] = (int32_t)end;
+      T.level[id] = l;
+      T.cell[id] = K.prefix(i, l);
+      T.skip[id] = min((int64_t)nstart[end], T.cap_nodes);
+      T.parent[id] = parent;
+      if (parent >= 0) atomicAdd(&T.nchild[parent], 1);
+    }
+    parent = id;
+    if (end - i <= L || l == K.B) break;
+    e = end;
+  }
+}
+
+__global__ void k_inst_info(const int64_t *__restrict__ inst_off, int ninst, int64_t n, const int32_t *nstart,
+                            Tree T) {
+  // single block: groups per instance (32 slots each), their exclusive scan, roots
+  __shared__ int32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < ninst; base += blockDim.x) {
+    int i = base + threadIdx.x;
+    int64_t lo = 0, hi = n;
+    if (i < ninst && ninst > 1 && inst_off) {
+      lo = inst_off[i];
+      hi = inst_off[i + 1];
+    }
+    int32_t g = (i < ninst) ? (int32_t)((hi - lo + kWarp - 1) / kWarp) : 0;
+    int32_t tot;
+    int32_t off = block_excl_scan(g, &tot);
+    if (i < ninst) {
+      T.inst_goff[i] = carry + off;
+      T.inst_root[i] = (hi > lo) ? nstart[lo] : -1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    T.inst_goff[ninst] = carry;
+    *T.ngroups = carry;
+  }
+}
+
+__global__ void k_groups(const int64_t *__restrict__ inst_off, int ninst, int64_t n, Tree T) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int k = inst_of(inst_off, ninst, i);
+  int64_t lo = (ninst > 1 && inst_off) ? inst_off[k] : 0;
+  int64_t hi = (ninst > 1 && inst_off) ? inst_off[k + 1] : n;
+  int64_t r = i - lo;
+  if (r % kWarp) return;
+  int32_t g = T.inst_goff[k] + (int32_t)(r / kWarp);
+  T.grp_start[g] = (int32_t)i;
+  T.grp_end[g] = (int32_t)min(i + kWarp, hi);
+  T.grp_inst[g] = k;
+}
+
+// ---------------------------------------------------------------------------
+// Node moments, bottom-up
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float f_down(double v) { return __double2float_rd(v); }
+__device__ __forceinline__ float f_up(double v) { return __double2float_ru(v); }
+
+__global__ void k_moments(Tree T, const double *__restrict__ x, const double *__restrict__ y,
+                          const double *__restrict__ z, const double *__restrict__ m, const double *__restrict__ h,
+                          int dim, int L, const int64_t *__restrict__ inst_off, int ninst,
+                          const Units *__restrict__ U) {
+  int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int nn = *T.nnodes;
+  if (id >= nn) return;
+  int32_t f = T.first[id], e = T.end[id];
+  if (!(e - f <= L || T.level[id] == T.max_depth)) return;  // only leaves start
+  const double *X[3] = {x, y, z};
+  const int64_t cap = T.cap_nodes;
+  int inst = inst_of(inst_off, ninst, f);
+  double ilo[3] = {T.inst_lo[3 * inst], T.inst_lo[3 * inst + 1], T.inst_lo[3 * inst + 2]};
+  // leaf: straight from its particles, in slot order
+  double M = 0.0, mx[3] = {0, 0, 0}, lo[3], hi[3], hm = 0.0;
+  const double inf = __longlong_as_double(0x7ff0000000000000LL);
+  for (int ax = 0; ax < 3; ++ax) {
+    lo[ax] = inf;
+    hi[ax] = -inf;
+  }
+  for (int32_t j = f; j < e; ++j) {
+    int32_t a = T.perm[j];
+    double ma = m[a];
+    M += ma;
+    hm = fmax(hm, h[a]);
+    for (int ax = 0; ax < dim; ++ax) {
+      double v = X[ax][a];
+      mx[ax] += ma * v;
+      lo[ax] = fmin(lo[ax], v);
+      hi[ax] = fmax(hi[ax], v);
+    }
+  }
+  int64_t node = id;
+  for (int depth = 0; depth < 64; ++depth) {
+    T.mass[node] = M;
+    T.hmax[node] = hm;
+    for (int ax = 0; ax < 3; ++ax) {
+      bool use = ax < dim;
+      T.com[ax * cap + node] = use ? mx[ax] / M : 0.0;
+      T.bblo[ax * cap + node] = use ? lo[ax] : 0.0;
+      T.bbhi[ax * cap + node] = use ? hi[ax] : 0.0;
+    }
+    {
+      const double iL = U->invL;
+      T.fbox_lo[node] = make_float4(f_down((lo[0] - ilo[0]) * iL), f_down((lo[1] - ilo[1]) * iL),
+                                    dim == 3 ? f_down((lo[2] - ilo[2]) * iL) : 0.f, f_up(hm * iL));
+      T.fbox_hi[node] = make_float4(f_up((hi[0] - ilo[0]) * iL), f_up((hi[1] - ilo[1]) * iL),
+                                    dim == 3 ? f_up((hi[2] - ilo[2]) * iL) : 0.f, 0.f);
+      float ch[3], cl[3];
+      for (int ax = 0; ax < 3; ++ax) {
+        double X = ax < dim ? (mx[ax] / M - ilo[ax]) * iL : 0.0;
+        ch[ax] = __double2float_rn(X);
+        cl[ax] = __double2float_rn(X - (double)ch[ax]);
+      }
+      T.fcom_hi[node] = make_float4(ch[0], ch[1], ch[2], __double2float_rn(M * U->invM));
+      T.fcom_lo[node] = make_float4(cl[0], cl[1], cl[2],
+                                    __double2float_rn(ldexp(T.inst_s0[inst], -T.level[node]) * iL));
+    }
+    int32_t p = T.parent[node];
+    if (p < 0) return;
+    __threadfence();
+    int old = atomicAdd(&T.arrived[p], 1);
+    if (old != T.nchild[p] - 1) return;
+    __threadfence();
+    // last child in: combine all children of p in child order
+    M = 0.0;
+    hm = 0.0;
+    for (int ax = 0; ax < 3; ++ax) {
+      mx[ax] = 0.0;
+      lo[ax] = inf;
+      hi[ax] = -inf;
+    }
+    int32_t stop = T.skip[p];
+    int guard = 0;
+    for (int32_t cc = p + 1; cc < stop && guard < 64; cc = T.skip[cc], ++guard) {
+      double mc = __ldcg(&T.mass[cc]);
+      M += mc;
+      hm = fmax(hm, __ldcg(&T.hmax[cc]));
+      for (int ax = 0; ax < dim; ++ax) {
+        mx[ax] += mc * __ldcg(&T.com[ax * cap + cc]);
+        lo[ax] = fmin(lo[ax], __ldcg(&T.bblo[ax * cap + cc]));
+        hi[ax] = fmax(hi[ax], __ldcg(&T.bbhi[ax * cap + cc]));
+      }
+    }
+    node = p;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host orchestration
+// ---------------------------------------------------------------------------
+void pack_f32(sph_ctx *c, const sph_state *s, cudaStream_t st) {
+  int64_t n = s->n;
+  if (n == 0) return;
+  k_pack<<<nblk(n, 256), 256, 0, st>>>(s->x[0], s->x[1], s->x[2], s->v[0], s->v[1], s->v[2], s->h, s->m, s->rho, n,
+                                       s->dim, s->inst_off, s->ninst, c->tree.inst_lo, c->units, c->pk);
+}
+
+void tree_build(sph_ctx *c, const sph_state *s, int leaf_size, int max_depth, cudaStream_t st) {
+  Tree &T = c->tree;
+  const int64_t n = s->n;
+  const int ninst = s->ninst > 0 ? s->ninst : 1;
+  const int dim = s->dim;
+  T.leaf_size = leaf_size;
+  T.max_depth = max_depth;
+  T.dim = dim;
+  T.ninst = ninst;
+  T.n = n;
+  k_bbox_init<<<nblk(ninst, 128), 128, 0, st>>>(T.inst_bb, ninst);
+  if (n > 0) {
+    if (ninst > 1)
+      k_bbox<<<ninst, 256, 0, st>>>(s->x[0], s->x[1], s->x[2], s->v[0], s->v[1], s->v[2], s->h, s->rho, n, dim,
+                                   s->inst_off, ninst, T.inst_bb, c->d_err);
+    else
+      k_bbox<<<min(nblk(n, 256), 152 * 8), 256, 0, st>>>(s->x[0], s->x[1], s->x[2], s->v[0], s->v[1], s->v[2], s->h,
+                                                        s->rho, n, dim, nullptr, 1, T.inst_bb, c->d_err);
+  }
+  k_root<<<nblk(ninst, 128), 128, 0, st>>>(T.inst_bb, ninst, dim, T.inst_lo, T.inst_s0);
+  k_units<<<1, 32, 0, st>>>(s->h, s->m, n, dim, c->vscale, c->mt, c->units);
+  if (n > 0) {
+    k_keys<<<nblk(n, 256), 256, 0, st>>>(s->x[0], s->x[1], s->x[2], n, dim, max_depth, s->inst_off, ninst,
+                                         T.inst_lo, T.inst_s0, T.keys[0], T.vals[0]);
+    int ibits = 0;
+    while ((1 << ibits) < ninst) ++ibits;
+    radix_sort(c, n, dim * max_depth + ibits, st);
+  } else {
+    T.skey = T.keys[0];
+    T.perm = T.vals[0];
+  }
+  pack_f32(c, s, st);
+  KeyLevels K{T.skey, dim, max_depth};
+  k_node_count<<<nblk(n + 1, 256), 256, 0, st>>>(K, n, leaf_size, s->inst_off, ninst, T.ncount);
+  scan_excl_i32(T.ncount, T.nstart, n + 1, T.scan_tmp, st);
+  cudaMemsetAsync(T.nchild, 0, sizeof(int32_t) * T.cap_nodes, st);
+  cudaMemsetAsync(T.arrived, 0, sizeof(int32_t) * T.cap_nodes, st);
+  k_node_emit<<<nblk(n + 1, 256), 256, 0, st>>>(K, n, leaf_size, s->inst_off, ninst, T.nstart, T, c->d_err);
+  k_moments<<<nblk(T.cap_nodes, 256), 256, 0, st>>>(
+      T, s->x[0], s->x[1], s->x[2], s->m, s->h, dim, leaf_size, s->inst_off, ninst, c->units);
+  k_inst_info<<<1, 1024, 0, st>>>(s->inst_off, ninst, n, T.nstart, T);
+  if (n > 0) k_groups<<<nblk(n, 256), 256, 0, st>>>(s->inst_off, ninst, n, T);
+}
+
+// ---------------------------------------------------------------------------
+// In-place reorder of the caller's state along the tree
+// ---------------------------------------------------------------------------
+__global__ void k_gather_d(const double *__restrict__ src, double *__restrict__ dst, const int32_t *__restrict__ perm,
+                           int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[perm[i]];
+}
+__global__ void k_gather_i(const int32_t *__restrict__ src, int32_t *__restrict__ dst,
+                           const int32_t *__restrict__ perm, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[perm[i]];
+}
+__global__ void k_iota(int32_t *p, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = (int32_t)i;
+}
+
+void tree_reorder_state(sph_ctx *c, sph_state *s, cudaStream_t st) {
+  const int64_t n = s->n;
+  if (n == 0) return;
+  const int32_t *perm = c->tree.perm;
+  double *buf = c->st.gather;
+  auto gd = [&](double *f) {
+    if (!f) return;
+    k_gather_d<<<nblk(n, 256), 256, 0, st>>>(f, buf, perm, n);
+    cudaMemcpyAsync(f, buf, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  };
+  auto gi = [&](int32_t *f) {
+    if (!f) return;
+    k_gather_i<<<nblk(n, 256), 256, 0, st>>>(f, c->st.gather_i, perm, n);
+    cudaMemcpyAsync(f, c->st.gather_i, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st);
+  };
+  for (int ax = 0; ax < s->dim; ++ax) {
+    gd(s->x[ax]);
+    gd(s->v[ax]);
+  }
+  gd(s->rho);
+  gd(s->u);
+  gd(s->m);
+  gd(s->h);
+  gd(s->dmg);
+  if (s->S)
+    for (int k = 0; k < nsym(s->dim); ++k) gd(s->S + (int64_t)k * n);
+  gi(s->mat);
+  gi(s->id);
+  k_iota<<<nblk(n, 256), 256, 0, st>>>(c->tree.perm, n);
+  pack_f32(c, s, st);
+}
+
+// ---------------------------------------------------------------------------
+// Node export (tests)
+// ---------------------------------------------------------------------------
+__global__ void k_export_nodes(Tree T, int64_t cap, int dim, int32_t *level, int64_t *cell, int64_t *count,
+                               double *mass, double *com) {
+  int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int nn = *T.nnodes;
+  if (id >= nn || id >= cap) return;
+  int l = T.level[id];
+  unsigned long long pre = T.cell[id] & ((l * dim >= 64) ? ~0ULL : ((1ULL << (l * dim)) - 1ULL));
+  level[id] = l;
+  count[id] = T.end[id] - T.first[id];
+  mass[id] = T.mass[id];
+  if (dim == 3) {
+    cell[3 * id] = (int64_t)compact3(pre);
+    cell[3 * id + 1] = (int64_t)compact3(pre >> 1);
+    cell[3 * id + 2] = (int64_t)compact3(pre >> 2);
+  } else {
+    cell[3 * id] = (int64_t)compact2(pre);
+    cell[3 * id + 1] = (int64_t)compact2(pre >> 1);
+    cell[3 * id + 2] = 0;
+  }
+  for (int ax = 0; ax < 3; ++ax) com[3 * id + ax] = T.com[ax * T.cap_nodes + id];
+}
+
+void export_nodes(sph_ctx *c, int64_t cap, int32_t *level, int64_t *cell, int64_t *count, double *mass, double *com,
+                  cudaStream_t st) {
+  k_export_nodes<<<nblk(cap, 256), 256, 0, st>>>(c->tree, cap, c->tree.dim, level, cell, count, mass, com);
+}
+
+}  // namespace sph

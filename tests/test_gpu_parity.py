@@ -1,0 +1,303 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on
+the same seeded inputs.  Tree nodes and partner sets must be identical;
+FP64 right-hand sides agree to 1e-12 and mixed ones to 1e-5 of the oracle's
+per-particle magnitude sums (sum_b |term_b|)."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+from paper_1604_03290_gb300 import workloads as wl
+from parity_util import compare_rhs, field_scales
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "mixed": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1604_03290_gb300 import sph
+    return sph
+
+
+def _cloud_points(rng, n, dim, coincident=5):
+    x = rng.normal(size=(dim, n)) ** 3
+    x[:, :coincident] = x[:, [coincident]]
+    return x
+
+
+def _bare_set(x, m=None, h=None):
+    dim, n = x.shape
+    return wl.ParticleSet(dim=dim, x=x, v=np.zeros((dim, n)), rho=np.ones(n), u=np.zeros(n),
+                          m=np.ones(n) if m is None else m, h=np.full(n, 0.1) if h is None else h,
+                          mat=np.zeros(n, np.int32), id=np.arange(n, dtype=np.int32),
+                          materials=[wl.Material()], params=wl.Params(dim=dim))
+
+
+# ---------------------------------------------------------------------------
+# Tree and partners
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,L", [(3, 16), (3, 1), (2, 4), (3, 8), (2, 32)])
+def test_tree_nodes_identical(orc, S, dim, L):
+    rng = np.random.default_rng(21)
+    n = 4000
+    x = _cloud_points(rng, n, dim)
+    m = rng.uniform(0.5, 2.0, n)
+    ps = _bare_set(x, m)
+    ctx = S.Context(dim, n, leaf_size=L)
+    ds = S.DeviceState(ps)
+    S.build_tree(ctx, ds, L, 21)
+    g = {k: v.cpu().numpy() for k, v in S.tree_nodes(ctx, 8 * n).items()}
+    o = orc.tree_nodes(x, m, dim, L, 21)
+    np.testing.assert_array_equal(g["level"], o["level"])
+    np.testing.assert_array_equal(g["cell"], o["cell"])
+    np.testing.assert_array_equal(g["count"], o["count"])
+    np.testing.assert_allclose(g["mass"], o["mass"], rtol=1e-13)
+    np.testing.assert_allclose(g["com"][:, :dim], o["com"][:, :dim], rtol=0, atol=1e-12 * np.abs(x).max())
+
+
+def _csr_equal(goff, gidx, ooff, oidx):
+    np.testing.assert_array_equal(goff, ooff)
+    np.testing.assert_array_equal(gidx, oidx)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("kind", ["uniform_h", "variable_h", "lattice", "clustered"])
+def test_partner_sets_identical(orc, S, dim, kind):
+    rng = np.random.default_rng(22)
+    if kind == "lattice":
+        ps = wl.lattice_block(seed=3, nx=14, ny=14, nz=14 if dim == 3 else 1, dim=dim, jitter=0.0)
+        x, h = ps.x, ps.h
+    else:
+        n = 5000
+        x = rng.uniform(0, 10.0 if dim == 3 else 40.0, size=(dim, n))
+        h = np.full(n, 1.1) if kind != "variable_h" else rng.uniform(0.5, 1.7, n)
+        if kind == "clustered":
+            x = _cloud_points(rng, n, dim, coincident=40) * 3
+            h = np.full(n, 0.03)
+    n = x.shape[1]
+    ps = _bare_set(x, h=h)
+    ooff, oidx = orc.neighbours(x, h, dim, method="grid")
+    kmax = int(np.diff(ooff).max()) + 1  # exactly enough
+    ctx = S.Context(dim, n, max_neighbours=kmax)
+    ds = S.DeviceState(ps)
+    for L in (16, 3):
+        off, idx = S.neighbours(ctx, ds, leaf_size=L, max_depth=21)
+        _csr_equal(off.cpu().numpy(), idx.cpu().numpy(), ooff, oidx)
+    if kmax > 2:  # one partner too many for the capacity: reported, not truncated silently
+        with pytest.raises(S.SphError) as e:
+            S.neighbours(S.Context(dim, n, max_neighbours=kmax - 2), ds)
+        assert e.value.status == S.SPH_ERR_CAPACITY
+
+
+def test_partners_respect_instances(orc, S):
+    rng = np.random.default_rng(23)
+    a = rng.uniform(0, 5, size=(3, 1500))
+    b = rng.uniform(0, 5, size=(3, 2200))  # overlaps a in space
+    x = np.concatenate([a, b], 1)
+    h = rng.uniform(0.6, 1.0, x.shape[1])
+    ps = _bare_set(x, h=h)
+    ps.inst_off = np.array([0, 1500, 3700], np.int64)
+    ctx = S.Context(3, x.shape[1], max_instances=4, max_neighbours=256)
+    off, idx = S.neighbours(ctx, S.DeviceState(ps), 16, 19)
+    off, idx = off.cpu().numpy(), idx.cpu().numpy()
+    oa, ia = orc.neighbours(a, h[:1500], 3)
+    ob, ib = orc.neighbours(b, h[1500:], 3)
+    ref_off = np.concatenate([oa, ob[1:] + oa[-1]])
+    ref_idx = np.concatenate([ia, ib + 1500])
+    _csr_equal(off, idx, ref_off, ref_idx)
+
+
+# ---------------------------------------------------------------------------
+# Right-hand side
+# ---------------------------------------------------------------------------
+def _random_solid(seed=0, dim=3, n_side=10, damage=True):
+    ps = wl.lattice_block(seed=seed, nx=n_side, ny=n_side, nz=n_side if dim == 3 else 1, dim=dim, jitter=0.2)
+    rng = np.random.default_rng(seed + 50)
+    n = ps.n
+    ps.v = rng.normal(0, 0.05, (dim, n))
+    ps.rho = 1.0 + rng.normal(0, 0.03, n)
+    ps.u = rng.uniform(0, 0.1, n)
+    ps.S = rng.normal(0, 0.02, (ps.nsym, n))
+    ps.materials = [replace(ps.materials[0], Y0=0.05, damage=damage, K0=1.0, mu=0.5)]
+    if damage:
+        ps.dmg = rng.uniform(0, 0.6, n)
+        ps.flaw_off, ps.flaw_eps = wl.weibull_flaws(rng, n, float(n), 1e10, 6.0)
+    ps.params = replace(ps.params, eps_s=0.2, n_as=4.0, xsph=0.5)
+    return ps
+
+
+def _small_impact(seed=31):
+    ps = wl.measurement_1m(seed=seed, n_side=18)
+    return ps
+
+
+def _small_cloud():
+    ps = wl.cloud_collapse(seed=3, n=6000)
+    return ps
+
+
+def _small_batch():
+    ps = wl.batched_impacts(seed=5, ninst=3, nmin=400, nmax=1500)
+    rng = np.random.default_rng(9)
+    ps.u = rng.uniform(0, 1e7, ps.n)
+    ps.S = rng.normal(0, 1e8, (6, ps.n))
+    ps.params = replace(ps.params, max_depth=19)
+    return ps
+
+
+CASES = {
+    "solid3d": lambda: _random_solid(0, 3),
+    "solid2d": lambda: _random_solid(1, 2, n_side=30),
+    "rings": lambda: wl.rings_2d(artificial_stress=True),
+    "impact": _small_impact,
+    "cloud": _small_cloud,
+    "batch": _small_batch,
+}
+
+
+def _gpu_rhs(S, ps, prec, kmax=160):
+    ctx = S.Context(ps.dim, ps.n, max_instances=max(ps.ninst, 1), max_neighbours=kmax, leaf_size=ps.params.leaf_size)
+    ds = S.DeviceState(ps)
+    out = S.rhs(ctx, ds, ps.materials, replace(ps.params, precision=prec))
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    g["rho"] = ds.rho.cpu().numpy()
+    return g
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", list(CASES))
+def test_rhs_matches_oracle(orc, S, case, prec):
+    ps = CASES[case]()
+    o = orc.rhs(ps, ps.materials, ps.params)
+    g = _gpu_rhs(S, ps, prec)
+    np.testing.assert_array_equal(g["nnb"], o["nnb"])
+    fields = ("drho", "dv", "du", "dS", "dxdt", "p", "cs")
+    if ps.params.density_sum:
+        fields = fields + ("rho",)
+    errs = compare_rhs(ps, o, g, TOL[prec], fields=fields, prec=prec)
+    print(case, prec, errs)
+    if ps.dmg is not None:
+        same = g["n_act"] == o["n_act"]
+        if prec == "fp64":
+            assert same.all()
+        else:
+            assert same.mean() > 0.999
+        sc = field_scales(ps, o, prec, TOL[prec])["ddmg"]
+        assert np.abs(g["ddmg"] - o["ddmg"])[same].max() <= TOL[prec] * 10 * sc
+
+
+# ---------------------------------------------------------------------------
+# Gravity
+# ---------------------------------------------------------------------------
+def _grav_scale(x, m, h, G, eg):
+    d = x[:, :, None] - x[:, None, :]
+    r2 = (d ** 2).sum(0)
+    q = r2 + (eg * h[:, None]) ** 2
+    np.fill_diagonal(q, np.inf)
+    return G * (m[None, :] * np.sqrt(r2) / q ** 1.5).sum(1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("theta,L,dim", [(0.0, 8, 3), (0.5, 8, 3), (0.6, 16, 3), (0.5, 1, 3), (0.5, 4, 2)])
+def test_gravity_matches_oracle(orc, S, prec, theta, L, dim):
+    rng = np.random.default_rng(41)
+    n = 2500
+    x = rng.normal(size=(dim, n))
+    m = rng.uniform(0.5, 1.5, n)
+    h = rng.uniform(0.02, 0.1, n)
+    ps = _bare_set(x, m, h)
+    prm = wl.Params(dim=dim, G=1.3, theta=theta, eps_grav=0.5, leaf_size=L, precision=prec)
+    ctx = S.Context(dim, n, leaf_size=L)
+    g = S.gravity(ctx, S.DeviceState(ps), prm).cpu().numpy()
+    o = orc.gravity_bh(x, m, h, dim, 1.3, theta, 0.5, L)
+    sc = _grav_scale(x, m, h, 1.3, 0.5)
+    err = (np.abs(g - o) / sc).max()
+    assert err <= TOL[prec], err
+    if theta == 0.0:
+        d = orc.gravity_direct(x, m, h, dim, 1.3, 0.5)
+        assert (np.abs(g - d) / sc).max() <= TOL[prec]
+
+
+# ---------------------------------------------------------------------------
+# Predictor-corrector steps
+# ---------------------------------------------------------------------------
+def _by_id(d, ids):
+    order = np.argsort(ids)
+    return {k: (None if v is None else v[..., order]) for k, v in d.items()}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("case,nsteps,fixed", [("solid3d", 3, True), ("solid3d", 2, False), ("rings", 4, True),
+                                               ("impact", 2, False), ("batch", 2, False), ("cloud", 2, False)])
+def test_steps_match_oracle(orc, S, case, nsteps, fixed, prec):
+    ps = CASES[case]()
+    if fixed:
+        dt = ps.params.dt_fixed if ps.params.dt_fixed > 0 else 0.02
+        ps.params = replace(ps.params, dt_fixed=dt)
+    ost, olog = orc.step(ps, ps.materials, ps.params, nsteps)
+    ctx = S.Context(ps.dim, ps.n, max_instances=max(ps.ninst, 1), max_neighbours=160, leaf_size=ps.params.leaf_size)
+    ds = S.DeviceState(ps)
+    dt = S.step(ctx, ds, ps.materials, replace(ps.params, precision=prec), nsteps).cpu().numpy()
+    np.testing.assert_allclose(dt, olog[-1], rtol=1e-9 if prec == "fp64" else 1e-4)
+    g = ds.to_numpy()
+    g = _by_id(g, g["id"])
+    tol = 1e-9 if prec == "fp64" else 2e-5
+    for f in ("x", "v", "rho", "u", "S", "dmg"):
+        if ost.get(f) is None:
+            continue
+        init = getattr(ps, f)
+        change = np.abs(ost[f] - init).max()
+        scale = change + 1e-300
+        if f == "x":
+            scale = max(change, 1e-6 * np.abs(init).max())
+        err = np.abs(g[f] - ost[f]).max() / scale
+        assert err <= tol, (f, err)
+
+
+# ---------------------------------------------------------------------------
+# Error reporting (faults made on the host side; nothing traps or hangs)
+# ---------------------------------------------------------------------------
+def test_errors_are_reported_and_context_survives(orc, S):
+    ps = _random_solid(2, 3, n_side=8, damage=False)
+    small = S.Context(3, ps.n, max_neighbours=8)
+    ds = S.DeviceState(ps)
+    with pytest.raises(S.SphError) as e:
+        S.rhs(small, ds, ps.materials, ps.params)
+    assert e.value.status == S.SPH_ERR_CAPACITY
+    ctx = S.Context(3, ps.n, max_neighbours=160)
+    bad = ps.copy()
+    bad.x[0, 5] = np.nan
+    with pytest.raises(S.SphError) as e:
+        S.rhs(ctx, S.DeviceState(bad), ps.materials, ps.params)
+    assert e.value.status == S.SPH_ERR_NONFINITE
+    bad = ps.copy()
+    bad.h[3] = 0.0
+    with pytest.raises(S.SphError) as e:
+        S.rhs(ctx, S.DeviceState(bad), ps.materials, ps.params)
+    assert e.value.status == S.SPH_ERR_NONFINITE
+    with pytest.raises(S.SphError) as e:
+        S.rhs(ctx, ds, ps.materials, replace(ps.params, leaf_size=64))
+    assert e.value.status == S.SPH_ERR_INVALID
+    big = _random_solid(3, 3, n_side=9, damage=False)
+    with pytest.raises(S.SphError) as e:
+        S.rhs(ctx, S.DeviceState(big), big.materials, big.params)
+    assert e.value.status == S.SPH_ERR_INVALID
+    # the context still works after the errors
+    o = orc.rhs(ps, ps.materials, ps.params)
+    out = S.rhs(ctx, ds, ps.materials, ps.params)
+    compare_rhs(ps, o, {k: v.cpu().numpy() for k, v in out.items()}, TOL["fp64"], prec="fp64")
+
+
+def test_empty_and_single_particle(S):
+    one = _bare_set(np.zeros((3, 1)))
+    ctx = S.Context(3, 4)
+    out = S.rhs(ctx, S.DeviceState(one), one.materials, one.params)
+    assert out["nnb"].item() == 0 and float(out["dv"].abs().max()) == 0.0
+    empty = _bare_set(np.zeros((3, 0)))
+    S.rhs(ctx, S.DeviceState(empty), empty.materials, empty.params)
+    assert S.gravity(ctx, S.DeviceState(one), wl.Params(dim=3)).abs().max().item() == 0.0
