@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""Throughput of the SPH predictor-corrector step on GB300.
+
+One step = tree build, state reorder, partner search, both neighbour passes
+with the constitutive update, the device-side time step and the predictor
+update, then tree, partners and passes again at the predicted state and the
+corrector update (sph_step).  Workload: aluminium sphere into aluminium cube,
+Tillotson EOS, strength, von Mises yield and Grady-Kipp damage, 100^3 cube
+particles plus a 1 cm projectile (1,004,189 particles), with a perturbed state
+so every branch runs.  Metric: particle-updates per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own replica
+(the single-body workload does not shard), max time over ranks.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SPH step particle-updates/s (mixed precision, 1M-particle Al impact)"
+UNIT = "particle-updates/s"
+WORKLOAD = ("al_impact_1M: Al6061 cube 100^3 (dx = 1 mm) + 1 cm sphere (dx/2), Tillotson EOS, mu = 27 GPa, "
+            "Y0 = 0.3 GPa, Grady-Kipp damage (k = 5e34, m = 8.5), perturbed state (seed 11), "
+            "predictor-corrector sph_step, no gravity")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n-side", type=int, default=100)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--cpu-side", type=int, default=40, help="cube side of the CPU-baseline sample")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# nvidia-smi clock sampling during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ----------------------------------------------------------------------------
+# Byte model of the kernels (algorithmic bytes per particle, mixed mode)
+# ----------------------------------------------------------------------------
+def algorithmic_bytes(phase, K, n_flaw_mean, dim=3):
+    """HBM bytes one particle must move in one launch of `phase`, counting each
+    array once (partner data reused from cache): K = mean partners."""
+    ns = 6 if dim == 3 else 3
+    lg = math.log2(max(n_flaw_mean, 1.0)) + 1.0
+    if phase == "passA":
+        reads = 64 + 8 + 8 + 8 * ns + 8 + 4 + 4 + 16 + 4 * lg + 4 + 4 * K  # packs, rho, u, S, dmg, mat, id, flaws, list
+        writes = 8 + 8 * dim + 8 * ns + 8 + 4 + 32  # drho, dx, dS, ddmg, n_act, T pack
+        return reads + writes
+    if phase == "passB":
+        return 64 + 32 + 4 + 4 * K + 8 * dim + 8  # packs, T pack, list; dv, du
+    if phase == "partners":
+        return 32 + 4 + 4 + 4 * K + 4  # positions, perm, slot; list and count
+    raise KeyError(phase)
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle as a baseline (the oracle as it stands, all host cores)
+# ----------------------------------------------------------------------------
+def cpu_baseline(n_side, steps=1):
+    import oracle
+    from paper_1604_03290_gb300 import workloads as wl
+    oracle.build()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    oracle.set_threads(cores)
+    ps = wl.measurement_1m(seed=11, n_side=n_side)
+    t0 = time.perf_counter()
+    oracle.step(ps, ps.materials, ps.params, steps)
+    dt = time.perf_counter() - t0
+    return {"value": ps.n * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "same physics at %d^3 cube particles (%d particles), %d predictor-corrector step(s), "
+                      "%.1f s on %d host threads" % (n_side, ps.n, steps, dt, cores), "seconds": dt}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    base = cpu_baseline(args.cpu_side, steps=max(args.steps, 1))
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * base["seconds"] / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_cube_side": args.cpu_side},
+            "cpu_baseline": {k: base[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import numpy as np
+    import torch
+    from dataclasses import replace
+
+    from paper_1604_03290_gb300 import sph
+    from paper_1604_03290_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ps = wl.measurement_1m(seed=11, n_side=args.n_side)
+    n = ps.n
+    prm = replace(ps.params, precision="mixed")
+    ctx = sph.Context(3, n, max_neighbours=128, leaf_size=prm.leaf_size)
+    stream = torch.cuda.current_stream()
+
+    # mean partner count and flaw count for the byte model (outside timing)
+    ds = sph.DeviceState(ps)
+    out = sph.rhs(ctx, ds, ps.materials, prm)
+    K = float(out["nnb"].double().mean().item())
+    n_flaw = float(np.diff(ps.flaw_off).mean())
+    del out
+
+    # ---- device-resident throughput (mixed) ----
+    ds = sph.DeviceState(ps)
+    for _ in range(args.warmup):
+        sph.step(ctx, ds, ps.materials, prm, 1, check=False)
+    ctx.sync_status()
+    clocks = ClockSampler(local)
+    barrier()
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.3)
+    ctx.profile(True)
+    l0 = sph.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        sph.step(ctx, ds, ps.materials, prm, 1, check=False)
+    e1.record(stream)
+    e1.synchronize()
+    launches = sph.launch_count() - l0
+    phases = ctx.profile_read()
+    ctx.profile(False)
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop() if rank == 0 else None
+    barrier()
+    ctx.sync_status()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n * args.steps / (ms * 1e-3)
+
+    # ---- roofline of the dominant kernel ----
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm_peak, peak_src = 6800.0, "fallback 6.8 TB/s"
+    if os.path.exists(peaks_path):
+        with open(peaks_path) as f:
+            hbm_peak = float(json.load(f)["hbm_gbs"])
+        peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)"
+    timed = {p: v for p, v in phases.items() if v[1] > 0 and p in ("passA", "passB", "partners")}
+    dom = max(timed, key=lambda p: timed[p][0]) if timed else "passB"
+    per_launch_ms = timed[dom][0] / timed[dom][1] if timed else float("nan")
+    bytes_per_launch = algorithmic_bytes(dom, K, n_flaw) * n
+    achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+            "bytes_per_particle": algorithmic_bytes(dom, K, n_flaw), "mean_partners": K,
+            "avg_launch_ms": per_launch_ms}
+    total_ms = sum(v[0] for v in phases.values())
+    phase_report = {p: {"ms_per_step": v[0] / args.steps, "share": v[0] / total_ms if total_ms else None,
+                        "launch_ms": v[0] / v[1] if v[1] else None}
+                    for p, v in phases.items() if v[1] > 0}
+
+    # ---- FP64 step on the same workload ----
+    fp64 = None
+    if args.fp64_steps > 0:
+        prm64 = replace(prm, precision="fp64")
+        ds64 = sph.DeviceState(ps)
+        sph.step(ctx, ds64, ps.materials, prm64, 1, check=False)
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        sph.step(ctx, ds64, ps.materials, prm64, args.fp64_steps, check=False)
+        f1.record(stream)
+        f1.synchronize()
+        ctx.sync_status()
+        ms64 = f0.elapsed_time(f1) / args.fp64_steps
+        fp64 = {"value": n / (ms64 * 1e-3), "ms_per_step": ms64, "unit": UNIT}
+        del ds64
+
+    # ---- end to end through the C ABI with host buffers ----
+    host = {k: (None if v is None else v.detach().cpu().pin_memory()) for k, v in
+            {"x": ds.x, "v": ds.v, "rho": ds.rho, "u": ds.u, "m": ds.m, "h": ds.h, "S": ds.S, "dmg": ds.dmg,
+             "mat": ds.mat, "id": ds.id}.items()}
+    h2d = sum(t.numel() * t.element_size() for t in host.values() if t is not None)
+    d2h = sum(host[k].numel() * host[k].element_size() for k in ("x", "v", "rho", "u", "S", "dmg", "id"))
+    e2e_steps = max(3, args.steps // 3)
+    barrier()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(e2e_steps):
+        for k, t in host.items():
+            getattr(ds, k).copy_(t, non_blocking=True)
+        sph.step(ctx, ds, ps.materials, prm, 1, check=False)
+        for k in ("x", "v", "rho", "u", "S", "dmg", "id"):
+            host[k].copy_(getattr(ds, k), non_blocking=True)
+    g1.record(stream)
+    g1.synchronize()
+    ms_e2e = g0.elapsed_time(g1)
+    if dist is not None:
+        t = torch.tensor([ms_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e = {"value": world * n * e2e_steps / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        b = cpu_baseline(args.cpu_side, steps=1)
+        cpu = {k: b[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32 pair/f64 state (mixed)", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n_particles": n, "mean_partners": K,
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "l2": "inputs larger than L2 (state %.0f MB, partner lists %.0f MB)" %
+                                 (144 * n / 1e6, 4 * K * n / 1e6)},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, "fp64": fp64,
+                "speedup_mixed_over_fp64": (value / world / fp64["value"]) if fp64 else None,
+                "phases": phase_report}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -197,6 +197,19 @@ sph_status sph_gravity(sph_ctx *ctx, const sph_state *state, const sph_params *p
 sph_status sph_step(sph_ctx *ctx, sph_state *state, const sph_material *mats, int32_t nmat, const sph_params *params,
                     double *dt, int32_t nsteps, void *stream);
 
+/* Optional per-phase timing.  When enabled, every phase of sph_rhs and
+ * sph_step is bracketed by CUDA events recorded on the call's stream (at most
+ * 8192 phases between reads; later ones go untimed).  Phases, in order:
+ * 0 tree build, 1 state reorder, 2 partner search, 3 density sum,
+ * 4 neighbour pass A with the constitutive update, 5 momentum/energy pass B,
+ * 6 gravity, 7 integrator (time step and updates). */
+sph_status sph_profile_enable(sph_ctx *ctx, int32_t on);
+/* Milliseconds and call counts per phase since the last read (nphase
+ * entries of each); synchronises on the recorded events, then resets. */
+sph_status sph_profile_read(sph_ctx *ctx, double *ms, int32_t *calls, int32_t nphase);
+/* Number of kernels this library has launched in this process. */
+int64_t sph_launch_count(void);
+
 /* Peak FMA throughput of this device, measured by a register-resident loop
  * (precision SPH_FP64 or SPH_MIXED = FP32); returns FLOP/s (2 per FMA) in
  * *flops.  Blocks. */

@@ -14,6 +14,22 @@ void export_nodes(sph_ctx *c, int64_t cap, int32_t *level, int64_t *cell, int64_
 
 using namespace sph;
 
+namespace sph {
+std::atomic<int64_t> g_launches{0};
+
+int prof_begin(sph_ctx *c, cudaStream_t st, int phase) {
+  if (!c->prof || c->prof_used >= kMaxProfEvents) return -1;
+  int i = c->prof_used++;
+  c->prof_phase[i] = phase;
+  cudaEventRecord(c->prof_ev[2 * i], st);
+  return i;
+}
+
+void prof_end(sph_ctx *c, cudaStream_t st, int idx) {
+  if (idx >= 0) cudaEventRecord(c->prof_ev[2 * idx + 1], st);
+}
+}  // namespace sph
+
 static sph_status fail(sph_ctx *c, sph_status s, const char *msg) {
   if (c) snprintf(c->err, sizeof(c->err), "%s", msg);
   return s;
@@ -73,8 +89,8 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   T.hist = ctx_alloc<uint32_t>(c, T.hist_cap, ok);
   T.ncount = ctx_alloc<int32_t>(c, N + 1, ok);
   T.nstart = ctx_alloc<int32_t>(c, N + 1, ok);
-  T.scan_tmp = ctx_alloc<int32_t>(c, (N + 1) / 4096 + 2, ok);
   T.cap_nodes = std::max<int64_t>(4096, leaf_size <= 2 ? 4 * N : 2 * N);
+  T.scan_tmp = ctx_alloc<int32_t>(c, (std::max(N, T.cap_nodes) + 1) / 4096 + 2, ok);
   const int64_t cn = T.cap_nodes;
   T.nnodes = ctx_alloc<int32_t>(c, 1, ok);
   T.first = ctx_alloc<int32_t>(c, cn, ok);
@@ -99,8 +115,9 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   T.inst_lo = ctx_alloc<double>(c, 3 * ci, ok);
   T.inst_s0 = ctx_alloc<double>(c, ci, ok);
   T.inst_root = ctx_alloc<int32_t>(c, ci, ok);
-  T.inst_goff = ctx_alloc<int32_t>(c, ci + 1, ok);
-  T.cap_groups = N / kWarp + ci + 1;
+  T.gcnt = ctx_alloc<int32_t>(c, cn + 1, ok);
+  T.gstart = ctx_alloc<int32_t>(c, cn + 1, ok);
+  T.cap_groups = N + ci + 1;
   T.grp_start = ctx_alloc<int32_t>(c, T.cap_groups, ok);
   T.grp_end = ctx_alloc<int32_t>(c, T.cap_groups, ok);
   T.grp_inst = ctx_alloc<int32_t>(c, T.cap_groups, ok);
@@ -156,6 +173,11 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
 
 void sph_destroy(sph_ctx *c) {
   if (!c) return;
+  if (c->prof_ev) {
+    for (int i = 0; i < 2 * kMaxProfEvents; ++i) cudaEventDestroy(c->prof_ev[i]);
+    delete[] c->prof_ev;
+    delete[] c->prof_phase;
+  }
   for (int i = 0; i < c->nallocs; ++i) cudaFree(c->allocs[i]);
   if (c->h_err) cudaFreeHost(c->h_err);
   delete c;
@@ -262,12 +284,29 @@ static sph_status finish(sph_ctx *c, const sph_params *p, cudaStream_t st, const
 }
 
 // One full right-hand side on state s into out (tree + partners + passes).
+static void timed_tree(sph_ctx *c, const sph_state *s, const sph_params &p, cudaStream_t st) {
+  int pr = prof_begin(c, st, PH_TREE);
+  tree_build(c, s, p.leaf_size, p.max_depth, st);
+  prof_end(c, st, pr);
+}
+
+static void partners_gravity_passes(sph_ctx *c, sph_state *s, const MatTable &mt, const sph_params &p,
+                                    const sph_derivs &out, cudaStream_t st) {
+  int pr = prof_begin(c, st, PH_PARTNERS);
+  find_partners(c, s, st);
+  prof_end(c, st, pr);
+  if (p.gravity) {
+    pr = prof_begin(c, st, PH_GRAVITY);
+    gravity_walk(c, s, p, c->ag, c->ag + c->cap_n, c->ag + 2 * c->cap_n, st);
+    prof_end(c, st, pr);
+  }
+  rhs_passes(c, s, mt, p, out, st);
+}
+
 static void rhs_all(sph_ctx *c, sph_state *s, const MatTable &mt, const sph_params &p, const sph_derivs &out,
                     cudaStream_t st) {
-  tree_build(c, s, p.leaf_size, p.max_depth, st);
-  find_partners(c, s, st);
-  if (p.gravity) gravity_walk(c, s, p, c->ag, c->ag + c->cap_n, c->ag + 2 * c->cap_n, st);
-  rhs_passes(c, s, mt, p, out, st);
+  timed_tree(c, s, p, st);
+  partners_gravity_passes(c, s, mt, p, out, st);
 }
 
 extern "C" {
@@ -384,19 +423,58 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
   }
   for (int it = 0; it < nsteps; ++it) {
     // order the state along the tree once per step (coalesced partner gathers)
-    tree_build(c, s, p->leaf_size, p->max_depth, st);
+    timed_tree(c, s, *p, st);
+    int pr = prof_begin(c, st, PH_REORDER);
     tree_reorder_state(c, s, st);
-    find_partners(c, s, st);
-    if (p->gravity) gravity_walk(c, s, *p, c->ag, c->ag + c->cap_n, c->ag + 2 * c->cap_n, st);
-    rhs_passes(c, s, mt, *p, d[0], st);
+    prof_end(c, st, pr);
+    partners_gravity_passes(c, s, mt, *p, d[0], st);
+    pr = prof_begin(c, st, PH_INTEGRATE);
     timestep_reduce(c, s, *p, d[0], st);
     pc_update(c, s, &q, d[0], 0.5, mt, *p, st);
+    prof_end(c, st, pr);
     rhs_all(c, &q, mt, *p, d[1], st);
+    pr = prof_begin(c, st, PH_INTEGRATE);
     pc_update(c, s, s, d[1], 1.0, mt, *p, st);
+    prof_end(c, st, pr);
   }
   if (dt && nsteps > 0) cudaMemcpyAsync(dt, B.dt, sizeof(double) * ninst, cudaMemcpyDeviceToDevice, st);
   return finish(c, p, st, "sph_step");
 }
+
+sph_status sph_profile_enable(sph_ctx *c, int32_t on) {
+  if (!c) return SPH_ERR_INVALID;
+  if (on && !c->prof_ev) {
+    c->prof_ev = new cudaEvent_t[2 * kMaxProfEvents];
+    c->prof_phase = new int32_t[kMaxProfEvents];
+    for (int i = 0; i < 2 * kMaxProfEvents; ++i)
+      if (cudaEventCreate(&c->prof_ev[i]) != cudaSuccess) return cuda_check(c, "sph_profile_enable");
+  }
+  c->prof = on ? 1 : 0;
+  c->prof_used = 0;
+  return SPH_OK;
+}
+
+sph_status sph_profile_read(sph_ctx *c, double *ms, int32_t *calls, int32_t nphase) {
+  if (!c || !ms || !calls || nphase < 1) return SPH_ERR_INVALID;
+  for (int k = 0; k < nphase; ++k) {
+    ms[k] = 0.0;
+    calls[k] = 0;
+  }
+  for (int i = 0; i < c->prof_used; ++i) {
+    if (cudaEventSynchronize(c->prof_ev[2 * i + 1]) != cudaSuccess) return cuda_check(c, "sph_profile_read");
+    float t = 0.f;
+    cudaEventElapsedTime(&t, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]);
+    int ph = c->prof_phase[i];
+    if (ph < nphase) {
+      ms[ph] += t;
+      calls[ph] += 1;
+    }
+  }
+  c->prof_used = 0;
+  return cuda_check(c, "sph_profile_read");
+}
+
+int64_t sph_launch_count(void) { return sph::g_launches.load(); }
 
 }  // extern "C"
 

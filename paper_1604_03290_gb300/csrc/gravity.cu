@@ -194,8 +194,8 @@ void gravity_walk(sph_ctx *c, const sph_state *s, const sph_params &p, double *a
   A.U = c->units;
   A.err = c->d_err;
   int blocks = 152 * 8;
-  if (p.precision == SPH_MIXED) k_gravity<true><<<blocks, kGrWarps * 32, 0, st>>>(A);
-  else k_gravity<false><<<blocks, kGrWarps * 32, 0, st>>>(A);
+  if (p.precision == SPH_MIXED) { k_gravity<true><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
+  else { k_gravity<false><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
 }
 
 }  // namespace sph

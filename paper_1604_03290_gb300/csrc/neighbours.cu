@@ -63,14 +63,19 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_partners(Tree T, PackedF32 pk
     const float lx = __shfl_sync(0xffffffffu, Q.x, 0), ly = __shfl_sync(0xffffffffu, Q.y, 0),
                 lz = __shfl_sync(0xffffffffu, Q.z, 0);
     const float rax = (P.x - cx) + (Q.x - lx), ray = (P.y - cy) + (Q.y - ly), raz = (P.z - cz) + (Q.z - lz);
-    // group box (hi coordinates) and largest h
+    // group box (hi coordinates, for the node test) and largest h
     float gl[3] = {act ? P.x : 3e38f, act ? P.y : 3e38f, act ? P.z : 3e38f};
     float gh[3] = {act ? P.x : -3e38f, act ? P.y : -3e38f, act ? P.z : -3e38f};
     float hg = act ? P.w : 0.f;
+    // the same box relative to the reference point, for culling candidates
+    float rl[3] = {act ? rax : 3e38f, act ? ray : 3e38f, act ? raz : 3e38f};
+    float rh[3] = {act ? rax : -3e38f, act ? ray : -3e38f, act ? raz : -3e38f};
     for (int o = 16; o > 0; o >>= 1) {
       for (int ax = 0; ax < 3; ++ax) {
         gl[ax] = fminf(gl[ax], __shfl_xor_sync(0xffffffffu, gl[ax], o));
         gh[ax] = fmaxf(gh[ax], __shfl_xor_sync(0xffffffffu, gh[ax], o));
+        rl[ax] = fminf(rl[ax], __shfl_xor_sync(0xffffffffu, rl[ax], o));
+        rh[ax] = fmaxf(rh[ax], __shfl_xor_sync(0xffffffffu, rh[ax], o));
       }
       hg = fmaxf(hg, __shfl_xor_sync(0xffffffffu, hg, o));
     }
@@ -80,28 +85,45 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_partners(Tree T, PackedF32 pk
       gl[ax] -= slack;
       gh[ax] += slack;
     }
+    // relative coordinates carry an error of a few 1e-7 of the group's extent + h
+    const float rslack = 1e-5f * (fmaxf(fmaxf(rh[0] - rl[0], rh[1] - rl[1]), rh[2] - rl[2]) + hg);
+    const unsigned lt_mask = (1u << lane) - 1u;
     const int32_t root = T.inst_root[inst];
     const int32_t stop = root >= 0 ? T.skip[root] : root;
     int cnt = 0;
     int iter = 0;
     for (int32_t nd = root; nd < stop && iter <= nnodes; ++iter) {
-      const float4 bl = T.fbox_lo[nd], bh = T.fbox_hi[nd];
+      const float4 bl = __ldg(&T.fbox_lo[nd]), bh = __ldg(&T.fbox_hi[nd]);
       float gx = fmaxf(0.f, fmaxf(bl.x - gh[0], gl[0] - bh.x));
       float gy = fmaxf(0.f, fmaxf(bl.y - gh[1], gl[1] - bh.y));
       float gz = fmaxf(0.f, fmaxf(bl.z - gh[2], gl[2] - bh.z));
       float d2 = gx * gx + gy * gy + gz * gz;
       float thr = 0.5f * (hg + bl.w) * (1.0f + 1e-5f);
       if (d2 <= thr * thr) {
-        const int32_t f = T.first[nd], e = T.end[nd];
-        if (e - f <= L || T.level[nd] == B) {
+        const int32_t f = __ldg(&T.first[nd]), e = __ldg(&T.end[nd]);
+        if (e - f <= L || __ldg(&T.level[nd]) == B) {
           for (int32_t base = f; base < e; base += kMaxLeaf) {  // leaves at full depth may exceed 32
-            const int c = min(e - base, kMaxLeaf);
-            if (lane < c) {
-              int32_t b = T.perm[base + lane];
-              float4 Pb = pk.px[b], Qb = pk.pxl[b];
-              sc[w][lane] = make_float4((Pb.x - cx) + (Qb.x - lx), (Pb.y - cy) + (Qb.y - ly),
-                                        (Pb.z - cz) + (Qb.z - lz), Pb.w);
-              sb[w][lane] = b;
+            // stage the candidates that come within reach of the group's box
+            bool keep = false;
+            float4 cand = make_float4(0.f, 0.f, 0.f, 0.f);
+            int32_t b = -1;
+            if (base + lane < e) {
+              b = __ldg(&T.perm[base + lane]);
+              float4 Pb = __ldg(&pk.px[b]), Qb = __ldg(&pk.pxl[b]);
+              cand = make_float4((Pb.x - cx) + (Qb.x - lx), (Pb.y - cy) + (Qb.y - ly), (Pb.z - cz) + (Qb.z - lz),
+                                 Pb.w);
+              float qx = fmaxf(0.f, fmaxf(rl[0] - cand.x, cand.x - rh[0]));
+              float qy = fmaxf(0.f, fmaxf(rl[1] - cand.y, cand.y - rh[1]));
+              float qz = fmaxf(0.f, fmaxf(rl[2] - cand.z, cand.z - rh[2]));
+              float reach = 0.5f * (hg + cand.w) * (1.0f + 1e-5f) + rslack;
+              keep = qx * qx + qy * qy + qz * qz <= reach * reach;
+            }
+            const unsigned km = __ballot_sync(0xffffffffu, keep);
+            const int c = __popc(km);
+            if (keep) {
+              const int pos = __popc(km & lt_mask);
+              sc[w][pos] = cand;
+              sb[w][pos] = b;
             }
             __syncwarp();
             if (act) {
@@ -124,12 +146,12 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_partners(Tree T, PackedF32 pk
             }
             __syncwarp();
           }
-          nd = T.skip[nd];
+          nd = __ldg(&T.skip[nd]);
         } else {
           nd = nd + 1;
         }
       } else {
-        nd = T.skip[nd];
+        nd = __ldg(&T.skip[nd]);
       }
     }
     if (iter > nnodes) raise_err(err, ERR_TIMEOUT);
@@ -143,8 +165,8 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_partners(Tree T, PackedF32 pk
 void find_partners(sph_ctx *c, const sph_state *s, cudaStream_t st) {
   if (s->n == 0) return;
   int blocks = 152 * 12;
-  k_partners<<<blocks, kNbWarps * 32, 0, st>>>(c->tree, c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim, c->kmax,
-                                              c->nb_idx, c->nb_cnt, c->cap_n, c->d_err);
+  { k_partners<<<blocks, kNbWarps * 32, 0, st>>>(c->tree, c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim, c->kmax,
+                                              c->nb_idx, c->nb_cnt, c->cap_n, c->d_err); ++sph::g_launches; }
 }
 
 // ---------------------------------------------------------------------------
@@ -184,10 +206,10 @@ void scan_counts(sph_ctx *c, const int32_t *in, int32_t *out, int64_t m, cudaStr
 
 void partners_to_csr(sph_ctx *c, const sph_state *s, int64_t *off, int32_t *idx, int64_t cap, cudaStream_t st) {
   int64_t n = s->n;
-  k_cnt_copy<<<nblk(n + 1, 256), 256, 0, st>>>(c->nb_cnt, c->tree.ncount, n);
+  { k_cnt_copy<<<nblk(n + 1, 256), 256, 0, st>>>(c->nb_cnt, c->tree.ncount, n); ++sph::g_launches; }
   scan_counts(c, c->tree.ncount, c->tree.nstart, n + 1, st);
-  k_csr_fill<<<nblk(n + 1, 128), 128, 0, st>>>(c->nb_idx, c->nb_cnt, c->cap_n, c->tree.nstart, n, off, idx, cap,
-                                               c->d_err);
+  { k_csr_fill<<<nblk(n + 1, 128), 128, 0, st>>>(c->nb_idx, c->nb_cnt, c->cap_n, c->tree.nstart, n, off, idx, cap,
+                                               c->d_err); ++sph::g_launches; }
 }
 
 }  // namespace sph

@@ -740,21 +740,28 @@ void rhs_passes(sph_ctx *c, sph_state *s, const MatTable &mt, const sph_params &
   A.err = c->d_err;
   const bool mixed = p.precision == SPH_MIXED;
   const int T = 128;
+  int pr = -1;
   if (p.density_sum) {
-    if (mixed) k_density_sum<true><<<nblk(n, T), T, 0, st>>>(A);
-    else k_density_sum<false><<<nblk(n, T), T, 0, st>>>(A);
-    k_repack_rho<<<nblk(n, 256), 256, 0, st>>>(s->rho, s->m, c->pk, n, c->units);
+    pr = prof_begin(c, st, PH_DENSITY);
+    if (mixed) { k_density_sum<true><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    else { k_density_sum<false><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    { k_repack_rho<<<nblk(n, 256), 256, 0, st>>>(s->rho, s->m, c->pk, n, c->units); ++sph::g_launches; }
+    prof_end(c, st, pr);
   }
-  if (mixed) k_passA<true><<<nblk(n, T), T, 0, st>>>(A);
-  else k_passA<false><<<nblk(n, T), T, 0, st>>>(A);
+  pr = prof_begin(c, st, PH_PASSA);
+  if (mixed) { k_passA<true><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+  else { k_passA<false><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+  prof_end(c, st, pr);
   const bool as = p.eps_s > 0.0;
+  pr = prof_begin(c, st, PH_PASSB);
   if (mixed) {
-    if (as) k_passB<true, true><<<nblk(n, T), T, 0, st>>>(A);
-    else k_passB<true, false><<<nblk(n, T), T, 0, st>>>(A);
+    if (as) { k_passB<true, true><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    else { k_passB<true, false><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
   } else {
-    if (as) k_passB<false, true><<<nblk(n, T), T, 0, st>>>(A);
-    else k_passB<false, false><<<nblk(n, T), T, 0, st>>>(A);
+    if (as) { k_passB<false, true><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    else { k_passB<false, false><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
   }
+  prof_end(c, st, pr);
 }
 
 }  // namespace sph

@@ -7,9 +7,18 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <atomic>
+
 #include "sph.h"
 
 namespace sph {
+
+// Kernels launched by this library in this process (every launch site adds 1).
+extern std::atomic<int64_t> g_launches;
+
+// Phases timed by the optional profiler (CUDA events on the launch stream).
+enum { PH_TREE = 0, PH_REORDER, PH_PARTNERS, PH_DENSITY, PH_PASSA, PH_PASSB, PH_GRAVITY, PH_INTEGRATE, PH_COUNT };
+constexpr int kMaxProfEvents = 8192;
 
 // ---------------------------------------------------------------------------
 // Device error word bits (OR-ed by kernels, read by sph_sync_status).
@@ -64,8 +73,8 @@ struct Tree {
   double *inst_lo;     // 3 per instance
   double *inst_s0;
   int32_t *inst_root;
-  int32_t *inst_goff;  // groups before each instance (ninst + 1)
-  // walk groups: up to 32 consecutive slots of one instance
+  // walk groups: up to 32 consecutive slots inside one tree cell
+  int32_t *gcnt, *gstart;  // per node: groups it starts, and their exclusive scan (cap_nodes + 1)
   int32_t *grp_start, *grp_end, *grp_inst;
   int32_t *ngroups;    // device scalar
   int64_t cap_groups;
@@ -134,6 +143,11 @@ struct sph_ctx {
   sph::Units *units;    // device
   double vscale;        // host: velocity scale for the time unit
   sph::MatTable mt;     // host copy of the materials of the current call
+  // profiler
+  int prof;
+  int prof_used;
+  cudaEvent_t *prof_ev;       // 2 * kMaxProfEvents
+  int32_t *prof_phase;        // kMaxProfEvents
   sph::StepBufs st;
   // allocation list
   void *allocs[128];
@@ -240,6 +254,9 @@ enum { MF_RHO0, MF_CS, MF_K0, MF_NM, MF_AT, MF_BT, MF_E0, MF_EIV, MF_ECV, MF_AA,
        MF_RHOCUT, MF_MU, MF_Y0 };
 
 double velocity_scale(const MatTable &mt);
+// api.cu: profiler hooks (no-ops unless enabled)
+int prof_begin(sph_ctx *c, cudaStream_t st, int phase);
+void prof_end(sph_ctx *c, cudaStream_t st, int idx);
 // tree.cu
 void tree_build(sph_ctx *c, const sph_state *s, int leaf_size, int max_depth, cudaStream_t st);
 void tree_reorder_state(sph_ctx *c, sph_state *s, cudaStream_t st);

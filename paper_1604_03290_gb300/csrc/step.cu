@@ -75,7 +75,7 @@ __global__ void k_dt_final(const unsigned long long *enc, double *dt, int ninst,
 
 void timestep_reduce(sph_ctx *c, const sph_state *s, const sph_params &p, const sph_derivs &d, cudaStream_t st) {
   const int ninst = s->ninst > 0 ? s->ninst : 1;
-  k_dt_init<<<nblk(ninst, 128), 128, 0, st>>>(c->st.dt_enc, ninst, p.dt_max);
+  { k_dt_init<<<nblk(ninst, 128), 128, 0, st>>>(c->st.dt_enc, ninst, p.dt_max); ++sph::g_launches; }
   if (p.dt_fixed <= 0.0 && s->n > 0) {
     DtArgs A;
     memset(&A, 0, sizeof(A));
@@ -96,9 +96,9 @@ void timestep_reduce(sph_ctx *c, const sph_state *s, const sph_params &p, const 
     A.ninst = ninst;
     A.prm = p;
     A.enc = c->st.dt_enc;
-    k_dt<<<nblk(s->n, 256), 256, 0, st>>>(A);
+    { k_dt<<<nblk(s->n, 256), 256, 0, st>>>(A); ++sph::g_launches; }
   }
-  k_dt_final<<<nblk(ninst, 128), 128, 0, st>>>(c->st.dt_enc, c->st.dt, ninst, p.dt_fixed, nullptr);
+  { k_dt_final<<<nblk(ninst, 128), 128, 0, st>>>(c->st.dt_enc, c->st.dt, ninst, p.dt_fixed, nullptr); ++sph::g_launches; }
 }
 
 // ---------------------------------------------------------------------------
@@ -195,7 +195,7 @@ void pc_update(sph_ctx *c, const sph_state *base, sph_state *out, const sph_deri
   A.frac = frac;
   A.mt = mt;
   A.density_sum = p.density_sum;
-  k_pc<<<nblk(base->n, 256), 256, 0, st>>>(A);
+  { k_pc<<<nblk(base->n, 256), 256, 0, st>>>(A); ++sph::g_launches; }
 }
 
 }  // namespace sph

@@ -374,10 +374,10 @@ static void radix_sort(sph_ctx *c, int64_t n, int bits, cudaStream_t st) {
   int src = 0;
   for (int p = 0; p < passes; ++p) {
     int shift = 8 * p;
-    k_radix_hist<<<nblocks, kSortThreads, 0, st>>>(T.keys[src], n, shift, T.hist, nblocks);
-    k_scan_u32_1blk<<<1, 1024, 0, st>>>(T.hist, (int64_t)256 * nblocks);
-    k_radix_scatter<<<nblocks, kSortThreads, 0, st>>>(T.keys[src], T.vals[src], T.keys[src ^ 1], T.vals[src ^ 1], n,
-                                                     shift, T.hist, nblocks);
+    { k_radix_hist<<<nblocks, kSortThreads, 0, st>>>(T.keys[src], n, shift, T.hist, nblocks); ++sph::g_launches; }
+    { k_scan_u32_1blk<<<1, 1024, 0, st>>>(T.hist, (int64_t)256 * nblocks); ++sph::g_launches; }
+    { k_radix_scatter<<<nblocks, kSortThreads, 0, st>>>(T.keys[src], T.vals[src], T.keys[src ^ 1], T.vals[src ^ 1], n,
+                                                     shift, T.hist, nblocks); ++sph::g_launches; }
     src ^= 1;
   }
   T.skey = T.keys[src];
@@ -455,9 +455,9 @@ __global__ void k_scan_add(int32_t *out, int64_t m, const int32_t *tile_sums) {
 
 static void scan_excl_i32(const int32_t *in, int32_t *out, int64_t m, int32_t *tmp, cudaStream_t st) {
   int tiles = nblk(m, kScanTile);
-  k_scan_tiles<<<tiles, kScanThreads, 0, st>>>(in, out, m, tmp);
-  k_scan_tops<<<1, 1024, 0, st>>>(tmp, tiles);
-  k_scan_add<<<nblk(m, 256), 256, 0, st>>>(out, m, tmp);
+  { k_scan_tiles<<<tiles, kScanThreads, 0, st>>>(in, out, m, tmp); ++sph::g_launches; }
+  { k_scan_tops<<<1, 1024, 0, st>>>(tmp, tiles); ++sph::g_launches; }
+  { k_scan_add<<<nblk(m, 256), 256, 0, st>>>(out, m, tmp); ++sph::g_launches; }
 }
 
 void scan_counts(sph_ctx *c, const int32_t *in, int32_t *out, int64_t m, cudaStream_t st) {
@@ -587,48 +587,102 @@ __global__ void k_node_emit(KeyLevels K, int64_t n, int L, const int64_t *__rest
   }
 }
 
-__global__ void k_inst_info(const int64_t *__restrict__ inst_off, int ninst, int64_t n, const int32_t *nstart,
-                            Tree T) {
-  // single block: groups per instance (32 slots each), their exclusive scan, roots
-  __shared__ int32_t carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (int base = 0; base < ninst; base += blockDim.x) {
-    int i = base + threadIdx.x;
-    int64_t lo = 0, hi = n;
-    if (i < ninst && ninst > 1 && inst_off) {
-      lo = inst_off[i];
-      hi = inst_off[i + 1];
-    }
-    int32_t g = (i < ninst) ? (int32_t)((hi - lo + kWarp - 1) / kWarp) : 0;
-    int32_t tot;
-    int32_t off = block_excl_scan(g, &tot);
-    if (i < ninst) {
-      T.inst_goff[i] = carry + off;
-      T.inst_root[i] = (hi > lo) ? nstart[lo] : -1;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) carry += tot;
-    __syncthreads();
+__global__ void k_inst_roots(const int64_t *__restrict__ inst_off, int ninst, int64_t n, const int32_t *nstart,
+                             Tree T) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ninst) return;
+  int64_t lo = 0, hi = n;
+  if (ninst > 1 && inst_off) {
+    lo = inst_off[i];
+    hi = inst_off[i + 1];
   }
-  if (threadIdx.x == 0) {
-    T.inst_goff[ninst] = carry;
-    *T.ngroups = carry;
-  }
+  T.inst_root[i] = (hi > lo) ? nstart[lo] : -1;
 }
 
-__global__ void k_groups(const int64_t *__restrict__ inst_off, int ninst, int64_t n, Tree T) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int k = inst_of(inst_off, ninst, i);
-  int64_t lo = (ninst > 1 && inst_off) ? inst_off[k] : 0;
-  int64_t hi = (ninst > 1 && inst_off) ? inst_off[k + 1] : n;
-  int64_t r = i - lo;
-  if (r % kWarp) return;
-  int32_t g = T.inst_goff[k] + (int32_t)(r / kWarp);
-  T.grp_start[g] = (int32_t)i;
-  T.grp_end[g] = (int32_t)min(i + kWarp, hi);
-  T.grp_inst[g] = k;
+// Walk groups: runs of consecutive sibling cells that each hold at most 32
+// particles, packed greedily up to 32 particles by their parent (a node with
+// more than 32); a root with at most 32 particles is one group, and a leaf at
+// full depth with more than 32 is cut into runs of 32.  Siblings are adjacent
+// in Morton order, so a group is a compact block of space, and together the
+// groups partition the particles in slot order.
+__device__ __forceinline__ int node_count(const Tree &T, int32_t id) { return T.end[id] - T.first[id]; }
+
+template <bool EMIT>
+__device__ int group_runs(const Tree &T, int32_t id, int32_t g0, int inst) {
+  const int c = node_count(T, id);
+  const bool leaf = c <= T.leaf_size || T.level[id] == T.max_depth;
+  int g = 0;
+  if (c <= kWarp) {
+    if (T.parent[id] >= 0) return 0;  // packed by its parent
+    if (EMIT && g0 < T.cap_groups) {
+      T.grp_start[g0] = T.first[id];
+      T.grp_end[g0] = T.end[id];
+      T.grp_inst[g0] = inst;
+    }
+    return 1;
+  }
+  if (leaf) {
+    const int32_t f = T.first[id], e = T.end[id];
+    for (int32_t s = f; s < e; s += kWarp, ++g)
+      if (EMIT && g0 + g < T.cap_groups) {
+        T.grp_start[g0 + g] = s;
+        T.grp_end[g0 + g] = min(s + kWarp, e);
+        T.grp_inst[g0 + g] = inst;
+      }
+    return g;
+  }
+  int32_t run_s = -1, run_e = -1;
+  int run = 0;
+  const int32_t stop = T.skip[id];
+  int guard = 0;
+  for (int32_t ch = id + 1; ch < stop && guard < 64; ch = T.skip[ch], ++guard) {
+    const int cc = node_count(T, ch);
+    if (cc <= kWarp && run + cc <= kWarp) {
+      if (run == 0) run_s = T.first[ch];
+      run += cc;
+      run_e = T.end[ch];
+      continue;
+    }
+    if (run > 0) {  // close the current run
+      if (EMIT && g0 + g < T.cap_groups) {
+        T.grp_start[g0 + g] = run_s;
+        T.grp_end[g0 + g] = run_e;
+        T.grp_inst[g0 + g] = inst;
+      }
+      ++g;
+      run = 0;
+    }
+    if (cc <= kWarp) {  // starts a new run
+      run_s = T.first[ch];
+      run_e = T.end[ch];
+      run = cc;
+    }
+  }
+  if (run > 0) {
+    if (EMIT && g0 + g < T.cap_groups) {
+      T.grp_start[g0 + g] = run_s;
+      T.grp_end[g0 + g] = run_e;
+      T.grp_inst[g0 + g] = inst;
+    }
+    ++g;
+  }
+  return g;
+}
+
+__global__ void k_group_count(Tree T, int32_t *gcnt) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id > T.cap_nodes) return;
+  const int nn = *T.nnodes;
+  gcnt[id] = id < nn ? group_runs<false>(T, (int32_t)id, 0, 0) : 0;
+}
+
+__global__ void k_group_emit(Tree T, const int32_t *__restrict__ gstart, const int64_t *__restrict__ inst_off,
+                             int ninst) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nn = *T.nnodes;
+  if (id == 0) *T.ngroups = min(gstart[nn], (int32_t)T.cap_groups);
+  if (id >= nn || gstart[id + 1] == gstart[id]) return;
+  group_runs<true>(T, (int32_t)id, gstart[id], inst_of(inst_off, ninst, T.first[id]));
 }
 
 // ---------------------------------------------------------------------------
@@ -731,8 +785,8 @@ __global__ void k_moments(Tree T, const double *__restrict__ x, const double *__
 void pack_f32(sph_ctx *c, const sph_state *s, cudaStream_t st) {
   int64_t n = s->n;
   if (n == 0) return;
-  k_pack<<<nblk(n, 256), 256, 0, st>>>(s->x[0], s->x[1], s->x[2], s->v[0], s->v[1], s->v[2], s->h, s->m, s->rho, n,
-                                       s->dim, s->inst_off, s->ninst, c->tree.inst_lo, c->units, c->pk);
+  { k_pack<<<nblk(n, 256), 256, 0, st>>>(s->x[0], s->x[1], s->x[2], s->v[0], s->v[1], s->v[2], s->h, s->m, s->rho, n,
+                                       s->dim, s->inst_off, s->ninst, c->tree.inst_lo, c->units, c->pk); ++sph::g_launches; }
 }
 
 void tree_build(sph_ctx *c, const sph_state *s, int leaf_size, int max_depth, cudaStream_t st) {
@@ -745,20 +799,20 @@ void tree_build(sph_ctx *c, const sph_state *s, int leaf_size, int max_depth, cu
   T.dim = dim;
   T.ninst = ninst;
   T.n = n;
-  k_bbox_init<<<nblk(ninst, 128), 128, 0, st>>>(T.inst_bb, ninst);
+  { k_bbox_init<<<nblk(ninst, 128), 128, 0, st>>>(T.inst_bb, ninst); ++sph::g_launches; }
   if (n > 0) {
     if (ninst > 1)
-      k_bbox<<<ninst, 256, 0, st>>>(s->x[0], s->x[1], s->x[2], s->v[0], s->v[1], s->v[2], s->h, s->rho, n, dim,
-                                   s->inst_off, ninst, T.inst_bb, c->d_err);
+      { k_bbox<<<ninst, 256, 0, st>>>(s->x[0], s->x[1], s->x[2], s->v[0], s->v[1], s->v[2], s->h, s->rho, n, dim,
+                                   s->inst_off, ninst, T.inst_bb, c->d_err); ++sph::g_launches; }
     else
-      k_bbox<<<min(nblk(n, 256), 152 * 8), 256, 0, st>>>(s->x[0], s->x[1], s->x[2], s->v[0], s->v[1], s->v[2], s->h,
-                                                        s->rho, n, dim, nullptr, 1, T.inst_bb, c->d_err);
+      { k_bbox<<<min(nblk(n, 256), 152 * 8), 256, 0, st>>>(s->x[0], s->x[1], s->x[2], s->v[0], s->v[1], s->v[2], s->h,
+                                                        s->rho, n, dim, nullptr, 1, T.inst_bb, c->d_err); ++sph::g_launches; }
   }
-  k_root<<<nblk(ninst, 128), 128, 0, st>>>(T.inst_bb, ninst, dim, T.inst_lo, T.inst_s0);
-  k_units<<<1, 32, 0, st>>>(s->h, s->m, n, dim, c->vscale, c->mt, c->units);
+  { k_root<<<nblk(ninst, 128), 128, 0, st>>>(T.inst_bb, ninst, dim, T.inst_lo, T.inst_s0); ++sph::g_launches; }
+  { k_units<<<1, 32, 0, st>>>(s->h, s->m, n, dim, c->vscale, c->mt, c->units); ++sph::g_launches; }
   if (n > 0) {
-    k_keys<<<nblk(n, 256), 256, 0, st>>>(s->x[0], s->x[1], s->x[2], n, dim, max_depth, s->inst_off, ninst,
-                                         T.inst_lo, T.inst_s0, T.keys[0], T.vals[0]);
+    { k_keys<<<nblk(n, 256), 256, 0, st>>>(s->x[0], s->x[1], s->x[2], n, dim, max_depth, s->inst_off, ninst,
+                                         T.inst_lo, T.inst_s0, T.keys[0], T.vals[0]); ++sph::g_launches; }
     int ibits = 0;
     while ((1 << ibits) < ninst) ++ibits;
     radix_sort(c, n, dim * max_depth + ibits, st);
@@ -768,15 +822,17 @@ void tree_build(sph_ctx *c, const sph_state *s, int leaf_size, int max_depth, cu
   }
   pack_f32(c, s, st);
   KeyLevels K{T.skey, dim, max_depth};
-  k_node_count<<<nblk(n + 1, 256), 256, 0, st>>>(K, n, leaf_size, s->inst_off, ninst, T.ncount);
+  { k_node_count<<<nblk(n + 1, 256), 256, 0, st>>>(K, n, leaf_size, s->inst_off, ninst, T.ncount); ++sph::g_launches; }
   scan_excl_i32(T.ncount, T.nstart, n + 1, T.scan_tmp, st);
   cudaMemsetAsync(T.nchild, 0, sizeof(int32_t) * T.cap_nodes, st);
   cudaMemsetAsync(T.arrived, 0, sizeof(int32_t) * T.cap_nodes, st);
-  k_node_emit<<<nblk(n + 1, 256), 256, 0, st>>>(K, n, leaf_size, s->inst_off, ninst, T.nstart, T, c->d_err);
-  k_moments<<<nblk(T.cap_nodes, 256), 256, 0, st>>>(
-      T, s->x[0], s->x[1], s->x[2], s->m, s->h, dim, leaf_size, s->inst_off, ninst, c->units);
-  k_inst_info<<<1, 1024, 0, st>>>(s->inst_off, ninst, n, T.nstart, T);
-  if (n > 0) k_groups<<<nblk(n, 256), 256, 0, st>>>(s->inst_off, ninst, n, T);
+  { k_node_emit<<<nblk(n + 1, 256), 256, 0, st>>>(K, n, leaf_size, s->inst_off, ninst, T.nstart, T, c->d_err); ++sph::g_launches; }
+  { k_moments<<<nblk(T.cap_nodes, 256), 256, 0, st>>>(
+      T, s->x[0], s->x[1], s->x[2], s->m, s->h, dim, leaf_size, s->inst_off, ninst, c->units); ++sph::g_launches; }
+  { k_inst_roots<<<nblk(ninst, 128), 128, 0, st>>>(s->inst_off, ninst, n, T.nstart, T); ++sph::g_launches; }
+  { k_group_count<<<nblk(T.cap_nodes + 1, 256), 256, 0, st>>>(T, T.gcnt); ++sph::g_launches; }
+  scan_excl_i32(T.gcnt, T.gstart, T.cap_nodes + 1, T.scan_tmp, st);
+  { k_group_emit<<<nblk(T.cap_nodes, 256), 256, 0, st>>>(T, T.gstart, s->inst_off, ninst); ++sph::g_launches; }
 }
 
 // ---------------------------------------------------------------------------
@@ -804,12 +860,12 @@ void tree_reorder_state(sph_ctx *c, sph_state *s, cudaStream_t st) {
   double *buf = c->st.gather;
   auto gd = [&](double *f) {
     if (!f) return;
-    k_gather_d<<<nblk(n, 256), 256, 0, st>>>(f, buf, perm, n);
+    { k_gather_d<<<nblk(n, 256), 256, 0, st>>>(f, buf, perm, n); ++sph::g_launches; }
     cudaMemcpyAsync(f, buf, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
   };
   auto gi = [&](int32_t *f) {
     if (!f) return;
-    k_gather_i<<<nblk(n, 256), 256, 0, st>>>(f, c->st.gather_i, perm, n);
+    { k_gather_i<<<nblk(n, 256), 256, 0, st>>>(f, c->st.gather_i, perm, n); ++sph::g_launches; }
     cudaMemcpyAsync(f, c->st.gather_i, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st);
   };
   for (int ax = 0; ax < s->dim; ++ax) {
@@ -825,7 +881,7 @@ void tree_reorder_state(sph_ctx *c, sph_state *s, cudaStream_t st) {
     for (int k = 0; k < nsym(s->dim); ++k) gd(s->S + (int64_t)k * n);
   gi(s->mat);
   gi(s->id);
-  k_iota<<<nblk(n, 256), 256, 0, st>>>(c->tree.perm, n);
+  { k_iota<<<nblk(n, 256), 256, 0, st>>>(c->tree.perm, n); ++sph::g_launches; }
   pack_f32(c, s, st);
 }
 
@@ -856,7 +912,7 @@ __global__ void k_export_nodes(Tree T, int64_t cap, int dim, int32_t *level, int
 
 void export_nodes(sph_ctx *c, int64_t cap, int32_t *level, int64_t *cell, int64_t *count, double *mass, double *com,
                   cudaStream_t st) {
-  k_export_nodes<<<nblk(cap, 256), 256, 0, st>>>(c->tree, cap, c->tree.dim, level, cell, count, mass, com);
+  { k_export_nodes<<<nblk(cap, 256), 256, 0, st>>>(c->tree, cap, c->tree.dim, level, cell, count, mass, com); ++sph::g_launches; }
 }
 
 }  // namespace sph

@@ -26,6 +26,7 @@ SPH_OK, SPH_ERR_INVALID, SPH_ERR_CAPACITY, SPH_ERR_NONFINITE, SPH_ERR_TIMEOUT, S
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "CAPACITY", 3: "NONFINITE", 4: "TIMEOUT", 5: "CUDA"}
 EOS = {"linear": 0, "murnaghan": 1, "tillotson": 2, "isothermal": 3}
 PRECISION = {"fp64": 0, "mixed": 1}
+PHASES = ("tree", "reorder", "partners", "density", "passA", "passB", "gravity", "integrate")
 
 
 class SphError(RuntimeError):
@@ -93,8 +94,13 @@ def lib():
             L.sph_step.argtypes = [_vp, C.POINTER(State), C.POINTER(Material), C.c_int32, C.POINTER(Params), _vp,
                                    C.c_int32, _vp]
             L.sph_measure_fma_peak.argtypes = [C.c_int32, C.POINTER(C.c_double)]
+            L.sph_profile_enable.argtypes = [_vp, C.c_int32]
+            L.sph_profile_read.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_int32]
+            L.sph_launch_count.argtypes = []
+            L.sph_launch_count.restype = C.c_int64
             for f in ("sph_create", "sph_sync_status", "sph_build_tree", "sph_tree_nodes", "sph_neighbours",
-                      "sph_rhs", "sph_gravity", "sph_step", "sph_measure_fma_peak"):
+                      "sph_rhs", "sph_gravity", "sph_step", "sph_measure_fma_peak", "sph_profile_enable",
+                      "sph_profile_read"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -183,6 +189,15 @@ class Context:
 
     def sync_status(self, stream=None):
         self.check(self._lib.sph_sync_status(self.h, _stream(stream)), "device status")
+
+    def profile(self, on=True):
+        self.check(self._lib.sph_profile_enable(self.h, int(on)), "sph_profile_enable")
+
+    def profile_read(self):
+        ms = (C.c_double * len(PHASES))()
+        calls = (C.c_int32 * len(PHASES))()
+        self.check(self._lib.sph_profile_read(self.h, ms, calls, len(PHASES)), "sph_profile_read")
+        return {p: (ms[i], calls[i]) for i, p in enumerate(PHASES)}
 
 
 class DeviceState:
@@ -318,6 +333,10 @@ def step(ctx: Context, ds: DeviceState, materials, params: wl.Params, nsteps: in
     ctx.check(ctx._lib.sph_step(ctx.h, C.byref(st), M, len(materials), C.byref(P), _ptr(dt), int(nsteps),
                                 _stream(stream)), "sph_step")
     return dt
+
+
+def launch_count() -> int:
+    return int(lib().sph_launch_count())
 
 
 def measure_fma_peak(precision="mixed"):
