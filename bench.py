@@ -104,6 +104,15 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # Byte model of the kernels (algorithmic bytes per particle, mixed mode)
 # ----------------------------------------------------------------------------
+# DRAM bytes per particle of one launch, from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) as summarised under profiles/; per-particle so that a
+# capture on a smaller case scales to the full launch.  Kernels without an
+# entry report traffic null.
+NCU_TRAFFIC_PER_PARTICLE = {
+    "partners": 298.0,  # profiles/k_partners_al_impact_514k.md
+}
+
+
 def algorithmic_bytes(phase, K, n_flaw_mean, dim=3):
     """HBM bytes one particle must move in one launch of `phase`, counting each
     array once (partner data reused from cache): K = mean partners."""
@@ -238,7 +247,9 @@ def main():
     bytes_per_launch = algorithmic_bytes(dom, K, n_flaw) * n
     achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+            "frac": achieved / hbm_peak,
+            "traffic": (NCU_TRAFFIC_PER_PARTICLE[dom] * n) if dom in NCU_TRAFFIC_PER_PARTICLE else None,
+            "peak_source": peak_src,
             "bytes_per_particle": algorithmic_bytes(dom, K, n_flaw), "mean_partners": K,
             "avg_launch_ms": per_launch_ms}
     total_ms = sum(v[0] for v in phases.values())

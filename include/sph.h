@@ -125,6 +125,19 @@ typedef struct {
 
 typedef struct sph_ctx sph_ctx;
 
+/* Launch shapes and walk granularity of a context.  None of them changes a
+ * result: the partner set, the sums and their order are the same for every
+ * value.  walk_leaf: the partner walk stops descending at nodes of at most
+ * this many particles and tests their whole particle range (8..1024).
+ * walk_blocks_per_sm: resident blocks per SM of the persistent walk grids
+ * (1..32).  pass_threads: threads per block of the neighbour passes (64 or 128). */
+typedef struct {
+  int32_t walk_leaf;
+  int32_t walk_blocks_per_sm;
+  int32_t pass_threads;
+  int32_t reserved;
+} sph_tuning;
+
 /* Creates a context for up to max_particles particles in up to
  * max_instances instances, max_neighbours partners per particle and tree
  * leaves of up to leaf_size (1..32) particles; allocates all scratch on the
@@ -196,6 +209,10 @@ sph_status sph_gravity(sph_ctx *ctx, const sph_state *state, const sph_params *p
  * octree, so particle order changes; id follows the particles. */
 sph_status sph_step(sph_ctx *ctx, sph_state *state, const sph_material *mats, int32_t nmat, const sph_params *params,
                     double *dt, int32_t nsteps, void *stream);
+
+/* Reads / replaces the tuning of a context (defaults: 64, 16, 128). */
+sph_status sph_get_tuning(const sph_ctx *ctx, sph_tuning *out);
+sph_status sph_set_tuning(sph_ctx *ctx, const sph_tuning *t);
 
 /* Optional per-phase timing.  When enabled, every phase of sph_rhs and
  * sph_step is bracketed by CUDA events recorded on the call's stream (at most

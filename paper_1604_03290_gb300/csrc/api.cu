@@ -76,6 +76,11 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   c->cap_inst = max_instances;
   c->kmax = max_neighbours;
   c->leaf_default = leaf_size;
+  c->tune.walk_leaf = 64;
+  c->tune.walk_blocks_per_sm = 16;
+  c->tune.pass_threads = 128;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (c->num_sms < 1) c->num_sms = 1;
   const int64_t N = max_particles;
   bool ok = true;
   c->d_err = ctx_alloc<int32_t>(c, 1, ok);
@@ -99,6 +104,7 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   T.parent = ctx_alloc<int32_t>(c, cn, ok);
   T.nchild = ctx_alloc<int32_t>(c, cn, ok);
   T.arrived = ctx_alloc<int32_t>(c, cn, ok);
+  T.child = ctx_alloc<int32_t>(c, 8 * cn, ok);
   T.level = ctx_alloc<int32_t>(c, cn, ok);
   T.cell = ctx_alloc<unsigned long long>(c, cn, ok);
   T.mass = ctx_alloc<double>(c, cn, ok);
@@ -439,6 +445,22 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
   }
   if (dt && nsteps > 0) cudaMemcpyAsync(dt, B.dt, sizeof(double) * ninst, cudaMemcpyDeviceToDevice, st);
   return finish(c, p, st, "sph_step");
+}
+
+sph_status sph_get_tuning(const sph_ctx *c, sph_tuning *out) {
+  if (!c || !out) return SPH_ERR_INVALID;
+  *out = c->tune;
+  return SPH_OK;
+}
+
+sph_status sph_set_tuning(sph_ctx *c, const sph_tuning *t) {
+  if (!c || !t) return SPH_ERR_INVALID;
+  const int pt = t->pass_threads;
+  if (t->walk_leaf < 8 || t->walk_leaf > 1024 || t->walk_blocks_per_sm < 1 || t->walk_blocks_per_sm > 32 ||
+      !(pt == 64 || pt == 128))
+    return fail(c, SPH_ERR_INVALID, "tuning out of range");
+  c->tune = *t;
+  return SPH_OK;
 }
 
 sph_status sph_profile_enable(sph_ctx *c, int32_t on) {

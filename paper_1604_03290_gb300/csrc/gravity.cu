@@ -193,7 +193,7 @@ void gravity_walk(sph_ctx *c, const sph_state *s, const sph_params &p, double *a
   A.out[2] = az;
   A.U = c->units;
   A.err = c->d_err;
-  int blocks = 152 * 8;
+  int blocks = c->num_sms * 8;
   if (p.precision == SPH_MIXED) { k_gravity<true><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
   else { k_gravity<false><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
 }

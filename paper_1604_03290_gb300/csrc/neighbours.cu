@@ -43,12 +43,14 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_partners(Tree T, PackedF32 pk
                                                             const double *__restrict__ z,
                                                             const double *__restrict__ h, int dim, int kmax,
                                                             int32_t *__restrict__ nb_idx, int32_t *__restrict__ nb_cnt,
-                                                            int64_t ld, int32_t *err) {
+                                                            int64_t ld, int walk_leaf, int32_t *err) {
   __shared__ float4 sc[kNbWarps][kMaxLeaf];
   __shared__ int32_t sb[kNbWarps][kMaxLeaf];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ngroups = *T.ngroups;
-  const int L = T.leaf_size, B = T.max_depth;
+  // The walk stops at nodes of at most walk_leaf particles (or tree leaves)
+  // and culls their whole particle range: any stopping rule gives the same set.
+  const int L = max(T.leaf_size, walk_leaf), B = T.max_depth;
   const int nnodes = *T.nnodes;
   for (int g = blockIdx.x * kNbWarps + w; g < ngroups; g += gridDim.x * kNbWarps) {
     const int32_t s0 = T.grp_start[g], s1 = T.grp_end[g], inst = T.grp_inst[g];
@@ -164,9 +166,9 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_partners(Tree T, PackedF32 pk
 
 void find_partners(sph_ctx *c, const sph_state *s, cudaStream_t st) {
   if (s->n == 0) return;
-  int blocks = 152 * 12;
+  int blocks = c->num_sms * c->tune.walk_blocks_per_sm;
   { k_partners<<<blocks, kNbWarps * 32, 0, st>>>(c->tree, c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim, c->kmax,
-                                              c->nb_idx, c->nb_cnt, c->cap_n, c->d_err); ++sph::g_launches; }
+                                              c->nb_idx, c->nb_cnt, c->cap_n, c->tune.walk_leaf, c->d_err); ++sph::g_launches; }
 }
 
 // ---------------------------------------------------------------------------

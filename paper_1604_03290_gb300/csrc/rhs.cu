@@ -739,7 +739,7 @@ void rhs_passes(sph_ctx *c, sph_state *s, const MatTable &mt, const sph_params &
   A.prm = p;
   A.err = c->d_err;
   const bool mixed = p.precision == SPH_MIXED;
-  const int T = 128;
+  const int T = c->tune.pass_threads;
   int pr = -1;
   if (p.density_sum) {
     pr = prof_begin(c, st, PH_DENSITY);

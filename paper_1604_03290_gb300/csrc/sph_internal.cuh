@@ -60,6 +60,7 @@ struct Tree {
   int64_t cap_nodes;
   int32_t *nnodes;     // device scalar
   int32_t *first, *end, *skip, *parent, *nchild, *arrived, *level;
+  int32_t *child;      // up to 8 child ids per node, in arrival order
   unsigned long long *cell;  // level prefix of the key (instance bits included)
   double *mass, *com;  // com: 3 * cap_nodes, component-major
   double *bblo, *bbhi; // tight particle box, 3 * cap_nodes each
@@ -143,6 +144,8 @@ struct sph_ctx {
   sph::Units *units;    // device
   double vscale;        // host: velocity scale for the time unit
   sph::MatTable mt;     // host copy of the materials of the current call
+  sph_tuning tune;      // launch shapes and walk granularity
+  int num_sms;
   // profiler
   int prof;
   int prof_used;

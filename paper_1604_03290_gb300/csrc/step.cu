@@ -53,15 +53,39 @@ __global__ void k_dt(DtArgs A) {
     if (A.dmg && A.ddmg && A.ddmg[a] > 0.0)
       dt = fmin(dt, P.c_quantity * (fabs(A.dmg[a]) + P.dmg_floor) / A.ddmg[a]);
   }
-  // warp-level min when the warp lies in one instance, else per lane
+  // warp-level min when the warp lies in one instance, else per lane; then one
+  // atomic per run of equal instances among the block's warps
   const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __shared__ double wmin[32];
+  __shared__ int winst[32];
   int inst0 = __shfl_sync(full, inst, 0);
   bool same = __all_sync(full, inst == inst0 || a >= A.n);
   if (same) {
     for (int o = 16; o > 0; o >>= 1) dt = fmin(dt, __shfl_xor_sync(full, dt, o));
-    if ((threadIdx.x & 31) == 0 && (a < A.n || dt < P.dt_max)) atomicMin(&A.enc[inst0], dbl_to_ord(dt));
-  } else if (a < A.n) {
-    atomicMin(&A.enc[inst], dbl_to_ord(dt));
+  } else {
+    if (a < A.n) atomicMin(&A.enc[inst], dbl_to_ord(dt));
+    dt = P.dt_max;  // already reported
+  }
+  if (lane == 0) {
+    wmin[w] = dt;
+    winst[w] = inst0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    double cur = wmin[0];
+    int ci = winst[0];
+    for (int k = 1; k < nw; ++k) {
+      if (winst[k] == ci) {
+        cur = fmin(cur, wmin[k]);
+      } else {
+        if (cur < P.dt_max) atomicMin(&A.enc[ci], dbl_to_ord(cur));
+        cur = wmin[k];
+        ci = winst[k];
+      }
+    }
+    if (cur < P.dt_max) atomicMin(&A.enc[ci], dbl_to_ord(cur));
   }
 }
 

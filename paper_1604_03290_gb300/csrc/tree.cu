@@ -367,6 +367,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const unsigned l
   }
 }
 
+static void scan_excl_i32(const int32_t *in, int32_t *out, int64_t m, int32_t *tmp, cudaStream_t st);
+
 static void radix_sort(sph_ctx *c, int64_t n, int bits, cudaStream_t st) {
   Tree &T = c->tree;
   int nblocks = nblk(n, kSortTile);
@@ -375,7 +377,7 @@ static void radix_sort(sph_ctx *c, int64_t n, int bits, cudaStream_t st) {
   for (int p = 0; p < passes; ++p) {
     int shift = 8 * p;
     { k_radix_hist<<<nblocks, kSortThreads, 0, st>>>(T.keys[src], n, shift, T.hist, nblocks); ++sph::g_launches; }
-    { k_scan_u32_1blk<<<1, 1024, 0, st>>>(T.hist, (int64_t)256 * nblocks); ++sph::g_launches; }
+    scan_excl_i32((const int32_t *)T.hist, (int32_t *)T.hist, (int64_t)256 * nblocks, T.scan_tmp, st);
     { k_radix_scatter<<<nblocks, kSortThreads, 0, st>>>(T.keys[src], T.vals[src], T.keys[src ^ 1], T.vals[src ^ 1], n,
                                                      shift, T.hist, nblocks); ++sph::g_launches; }
     src ^= 1;
@@ -579,7 +581,10 @@ __global__ void k_node_emit(KeyLevels K, int64_t n, int L, const int64_t *__rest
       T.cell[id] = K.prefix(i, l);
       T.skip[id] = min((int64_t)nstart[end], T.cap_nodes);
       T.parent[id] = parent;
-      if (parent >= 0) atomicAdd(&T.nchild[parent], 1);
+      if (parent >= 0) {
+        const int r = atomicAdd(&T.nchild[parent], 1);
+        if (r < 8) T.child[8 * (int64_t)parent + r] = id;
+      }
     }
     parent = id;
     if (end - i <= L || l == K.B) break;
@@ -755,7 +760,7 @@ __global__ void k_moments(Tree T, const double *__restrict__ x, const double *__
     int old = atomicAdd(&T.arrived[p], 1);
     if (old != T.nchild[p] - 1) return;
     __threadfence();
-    // last child in: combine all children of p in child order
+    // last child in: combine all children of p, in ascending id (= child) order
     M = 0.0;
     hm = 0.0;
     for (int ax = 0; ax < 3; ++ax) {
@@ -763,9 +768,20 @@ __global__ void k_moments(Tree T, const double *__restrict__ x, const double *__
       lo[ax] = inf;
       hi[ax] = -inf;
     }
-    int32_t stop = T.skip[p];
-    int guard = 0;
-    for (int32_t cc = p + 1; cc < stop && guard < 64; cc = T.skip[cc], ++guard) {
+    const int nc = min(T.nchild[p], 8);
+    int32_t ch[8];
+    for (int k = 0; k < nc; ++k) ch[k] = __ldcg(&T.child[8 * (int64_t)p + k]);
+    for (int k = 1; k < nc; ++k) {  // insertion sort of <= 8 ids
+      int32_t v = ch[k];
+      int j = k - 1;
+      while (j >= 0 && ch[j] > v) {
+        ch[j + 1] = ch[j];
+        --j;
+      }
+      ch[j + 1] = v;
+    }
+    for (int k = 0; k < nc; ++k) {
+      const int32_t cc = ch[k];
       double mc = __ldcg(&T.mass[cc]);
       M += mc;
       hm = fmax(hm, __ldcg(&T.hmax[cc]));

@@ -64,6 +64,11 @@ class State(C.Structure):
                 ("id", _vp), ("flaw_off", _vp), ("flaw_eps", _vp), ("inst_off", _vp)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("walk_leaf", C.c_int32), ("walk_blocks_per_sm", C.c_int32), ("pass_threads", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
 class Derivs(C.Structure):
     _fields_ = [("dx", _vp * 3), ("dv", _vp * 3), ("drho", _vp), ("du", _vp), ("dS", _vp), ("ddmg", _vp),
                 ("cs", _vp), ("p", _vp), ("n_act", _vp), ("nnb", _vp)]
@@ -96,11 +101,13 @@ def lib():
             L.sph_measure_fma_peak.argtypes = [C.c_int32, C.POINTER(C.c_double)]
             L.sph_profile_enable.argtypes = [_vp, C.c_int32]
             L.sph_profile_read.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_int32]
+            L.sph_get_tuning.argtypes = [_vp, C.POINTER(Tuning)]
+            L.sph_set_tuning.argtypes = [_vp, C.POINTER(Tuning)]
             L.sph_launch_count.argtypes = []
             L.sph_launch_count.restype = C.c_int64
             for f in ("sph_create", "sph_sync_status", "sph_build_tree", "sph_tree_nodes", "sph_neighbours",
                       "sph_rhs", "sph_gravity", "sph_step", "sph_measure_fma_peak", "sph_profile_enable",
-                      "sph_profile_read"):
+                      "sph_profile_read", "sph_get_tuning", "sph_set_tuning"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -189,6 +196,17 @@ class Context:
 
     def sync_status(self, stream=None):
         self.check(self._lib.sph_sync_status(self.h, _stream(stream)), "device status")
+
+    def get_tuning(self) -> dict:
+        t = Tuning()
+        self.check(self._lib.sph_get_tuning(self.h, C.byref(t)), "sph_get_tuning")
+        return {"walk_leaf": t.walk_leaf, "walk_blocks_per_sm": t.walk_blocks_per_sm, "pass_threads": t.pass_threads}
+
+    def set_tuning(self, **kw):
+        cur = self.get_tuning()
+        cur.update(kw)
+        t = Tuning(cur["walk_leaf"], cur["walk_blocks_per_sm"], cur["pass_threads"], 0)
+        self.check(self._lib.sph_set_tuning(self.h, C.byref(t)), "sph_set_tuning")
 
     def profile(self, on=True):
         self.check(self._lib.sph_profile_enable(self.h, int(on)), "sph_profile_enable")
