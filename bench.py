@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n-side", type=int, default=100)
     ap.add_argument("--fp64-steps", type=int, default=3)
-    ap.add_argument("--cpu-side", type=int, default=40, help="cube side of the CPU-baseline sample")
+    ap.add_argument("--cpu-side", type=int, default=100, help="cube side of the CPU-baseline sample")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 

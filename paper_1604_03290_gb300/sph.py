@@ -364,3 +364,27 @@ def measure_fma_peak(precision="mixed"):
     if st != SPH_OK:
         raise SphError(st, "sph_measure_fma_peak")
     return v.value
+
+
+class StepGraph:
+    """nsteps predictor-corrector steps captured once as a CUDA graph and
+    replayed with replay().  The state arrays of ``ds`` are baked into the
+    graph (they are updated in place at every replay); the context must not
+    be used by other calls while a replay runs."""
+
+    def __init__(self, ctx: Context, ds: DeviceState, materials, params: wl.Params, nsteps: int = 1):
+        self.graph = torch.cuda.CUDAGraph()
+        self.stream = torch.cuda.Stream()
+        self.stream.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(self.stream):
+            step(ctx, ds, materials, params, 1, check=False)  # warm-up outside the capture
+        torch.cuda.current_stream().wait_stream(self.stream)
+        torch.cuda.synchronize()
+        self.dt = torch.zeros(max(ds.ninst, 1), dtype=torch.float64, device=ds.x.device)
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            step(ctx, ds, materials, params, nsteps, check=False, dt_out=self.dt)
+        self.ctx = ctx
+
+    def replay(self):
+        self.graph.replay()
+        return self.dt
