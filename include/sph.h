@@ -210,6 +210,41 @@ sph_status sph_gravity(sph_ctx *ctx, const sph_state *state, const sph_params *p
 sph_status sph_step(sph_ctx *ctx, sph_state *state, const sph_material *mats, int32_t nmat, const sph_params *params,
                     double *dt, int32_t nsteps, void *stream);
 
+/* Reverse-mode derivative of sph_rhs at `state` (FP64, any requested
+ * precision is evaluated in FP64), with the partner lists and the damage of
+ * that evaluation held fixed and every branch (artificial viscosity on/off,
+ * yield on/off, EOS branch, C = I fallback) at its forward side.  Given the
+ * cotangents dbar of the outputs dx/dt, dv/dt, drho/dt, du/dt, dS/dt (device,
+ * layout of sph_derivs; NULL entries count as zero), it ADDS the cotangents of
+ * x, v, rho, u and S to the matching arrays of `state_bar` (device, layout of
+ * sph_state; its other fields are ignored) and ADDS to param_bar (device,
+ * ninst * nmat * 3 doubles, may be NULL) the cotangents of the shear modulus
+ * mu, the yield stress Y0 and the bulk modulus K of each material and
+ * instance; K scales K0, A_T and B_T together and is measured in units of the
+ * largest of them.  Requires continuity density, no artificial stress and no
+ * gravity (SPH_ERR_INVALID otherwise).  Builds the tree and partners itself. */
+sph_status sph_rhs_adjoint(sph_ctx *ctx, sph_state *state, const sph_material *mats, int32_t nmat,
+                           const sph_params *params, const sph_derivs *dbar, sph_state *state_bar, double *param_bar,
+                           void *stream);
+
+/* One predictor or corrector update without reordering (Sect. 3.4.1):
+ * out = Y(base + frac * dt * d) for x, v, rho (continuity), u and S, Y the von
+ * Mises limiter, damage and its cap as in sph_step.  dt: device, one per
+ * instance.  out may alias base. */
+sph_status sph_pc_update(sph_ctx *ctx, const sph_state *base, const sph_derivs *d, const sph_material *mats,
+                         int32_t nmat, const sph_params *params, const double *dt, double frac, sph_state *out,
+                         void *stream);
+
+/* Reverse of sph_pc_update with damage held fixed: given the cotangent of
+ * out (out_bar: x, v, rho, u, S), ADDS the cotangent of base to base_bar,
+ * WRITES frac * dt times the pre-limiter cotangent to d_bar (dx, dv, drho,
+ * du, dS) and ADDS the yield-stress cotangent to param_bar (as in
+ * sph_rhs_adjoint; may be NULL).  out_bar must not alias base_bar. */
+sph_status sph_pc_update_adjoint(sph_ctx *ctx, const sph_state *base, const sph_derivs *d,
+                                 const sph_material *mats, int32_t nmat, const sph_params *params, const double *dt,
+                                 double frac, const sph_state *out_bar, sph_state *base_bar, sph_derivs *d_bar,
+                                 double *param_bar, void *stream);
+
 /* Reads / replaces the tuning of a context (defaults: 64, 16, 128). */
 sph_status sph_get_tuning(const sph_ctx *ctx, sph_tuning *out);
 sph_status sph_set_tuning(sph_ctx *ctx, const sph_tuning *t);

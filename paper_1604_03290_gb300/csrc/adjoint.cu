@@ -1,0 +1,806 @@
+// Reverse-mode derivative (adjoint) of the right-hand side (Sect. 3.1) and of
+// the predictor-corrector update (Sect. 3.4.1), in FP64, with the partner
+// lists and the damage of the forward evaluation held fixed.
+//
+// Given cotangents of the right-hand side's outputs (dx/dt, dv/dt, drho/dt,
+// du/dt, dS/dt) the kernels accumulate the cotangents of the state (x, v,
+// rho, u, S) and of the material parameters (shear modulus mu, yield stress
+// Y0, bulk modulus K: a common scale of K0, A_T and B_T).  Every pair term of
+// particle a depends on both a and its partner b; because the lists are
+// symmetric (b in N(a) iff a in N(b)) each particle gathers, over its own
+// list, both the derivatives of its own terms and the derivatives of its
+// partners' terms with respect to itself.  No atomics, deterministic order.
+//
+//   k_adj_passB   reverse of the momentum / energy pass -> x, v, T, c_s, rho
+//   k_adj_update  pass-A sums recomputed, reverse of the constitutive update
+//                 (T = sigma/rho^2, damage-reduced stress, Hooke + Jaumann,
+//                 von Mises, EOS, grad v = G C with C = L^-1) -> S, u, rho,
+//                 parameters, and the cotangents of the pass-A sums
+//   k_adj_passA   reverse of the continuity / L / G / XSPH sums -> x, v, rho
+//
+// Not covered (argument error): artificial stress, density by kernel sum,
+// gravity.  Branch switches (viscosity on/off, yield on/off, EOS branches,
+// C = I fallback) are held at the forward evaluation's side.
+#include "eos.cuh"
+#include "sph_internal.cuh"
+
+namespace sph {
+
+struct AdjArgs {
+  int dim;
+  int64_t n, ld;
+  const double *x[3], *v[3], *rho, *u, *m, *h, *S, *dmg;
+  const int32_t *mat;
+  const int32_t *nb_idx, *nb_cnt;
+  const double *T, *cs;               // forward pass A (FP64, stride ld)
+  const double *bdx[3], *bdv[3], *bdrho, *bdu, *bdS;  // output cotangents
+  double *gx[3], *gv[3], *grho, *gu, *gS;             // accumulated state cotangents
+  double *Tbar, *csbar;               // scratch: 6 * ld, ld
+  double *inter;                      // scratch: 22 * ld (sum_rho_bar, Lbar 9, Gbar 9, xsph_bar 3)
+  double *pbar;                       // scratch: 3 * ld (mu, Y0, K per particle)
+  MatTable mt;
+  sph_params prm;
+};
+
+__device__ __forceinline__ int sidx(int dim, int i, int j) { return symk(dim, i, j); }
+
+// Kernel radial factors for a pair: phi = dW/dr / r and phi'(r)/r, W, dW/dr.
+struct KernelPair {
+  double phi, dphi_r, W, dWdr;
+};
+
+__device__ __forceinline__ KernelPair kernel_pair(int dim, double r, double hab) {
+  const double sig = kernel_sigma<double>(dim);
+  const double hinv = 1.0 / hab;
+  const double hD = hpow(hinv, dim);
+  const double gnorm = 6.0 * sig * hD * hinv;
+  const double q = r * hinv;
+  double s = 0.0, sp = 0.0, w = 0.0;
+  if (q < 0.5) {
+    s = 3.0 * q * q - 2.0 * q;
+    sp = 6.0 * q - 2.0;
+    w = 6.0 * q * q * q - 6.0 * q * q + 1.0;
+  } else if (q <= 1.0) {
+    const double t = 1.0 - q;
+    s = -t * t;
+    sp = 2.0 * t;
+    w = 2.0 * t * t * t;
+  }
+  KernelPair k;
+  k.dWdr = gnorm * s;
+  k.W = sig * hD * w;
+  const double d2W = gnorm * sp * hinv;
+  if (r > 0.0) {
+    k.phi = k.dWdr / r;
+    k.dphi_r = (d2W - k.phi) / (r * r);
+  } else {
+    k.phi = -2.0 * gnorm * hinv;  // limit of dW/dr / r at r = 0
+    k.dphi_r = 0.0;
+  }
+  return k;
+}
+
+// ---------------------------------------------------------------------------
+// Reverse of one momentum/energy pair term of particle a with partner b:
+//   dv_a += m_b B g,  du_a += -1/2 m_b w.(B g),  B = T_a + T_b - Pi I,  g = phi d
+// Given the cotangents vb (of dv_a) and ub (of du_a), returns the cotangents
+// of d = x_a - x_b, w = v_a - v_b, of B (symmetrised; it goes to T_a and T_b),
+// and half the cotangents of the pair's mean sound speed and density.
+// ---------------------------------------------------------------------------
+__device__ void pairB_adj(int dim, const double d[3], const double w[3], double hab, double rho_a, double rho_b,
+                          double cs_a, double cs_b, const double Ta[6], const double Tb[6], double mb,
+                          const double vb[3], double ub, const sph_params &P, double dbar[3], double wbar[3],
+                          double Bsym[6], double &cs_half, double &rho_half) {
+  const int ns = nsym(dim);
+  double r2 = 0.0;
+  for (int i = 0; i < dim; ++i) r2 += d[i] * d[i];
+  const double r = sqrt(r2);
+  const KernelPair K = kernel_pair(dim, r, hab);
+  double g[3] = {0, 0, 0};
+  for (int i = 0; i < dim; ++i) g[i] = K.phi * d[i];
+  double vx = 0.0;
+  for (int i = 0; i < dim; ++i) vx += w[i] * d[i];
+  double Pi = 0.0, dPi_dnu = 0.0, dnu_dvx = 0.0, dnu_dr2 = 0.0, dPi_dc = 0.0, dPi_drb = 0.0;
+  if (vx < 0.0) {
+    const double Q = r2 + P.eps_v * hab * hab;
+    const double nu = hab * vx / Q;
+    const double cb = 0.5 * (cs_a + cs_b), rb = 0.5 * (rho_a + rho_b);
+    Pi = (-P.alpha * cb * nu + P.beta * nu * nu) / rb;
+    dPi_dnu = (-P.alpha * cb + 2.0 * P.beta * nu) / rb;
+    dnu_dvx = hab / Q;
+    dnu_dr2 = -hab * vx / (Q * Q);
+    dPi_dc = -P.alpha * nu / rb;
+    dPi_drb = -Pi / rb;
+  }
+  double B[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      if (i < dim && j < dim) {
+        const int k = sidx(dim, i, j);
+        B[i][j] = Ta[k] + Tb[k] - (i == j ? Pi : 0.0);
+      } else {
+        B[i][j] = 0.0;
+      }
+    }
+  double Bg[3] = {0, 0, 0}, Bw[3] = {0, 0, 0}, Bv[3] = {0, 0, 0};
+  for (int i = 0; i < dim; ++i)
+    for (int j = 0; j < dim; ++j) {
+      Bg[i] += B[i][j] * g[j];
+      Bw[i] += B[i][j] * w[j];
+      Bv[i] += B[i][j] * vb[j];
+    }
+  // cotangents of B (general matrix), g and w
+  double Bbar[3][3];
+  double trB = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      Bbar[i][j] = (i < dim && j < dim) ? mb * vb[i] * g[j] - 0.5 * mb * ub * w[i] * g[j] : 0.0;
+      if (i == j) trB += Bbar[i][j];
+    }
+  double gbar[3] = {0, 0, 0};
+  for (int i = 0; i < 3; ++i) {
+    gbar[i] = mb * Bv[i] - 0.5 * mb * ub * Bw[i];
+    wbar[i] = -0.5 * mb * ub * Bg[i];
+    dbar[i] = 0.0;
+  }
+  for (int i = 0; i < dim; ++i)
+    for (int j = i; j < dim; ++j) Bsym[sidx(dim, i, j)] = 0.5 * (Bbar[i][j] + Bbar[j][i]);
+  for (int k = ns; k < 6; ++k) Bsym[k] = 0.0;
+  cs_half = 0.0;
+  rho_half = 0.0;
+  if (vx < 0.0) {
+    const double Pibar = -trB;
+    const double nubar = Pibar * dPi_dnu;
+    const double vxbar = nubar * dnu_dvx;
+    const double r2bar = nubar * dnu_dr2;
+    cs_half = 0.5 * Pibar * dPi_dc;
+    rho_half = 0.5 * Pibar * dPi_drb;
+    for (int i = 0; i < dim; ++i) {
+      wbar[i] += vxbar * d[i];
+      dbar[i] += vxbar * w[i] + 2.0 * r2bar * d[i];
+    }
+  }
+  double gd = 0.0;
+  for (int i = 0; i < dim; ++i) gd += gbar[i] * d[i];
+  for (int i = 0; i < dim; ++i) dbar[i] += K.phi * gbar[i] + K.dphi_r * gd * d[i];
+}
+
+__device__ __forceinline__ void load_T64(const AdjArgs &A, int64_t a, double t[6]) {
+  const int ns = nsym(A.dim);
+  for (int k = 0; k < 6; ++k) t[k] = k < ns ? A.T[(int64_t)k * A.ld + a] : 0.0;
+}
+
+__global__ void k_adj_passB(AdjArgs A) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= A.n) return;
+  const int dim = A.dim, ns = nsym(dim);
+  double xc[3] = {0, 0, 0}, vc[3] = {0, 0, 0}, vbc[3] = {0, 0, 0};
+  for (int i = 0; i < dim; ++i) {
+    xc[i] = A.x[i][c];
+    vc[i] = A.v[i][c];
+    vbc[i] = A.bdv[i] ? A.bdv[i][c] : 0.0;
+  }
+  const double ubc = A.bdu ? A.bdu[c] : 0.0;
+  double Tc[6];
+  load_T64(A, c, Tc);
+  const double hc = A.h[c], rc = A.rho[c], csc = A.cs[c], mc = A.m[c];
+  double gx[3] = {0, 0, 0}, gv[3] = {0, 0, 0}, Tb_acc[6] = {0, 0, 0, 0, 0, 0};
+  double csbar = 0.0, rhobar = 0.0;
+  const int cnt = A.nb_cnt[c];
+  for (int k = 0; k < cnt; ++k) {
+    const int32_t e = A.nb_idx[(int64_t)k * A.ld + c];
+    double d[3] = {0, 0, 0}, w[3] = {0, 0, 0}, vbe[3] = {0, 0, 0};
+    for (int i = 0; i < dim; ++i) {
+      d[i] = xc[i] - A.x[i][e];
+      w[i] = vc[i] - A.v[i][e];
+      vbe[i] = A.bdv[i] ? A.bdv[i][e] : 0.0;
+    }
+    const double ube = A.bdu ? A.bdu[e] : 0.0;
+    double Te[6];
+    load_T64(A, e, Te);
+    const double he = A.h[e], re = A.rho[e], cse = A.cs[e], me = A.m[e];
+    const double hab = 0.5 * (hc + he);
+    double db[3], wb[3], Bs[6], csh, rh;
+    // c's own term with partner e
+    pairB_adj(dim, d, w, hab, rc, re, csc, cse, Tc, Te, me, vbc, ubc, A.prm, db, wb, Bs, csh, rh);
+    for (int i = 0; i < dim; ++i) {
+      gx[i] += db[i];
+      gv[i] += wb[i];
+    }
+    for (int q = 0; q < ns; ++q) Tb_acc[q] += Bs[q];
+    csbar += csh;
+    rhobar += rh;
+    // e's term with partner c, differentiated with respect to c
+    double dn[3] = {-d[0], -d[1], -d[2]}, wn[3] = {-w[0], -w[1], -w[2]};
+    pairB_adj(dim, dn, wn, hab, re, rc, cse, csc, Te, Tc, mc, vbe, ube, A.prm, db, wb, Bs, csh, rh);
+    for (int i = 0; i < dim; ++i) {
+      gx[i] -= db[i];
+      gv[i] -= wb[i];
+    }
+    for (int q = 0; q < ns; ++q) Tb_acc[q] += Bs[q];
+    csbar += csh;
+    rhobar += rh;
+  }
+  for (int i = 0; i < dim; ++i) {
+    A.gx[i][c] += gx[i];
+    A.gv[i][c] += gv[i];
+  }
+  A.grho[c] += rhobar;
+  for (int q = 0; q < 6; ++q) A.Tbar[(int64_t)q * A.ld + c] = q < ns ? Tb_acc[q] : 0.0;
+  A.csbar[c] = csbar;
+}
+
+// ---------------------------------------------------------------------------
+// Constitutive update, recomputed and reversed
+// ---------------------------------------------------------------------------
+__device__ bool invert_L(int dim, const double L[3][3], double C[3][3]) {
+  double det;
+  if (dim == 2) det = L[0][0] * L[1][1] - L[0][1] * L[1][0];
+  else
+    det = L[0][0] * (L[1][1] * L[2][2] - L[1][2] * L[2][1]) - L[0][1] * (L[1][0] * L[2][2] - L[1][2] * L[2][0]) +
+          L[0][2] * (L[1][0] * L[2][1] - L[1][1] * L[2][0]);
+  double diag = 1.0;
+  for (int i = 0; i < dim; ++i) diag *= fabs(L[i][i]);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) C[i][j] = i == j ? 1.0 : 0.0;
+  if (!(fabs(det) > 1e-8 * diag) || !(diag > 0.0)) return false;
+  const double inv = 1.0 / det;
+  if (dim == 2) {
+    C[0][0] = L[1][1] * inv;
+    C[0][1] = -L[0][1] * inv;
+    C[1][0] = -L[1][0] * inv;
+    C[1][1] = L[0][0] * inv;
+    return true;
+  }
+  C[0][0] = (L[1][1] * L[2][2] - L[1][2] * L[2][1]) * inv;
+  C[0][1] = (L[0][2] * L[2][1] - L[0][1] * L[2][2]) * inv;
+  C[0][2] = (L[0][1] * L[1][2] - L[0][2] * L[1][1]) * inv;
+  C[1][0] = (L[1][2] * L[2][0] - L[1][0] * L[2][2]) * inv;
+  C[1][1] = (L[0][0] * L[2][2] - L[0][2] * L[2][0]) * inv;
+  C[1][2] = (L[0][2] * L[1][0] - L[0][0] * L[1][2]) * inv;
+  C[2][0] = (L[1][0] * L[2][1] - L[1][1] * L[2][0]) * inv;
+  C[2][1] = (L[0][1] * L[2][0] - L[0][0] * L[2][1]) * inv;
+  C[2][2] = (L[0][0] * L[1][1] - L[0][1] * L[1][0]) * inv;
+  return true;
+}
+
+// p and c_s of a material whose bulk-modulus constants are scaled by s.
+__device__ void eos_scaled(const sph_material &M0, double s, double rho, double u, double &p, double &cs, double *pr,
+                           double *pu) {
+  sph_material M = M0;
+  M.K0 *= s;
+  M.A_T *= s;
+  M.B_T *= s;
+  const EosC<double> K = eos_consts<double>(M, nullptr, nullptr);
+  eos_eval<double>(M, K, rho, u, p, cs, pr, pu);
+}
+
+__global__ void k_adj_update(AdjArgs A) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= A.n) return;
+  const int dim = A.dim, ns = nsym(dim);
+  const sph_params &P = A.prm;
+  // ---- pass-A sums, recomputed ----
+  double xc[3] = {0, 0, 0}, vc[3] = {0, 0, 0};
+  for (int i = 0; i < dim; ++i) {
+    xc[i] = A.x[i][c];
+    vc[i] = A.v[i][c];
+  }
+  const double hc = A.h[c], rc = A.rho[c];
+  double srho = 0.0, L[3][3], G[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) L[i][j] = G[i][j] = 0.0;
+  const int cnt = A.nb_cnt[c];
+  for (int k = 0; k < cnt; ++k) {
+    const int32_t e = A.nb_idx[(int64_t)k * A.ld + c];
+    double d[3] = {0, 0, 0}, w[3] = {0, 0, 0}, r2 = 0.0;
+    for (int i = 0; i < dim; ++i) {
+      d[i] = xc[i] - A.x[i][e];
+      w[i] = vc[i] - A.v[i][e];
+      r2 += d[i] * d[i];
+    }
+    const KernelPair K = kernel_pair(dim, sqrt(r2), 0.5 * (hc + A.h[e]));
+    const double vol = A.m[e] / A.rho[e];
+    double wg = 0.0;
+    for (int i = 0; i < dim; ++i) wg += w[i] * K.phi * d[i];
+    srho += vol * wg;
+    for (int i = 0; i < dim; ++i)
+      for (int j = 0; j < dim; ++j) {
+        L[i][j] -= vol * d[i] * K.phi * d[j];
+        G[i][j] -= vol * w[i] * K.phi * d[j];
+      }
+  }
+  double C[3][3];
+  const bool corr = P.consistency && cnt >= dim + 1 && invert_L(dim, L, C);
+  if (!corr)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) C[i][j] = i == j ? 1.0 : 0.0;
+  double gv[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < dim; ++k) s += G[i][k] * C[k][j];
+      gv[i][j] = (i < dim && j < dim) ? s : 0.0;
+    }
+  // ---- constitutive state ----
+  const int mi0 = A.mat ? A.mat[c] : 0;
+  const int mi = (mi0 >= 0 && mi0 < A.mt.nmat) ? mi0 : 0;
+  const sph_material &M = A.mt.m[mi];
+  const double uc = A.u[c];
+  double p, cs, pr, pu;
+  eos_scaled(M, 1.0, rc, uc, p, cs, &pr, &pu);
+  const bool strength = A.S != nullptr && M.strength;
+  double S[3][3], St[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) S[i][j] = (strength && i < dim && j < dim) ? A.S[(int64_t)sidx(dim, i, j) * A.n + c] : 0.0;
+  double J2 = 0.0;
+  for (int i = 0; i < dim; ++i)
+    for (int j = 0; j < dim; ++j) J2 += S[i][j] * S[i][j];
+  J2 *= 0.5;
+  double fY = 1.0;
+  if (strength && M.Y0 > 0.0 && J2 > 0.0) fY = fmin(M.Y0 * M.Y0 / (3.0 * J2), 1.0);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) St[i][j] = fY * S[i][j];
+  const bool damage = A.dmg != nullptr && M.damage;
+  double dd = 0.0;
+  if (damage) {
+    const double del = A.dmg[c];
+    dd = del * del * del;
+  }
+  // ---- reverse: T = sigma / rho^2 ----
+  double Tb[3][3], Tc[6];
+  load_T64(A, c, Tc);
+  double TbT = 0.0, trSig = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      Tb[i][j] = (i < dim && j < dim) ? A.Tbar[(int64_t)sidx(dim, i, j) * A.ld + c] : 0.0;
+      if (i < dim && j < dim) TbT += Tb[i][j] * Tc[sidx(dim, i, j)];
+    }
+  double rhobar = -2.0 * TbT / rc;
+  double sigbar[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) sigbar[i][j] = Tb[i][j] / (rc * rc);
+  for (int i = 0; i < dim; ++i) trSig += sigbar[i][i];
+  // sigma = -p_hat I + (1 - d) S_tilde
+  const double phatbar = -trSig;
+  const double pbar = p >= 0.0 ? phatbar : (1.0 - dd) * phatbar;
+  double Stbar[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Stbar[i][j] = (1.0 - dd) * sigbar[i][j];
+  // ---- reverse: dS = 2 mu (eps_dot - tr/D I) + R S_t - S_t R ----
+  double Sdb[3][3];  // full-matrix cotangent of dS (symmetric)
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double cst = (A.bdS && strength && i < dim && j < dim) ? A.bdS[(int64_t)sidx(dim, i, j) * A.n + c] : 0.0;
+      Sdb[i][j] = (i == j) ? cst : 0.5 * cst;
+    }
+  double ed[3][3], Rr[3][3], tr = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      ed[i][j] = 0.5 * (gv[i][j] + gv[j][i]);
+      Rr[i][j] = 0.5 * (gv[i][j] - gv[j][i]);
+    }
+  for (int i = 0; i < dim; ++i) tr += ed[i][i];
+  double mubar = 0.0, trSdb = 0.0;
+  for (int i = 0; i < dim; ++i) trSdb += Sdb[i][i];
+  for (int i = 0; i < dim; ++i)
+    for (int j = 0; j < dim; ++j) mubar += 2.0 * (ed[i][j] - (i == j ? tr / dim : 0.0)) * Sdb[i][j];
+  double edbar[3][3], Rbar[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      edbar[i][j] = (i < dim && j < dim) ? 2.0 * M.mu * (Sdb[i][j] - (i == j ? trSdb / dim : 0.0)) : 0.0;
+      double a1 = 0.0, a2 = 0.0, b1 = 0.0, b2 = 0.0;
+      for (int k = 0; k < dim; ++k) {
+        a1 += Sdb[i][k] * St[k][j];  // Z S_t
+        a2 += St[i][k] * Sdb[k][j];  // S_t Z
+        b1 += Rr[i][k] * Sdb[k][j];  // R Z
+        b2 += Sdb[i][k] * Rr[k][j];  // Z R
+      }
+      Rbar[i][j] = (i < dim && j < dim) ? a1 - a2 : 0.0;
+      if (i < dim && j < dim) Stbar[i][j] += -b1 + b2;
+    }
+  if (!strength)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) edbar[i][j] = Rbar[i][j] = 0.0;
+  double gvbar[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      gvbar[i][j] = 0.5 * (edbar[i][j] + edbar[j][i]) + 0.5 * (Rbar[i][j] - Rbar[j][i]);
+  // ---- reverse: S_t = f_Y S (stored components) ----
+  double Y0bar = 0.0;
+  if (strength && A.gS) {
+    double Stb_st[6], S_st[6];
+    for (int i = 0; i < dim; ++i)
+      for (int j = i; j < dim; ++j) {
+        const int k = sidx(dim, i, j);
+        Stb_st[k] = (i == j) ? Stbar[i][i] : Stbar[i][j] + Stbar[j][i];
+        S_st[k] = S[i][j];
+      }
+    double proj = 0.0;
+    for (int k = 0; k < ns; ++k) proj += Stb_st[k] * S_st[k];
+    const bool yielding = M.Y0 > 0.0 && J2 > 0.0 && M.Y0 * M.Y0 / (3.0 * J2) < 1.0;
+    for (int k = 0; k < ns; ++k) {
+      double sb = Stb_st[k];
+      if (yielding) {
+        const double wk = k < dim ? 1.0 : 2.0;
+        sb = fY * Stb_st[k] - fY / J2 * proj * wk * S_st[k];
+      }
+      A.gS[(int64_t)k * A.n + c] += sb;
+    }
+    if (yielding) Y0bar = proj * 2.0 * fY / M.Y0;
+  }
+  // ---- reverse: EOS (analytic dp/drho, dp/du; c_s and the bulk scale by central differences) ----
+  const double csbar = A.csbar[c];
+  double ubar = pbar * pu;
+  rhobar += pbar * pr;
+  double Kbar = 0.0;
+  {
+    const double er = 1e-6 * rc, eu = 1e-6 * (fabs(uc) + 1e-3 * fabs(M.E0) + 1e-30), es = 1e-6;
+    double p1, c1, p2, c2;
+    if (csbar != 0.0) {
+      eos_scaled(M, 1.0, rc + er, uc, p1, c1, nullptr, nullptr);
+      eos_scaled(M, 1.0, rc - er, uc, p2, c2, nullptr, nullptr);
+      rhobar += csbar * (c1 - c2) / (2.0 * er);
+      eos_scaled(M, 1.0, rc, uc + eu, p1, c1, nullptr, nullptr);
+      eos_scaled(M, 1.0, rc, uc - eu, p2, c2, nullptr, nullptr);
+      ubar += csbar * (c1 - c2) / (2.0 * eu);
+    }
+    const double Kref = fmax(fmax(M.K0, M.A_T), M.B_T);
+    if (Kref > 0.0) {
+      eos_scaled(M, 1.0 + es, rc, uc, p1, c1, nullptr, nullptr);
+      eos_scaled(M, 1.0 - es, rc, uc, p2, c2, nullptr, nullptr);
+      Kbar = (pbar * (p1 - p2) + csbar * (c1 - c2)) / (2.0 * es * Kref);
+    }
+  }
+  // ---- reverse: grad v = G C, C = L^-1 ----
+  double Gbar[3][3], Lbar[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < dim; ++k) s += gvbar[i][k] * C[j][k];  // gvbar C^T
+      Gbar[i][j] = (i < dim && j < dim) ? s : 0.0;
+      Lbar[i][j] = 0.0;
+    }
+  if (corr) {
+    double Cbar[3][3], T1[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < dim; ++k) s += G[k][i] * gvbar[k][j];  // G^T gvbar
+        Cbar[i][j] = s;
+      }
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < dim; ++k) s += Cbar[i][k] * C[j][k];  // Cbar C^T
+        T1[i][j] = s;
+      }
+    for (int i = 0; i < dim; ++i)
+      for (int j = 0; j < dim; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < dim; ++k) s += C[k][i] * T1[k][j];  // C^T (Cbar C^T)
+        Lbar[i][j] = -s;
+      }
+  }
+  // ---- reverse: drho = rho * sum_rho ; dx = v + xsph * xs ----
+  const double bdr = A.bdrho ? A.bdrho[c] : 0.0;
+  rhobar += bdr * srho;
+  A.grho[c] += rhobar;
+  A.gu[c] += ubar;
+  for (int i = 0; i < dim; ++i)
+    if (A.bdx[i]) A.gv[i][c] += A.bdx[i][c];
+  double *I = A.inter;
+  const int64_t ld = A.ld;
+  I[c] = rc * bdr;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      I[(1 + 3 * i + j) * ld + c] = Lbar[i][j];
+      I[(10 + 3 * i + j) * ld + c] = Gbar[i][j];
+    }
+  for (int i = 0; i < 3; ++i) I[(19 + i) * ld + c] = (i < dim && A.bdx[i]) ? P.xsph * A.bdx[i][c] : 0.0;
+  A.pbar[c] = strength ? mubar : 0.0;
+  A.pbar[ld + c] = Y0bar;
+  A.pbar[2 * ld + c] = Kbar;
+}
+
+// ---------------------------------------------------------------------------
+// Reverse of one pass-A pair term of particle a with partner b:
+//   sum_rho += vol_b w.g,  L -= vol_b d (x) g,  G -= vol_b w (x) g,
+//   xs -= 2 m_b/(rho_a + rho_b) W w,   vol_b = m_b / rho_b
+// ---------------------------------------------------------------------------
+__device__ void pairA_adj(int dim, const double d[3], const double w[3], double hab, double mb, double rho_a,
+                          double rho_b, const double *I, int64_t ld, int64_t a, double dbar[3], double wbar[3],
+                          double &rho_a_bar, double &rho_b_bar) {
+  double r2 = 0.0;
+  for (int i = 0; i < dim; ++i) r2 += d[i] * d[i];
+  const double r = sqrt(r2);
+  const KernelPair K = kernel_pair(dim, r, hab);
+  const double vol = mb / rho_b;
+  double g[3] = {0, 0, 0};
+  for (int i = 0; i < dim; ++i) g[i] = K.phi * d[i];
+  const double sr = I[a];
+  double Lb[3][3], Gb[3][3], xb[3];
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) {
+      Lb[i][j] = I[(1 + 3 * i + j) * ld + a];
+      Gb[i][j] = I[(10 + 3 * i + j) * ld + a];
+    }
+    xb[i] = I[(19 + i) * ld + a];
+  }
+  double gbar[3] = {0, 0, 0}, wg = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    dbar[i] = 0.0;
+    wbar[i] = 0.0;
+  }
+  for (int i = 0; i < dim; ++i) wg += w[i] * g[i];
+  double volbar = sr * wg;
+  for (int i = 0; i < dim; ++i) {
+    gbar[i] += sr * vol * w[i];
+    wbar[i] += sr * vol * g[i];
+  }
+  // L and G
+  for (int i = 0; i < dim; ++i) {
+    double Lg = 0.0, Gg = 0.0, LTd = 0.0, GTw = 0.0;
+    for (int j = 0; j < dim; ++j) {
+      Lg += Lb[i][j] * g[j];
+      Gg += Gb[i][j] * g[j];
+      LTd += Lb[j][i] * d[j];
+      GTw += Gb[j][i] * w[j];
+    }
+    dbar[i] += -vol * Lg;
+    wbar[i] += -vol * Gg;
+    gbar[i] += -vol * (LTd + GTw);
+    volbar += -d[i] * Lg - w[i] * Gg;
+  }
+  // XSPH
+  rho_a_bar = 0.0;
+  rho_b_bar = 0.0;
+  double wx = 0.0;
+  for (int i = 0; i < dim; ++i) wx += w[i] * xb[i];
+  if (wx != 0.0) {
+    const double cc = 2.0 * mb / (rho_a + rho_b);
+    for (int i = 0; i < dim; ++i) wbar[i] += -cc * K.W * xb[i];
+    const double Wbar = -cc * wx;
+    const double ccbar = -K.W * wx;
+    const double dcc = -cc / (rho_a + rho_b);
+    rho_a_bar += ccbar * dcc;
+    rho_b_bar += ccbar * dcc;
+    if (r > 0.0)
+      for (int i = 0; i < dim; ++i) dbar[i] += Wbar * K.dWdr * d[i] / r;
+  }
+  double gd = 0.0;
+  for (int i = 0; i < dim; ++i) gd += gbar[i] * d[i];
+  for (int i = 0; i < dim; ++i) dbar[i] += K.phi * gbar[i] + K.dphi_r * gd * d[i];
+  rho_b_bar += -volbar * vol / rho_b;
+}
+
+__global__ void k_adj_passA(AdjArgs A) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= A.n) return;
+  const int dim = A.dim;
+  double xc[3] = {0, 0, 0}, vc[3] = {0, 0, 0};
+  for (int i = 0; i < dim; ++i) {
+    xc[i] = A.x[i][c];
+    vc[i] = A.v[i][c];
+  }
+  const double hc = A.h[c], rc = A.rho[c], mc = A.m[c];
+  double gx[3] = {0, 0, 0}, gv[3] = {0, 0, 0}, grho = 0.0;
+  const int cnt = A.nb_cnt[c];
+  for (int k = 0; k < cnt; ++k) {
+    const int32_t e = A.nb_idx[(int64_t)k * A.ld + c];
+    double d[3] = {0, 0, 0}, w[3] = {0, 0, 0};
+    for (int i = 0; i < dim; ++i) {
+      d[i] = xc[i] - A.x[i][e];
+      w[i] = vc[i] - A.v[i][e];
+    }
+    const double he = A.h[e], re = A.rho[e], me = A.m[e];
+    const double hab = 0.5 * (hc + he);
+    double db[3], wb[3], ra, rb;
+    pairA_adj(dim, d, w, hab, me, rc, re, A.inter, A.ld, c, db, wb, ra, rb);  // c's own term
+    for (int i = 0; i < dim; ++i) {
+      gx[i] += db[i];
+      gv[i] += wb[i];
+    }
+    grho += ra;
+    double dn[3] = {-d[0], -d[1], -d[2]}, wn[3] = {-w[0], -w[1], -w[2]};
+    pairA_adj(dim, dn, wn, hab, mc, re, rc, A.inter, A.ld, e, db, wb, ra, rb);  // e's term, w.r.t. c
+    for (int i = 0; i < dim; ++i) {
+      gx[i] -= db[i];
+      gv[i] -= wb[i];
+    }
+    grho += rb;
+  }
+  for (int i = 0; i < dim; ++i) {
+    A.gx[i][c] += gx[i];
+    A.gv[i][c] += gv[i];
+  }
+  A.grho[c] += grho;
+}
+
+// Per-instance, per-material sums of the particle parameter cotangents, in a
+// fixed order (one block per instance): param_bar[(inst * nmat + mat) * 3 + k].
+__global__ void k_adj_params(const double *__restrict__ pbar, int64_t ld, const int32_t *__restrict__ mat,
+                             const int64_t *__restrict__ inst_off, int ninst, int64_t n, int nmat, double *out) {
+  const int inst = blockIdx.x;
+  const int64_t lo = (ninst > 1 && inst_off) ? inst_off[inst] : 0;
+  const int64_t hi = (ninst > 1 && inst_off) ? inst_off[inst + 1] : n;
+  __shared__ double sh[256][3];
+  for (int mm = 0; mm < nmat; ++mm) {
+    double acc[3] = {0, 0, 0};
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const int mi0 = mat ? mat[i] : 0;
+      const int mi = (mi0 >= 0 && mi0 < nmat) ? mi0 : 0;
+      if (mi != mm) continue;
+      for (int k = 0; k < 3; ++k) acc[k] += pbar[k * ld + i];
+    }
+    for (int k = 0; k < 3; ++k) sh[threadIdx.x][k] = acc[k];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s)
+        for (int k = 0; k < 3; ++k) sh[threadIdx.x][k] += sh[threadIdx.x + s][k];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0)
+      for (int k = 0; k < 3; ++k) out[((int64_t)inst * nmat + mm) * 3 + k] += sh[0][k];
+    __syncthreads();
+  }
+}
+
+void rhs_adjoint(sph_ctx *c, const sph_state *s, const MatTable &mt, const sph_params &p, const sph_derivs &dbar,
+                 sph_state *sbar, double *param_bar, cudaStream_t st) {
+  const int64_t n = s->n;
+  if (n == 0) return;
+  AdjArgs A;
+  memset(&A, 0, sizeof(A));
+  A.dim = s->dim;
+  A.n = n;
+  A.ld = c->cap_n;
+  for (int k = 0; k < 3; ++k) {
+    A.x[k] = s->x[k];
+    A.v[k] = s->v[k];
+    A.bdx[k] = dbar.dx[k];
+    A.bdv[k] = dbar.dv[k];
+    A.gx[k] = sbar->x[k];
+    A.gv[k] = sbar->v[k];
+  }
+  A.rho = s->rho;
+  A.u = s->u;
+  A.m = s->m;
+  A.h = s->h;
+  A.S = s->S;
+  A.dmg = s->dmg;
+  A.mat = s->mat;
+  A.nb_idx = c->nb_idx;
+  A.nb_cnt = c->nb_cnt;
+  A.T = (const double *)c->T;
+  A.cs = c->cs;
+  A.bdrho = dbar.drho;
+  A.bdu = dbar.du;
+  A.bdS = dbar.dS;
+  A.grho = sbar->rho;
+  A.gu = sbar->u;
+  A.gS = sbar->S;
+  // scratch: the step buffers of the second derivative set are free here
+  A.Tbar = c->st.d_S[1];
+  A.csbar = c->st.d_cs[1];
+  A.inter = c->adj_inter;
+  A.pbar = c->ag;
+  A.mt = mt;
+  A.prm = p;
+  const int T = 128;
+  { k_adj_passB<<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+  { k_adj_update<<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+  { k_adj_passA<<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+  const int ninst = s->ninst > 0 ? s->ninst : 1;
+  if (param_bar)
+    { k_adj_params<<<ninst, 256, 0, st>>>(c->ag, c->cap_n, s->mat, s->inst_off, ninst, n, mt.nmat, param_bar); ++sph::g_launches; }
+}
+
+// ---------------------------------------------------------------------------
+// Reverse of out = Y(base + frac dt d): the state cotangent passes to base,
+// frac dt times it to the derivatives, through the yield map for S.
+// ---------------------------------------------------------------------------
+struct PcAdjArgs {
+  int dim;
+  int64_t n;
+  const double *bS, *dS;
+  const int32_t *mat;
+  const int64_t *inst_off;
+  int ninst;
+  const double *dt;
+  double frac;
+  MatTable mt;
+  const double *ox[3], *ov[3], *orho, *ou, *oS;   // cotangent of out
+  double *gx[3], *gv[3], *grho, *gu, *gS;         // base cotangent (+=)
+  double *fx[3], *fv[3], *frho, *fu, *fS;         // derivative cotangent (=)
+  double *pY;                                     // per-particle Y0 cotangent (=)
+  int density_sum;
+};
+
+__global__ void k_pc_adj(PcAdjArgs A) {
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= A.n) return;
+  const int inst = inst_of(A.inst_off, A.ninst, a);
+  const double h = A.frac * A.dt[inst];
+  for (int ax = 0; ax < A.dim; ++ax) {
+    const double lx = A.ox[ax][a], lv = A.ov[ax][a];
+    A.gx[ax][a] += lx;
+    A.gv[ax][a] += lv;
+    A.fx[ax][a] = h * lx;
+    A.fv[ax][a] = h * lv;
+  }
+  A.grho[a] += A.orho[a];
+  A.frho[a] = A.density_sum ? 0.0 : h * A.orho[a];
+  A.gu[a] += A.ou[a];
+  A.fu[a] = h * A.ou[a];
+  double yb = 0.0;
+  if (A.bS) {
+    const int ns = nsym(A.dim);
+    const int mi0 = A.mat ? A.mat[a] : 0;
+    const sph_material &M = A.mt.m[(mi0 >= 0 && mi0 < A.mt.nmat) ? mi0 : 0];
+    double Sp[6], lo[6], J2 = 0.0, proj = 0.0;
+    for (int k = 0; k < ns; ++k) {
+      Sp[k] = A.bS[(int64_t)k * A.n + a] + h * A.dS[(int64_t)k * A.n + a];
+      lo[k] = A.oS[(int64_t)k * A.n + a];
+      J2 += (k < A.dim ? 1.0 : 2.0) * Sp[k] * Sp[k];
+      proj += lo[k] * Sp[k];
+    }
+    J2 *= 0.5;
+    const bool yielding = M.strength && M.Y0 > 0.0 && J2 > 0.0 && M.Y0 * M.Y0 / (3.0 * J2) < 1.0;
+    const double f = yielding ? M.Y0 * M.Y0 / (3.0 * J2) : 1.0;
+    for (int k = 0; k < ns; ++k) {
+      double sb = lo[k];
+      if (yielding) sb = f * lo[k] - f / J2 * proj * (k < A.dim ? 1.0 : 2.0) * Sp[k];
+      A.gS[(int64_t)k * A.n + a] += sb;
+      A.fS[(int64_t)k * A.n + a] = h * sb;
+    }
+    if (yielding) yb = proj * 2.0 * f / M.Y0;
+  }
+  A.pY[a] = yb;
+}
+
+void pc_update_adjoint(sph_ctx *c, const sph_state *base, const sph_derivs &d, const double *dt, double frac,
+                       const MatTable &mt, const sph_params &p, const sph_state *obar, sph_state *gbar,
+                       sph_derivs *fbar, double *param_bar, cudaStream_t st) {
+  const int64_t n = base->n;
+  if (n == 0) return;
+  PcAdjArgs A;
+  memset(&A, 0, sizeof(A));
+  A.dim = base->dim;
+  A.n = n;
+  A.bS = base->S;
+  A.dS = d.dS;
+  A.mat = base->mat;
+  A.inst_off = base->inst_off;
+  A.ninst = base->ninst > 0 ? base->ninst : 1;
+  A.dt = dt;
+  A.frac = frac;
+  A.mt = mt;
+  for (int k = 0; k < 3; ++k) {
+    A.ox[k] = obar->x[k];
+    A.ov[k] = obar->v[k];
+    A.gx[k] = gbar->x[k];
+    A.gv[k] = gbar->v[k];
+    A.fx[k] = fbar->dx[k];
+    A.fv[k] = fbar->dv[k];
+  }
+  A.orho = obar->rho;
+  A.ou = obar->u;
+  A.oS = obar->S;
+  A.grho = gbar->rho;
+  A.gu = gbar->u;
+  A.gS = gbar->S;
+  A.frho = fbar->drho;
+  A.fu = fbar->du;
+  A.fS = fbar->dS;
+  // per-particle Y0 cotangent in the parameter scratch (mu and K stay zero)
+  cudaMemsetAsync(c->ag, 0, sizeof(double) * 3 * c->cap_n, st);
+  A.pY = c->ag + c->cap_n;
+  A.density_sum = p.density_sum;
+  { k_pc_adj<<<nblk(n, 256), 256, 0, st>>>(A); ++sph::g_launches; }
+  const int ninst = base->ninst > 0 ? base->ninst : 1;
+  if (param_bar)
+    { k_adj_params<<<ninst, 256, 0, st>>>(c->ag, c->cap_n, base->mat, base->inst_off, ninst, n, mt.nmat, param_bar); ++sph::g_launches; }
+}
+
+}  // namespace sph

@@ -141,6 +141,7 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   c->p = ctx_alloc<double>(c, N, ok);
   c->ag = ctx_alloc<double>(c, 3 * N, ok);
   c->units = ctx_alloc<Units>(c, 1, ok);
+  c->adj_inter = ctx_alloc<double>(c, 22 * N, ok);
   c->vscale = 1.0;
   StepBufs &S = c->st;
   for (int k = 0; k < 3; ++k) {
@@ -445,6 +446,73 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
   }
   if (dt && nsteps > 0) cudaMemcpyAsync(dt, B.dt, sizeof(double) * ninst, cudaMemcpyDeviceToDevice, st);
   return finish(c, p, st, "sph_step");
+}
+
+sph_status sph_rhs_adjoint(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t nmat, const sph_params *p,
+                           const sph_derivs *dbar, sph_state *sbar, double *param_bar, void *stream) {
+  sph_status r = check_state(c, s);
+  if (r != SPH_OK) return r;
+  MatTable mt;
+  if ((r = check_params(c, s, mats, nmat, p, mt)) != SPH_OK) return r;
+  if (!dbar || !sbar) return fail(c, SPH_ERR_INVALID, "null cotangents");
+  if (p->density_sum || p->gravity || p->eps_s > 0.0)
+    return fail(c, SPH_ERR_INVALID, "adjoint needs continuity density, no gravity and no artificial stress");
+  if (s->n > 0) {
+    for (int ax = 0; ax < s->dim; ++ax)
+      if (!sbar->x[ax] || !sbar->v[ax]) return fail(c, SPH_ERR_INVALID, "state_bar x and v are required");
+    if (!sbar->rho || !sbar->u || (s->S && !sbar->S)) return fail(c, SPH_ERR_INVALID, "state_bar rho, u, S required");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  set_materials(c, &mt);
+  sph_params q = *p;
+  q.precision = SPH_FP64;
+  // forward evaluation in FP64: partner lists, T = sigma / rho^2 and c_s
+  StepBufs &B = c->st;
+  sph_derivs fwd;
+  memset(&fwd, 0, sizeof(fwd));
+  for (int k = 0; k < 3; ++k) {
+    fwd.dx[k] = B.d_x[0][k];
+    fwd.dv[k] = B.d_v[0][k];
+  }
+  fwd.drho = B.d_rho[0];
+  fwd.du = B.d_u[0];
+  fwd.dS = B.d_S[0];
+  fwd.ddmg = B.d_dmg[0];
+  fwd.n_act = B.d_nact[0];
+  tree_build(c, s, q.leaf_size, q.max_depth, st);
+  find_partners(c, s, st);
+  rhs_passes(c, s, mt, q, fwd, st);
+  rhs_adjoint(c, s, mt, q, *dbar, sbar, param_bar, st);
+  return finish(c, p, st, "sph_rhs_adjoint");
+}
+
+sph_status sph_pc_update(sph_ctx *c, const sph_state *base, const sph_derivs *d, const sph_material *mats,
+                         int32_t nmat, const sph_params *p, const double *dt, double frac, sph_state *out,
+                         void *stream) {
+  sph_status r = check_state(c, base);
+  if (r != SPH_OK) return r;
+  MatTable mt;
+  if ((r = check_params(c, base, mats, nmat, p, mt)) != SPH_OK) return r;
+  if (!d || !dt || !out) return fail(c, SPH_ERR_INVALID, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int ninst = base->ninst > 0 ? base->ninst : 1;
+  cudaMemcpyAsync(c->st.dt, dt, sizeof(double) * ninst, cudaMemcpyDeviceToDevice, st);
+  pc_update(c, base, out, *d, frac, mt, *p, st);
+  return finish(c, p, st, "sph_pc_update");
+}
+
+sph_status sph_pc_update_adjoint(sph_ctx *c, const sph_state *base, const sph_derivs *d, const sph_material *mats,
+                                 int32_t nmat, const sph_params *p, const double *dt, double frac,
+                                 const sph_state *out_bar, sph_state *base_bar, sph_derivs *d_bar, double *param_bar,
+                                 void *stream) {
+  sph_status r = check_state(c, base);
+  if (r != SPH_OK) return r;
+  MatTable mt;
+  if ((r = check_params(c, base, mats, nmat, p, mt)) != SPH_OK) return r;
+  if (!d || !dt || !out_bar || !base_bar || !d_bar) return fail(c, SPH_ERR_INVALID, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  pc_update_adjoint(c, base, *d, dt, frac, mt, *p, out_bar, base_bar, d_bar, param_bar, st);
+  return finish(c, p, st, "sph_pc_update_adjoint");
 }
 
 sph_status sph_get_tuning(const sph_ctx *c, sph_tuning *out) {

@@ -31,6 +31,7 @@
 // that rho - rho0 (the cold-expansion cancellation) is formed in FP64.
 #include <type_traits>
 
+#include "eos.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -242,101 +243,6 @@ __device__ void sym_eigen(int dim, R A[3][3], R w[3], R V[3][3]) {
     }
   }
   for (int i = 0; i < 3; ++i) w[i] = i < dim ? A[i][i] : R(0);
-}
-
-// Equation of state (Sect. 2.5) -> pressure and sound speed, in R and in the
-// units of the constants (SI in FP64 mode, code units in mixed mode).
-// Branch decisions and rho - rho0 (the cold-expansion cancellation) use the
-// SI doubles in every mode.
-template <class R>
-struct EosC {
-  R rho0, cs, K0, nM, A, B, E0, a, b, alpha, beta;
-  double iE, irho;  // SI -> code for specific energy and density
-};
-
-template <class R>
-__device__ __forceinline__ EosC<R> eos_consts(const sph_material &M, const float *mf, const Units *U);
-
-template <>
-__device__ __forceinline__ EosC<double> eos_consts<double>(const sph_material &M, const float *, const Units *) {
-  return EosC<double>{M.rho0, M.cs, M.K0, M.n_M, M.A_T, M.B_T, M.E0, M.a_T, M.b_T, M.alpha_T, M.beta_T, 1.0, 1.0};
-}
-template <>
-__device__ __forceinline__ EosC<float> eos_consts<float>(const sph_material &, const float *f, const Units *U) {
-  return EosC<float>{f[MF_RHO0], f[MF_CS], f[MF_K0], f[MF_NM], f[MF_AT], f[MF_BT], f[MF_E0], f[MF_AA], f[MF_BB],
-                     f[MF_ALPHA], f[MF_BETA], U->invE, U->invrho};
-}
-
-template <class R>
-__device__ void eos_eval(const sph_material &M, const EosC<R> &K, double rho_d, double u_d, R &p, R &cs) {
-  const double drho = rho_d - M.rho0;
-  const R chi = (R)(drho / M.rho0);
-  const R rho = (R)(rho_d * K.irho), u = (R)(u_d * K.iE), rho0 = K.rho0;
-  switch (M.eos) {
-    case SPH_EOS_LINEAR: {
-      p = K.cs * K.cs * (R)(drho * K.irho);
-      if (M.rho_cut > 0.0 && rho_d / M.rho0 < M.rho_cut) p = R(0);
-      cs = K.cs;
-      return;
-    }
-    case SPH_EOS_MURNAGHAN: {
-      // K0/n ((rho/rho0)^n - 1) = K0/n expm1(n log1p(chi)), accurate near rho0
-      R lg = log1p(chi);
-      p = K.K0 / K.nM * expm1(K.nM * lg);
-      cs = sqrt(K.K0 / rho0 * exp((K.nM - R(1)) * lg));
-      return;
-    }
-    case SPH_EOS_ISOTHERMAL: {
-      p = K.cs * K.cs * rho;
-      cs = K.cs;
-      return;
-    }
-    default:
-      break;
-  }
-  // Tillotson (Eqs. tillo1, tillo2)
-  const R A = K.A, B = K.B, E0 = K.E0, a = K.a, b = K.b;
-  const R eta = R(1) + chi;
-  const R w = R(1) + u / (E0 * eta * eta);
-  const R dw_drho = -R(2) * u / (E0 * eta * eta * eta * rho0);
-  const R dw_du = R(1) / (E0 * eta * eta);
-  // compressed / cold branch
-  const R kc = a + b / w;
-  const R pc = kc * rho * u + A * chi + B * chi * chi;
-  const R pcr = kc * u - b / (w * w) * dw_drho * rho * u + (A + R(2) * B * chi) / rho0;
-  const R pcu = kc * rho - b / (w * w) * dw_du * rho * u;
-  R pr, pu;
-  if (drho >= 0.0 || u_d <= M.E_iv) {
-    p = pc;
-    pr = pcr;
-    pu = pcu;
-  } else {
-    // expanded branch; z = rho0/rho - 1 = -chi/eta (density floored at 1e-3 rho0 inside the exponentials)
-    const bool floored = !(rho_d > 1e-3 * M.rho0);
-    const R z = floored ? R(999) : -chi / eta;
-    const R dz = floored ? R(0) : -rho0 / (rho * rho);
-    const R eb = exp(-K.beta * z), ea = exp(-K.alpha * z * z);
-    const R X = b * rho * u / w + A * chi * eb;
-    const R dX = b * u / w - b * rho * u / (w * w) * dw_drho + A / rho0 * eb + A * chi * eb * (-K.beta) * dz;
-    const R dY = ea * (-R(2) * K.alpha * z) * dz;
-    const R pe = a * rho * u + X * ea;
-    const R per = a * u + dX * ea + X * dY;
-    const R peu = a * rho + (b * rho / w - b * rho * u / (w * w) * dw_du) * ea;
-    if (u_d >= M.E_cv) {
-      p = pe;
-      pr = per;
-      pu = peu;
-    } else {
-      const R dE = (R)((M.E_cv - M.E_iv) * K.iE);
-      const R wu = (R)((u_d - M.E_iv) * K.iE), wl = (R)((M.E_cv - u_d) * K.iE);
-      p = (wu * pe + wl * pc) / dE;
-      pr = (wu * per + wl * pcr) / dE;
-      pu = ((pe - pc) + wu * peu + wl * pcu) / dE;
-    }
-  }
-  R c2 = pr + p / (rho * rho) * pu;
-  const R cmin = A / rho0;
-  cs = sqrt(c2 > cmin ? c2 : cmin);
 }
 
 // ---------------------------------------------------------------------------

@@ -141,6 +141,7 @@ struct sph_ctx {
   double *cs;
   double *p;
   double *ag;           // gravity acceleration, 3 * cap_n
+  double *adj_inter;    // adjoint scratch, 22 * cap_n
   sph::Units *units;    // device
   double vscale;        // host: velocity scale for the time unit
   sph::MatTable mt;     // host copy of the materials of the current call
@@ -273,6 +274,12 @@ void rhs_passes(sph_ctx *c, sph_state *s, const MatTable &mt, const sph_params &
 // gravity.cu
 void gravity_walk(sph_ctx *c, const sph_state *s, const sph_params &p, double *ax, double *ay, double *az,
                   cudaStream_t st);
+// adjoint.cu
+void rhs_adjoint(sph_ctx *c, const sph_state *s, const MatTable &mt, const sph_params &p, const sph_derivs &dbar,
+                 sph_state *sbar, double *param_bar, cudaStream_t st);
+void pc_update_adjoint(sph_ctx *c, const sph_state *base, const sph_derivs &d, const double *dt, double frac,
+                       const MatTable &mt, const sph_params &p, const sph_state *obar, sph_state *gbar,
+                       sph_derivs *fbar, double *param_bar, cudaStream_t st);
 // step.cu
 void timestep_reduce(sph_ctx *c, const sph_state *s, const sph_params &p, const sph_derivs &d, cudaStream_t st);
 void pc_update(sph_ctx *c, const sph_state *base, sph_state *out, const sph_derivs &d, double frac,

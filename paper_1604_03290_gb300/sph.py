@@ -101,13 +101,21 @@ def lib():
             L.sph_measure_fma_peak.argtypes = [C.c_int32, C.POINTER(C.c_double)]
             L.sph_profile_enable.argtypes = [_vp, C.c_int32]
             L.sph_profile_read.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_int32]
+            L.sph_rhs_adjoint.argtypes = [_vp, C.POINTER(State), C.POINTER(Material), C.c_int32, C.POINTER(Params),
+                                          C.POINTER(Derivs), C.POINTER(State), _vp, _vp]
+            L.sph_pc_update.argtypes = [_vp, C.POINTER(State), C.POINTER(Derivs), C.POINTER(Material), C.c_int32,
+                                        C.POINTER(Params), _vp, C.c_double, C.POINTER(State), _vp]
+            L.sph_pc_update_adjoint.argtypes = [_vp, C.POINTER(State), C.POINTER(Derivs), C.POINTER(Material),
+                                                C.c_int32, C.POINTER(Params), _vp, C.c_double, C.POINTER(State),
+                                                C.POINTER(State), C.POINTER(Derivs), _vp, _vp]
             L.sph_get_tuning.argtypes = [_vp, C.POINTER(Tuning)]
             L.sph_set_tuning.argtypes = [_vp, C.POINTER(Tuning)]
             L.sph_launch_count.argtypes = []
             L.sph_launch_count.restype = C.c_int64
             for f in ("sph_create", "sph_sync_status", "sph_build_tree", "sph_tree_nodes", "sph_neighbours",
                       "sph_rhs", "sph_gravity", "sph_step", "sph_measure_fma_peak", "sph_profile_enable",
-                      "sph_profile_read", "sph_get_tuning", "sph_set_tuning"):
+                      "sph_profile_read", "sph_get_tuning", "sph_set_tuning", "sph_rhs_adjoint", "sph_pc_update",
+                      "sph_pc_update_adjoint"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -260,6 +268,30 @@ class DeviceState:
         s.inst_off = _ptr(self.inst_off) if self.ninst > 1 else None
         return s
 
+    def clone(self):
+        """A copy of the evolving fields (x, v, rho, u, S, dmg) sharing the constant ones."""
+        c = object.__new__(DeviceState)
+        c.__dict__.update(self.__dict__)
+        for k in ("x", "v", "rho", "u", "S", "dmg"):
+            t = getattr(self, k)
+            setattr(c, k, None if t is None else t.clone())
+        return c
+
+    def copy_from(self, other):
+        for k in ("x", "v", "rho", "u", "S", "dmg"):
+            t = getattr(self, k)
+            if t is not None:
+                t.copy_(getattr(other, k))
+
+    def zeros_like(self):
+        """Same layout, evolving fields set to zero (a cotangent container)."""
+        c = self.clone()
+        for k in ("x", "v", "rho", "u", "S", "dmg"):
+            t = getattr(c, k)
+            if t is not None:
+                t.zero_()
+        return c
+
     def to_numpy(self):
         g = lambda t: None if t is None else t.detach().cpu().numpy()
         return {"x": g(self.x), "v": g(self.v), "rho": g(self.rho), "u": g(self.u), "S": g(self.S),
@@ -355,6 +387,39 @@ def step(ctx: Context, ds: DeviceState, materials, params: wl.Params, nsteps: in
 
 def launch_count() -> int:
     return int(lib().sph_launch_count())
+
+
+def rhs_adjoint(ctx: Context, ds: DeviceState, materials, params: wl.Params, dbar, sbar: DeviceState,
+                param_bar=None, check=True, stream=None):
+    """Adds the cotangents of x, v, rho, u, S (into sbar) and of the material
+    parameters (into param_bar, shape (ninst, nmat, 3): mu, Y0, K) given the
+    cotangents dbar of the right-hand side's outputs (dict like alloc_derivs)."""
+    st, sb = ds.struct(), sbar.struct()
+    P = params_struct(params, check)
+    d = derivs_struct(dbar)
+    M = materials_array(materials)
+    ctx.check(ctx._lib.sph_rhs_adjoint(ctx.h, C.byref(st), M, len(materials), C.byref(P), C.byref(d), C.byref(sb),
+                                       _ptr(param_bar), _stream(stream)), "sph_rhs_adjoint")
+
+
+def pc_update(ctx: Context, base: DeviceState, d, materials, params: wl.Params, dt, frac, out: DeviceState,
+              check=True, stream=None):
+    sb, so = base.struct(), out.struct()
+    P = params_struct(params, check)
+    M = materials_array(materials)
+    ctx.check(ctx._lib.sph_pc_update(ctx.h, C.byref(sb), C.byref(derivs_struct(d)), M, len(materials), C.byref(P),
+                                     _ptr(dt), float(frac), C.byref(so), _stream(stream)), "sph_pc_update")
+
+
+def pc_update_adjoint(ctx: Context, base: DeviceState, d, materials, params: wl.Params, dt, frac,
+                      out_bar: DeviceState, base_bar: DeviceState, d_bar, param_bar=None, check=True, stream=None):
+    sb, ob, bb = base.struct(), out_bar.struct(), base_bar.struct()
+    P = params_struct(params, check)
+    M = materials_array(materials)
+    ctx.check(ctx._lib.sph_pc_update_adjoint(ctx.h, C.byref(sb), C.byref(derivs_struct(d)), M, len(materials),
+                                             C.byref(P), _ptr(dt), float(frac), C.byref(ob), C.byref(bb),
+                                             C.byref(derivs_struct(d_bar)), _ptr(param_bar), _stream(stream)),
+              "sph_pc_update_adjoint")
 
 
 def measure_fma_peak(precision="mixed"):
