@@ -182,6 +182,40 @@ sph_status sph_tree_nodes(sph_ctx *ctx, int64_t cap, int32_t *level, int64_t *ce
 sph_status sph_neighbours(sph_ctx *ctx, const sph_state *state, int32_t leaf_size, int32_t max_depth,
                           int64_t *nb_offset, int32_t *nb_index, int64_t nb_capacity, void *stream);
 
+/* Bytes of the fixed device scratch behind sph_neighbours_static (64 MiB). */
+#define SPH_STATIC_SCRATCH_BYTES (64LL << 20)
+
+/* sph_neighbours without a context, for callers that may not allocate
+ * device memory: a plug-in whose host application owns the device memory
+ * and hands libraries only the buffers they work on, or a real-time loop
+ * with a memory budget fixed at start-up, where cudaMalloc can fail or
+ * cudaFree would stall every stream of the device.  The paper has no
+ * counterpart; this is a packaging of the partner search above.
+ *
+ * Same state, leaf_size, max_depth, outputs (nb_offset, nb_index,
+ * nb_capacity), partner lists and error codes as sph_neighbours, with
+ * max_neighbours the per-particle limit a context would hold.  The tree,
+ * packed positions and partner columns live in one array of
+ * SPH_STATIC_SCRATCH_BYTES bytes inside the library's device code; every
+ * device that loads the library holds it until the process exits.  A call
+ * needs about 570 + 4 * max_neighbours bytes per particle and at least
+ * 0.9 MiB, so the array holds about 60 000 particles at max_neighbours =
+ * 128; larger n returns SPH_ERR_CAPACITY, before touching the device, with a
+ * message that gives the bytes needed.  The call itself allocates nothing:
+ * no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and keeps it; make that
+ * first call before any stream capture.  All calls on a device share the
+ * array and it keeps the last call's contents (each call clears its own error
+ * word): calls whose work overlaps on the GPU, from two streams or two host
+ * threads, race and corrupt each other's results, so serialise them.  Blocks
+ * on `stream` at the end to read the error word.  msg (host, msg_len bytes,
+ * may be NULL) receives the error message, or "" on success. */
+sph_status sph_neighbours_static(const sph_state *state, int32_t leaf_size, int32_t max_depth,
+                                 int32_t max_neighbours, int64_t *nb_offset, int32_t *nb_index,
+                                 int64_t nb_capacity, char *msg, int32_t msg_len, void *stream);
+
 /* One right-hand side: tree, partners, (density sum), the neighbour pass for
  * continuity / velocity gradient / XSPH, the per-particle constitutive update
  * (EOS, Hooke + Jaumann, yield, damage, artificial stress), the momentum and

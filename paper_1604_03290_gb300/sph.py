@@ -96,6 +96,8 @@ def lib():
             L.sph_rhs.argtypes = [_vp, C.POINTER(State), C.POINTER(Material), C.c_int32, C.POINTER(Params),
                                   C.POINTER(Derivs), _vp]
             L.sph_gravity.argtypes = [_vp, C.POINTER(State), C.POINTER(Params), _vp, _vp, _vp, _vp]
+            L.sph_neighbours_static.argtypes = [C.POINTER(State), C.c_int32, C.c_int32, C.c_int32, _vp, _vp,
+                                                C.c_int64, C.c_char_p, C.c_int32, _vp]
             L.sph_step.argtypes = [_vp, C.POINTER(State), C.POINTER(Material), C.c_int32, C.POINTER(Params), _vp,
                                    C.c_int32, _vp]
             L.sph_measure_fma_peak.argtypes = [C.c_int32, C.POINTER(C.c_double)]
@@ -113,6 +115,7 @@ def lib():
             L.sph_launch_count.argtypes = []
             L.sph_launch_count.restype = C.c_int64
             for f in ("sph_create", "sph_sync_status", "sph_build_tree", "sph_tree_nodes", "sph_neighbours",
+                      "sph_neighbours_static",
                       "sph_rhs", "sph_gravity", "sph_step", "sph_measure_fma_peak", "sph_profile_enable",
                       "sph_profile_read", "sph_get_tuning", "sph_set_tuning", "sph_rhs_adjoint", "sph_pc_update",
                       "sph_pc_update_adjoint"):
@@ -351,6 +354,24 @@ def neighbours(ctx: Context, ds: DeviceState, leaf_size=16, max_depth=21, capaci
     st = ds.struct()
     ctx.check(ctx._lib.sph_neighbours(ctx.h, C.byref(st), int(leaf_size), int(max_depth), _ptr(off), _ptr(idx),
                                       int(cap), _stream(stream)), "sph_neighbours")
+    return off, idx[: int(off[-1].item())]
+
+
+def neighbours_static(ds: DeviceState, leaf_size=16, max_depth=21, max_neighbours=128, capacity=None,
+                      stream=None):
+    """Partner lists as ``neighbours`` gives them, through the entry point that
+    allocates no device memory (its scratch is a fixed array in the library).
+    The output tensors here are allocated by the caller (this function)."""
+    L = lib()
+    cap = capacity if capacity is not None else ds.n * max_neighbours
+    off = torch.zeros(ds.n + 1, dtype=torch.int64, device=ds.x.device)
+    idx = torch.zeros(max(cap, 1), dtype=torch.int32, device=ds.x.device)
+    st = ds.struct()
+    msg = C.create_string_buffer(512)
+    r = L.sph_neighbours_static(C.byref(st), int(leaf_size), int(max_depth), int(max_neighbours), _ptr(off),
+                                _ptr(idx), int(cap), msg, len(msg), _stream(stream))
+    if r != SPH_OK:
+        raise SphError(r, "sph_neighbours_static: %s" % msg.value.decode())
     return off, idx[: int(off[-1].item())]
 
 
