@@ -98,6 +98,7 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   T.scan_tmp = ctx_alloc<int32_t>(c, (std::max(N, T.cap_nodes) + 1) / 4096 + 2, ok);
   const int64_t cn = T.cap_nodes;
   T.nnodes = ctx_alloc<int32_t>(c, 1, ok);
+  T.nleaf = ctx_alloc<int32_t>(c, 1, ok);
   T.first = ctx_alloc<int32_t>(c, cn, ok);
   T.end = ctx_alloc<int32_t>(c, cn, ok);
   T.skip = ctx_alloc<int32_t>(c, cn, ok);
@@ -120,6 +121,7 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   T.inst_bb = ctx_alloc<unsigned long long>(c, 6 * ci, ok);
   T.inst_lo = ctx_alloc<double>(c, 3 * ci, ok);
   T.inst_s0 = ctx_alloc<double>(c, ci, ok);
+  T.inst_rs0 = ctx_alloc<double>(c, ci, ok);
   T.inst_root = ctx_alloc<int32_t>(c, ci, ok);
   T.gcnt = ctx_alloc<int32_t>(c, cn + 1, ok);
   T.gstart = ctx_alloc<int32_t>(c, cn + 1, ok);

@@ -1,6 +1,9 @@
 // Equations of state shared by the right-hand side and its adjoint.
 #pragma once
 
+#include <type_traits>
+
+#include "fpbits.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -31,9 +34,24 @@ __device__ __forceinline__ EosC<float> eos_consts<float>(const sph_material &, c
 template <class R>
 __device__ void eos_eval(const sph_material &M, const EosC<R> &K, double rho_d, double u_d, R &p, R &cs,
                          R *pr_out = nullptr, R *pu_out = nullptr) {
+  constexpr bool F32 = std::is_same<R, float>::value;
   const double drho = rho_d - M.rho0;
-  const R chi = (R)(drho / M.rho0);
-  const R rho = (R)(rho_d * K.irho), u = (R)(u_d * K.iE), rho0 = K.rho0;
+  R chi, rho, u;
+  const R rho0 = K.rho0;
+  int kE = 0;
+  if constexpr (F32) {
+    // code-unit views by exponent shifts (the units are powers of two); chi
+    // from the FP64 difference, in FP32
+    const int kr = pow2_exp(K.irho);
+    kE = pow2_exp(K.iE);
+    rho = to_f32_scaled(rho_d, kr, K.irho);
+    u = to_f32_scaled(u_d, kE, K.iE);
+    chi = __fdiv_rn(to_f32_scaled(drho, kr, K.irho), rho0);
+  } else {
+    chi = (R)(drho / M.rho0);
+    rho = (R)(rho_d * K.irho);
+    u = (R)(u_d * K.iE);
+  }
   switch (M.eos) {
     case SPH_EOS_LINEAR: {
       p = K.cs * K.cs * (R)(drho * K.irho);
@@ -79,13 +97,14 @@ __device__ void eos_eval(const sph_material &M, const EosC<R> &K, double rho_d, 
   const R pcr = kc * u - b / (w * w) * dw_drho * rho * u + (A + R(2) * B * chi) / rho0;
   const R pcu = kc * rho - b / (w * w) * dw_du * rho * u;
   R pr, pu;
-  if (drho >= 0.0 || u_d <= M.E_iv) {
+  const bool cold = F32 ? (nonneg_bits(drho) || le_bits(u_d, M.E_iv)) : (drho >= 0.0 || u_d <= M.E_iv);
+  if (cold) {
     p = pc;
     pr = pcr;
     pu = pcu;
   } else {
     // expanded branch; z = rho0/rho - 1 = -chi/eta (density floored at 1e-3 rho0 inside the exponentials)
-    const bool floored = !(rho_d > 1e-3 * M.rho0);
+    const bool floored = F32 ? le_bits(rho_d, 1e-3 * M.rho0) : !(rho_d > 1e-3 * M.rho0);
     const R z = floored ? R(999) : -chi / eta;
     const R dz = floored ? R(0) : -rho0 / (rho * rho);
     const R eb = exp(-K.beta * z), ea = exp(-K.alpha * z * z);
@@ -95,13 +114,21 @@ __device__ void eos_eval(const sph_material &M, const EosC<R> &K, double rho_d, 
     const R pe = a * rho * u + X * ea;
     const R per = a * u + dX * ea + X * dY;
     const R peu = a * rho + (b * rho / w - b * rho * u / (w * w) * dw_du) * ea;
-    if (u_d >= M.E_cv) {
+    if (F32 ? le_bits(M.E_cv, u_d) : u_d >= M.E_cv) {
       p = pe;
       pr = per;
       pu = peu;
     } else {
-      const R dE = (R)((M.E_cv - M.E_iv) * K.iE);
-      const R wu = (R)((u_d - M.E_iv) * K.iE), wl = (R)((M.E_cv - u_d) * K.iE);
+      R dE, wu, wl;
+      if constexpr (F32) {
+        dE = to_f32_scaled(M.E_cv - M.E_iv, kE, K.iE);
+        wu = to_f32_scaled(u_d - M.E_iv, kE, K.iE);
+        wl = to_f32_scaled(M.E_cv - u_d, kE, K.iE);
+      } else {
+        dE = (R)((M.E_cv - M.E_iv) * K.iE);
+        wu = (R)((u_d - M.E_iv) * K.iE);
+        wl = (R)((M.E_cv - u_d) * K.iE);
+      }
       p = (wu * pe + wl * pc) / dE;
       pr = (wu * per + wl * pcr) / dE;
       pu = ((pe - pc) + wu * peu + wl * pcu) / dE;

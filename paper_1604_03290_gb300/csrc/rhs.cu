@@ -32,6 +32,7 @@
 #include <type_traits>
 
 #include "eos.cuh"
+#include "fpbits.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -67,6 +68,18 @@ __device__ __forceinline__ float rsqrt_or_zero<float>(float r2) {
 template <>
 __device__ __forceinline__ double rsqrt_or_zero<double>(double r2) {
   return r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
+}
+
+// 1 / x, correctly rounded: the same value as the division
+template <class R>
+__device__ __forceinline__ R rcp_rn(R x);
+template <>
+__device__ __forceinline__ float rcp_rn<float>(float x) {
+  return __frcp_rn(x);
+}
+template <>
+__device__ __forceinline__ double rcp_rn<double>(double x) {
+  return __drcp_rn(x);
 }
 
 // ---------------------------------------------------------------------------
@@ -133,18 +146,18 @@ struct Own<true> {
 // ---------------------------------------------------------------------------
 // Density by kernel sum (Eq. density_by_kernel_sum) including m_a W(0; h_a).
 // ---------------------------------------------------------------------------
-template <bool MIXED>
+template <bool MIXED, int DIM>
 __global__ void __launch_bounds__(128) k_density_sum(RhsArgs A) {
   using R = typename std::conditional<MIXED, float, double>::type;
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= A.n) return;
   Own<MIXED> o;
   o.load(A, a);
-  const int dim = A.dim;
+  constexpr int dim = DIM;
   const R sig = kernel_sigma<R>(dim);
   KahanT<R> sum;
   {
-    R hinv = R(1) / (R)o.h;
+    R hinv = rcp_rn((R)o.h);
     sum.add((R)o.m * sig * hpow(hinv, dim));
   }
   const int cnt = A.nb_cnt[a];
@@ -154,7 +167,7 @@ __global__ void __launch_bounds__(128) k_density_sum(RhsArgs A) {
     o.pair(A, b, d, w, hb, rhob, mb, vol);
     R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     R r = r2 * rsqrt_or_zero(r2);
-    R hinv = R(1) / (R(0.5) * ((R)o.h + hb));
+    R hinv = rcp_rn(R(0.5) * ((R)o.h + hb));
     sum.add(mb * kern_W(r * hinv, sig * hpow(hinv, dim)));
   }
   A.rho_out[a] = sum.value() * (MIXED ? A.U->rho : 1.0);
@@ -172,7 +185,7 @@ __device__ __forceinline__ R det_of(int dim, const R M[3][3]) {
 
 // C = L^-1 by cofactors; identity when L is (nearly) singular.
 template <class R>
-__device__ void correction_tensor(int dim, const R L[3][3], bool enable, R C[3][3]) {
+__device__ __forceinline__ void correction_tensor(int dim, const R L[3][3], bool enable, R C[3][3]) {
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) C[i][j] = i == j ? R(1) : R(0);
   if (!enable) return;
@@ -180,7 +193,7 @@ __device__ void correction_tensor(int dim, const R L[3][3], bool enable, R C[3][
   R diag = R(1);
   for (int i = 0; i < dim; ++i) diag *= fabs(L[i][i]);
   if (!(fabs(det) > R(1e-8) * diag) || !(diag > R(0))) return;
-  R inv = R(1) / det;
+  R inv = rcp_rn(det);
   if (dim == 2) {
     C[0][0] = L[1][1] * inv;
     C[0][1] = -L[0][1] * inv;
@@ -226,7 +239,7 @@ __device__ __forceinline__ void jacobi_rotate(int p, int q, R A[3][3], R V[3][3]
 }
 
 template <class R>
-__device__ void sym_eigen(int dim, R A[3][3], R w[3], R V[3][3]) {
+__device__ __forceinline__ void sym_eigen(int dim, R A[3][3], R w[3], R V[3][3]) {
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) V[i][j] = i == j ? R(1) : R(0);
   if (dim == 2) {
@@ -248,12 +261,12 @@ __device__ void sym_eigen(int dim, R A[3][3], R w[3], R V[3][3]) {
 // ---------------------------------------------------------------------------
 // Pass A + per-particle update
 // ---------------------------------------------------------------------------
-template <bool MIXED>
+template <bool MIXED, int DIM>
 __global__ void __launch_bounds__(128) k_passA(RhsArgs A) {
   using R = typename std::conditional<MIXED, float, double>::type;
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= A.n) return;
-  const int dim = A.dim;
+  constexpr int dim = DIM;
   const sph_params &P = A.prm;
   Own<MIXED> o;
   o.load(A, a);
@@ -272,7 +285,7 @@ __global__ void __launch_bounds__(128) k_passA(RhsArgs A) {
     const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     const R rinv = rsqrt_or_zero(r2);
     const R r = r2 * rinv;
-    const R hinv = R(1) / (R(0.5) * (ha + hb));
+    const R hinv = rcp_rn(R(0.5) * (ha + hb));
     const R q = r * hinv;
     const R hD = hpow(hinv, dim);
     const R fr = kern_dW(q, R(6) * sig * hD * hinv) * rinv;
@@ -322,7 +335,13 @@ __global__ void __launch_bounds__(128) k_passA(RhsArgs A) {
   const bool strength = A.S != nullptr && M.strength;
   if (strength) {
     for (int i = 0; i < dim; ++i)
-      for (int j = 0; j < dim; ++j) S[i][j] = (R)(A.S[(int64_t)symk(dim, i, j) * A.n + a] * f_sig);
+      for (int j = 0; j < dim; ++j) {
+        const double sv = A.S[(int64_t)symk(dim, i, j) * A.n + a];
+        if constexpr (MIXED)
+          S[i][j] = to_f32_scaled(sv, pow2_exp(f_sig), f_sig);
+        else
+          S[i][j] = sv;
+      }
     // von Mises: f_Y = min(Y0^2 / (3 J2), 1)
     if (M.Y0 > 0.0) {
       R J2 = R(0);
@@ -349,7 +368,12 @@ __global__ void __launch_bounds__(128) k_passA(RhsArgs A) {
           R Rkj = R(0.5) * (gv[k][j] - gv[j][k]);
           rot += Rik * S[k][j] - S[i][k] * Rkj;
         }
-        A.dS[(int64_t)symk(dim, i, j) * A.n + a] = (double)(mu2 * ed + rot) * (MIXED ? A.U->sig * A.U->invT : 1.0);
+        if constexpr (MIXED) {
+          const double us = A.U->sig * A.U->invT;
+          A.dS[(int64_t)symk(dim, i, j) * A.n + a] = to_f64_scaled(mu2 * ed + rot, pow2_exp(us), us);
+        } else {
+          A.dS[(int64_t)symk(dim, i, j) * A.n + a] = mu2 * ed + rot;
+        }
       }
   } else if (A.S != nullptr && A.dS != nullptr) {
     for (int k = 0; k < ns; ++k) A.dS[(int64_t)k * A.n + a] = 0.0;
@@ -415,7 +439,7 @@ __global__ void __launch_bounds__(128) k_passA(RhsArgs A) {
       }
   }
   // outputs
-  const R irr = R(1) / rr;
+  const R irr = rcp_rn(rr);
   R T[6], Zc[6];
   for (int i = 0; i < dim; ++i)
     for (int j = i; j < dim; ++j) {
@@ -442,16 +466,30 @@ __global__ void __launch_bounds__(128) k_passA(RhsArgs A) {
     }
     A.csd[a] = cs;
   }
-  const double u_drho = MIXED ? A.U->rho * A.U->invT : 1.0, u_v = MIXED ? A.U->V : 1.0;
-  const double u_t = MIXED ? A.U->invT : 1.0, u_sig = MIXED ? A.U->sig : 1.0;
-  if (A.drho) A.drho[a] = P.density_sum ? 0.0 : (double)rhoa * drho.value() * u_drho;
-  for (int ax = 0; ax < dim; ++ax)
-    if (A.dx[ax]) A.dx[ax][a] = A.v[ax][a] + P.xsph * (double)xs[ax] * u_v;
-  if (A.ddmg) A.ddmg[a] = (double)ddel * u_t;
+  if constexpr (MIXED) {
+    // back to SI by exponent shifts (the code units are powers of two); the
+    // product rho_a * sum is formed exactly as a float pair
+    const double u_drho = A.U->rho * A.U->invT, u_v = A.U->V, u_t = A.U->invT, u_sig = A.U->sig;
+    const int k_drho = pow2_exp(u_drho), k_v = pow2_exp(u_v), k_t = pow2_exp(u_t), k_sig = pow2_exp(u_sig);
+    if (A.drho) {
+      const float sum = drho.value(), hi = rhoa * sum, lo = fmaf(rhoa, sum, -hi);
+      A.drho[a] = P.density_sum ? 0.0 : to_f64_scaled(hi, k_drho, u_drho) + to_f64_scaled(lo, k_drho, u_drho);
+    }
+    for (int ax = 0; ax < dim; ++ax)
+      if (A.dx[ax]) A.dx[ax][a] = A.v[ax][a] + P.xsph * to_f64_scaled(xs[ax], k_v, u_v);
+    if (A.ddmg) A.ddmg[a] = to_f64_scaled(ddel, k_t, u_t);
+    if (A.p_out) A.p_out[a] = to_f64_scaled(p, k_sig, u_sig);
+    if (A.cs_out) A.cs_out[a] = to_f64_scaled(cs, k_v, u_v);
+  } else {
+    if (A.drho) A.drho[a] = P.density_sum ? 0.0 : rhoa * drho.value();
+    for (int ax = 0; ax < dim; ++ax)
+      if (A.dx[ax]) A.dx[ax][a] = A.v[ax][a] + P.xsph * xs[ax];
+    if (A.ddmg) A.ddmg[a] = ddel;
+    if (A.p_out) A.p_out[a] = p;
+    if (A.cs_out) A.cs_out[a] = cs;
+  }
   if (A.nact) A.nact[a] = nact;
   if (A.nnb) A.nnb[a] = cnt;
-  if (A.p_out) A.p_out[a] = (double)p * u_sig;
-  if (A.cs_out) A.cs_out[a] = (double)cs * u_v;
 }
 
 // ---------------------------------------------------------------------------
@@ -514,12 +552,13 @@ __device__ __forceinline__ R ipow(R f, R n) {
   return pow(f, n);
 }
 
-template <bool MIXED, bool AS>
+template <bool MIXED, bool AS, int DIM>
 __global__ void __launch_bounds__(128) k_passB(RhsArgs A) {
   using R = typename std::conditional<MIXED, float, double>::type;
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= A.n) return;
-  const int dim = A.dim, ns = nsym(dim);
+  constexpr int dim = DIM;
+  const int ns = nsym(dim);
   const sph_params &P = A.prm;
   Own<MIXED> o;
   o.load(A, a);
@@ -542,7 +581,7 @@ __global__ void __launch_bounds__(128) k_passB(RhsArgs A) {
     const R rinv = rsqrt_or_zero(r2);
     const R r = r2 * rinv;
     const R hab = R(0.5) * (ha + hb);
-    const R hinv = R(1) / hab;
+    const R hinv = rcp_rn(hab);
     const R q = r * hinv;
     const R hD = hpow(hinv, dim);
     const R fr = kern_dW(q, R(6) * sig * hD * hinv) * rinv;
@@ -573,13 +612,23 @@ __global__ void __launch_bounds__(128) k_passB(RhsArgs A) {
     for (int i = 0; i < dim; ++i) acc[i].add(mb * sv[i]);
     du.add(R(-0.5) * mb * (w[0] * su[0] + w[1] * su[1] + w[2] * su[2]));
   }
-  const double u_acc = MIXED ? A.U->acc : 1.0, u_du = MIXED ? A.U->E * A.U->invT : 1.0;
-  for (int ax = 0; ax < dim; ++ax) {
-    double v = acc[ax].value() * u_acc;
-    if (A.ag) v += A.ag[(int64_t)ax * A.ld + a];
-    A.dv[ax][a] = v;
+  if constexpr (MIXED) {
+    const double u_acc = A.U->acc, u_du = A.U->E * A.U->invT;
+    const int k_acc = pow2_exp(u_acc), k_du = pow2_exp(u_du);
+    for (int ax = 0; ax < dim; ++ax) {
+      double v = to_f64_scaled(acc[ax].value(), k_acc, u_acc);
+      if (A.ag) v += A.ag[(int64_t)ax * A.ld + a];
+      A.dv[ax][a] = v;
+    }
+    if (A.du) A.du[a] = to_f64_scaled(du.value(), k_du, u_du);
+  } else {
+    for (int ax = 0; ax < dim; ++ax) {
+      double v = acc[ax].value();
+      if (A.ag) v += A.ag[(int64_t)ax * A.ld + a];
+      A.dv[ax][a] = v;
+    }
+    if (A.du) A.du[a] = du.value();
   }
-  if (A.du) A.du[a] = du.value() * u_du;
 }
 
 // ---------------------------------------------------------------------------
@@ -590,9 +639,12 @@ __global__ void k_repack_rho(const double *__restrict__ rho, const double *__res
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float4 v = pk.pv[i], w = pk.pvl[i];
-  const double r = rho[i] * U->invrho;
-  v.w = __double2float_rn(r);
-  w.w = __double2float_rn(m[i] * U->invM / r);
+  // as in the packing after the tree build: rho scaled by its power-of-two
+  // unit, and the volume m / rho from the FP32 views
+  float rf;
+  if (!f32_rn_scaled(rho[i], pow2_exp(U->invrho), rf)) rf = __double2float_rn(rho[i] * U->invrho);
+  v.w = rf;
+  w.w = __fdiv_rn(pk.pxl[i].w, rf);
   pk.pv[i] = v;
   pk.pvl[i] = w;
 }
@@ -647,26 +699,34 @@ void rhs_passes(sph_ctx *c, sph_state *s, const MatTable &mt, const sph_params &
   const bool mixed = p.precision == SPH_MIXED;
   const int T = c->tune.pass_threads;
   int pr = -1;
+  const bool d3 = s->dim == 3;
+#define SPH_LAUNCH(kern, ...)                                                     \
+  do {                                                                            \
+    if (d3) kern<__VA_ARGS__, 3><<<nblk(n, T), T, 0, st>>>(A);                   \
+    else kern<__VA_ARGS__, 2><<<nblk(n, T), T, 0, st>>>(A);                      \
+    ++sph::g_launches;                                                            \
+  } while (0)
   if (p.density_sum) {
     pr = prof_begin(c, st, PH_DENSITY);
-    if (mixed) { k_density_sum<true><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
-    else { k_density_sum<false><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    if (mixed) SPH_LAUNCH(k_density_sum, true);
+    else SPH_LAUNCH(k_density_sum, false);
     { k_repack_rho<<<nblk(n, 256), 256, 0, st>>>(s->rho, s->m, c->pk, n, c->units); ++sph::g_launches; }
     prof_end(c, st, pr);
   }
   pr = prof_begin(c, st, PH_PASSA);
-  if (mixed) { k_passA<true><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
-  else { k_passA<false><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+  if (mixed) SPH_LAUNCH(k_passA, true);
+  else SPH_LAUNCH(k_passA, false);
   prof_end(c, st, pr);
   const bool as = p.eps_s > 0.0;
   pr = prof_begin(c, st, PH_PASSB);
   if (mixed) {
-    if (as) { k_passB<true, true><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
-    else { k_passB<true, false><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    if (as) SPH_LAUNCH(k_passB, true, true);
+    else SPH_LAUNCH(k_passB, true, false);
   } else {
-    if (as) { k_passB<false, true><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
-    else { k_passB<false, false><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    if (as) SPH_LAUNCH(k_passB, false, true);
+    else SPH_LAUNCH(k_passB, false, false);
   }
+#undef SPH_LAUNCH
   prof_end(c, st, pr);
 }
 

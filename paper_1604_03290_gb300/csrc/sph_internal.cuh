@@ -52,8 +52,10 @@ struct Tree {
   int64_t hist_cap;
   int32_t *perm;       // sorted slot -> state index (points into vals[*])
   unsigned long long *skey;  // sorted keys (points into keys[*])
-  // per-slot node emission counts and their exclusive scan
+  // per-slot node emission counts and their exclusive scan; after the scan
+  // ncount holds the list of leaf ids (nleaf of them, in no fixed order)
   int32_t *ncount;
+  int32_t *nleaf;      // device scalar
   int32_t *nstart;
   int32_t *scan_tmp;
   // nodes (pre-order)
@@ -73,6 +75,7 @@ struct Tree {
   unsigned long long *inst_bb;  // 6 per instance: encoded min xyz, encoded max xyz
   double *inst_lo;     // 3 per instance
   double *inst_s0;
+  double *inst_rs0;    // 1 / s0, correctly rounded
   int32_t *inst_root;
   // walk groups: up to 32 consecutive slots inside one tree cell
   int32_t *gcnt, *gstart;  // per node: groups it starts, and their exclusive scan (cap_nodes + 1)

@@ -69,6 +69,7 @@ void layout(sph_ctx *c, Carve &k, int64_t n, int ninst, int leaf_size, int kmax)
   const int64_t cn = T.cap_nodes;
   T.scan_tmp = k.take<int32_t>((std::max(N, cn) + 1) / 4096 + 2);
   T.nnodes = k.take<int32_t>(1);
+  T.nleaf = k.take<int32_t>(1);
   T.first = k.take<int32_t>(cn);
   T.end = k.take<int32_t>(cn);
   T.skip = k.take<int32_t>(cn);
@@ -90,6 +91,7 @@ void layout(sph_ctx *c, Carve &k, int64_t n, int ninst, int leaf_size, int kmax)
   T.inst_bb = k.take<unsigned long long>(6 * (int64_t)ninst);
   T.inst_lo = k.take<double>(3 * (int64_t)ninst);
   T.inst_s0 = k.take<double>(ninst);
+  T.inst_rs0 = k.take<double>(ninst);
   T.inst_root = k.take<int32_t>(ninst);
   T.gcnt = k.take<int32_t>(cn + 1);
   T.gstart = k.take<int32_t>(cn + 1);

@@ -8,6 +8,7 @@
 //   component and d^1/3 (the paper's sqrt(q^2 / dq^2) with a floor so that a
 //   quantity starting at zero does not force dt = 0), capped at dt_max.
 // The acceleration limit takes the square root that makes it a time.
+#include "fpbits.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -26,7 +27,161 @@ struct DtArgs {
   int ninst;
   sph_params prm;
   unsigned long long *enc;
+  // FP32 copies of the constants, for the screening below
+  float f_courant, f_accel, f_quantity, f_u_floor, f_S_floor, f_dmg_floor, f_dt_max;
 };
+
+// FP32 view of a double for screening, built from its bits on the integer
+// pipe: the top 23 mantissa bits (truncated: relative error below 2^-23).
+// Outside 2^-60 <= |v| <= 2^60 (zero excepted) the view is not trusted and
+// `risky` is set; squares and quotients of trusted views stay in FP32's
+// normal range.
+__device__ __forceinline__ float screen_f32(double v, bool &risky) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  if ((b << 1) == 0ULL) return 0.f;
+  const unsigned hi = (unsigned)(b >> 32);
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  if (e < 1023 - 60 || e > 1023 + 60) {
+    risky = true;
+    return 0.f;
+  }
+  const unsigned mant = ((hi & 0xfffffu) << 3) | ((unsigned)b >> 29);
+  return __uint_as_float((hi & 0x80000000u) | ((unsigned)(e - 1023 + 127) << 23) | mant);
+}
+
+__device__ __forceinline__ bool bits_nonzero(double v) { return ((unsigned long long)__double_as_longlong(v) << 1) != 0ULL; }
+
+// The limits of one particle.  Every limit is first estimated in FP32 (within
+// about 1e-6 relative); the FP64 expression is then evaluated only for limits
+// whose estimate lies within 2^-12 of the smallest estimate, or whose inputs
+// the FP32 view does not trust.  Any limit skipped is larger than the one that
+// wins, so the minimum equals the all-FP64 minimum bit for bit, at about one
+// FP64 division per particle instead of eleven.
+__device__ double particle_dt(const DtArgs &A, int64_t a) {
+  const sph_params &P = A.prm;
+  const float inf = __int_as_float(0x7f800000);
+  float est[11];
+  unsigned risky = 0;
+  const double h = A.h[a], cs = A.cs[a];
+  bool r = false;
+  const float hf = screen_f32(h, r);
+  {
+    bool rc = r;
+    const float csf = screen_f32(cs, rc);
+    est[0] = (long long)__double_as_longlong(cs) > 0 ? A.f_courant * hf * __frcp_rn(csf) : inf;
+    if (rc) risky |= 1u;
+  }
+  double dvd[3] = {0.0, 0.0, 0.0};
+  {
+    bool ra = r, any = false;
+    float a2 = 0.f;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      if (ax >= A.dim) break;
+      dvd[ax] = A.dv[ax][a];
+      const float f = screen_f32(dvd[ax], ra);
+      a2 += f * f;
+      any |= bits_nonzero(dvd[ax]);
+    }
+    est[1] = any ? A.f_accel * sqrtf(hf) * rsqrtf(sqrtf(a2)) : inf;
+    if (ra) risky |= 2u;
+  }
+  const double drho = A.drho[a], rho = A.rho[a];
+  {
+    bool rr = false;
+    const float q = fabsf(screen_f32(rho, rr)), d = fabsf(screen_f32(drho, rr));
+    est[2] = (!P.density_sum && bits_nonzero(drho)) ? A.f_quantity * q * __frcp_rn(d) : inf;
+    if (rr) risky |= 4u;
+  }
+  const double du = A.du[a], u = A.u[a];
+  {
+    bool rr = false;
+    const float q = fabsf(screen_f32(u, rr)), d = fabsf(screen_f32(du, rr));
+    est[3] = bits_nonzero(du) ? A.f_quantity * (q + A.f_u_floor) * __frcp_rn(d) : inf;
+    if (rr) risky |= 8u;
+  }
+  const int ns = nsym(A.dim);
+  const bool has_S = A.S && A.dS;
+  for (int k = 0; k < 6; ++k) {
+    est[4 + k] = inf;
+    if (has_S && k < ns) {
+      bool rr = false;
+      const double q = A.S[(int64_t)k * A.n + a], dq = A.dS[(int64_t)k * A.n + a];
+      const float qf = fabsf(screen_f32(q, rr)), df = fabsf(screen_f32(dq, rr));
+      if (bits_nonzero(dq)) est[4 + k] = A.f_quantity * (qf + A.f_S_floor) * __frcp_rn(df);
+      if (rr) risky |= 16u << k;
+    }
+  }
+  est[10] = inf;
+  const bool has_d = A.dmg && A.ddmg;
+  double dd = 0.0, dq = 0.0;
+  if (has_d) {
+    bool rr = false;
+    dq = A.ddmg[a];
+    dd = A.dmg[a];
+    const float qf = fabsf(screen_f32(dd, rr)), df = screen_f32(dq, rr);
+    if ((long long)__double_as_longlong(dq) > 0) est[10] = A.f_quantity * (qf + A.f_dmg_floor) * __frcp_rn(df);
+    if (rr) risky |= 1024u;
+  }
+  float best = A.f_dt_max;
+#pragma unroll
+  for (int i = 0; i < 11; ++i)
+    if (!((risky >> i) & 1u)) best = fminf(best, est[i]);
+  const float thr = best * (1.f + 1.f / 4096.f);
+  unsigned pick = risky;
+#pragma unroll
+  for (int i = 0; i < 11; ++i)
+    if (est[i] <= thr) pick |= 1u << i;
+  // FP64, exactly as the limits are defined.  Every limit except the
+  // acceleration one has the form c (|q| + floor) / den (floor = 0 for the
+  // Courant and density limits, where |q| + 0 = |q|); the picked ones are
+  // evaluated in a loop with one division per pass, usually a single pass.
+  double dt = P.dt_max;
+  const unsigned avail = 0xfu | (has_S ? ((1u << ns) - 1u) << 4 : 0u) | (has_d ? 1024u : 0u);
+  pick &= avail;
+  unsigned rem = pick & ~2u;
+  while (rem) {
+    const int i = __ffs(rem) - 1;
+    rem &= rem - 1;
+    double q, d, c = P.c_quantity, fl = 0.0;
+    bool ok = true, absd = true;
+    if (i == 0) {
+      q = h;
+      d = cs;
+      c = P.c_courant;
+      absd = false;
+    } else if (i == 2) {
+      q = rho;
+      d = drho;
+      ok = !P.density_sum;
+    } else if (i == 3) {
+      q = u;
+      d = du;
+      fl = P.u_floor;
+    } else if (i < 10) {
+      q = A.S[(int64_t)(i - 4) * A.n + a];
+      d = A.dS[(int64_t)(i - 4) * A.n + a];
+      fl = P.S_floor;
+    } else {
+      q = dd;
+      d = dq;
+      fl = P.dmg_floor;
+      absd = false;
+    }
+    const uint64_t db = dbits(d) & (absd ? 0x7fffffffffffffffULL : ~0ULL);
+    const uint64_t qb = dbits(q) & 0x7fffffffffffffffULL;
+    if (ok && (int64_t)db > 0 && db <= 0x7ff0000000000000ULL)  // den > 0 (NaN excluded)
+      dt = fmin(dt, c * (bitsd(qb) + fl) / bitsd(db));
+  }
+  if (pick & 2u) {
+    double a2 = 0.0;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax)
+      if (ax < A.dim) a2 += dvd[ax] * dvd[ax];
+    if (a2 > 0.0) dt = fmin(dt, P.c_accel * sqrt(h / sqrt(a2)));
+  }
+  return dt;
+}
 
 __global__ void k_dt(DtArgs A) {
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -35,23 +190,7 @@ __global__ void k_dt(DtArgs A) {
   int inst = 0;
   if (a < A.n) {
     inst = inst_of(A.inst_off, A.ninst, a);
-    const double h = A.h[a];
-    const double cs = A.cs[a];
-    if (cs > 0.0) dt = fmin(dt, P.c_courant * h / cs);
-    double a2 = 0.0;
-    for (int ax = 0; ax < A.dim; ++ax) a2 += A.dv[ax][a] * A.dv[ax][a];
-    if (a2 > 0.0) dt = fmin(dt, P.c_accel * sqrt(h / sqrt(a2)));
-    if (!P.density_sum && fabs(A.drho[a]) > 0.0) dt = fmin(dt, P.c_quantity * fabs(A.rho[a]) / fabs(A.drho[a]));
-    if (fabs(A.du[a]) > 0.0) dt = fmin(dt, P.c_quantity * (fabs(A.u[a]) + P.u_floor) / fabs(A.du[a]));
-    if (A.S && A.dS) {
-      const int ns = nsym(A.dim);
-      for (int k = 0; k < ns; ++k) {
-        double q = A.S[(int64_t)k * A.n + a], dq = A.dS[(int64_t)k * A.n + a];
-        if (fabs(dq) > 0.0) dt = fmin(dt, P.c_quantity * (fabs(q) + P.S_floor) / fabs(dq));
-      }
-    }
-    if (A.dmg && A.ddmg && A.ddmg[a] > 0.0)
-      dt = fmin(dt, P.c_quantity * (fabs(A.dmg[a]) + P.dmg_floor) / A.ddmg[a]);
+    dt = particle_dt(A, a);
   }
   // warp-level min when the warp lies in one instance, else per lane; then one
   // atomic per run of equal instances among the block's warps
@@ -120,6 +259,13 @@ void timestep_reduce(sph_ctx *c, const sph_state *s, const sph_params &p, const 
     A.ninst = ninst;
     A.prm = p;
     A.enc = c->st.dt_enc;
+    A.f_courant = (float)p.c_courant;
+    A.f_accel = (float)p.c_accel;
+    A.f_quantity = (float)p.c_quantity;
+    A.f_u_floor = (float)p.u_floor;
+    A.f_S_floor = (float)p.S_floor;
+    A.f_dmg_floor = (float)p.dmg_floor;
+    A.f_dt_max = (float)p.dt_max;
     { k_dt<<<nblk(s->n, 256), 256, 0, st>>>(A); ++sph::g_launches; }
   }
   { k_dt_final<<<nblk(ninst, 128), 128, 0, st>>>(c->st.dt_enc, c->st.dt, ninst, p.dt_fixed, nullptr); ++sph::g_launches; }
@@ -167,16 +313,28 @@ __global__ void k_pc(PcArgs A) {
       J2 += (k < A.dim ? 1.0 : 2.0) * S[k] * S[k];  // off-diagonal terms appear twice in S:S
     }
     J2 *= 0.5;
-    double fY = 1.0;
-    if (M.strength && M.Y0 > 0.0 && J2 > 0.0) fY = fmin(M.Y0 * M.Y0 / (3.0 * J2), 1.0);
-    for (int k = 0; k < ns; ++k) A.oS[(int64_t)k * A.n + a] = S[k] * fY;
+    // f_Y = min(Y0^2 / (3 J2), 1) differs from 1 only if Y0^2 < 3 J2 (both
+    // rounded as in the quotient), so the division runs for yielding
+    // particles only; the result is the same bit for bit
+    const double y2 = M.Y0 * M.Y0, j3 = 3.0 * J2;
+    if (M.strength && M.Y0 > 0.0 && J2 > 0.0 && y2 < j3) {
+      const double fY = fmin(y2 / j3, 1.0);
+      for (int k = 0; k < ns; ++k) S[k] *= fY;
+    }
+    for (int k = 0; k < ns; ++k) A.oS[(int64_t)k * A.n + a] = S[k];
   }
   if (A.bdmg) {
-    double nd = A.bdmg[a] + dt * A.ddmg[a];
-    if (A.ddmg[a] > 0.0) {
+    const double dd = A.ddmg[a];
+    double nd = A.bdmg[a] + dt * dd;
+    if (dd > 0.0) {
       const int64_t idp = A.id ? A.id[a] : a;
       const int64_t ntot = A.flaw_off[idp + 1] - A.flaw_off[idp];
-      nd = fmin(nd, cbrt((double)A.nact[a] / (double)ntot));
+      // the cap (n_act / n_tot)^(1/3) binds only if nd^3 n_tot >= n_act; an
+      // FP32 test with a 2^-12 margin skips the cube root where it cannot
+      float ndf;
+      const bool below = f32_rn_scaled(nd, 0, ndf) && ndf >= 0.f &&
+                         ndf * ndf * ndf * (float)ntot < (float)A.nact[a] * (1.f - 1.f / 4096.f);
+      if (!below) nd = fmin(nd, cbrt((double)A.nact[a] / (double)ntot));
     }
     A.odmg[a] = fmin(nd, 1.0);
   }

@@ -14,7 +14,10 @@
 //   5. node mass, centre of mass and tight box bottom-up: the last child to
 //      arrive (atomic counter) combines its siblings in child order, so the
 //      result does not depend on arrival order.
+#include <climits>
+
 #include "sph_internal.cuh"
+#include "fpbits.cuh"
 
 namespace sph {
 
@@ -31,12 +34,19 @@ __global__ void k_bbox_init(unsigned long long *bb, int ninst) {
   }
 }
 
-__device__ __forceinline__ double warp_min(double v) {
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+// min / max of order-preserving encodings (integer pipe)
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w < v ? w : v;
+  }
   return v;
 }
-__device__ __forceinline__ double warp_max(double v) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
   return v;
 }
 
@@ -47,8 +57,8 @@ __global__ void k_bbox(const double *__restrict__ x, const double *__restrict__ 
                        const double *__restrict__ vx, const double *__restrict__ vy, const double *__restrict__ vz,
                        const double *__restrict__ h, const double *__restrict__ rho, int64_t n, int dim,
                        const int64_t *__restrict__ inst_off, int ninst, unsigned long long *bb, int32_t *err) {
-  const double inf = __longlong_as_double(0x7ff0000000000000LL);
-  double lo[3] = {inf, inf, inf}, hi[3] = {-inf, -inf, -inf};
+  // extrema as order-preserving integers: comparisons stay off the FP64 unit
+  unsigned long long lo[3] = {~0ULL, ~0ULL, ~0ULL}, hi[3] = {0ULL, 0ULL, 0ULL};
   int64_t i0, i1, stride;
   int inst;
   if (ninst > 1 && inst_off) {
@@ -64,21 +74,21 @@ __global__ void k_bbox(const double *__restrict__ x, const double *__restrict__ 
   }
   bool bad = false;
   for (int64_t i = i0; i < i1; i += stride) {
-    double p[3] = {x[i], y[i], dim == 3 ? z[i] : 0.0};
-    double v2 = vx[i] + vy[i] + (dim == 3 ? vz[i] : 0.0);
-    double hh = h[i], rr = rho[i];
-    bad |= !isfinite(p[0] + p[1] + p[2]) || !isfinite(v2) || !(hh > 0.0) || !isfinite(hh) || !(rr > 0.0) ||
-           !isfinite(rr);
+    const double p[3] = {x[i], y[i], dim == 3 ? z[i] : 0.0};
+    bad |= !finite_bits(p[0]) || !finite_bits(p[1]) || !finite_bits(p[2]) || !finite_bits(vx[i]) ||
+           !finite_bits(vy[i]) || (dim == 3 && !finite_bits(vz[i])) || !positive_finite_bits(h[i]) ||
+           !positive_finite_bits(rho[i]);
     for (int ax = 0; ax < 3; ++ax) {
-      lo[ax] = fmin(lo[ax], p[ax]);
-      hi[ax] = fmax(hi[ax], p[ax]);
+      const unsigned long long o = ord_of(p[ax]);
+      lo[ax] = o < lo[ax] ? o : lo[ax];
+      hi[ax] = o > hi[ax] ? o : hi[ax];
     }
   }
   if (bad) raise_err(err, ERR_NONFINITE);
-  __shared__ double s[6][32];
+  __shared__ unsigned long long s[6][32];
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int ax = 0; ax < 3; ++ax) {
-    double a = warp_min(lo[ax]), b = warp_max(hi[ax]);
+    unsigned long long a = warp_min_u64(lo[ax]), b = warp_max_u64(hi[ax]);
     if (lane == 0) {
       s[ax][w] = a;
       s[3 + ax][w] = b;
@@ -87,13 +97,13 @@ __global__ void k_bbox(const double *__restrict__ x, const double *__restrict__ 
   __syncthreads();
   if (w == 0) {
     for (int ax = 0; ax < 3; ++ax) {
-      double a = lane < nw ? s[ax][lane] : inf;
-      double b = lane < nw ? s[3 + ax][lane] : -inf;
-      a = warp_min(a);
-      b = warp_max(b);
+      unsigned long long a = lane < nw ? s[ax][lane] : ~0ULL;
+      unsigned long long b = lane < nw ? s[3 + ax][lane] : 0ULL;
+      a = warp_min_u64(a);
+      b = warp_max_u64(b);
       if (lane == 0) {
-        atomicMin(&bb[6 * inst + ax], dbl_to_ord(a));
-        atomicMax(&bb[6 * inst + 3 + ax], dbl_to_ord(b));
+        atomicMin(&bb[6 * inst + ax], a);
+        atomicMax(&bb[6 * inst + 3 + ax], b);
       }
     }
   }
@@ -102,7 +112,8 @@ __global__ void k_bbox(const double *__restrict__ x, const double *__restrict__ 
 // Root cube per instance (Sect. 3.5.1): corner = per-axis minimum, edge
 // s0 = max over axes of the extent, enlarged by 2^-20 so that the particle
 // at the maximum falls inside; a zero extent (one particle) gives s0 = 1.
-__global__ void k_root(const unsigned long long *bb, int ninst, int dim, double *lo_out, double *s0_out) {
+__global__ void k_root(const unsigned long long *bb, int ninst, int dim, double *lo_out, double *s0_out,
+                       double *rs0_out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ninst) return;
   double ext = 0.0;
@@ -116,7 +127,9 @@ __global__ void k_root(const unsigned long long *bb, int ninst, int dim, double 
     ext = fmax(ext, __dsub_rn(hi, lo));
   }
   double s0 = __dmul_rn(ext, 1.0 + 0x1p-20);
-  s0_out[i] = s0 > 0.0 ? s0 : 1.0;
+  s0 = s0 > 0.0 ? s0 : 1.0;
+  s0_out[i] = s0;
+  rs0_out[i] = __drcp_rn(s0);
 }
 
 // ---------------------------------------------------------------------------
@@ -169,19 +182,47 @@ __device__ __forceinline__ unsigned long long cell_index(double v, double lo, do
   return (unsigned long long)k;
 }
 
+// The same cell index with the quotient taken as (x - min) * (1/s0): within
+// 2 ulps of the correctly rounded quotient, so the floor can differ only when
+// the scaled value lies within a few ulps of an integer; those rare cases
+// take the division.  The floor and that test read the bits of the scaled
+// value (integer pipe); two FP64 operations remain per axis.
+__device__ __forceinline__ unsigned long long cell_index_fast(double v, double lo, double s0, double rs0, int B) {
+  const double t = __dmul_rn(__dsub_rn(v, lo), rs0);
+  const uint64_t tb = dbits(t);
+  const int et = (int)((tb >> 52) & 0x7ff);
+  if ((int64_t)tb <= 0 || et == 0) return (int64_t)tb < 0 ? cell_index(v, lo, s0, B) : 0ULL;  // 0, tiny or negative
+  const int E = et - 1023 + B;  // exponent of f = t * 2^B
+  const unsigned long long kmax = (1ULL << B) - 1;
+  if (E >= B) return kmax;
+  const uint64_t mant = (tb & ((1ULL << 52) - 1)) | (1ULL << 52);
+  bool near;
+  unsigned long long k;
+  if (E < 0) {
+    k = 0;
+    near = E == -1 && (mant & ((1ULL << 52) - 1)) >= (1ULL << 52) - 4;  // within 4 ulps below 1
+  } else {
+    const int sh = 52 - E;
+    k = mant >> sh;
+    const uint64_t frac = mant & ((1ULL << sh) - 1);
+    near = frac <= 4 || frac >= (1ULL << sh) - 4;
+  }
+  return near ? cell_index(v, lo, s0, B) : k;
+}
+
 __global__ void k_keys(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
                        int64_t n, int dim, int B, const int64_t *__restrict__ inst_off, int ninst,
-                       const double *__restrict__ ilo, const double *__restrict__ is0, unsigned long long *keys,
-                       int32_t *vals) {
+                       const double *__restrict__ ilo, const double *__restrict__ is0,
+                       const double *__restrict__ irs0, unsigned long long *keys, int32_t *vals) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int inst = inst_of(inst_off, ninst, i);
-  double s0 = is0[inst];
-  unsigned long long kx = cell_index(x[i], ilo[3 * inst + 0], s0, B);
-  unsigned long long ky = cell_index(y[i], ilo[3 * inst + 1], s0, B);
+  const double s0 = is0[inst], rs0 = irs0[inst];
+  unsigned long long kx = cell_index_fast(x[i], ilo[3 * inst + 0], s0, rs0, B);
+  unsigned long long ky = cell_index_fast(y[i], ilo[3 * inst + 1], s0, rs0, B);
   unsigned long long key;
   if (dim == 3) {
-    unsigned long long kz = cell_index(z[i], ilo[3 * inst + 2], s0, B);
+    unsigned long long kz = cell_index_fast(z[i], ilo[3 * inst + 2], s0, rs0, B);
     key = spread3(kx) | (spread3(ky) << 1) | (spread3(kz) << 2);
   } else {
     key = spread2(kx) | (spread2(ky) << 1);
@@ -248,22 +289,34 @@ __global__ void k_pack(const double *__restrict__ x, const double *__restrict__ 
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int inst = inst_of(inst_off, ninst, i);
-  const double iL = U->invL, iV = U->invV;
-  double X[3] = {(x[i] - ilo[3 * inst]) * iL, (y[i] - ilo[3 * inst + 1]) * iL,
-                 dim == 3 ? (z[i] - ilo[3 * inst + 2]) * iL : 0.0};
-  double V[3] = {vx[i] * iV, vy[i] * iV, dim == 3 ? vz[i] * iV : 0.0};
+  // the code units are powers of two: scaling is an exponent shift, and the
+  // conversions and hi/lo splits run on the integer pipe (fpbits.cuh); only
+  // the corner subtraction needs the FP64 unit
+  const int kL = pow2_exp(U->invL), kV = pow2_exp(U->invV), kM = pow2_exp(U->invM), kR = pow2_exp(U->invrho);
+  const double X[3] = {__dsub_rn(x[i], ilo[3 * inst]), __dsub_rn(y[i], ilo[3 * inst + 1]),
+                       dim == 3 ? __dsub_rn(z[i], ilo[3 * inst + 2]) : 0.0};
+  const double V[3] = {vx[i], vy[i], dim == 3 ? vz[i] : 0.0};
   float xh[3], xl[3], vh[3], vl[3];
   for (int ax = 0; ax < 3; ++ax) {
-    xh[ax] = __double2float_rn(X[ax]);
-    xl[ax] = __double2float_rn(X[ax] - (double)xh[ax]);
-    vh[ax] = __double2float_rn(V[ax]);
-    vl[ax] = __double2float_rn(V[ax] - (double)vh[ax]);
+    if (!f32_split_scaled(X[ax], kL, xh[ax], xl[ax])) {
+      const double Xs = X[ax] * U->invL;
+      xh[ax] = __double2float_rn(Xs);
+      xl[ax] = __double2float_rn(Xs - (double)xh[ax]);
+    }
+    if (!f32_split_scaled(V[ax], kV, vh[ax], vl[ax])) {
+      const double Vs = V[ax] * U->invV;
+      vh[ax] = __double2float_rn(Vs);
+      vl[ax] = __double2float_rn(Vs - (double)vh[ax]);
+    }
   }
-  double r = rho[i] * U->invrho, mm = m[i] * U->invM;
-  pk.px[i] = make_float4(xh[0], xh[1], xh[2], __double2float_rn(h[i] * iL));
-  pk.pxl[i] = make_float4(xl[0], xl[1], xl[2], __double2float_rn(mm));
-  pk.pv[i] = make_float4(vh[0], vh[1], vh[2], __double2float_rn(r));
-  pk.pvl[i] = make_float4(vl[0], vl[1], vl[2], __double2float_rn(mm / r));
+  float hf, mf, rf;
+  if (!f32_rn_scaled(h[i], kL, hf)) hf = __double2float_rn(h[i] * U->invL);
+  if (!f32_rn_scaled(m[i], kM, mf)) mf = __double2float_rn(m[i] * U->invM);
+  if (!f32_rn_scaled(rho[i], kR, rf)) rf = __double2float_rn(rho[i] * U->invrho);
+  pk.px[i] = make_float4(xh[0], xh[1], xh[2], hf);
+  pk.pxl[i] = make_float4(xl[0], xl[1], xl[2], mf);
+  pk.pv[i] = make_float4(vh[0], vh[1], vh[2], rf);
+  pk.pvl[i] = make_float4(vl[0], vl[1], vl[2], __fdiv_rn(mf, rf));
 }
 
 // ---------------------------------------------------------------------------
@@ -590,6 +643,15 @@ __global__ void k_node_emit(KeyLevels K, int64_t n, int L, const int64_t *__rest
     if (end - i <= L || l == K.B) break;
     e = end;
   }
+  // the chain ends at a leaf: list it for the moments pass
+  if (id < T.cap_nodes) {
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(T.nleaf, __popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    T.ncount[base + __popc(mask & ((1u << lane) - 1u))] = id;
+  }
 }
 
 __global__ void k_inst_roots(const int64_t *__restrict__ inst_off, int ninst, int64_t n, const int32_t *nstart,
@@ -693,66 +755,85 @@ __global__ void k_group_emit(Tree T, const int32_t *__restrict__ gstart, const i
 // ---------------------------------------------------------------------------
 // Node moments, bottom-up
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float f_down(double v) { return __double2float_rd(v); }
-__device__ __forceinline__ float f_up(double v) { return __double2float_ru(v); }
 
 __global__ void k_moments(Tree T, const double *__restrict__ x, const double *__restrict__ y,
                           const double *__restrict__ z, const double *__restrict__ m, const double *__restrict__ h,
                           int dim, int L, const int64_t *__restrict__ inst_off, int ninst,
                           const Units *__restrict__ U) {
-  int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int nn = *T.nnodes;
-  if (id >= nn) return;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= *T.nleaf) return;
+  const int64_t id = T.ncount[tid];  // one thread per leaf
   int32_t f = T.first[id], e = T.end[id];
-  if (!(e - f <= L || T.level[id] == T.max_depth)) return;  // only leaves start
   const double *X[3] = {x, y, z};
   const int64_t cap = T.cap_nodes;
   int inst = inst_of(inst_off, ninst, f);
-  double ilo[3] = {T.inst_lo[3 * inst], T.inst_lo[3 * inst + 1], T.inst_lo[3 * inst + 2]};
-  // leaf: straight from its particles, in slot order
-  double M = 0.0, mx[3] = {0, 0, 0}, lo[3], hi[3], hm = 0.0;
-  const double inf = __longlong_as_double(0x7ff0000000000000LL);
-  for (int ax = 0; ax < 3; ++ax) {
-    lo[ax] = inf;
-    hi[ax] = -inf;
-  }
+  const double ilo[3] = {T.inst_lo[3 * inst], T.inst_lo[3 * inst + 1], T.inst_lo[3 * inst + 2]};
+  const int kL = pow2_exp(U->invL), kM = pow2_exp(U->invM);
+  // Sums stay FP64.  Extrema are kept as order-preserving integers and h_max
+  // as the bits of a positive double, so that comparisons, like the scaled
+  // FP32 conversions below, stay off the FP64 unit.
+  double M = 0.0, mx[3] = {0, 0, 0};
+  unsigned long long lo[3] = {~0ULL, ~0ULL, ~0ULL}, hi[3] = {0ULL, 0ULL, 0ULL};
+  unsigned long long hm = 0ULL;
   for (int32_t j = f; j < e; ++j) {
     int32_t a = T.perm[j];
     double ma = m[a];
     M += ma;
-    hm = fmax(hm, h[a]);
-    for (int ax = 0; ax < dim; ++ax) {
+    const unsigned long long hb = dbits(h[a]);
+    hm = hb > hm ? hb : hm;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      if (ax >= dim) break;
       double v = X[ax][a];
       mx[ax] += ma * v;
-      lo[ax] = fmin(lo[ax], v);
-      hi[ax] = fmax(hi[ax], v);
+      const unsigned long long o = ord_of(v);
+      lo[ax] = o < lo[ax] ? o : lo[ax];
+      hi[ax] = o > hi[ax] ? o : hi[ax];
     }
   }
   int64_t node = id;
   for (int depth = 0; depth < 64; ++depth) {
-    T.mass[node] = M;
-    T.hmax[node] = hm;
+    const double iM = 1.0 / M;
+    double com[3], blo[3], bhi[3];
+#pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
-      bool use = ax < dim;
-      T.com[ax * cap + node] = use ? mx[ax] / M : 0.0;
-      T.bblo[ax * cap + node] = use ? lo[ax] : 0.0;
-      T.bbhi[ax * cap + node] = use ? hi[ax] : 0.0;
+      const bool use = ax < dim;
+      com[ax] = use ? mx[ax] * iM : 0.0;
+      blo[ax] = use ? of_ord(lo[ax]) : 0.0;
+      bhi[ax] = use ? of_ord(hi[ax]) : 0.0;
+      T.com[ax * cap + node] = com[ax];
+      T.bblo[ax * cap + node] = blo[ax];
+      T.bbhi[ax * cap + node] = bhi[ax];
     }
+    const double hmax = bitsd(hm);
+    T.mass[node] = M;
+    T.hmax[node] = hmax;
     {
-      const double iL = U->invL;
-      T.fbox_lo[node] = make_float4(f_down((lo[0] - ilo[0]) * iL), f_down((lo[1] - ilo[1]) * iL),
-                                    dim == 3 ? f_down((lo[2] - ilo[2]) * iL) : 0.f, f_up(hm * iL));
-      T.fbox_hi[node] = make_float4(f_up((hi[0] - ilo[0]) * iL), f_up((hi[1] - ilo[1]) * iL),
-                                    dim == 3 ? f_up((hi[2] - ilo[2]) * iL) : 0.f, 0.f);
-      float ch[3], cl[3];
+      // FP32 box rounded outwards and the COM as hi + lo, relative to the
+      // instance corner, in code units
+      float bl[3] = {0.f, 0.f, 0.f}, bh[3] = {0.f, 0.f, 0.f}, ch[3] = {0.f, 0.f, 0.f}, cl[3] = {0.f, 0.f, 0.f};
+#pragma unroll
       for (int ax = 0; ax < 3; ++ax) {
-        double X = ax < dim ? (mx[ax] / M - ilo[ax]) * iL : 0.0;
-        ch[ax] = __double2float_rn(X);
-        cl[ax] = __double2float_rn(X - (double)ch[ax]);
+        if (ax >= dim) break;
+        const double dl = __dsub_rn(blo[ax], ilo[ax]), dh = __dsub_rn(bhi[ax], ilo[ax]);
+        const double dc = __dsub_rn(com[ax], ilo[ax]);
+        if (!f32_dir_scaled(dl, kL, false, bl[ax])) bl[ax] = __double2float_rd(dl * U->invL);
+        if (!f32_dir_scaled(dh, kL, true, bh[ax])) bh[ax] = __double2float_ru(dh * U->invL);
+        if (!f32_split_scaled(dc, kL, ch[ax], cl[ax])) {
+          const double Xc = dc * U->invL;
+          ch[ax] = __double2float_rn(Xc);
+          cl[ax] = __double2float_rn(Xc - (double)ch[ax]);
+        }
       }
-      T.fcom_hi[node] = make_float4(ch[0], ch[1], ch[2], __double2float_rn(M * U->invM));
-      T.fcom_lo[node] = make_float4(cl[0], cl[1], cl[2],
-                                    __double2float_rn(ldexp(T.inst_s0[inst], -T.level[node]) * iL));
+      float hf, mf, ef;
+      if (!f32_dir_scaled(hmax, kL, true, hf)) hf = __double2float_ru(hmax * U->invL);
+      if (!f32_rn_scaled(M, kM, mf)) mf = __double2float_rn(M * U->invM);
+      const int lev = T.level[node];
+      if (!f32_rn_scaled(T.inst_s0[inst], kL - lev, ef)) ef = __double2float_rn(ldexp(T.inst_s0[inst], -lev) * U->invL);
+      T.fbox_lo[node] = make_float4(bl[0], bl[1], bl[2], hf);
+      T.fbox_hi[node] = make_float4(bh[0], bh[1], bh[2], 0.f);
+      T.fcom_hi[node] = make_float4(ch[0], ch[1], ch[2], mf);
+      T.fcom_lo[node] = make_float4(cl[0], cl[1], cl[2], ef);
     }
     int32_t p = T.parent[node];
     if (p < 0) return;
@@ -762,33 +843,42 @@ __global__ void k_moments(Tree T, const double *__restrict__ x, const double *__
     __threadfence();
     // last child in: combine all children of p, in ascending id (= child) order
     M = 0.0;
-    hm = 0.0;
+    hm = 0ULL;
+#pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
       mx[ax] = 0.0;
-      lo[ax] = inf;
-      hi[ax] = -inf;
+      lo[ax] = ~0ULL;
+      hi[ax] = 0ULL;
     }
     const int nc = min(T.nchild[p], 8);
     int32_t ch[8];
-    for (int k = 0; k < nc; ++k) ch[k] = __ldcg(&T.child[8 * (int64_t)p + k]);
-    for (int k = 1; k < nc; ++k) {  // insertion sort of <= 8 ids
-      int32_t v = ch[k];
-      int j = k - 1;
-      while (j >= 0 && ch[j] > v) {
-        ch[j + 1] = ch[j];
-        --j;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) ch[k] = k < nc ? __ldcg(&T.child[8 * (int64_t)p + k]) : INT_MAX;
+    // odd-even transposition sort of the 8 slots (unused slots sort last)
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int k = r & 1; k + 1 < 8; k += 2) {
+        const int32_t a = min(ch[k], ch[k + 1]), b = max(ch[k], ch[k + 1]);
+        ch[k] = a;
+        ch[k + 1] = b;
       }
-      ch[j + 1] = v;
-    }
-    for (int k = 0; k < nc; ++k) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (k >= nc) break;
       const int32_t cc = ch[k];
       double mc = __ldcg(&T.mass[cc]);
       M += mc;
-      hm = fmax(hm, __ldcg(&T.hmax[cc]));
-      for (int ax = 0; ax < dim; ++ax) {
+      const unsigned long long hb = dbits(__ldcg(&T.hmax[cc]));
+      hm = hb > hm ? hb : hm;
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) {
+        if (ax >= dim) break;
         mx[ax] += mc * __ldcg(&T.com[ax * cap + cc]);
-        lo[ax] = fmin(lo[ax], __ldcg(&T.bblo[ax * cap + cc]));
-        hi[ax] = fmax(hi[ax], __ldcg(&T.bbhi[ax * cap + cc]));
+        const unsigned long long ol = ord_of(__ldcg(&T.bblo[ax * cap + cc]));
+        const unsigned long long oh = ord_of(__ldcg(&T.bbhi[ax * cap + cc]));
+        lo[ax] = ol < lo[ax] ? ol : lo[ax];
+        hi[ax] = oh > hi[ax] ? oh : hi[ax];
       }
     }
     node = p;
@@ -824,11 +914,11 @@ void tree_build(sph_ctx *c, const sph_state *s, int leaf_size, int max_depth, cu
       { k_bbox<<<min(nblk(n, 256), 152 * 8), 256, 0, st>>>(s->x[0], s->x[1], s->x[2], s->v[0], s->v[1], s->v[2], s->h,
                                                         s->rho, n, dim, nullptr, 1, T.inst_bb, c->d_err); ++sph::g_launches; }
   }
-  { k_root<<<nblk(ninst, 128), 128, 0, st>>>(T.inst_bb, ninst, dim, T.inst_lo, T.inst_s0); ++sph::g_launches; }
+  { k_root<<<nblk(ninst, 128), 128, 0, st>>>(T.inst_bb, ninst, dim, T.inst_lo, T.inst_s0, T.inst_rs0); ++sph::g_launches; }
   { k_units<<<1, 32, 0, st>>>(s->h, s->m, n, dim, c->vscale, c->mt, c->units); ++sph::g_launches; }
   if (n > 0) {
     { k_keys<<<nblk(n, 256), 256, 0, st>>>(s->x[0], s->x[1], s->x[2], n, dim, max_depth, s->inst_off, ninst,
-                                         T.inst_lo, T.inst_s0, T.keys[0], T.vals[0]); ++sph::g_launches; }
+                                         T.inst_lo, T.inst_s0, T.inst_rs0, T.keys[0], T.vals[0]); ++sph::g_launches; }
     int ibits = 0;
     while ((1 << ibits) < ninst) ++ibits;
     radix_sort(c, n, dim * max_depth + ibits, st);
@@ -842,8 +932,9 @@ void tree_build(sph_ctx *c, const sph_state *s, int leaf_size, int max_depth, cu
   scan_excl_i32(T.ncount, T.nstart, n + 1, T.scan_tmp, st);
   cudaMemsetAsync(T.nchild, 0, sizeof(int32_t) * T.cap_nodes, st);
   cudaMemsetAsync(T.arrived, 0, sizeof(int32_t) * T.cap_nodes, st);
+  cudaMemsetAsync(T.nleaf, 0, sizeof(int32_t), st);
   { k_node_emit<<<nblk(n + 1, 256), 256, 0, st>>>(K, n, leaf_size, s->inst_off, ninst, T.nstart, T, c->d_err); ++sph::g_launches; }
-  { k_moments<<<nblk(T.cap_nodes, 256), 256, 0, st>>>(
+  { k_moments<<<nblk(std::max<int64_t>(n, 1), 256), 256, 0, st>>>(
       T, s->x[0], s->x[1], s->x[2], s->m, s->h, dim, leaf_size, s->inst_off, ninst, c->units); ++sph::g_launches; }
   { k_inst_roots<<<nblk(ninst, 128), 128, 0, st>>>(s->inst_off, ninst, n, T.nstart, T); ++sph::g_launches; }
   { k_group_count<<<nblk(T.cap_nodes + 1, 256), 256, 0, st>>>(T, T.gcnt); ++sph::g_launches; }
