@@ -167,6 +167,7 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
     S.d_nact[s] = ctx_alloc<int32_t>(c, N, ok);
   }
   S.dt_enc = ctx_alloc<unsigned long long>(c, ci, ok);
+  S.dmove = ctx_alloc<unsigned long long>(c, 1, ok);
   S.dt = ctx_alloc<double>(c, ci, ok);
   S.gather = ctx_alloc<double>(c, N, ok);
   S.gather_i = ctx_alloc<int32_t>(c, N, ok);
@@ -300,9 +301,10 @@ static void timed_tree(sph_ctx *c, const sph_state *s, const sph_params &p, cuda
 }
 
 static void partners_gravity_passes(sph_ctx *c, sph_state *s, const MatTable &mt, const sph_params &p,
-                                    const sph_derivs &out, cudaStream_t st) {
+                                    const sph_derivs &out, cudaStream_t st,
+                                    const unsigned long long *grow = nullptr) {
   int pr = prof_begin(c, st, PH_PARTNERS);
-  find_partners(c, s, st);
+  find_partners(c, s, st, grow);
   prof_end(c, st, pr);
   if (p.gravity) {
     pr = prof_begin(c, st, PH_GRAVITY);
@@ -437,11 +439,24 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
     tree_reorder_state(c, s, st);
     prof_end(c, st, pr);
     partners_gravity_passes(c, s, mt, *p, d[0], st);
+    // Without gravity the tree only serves the partner search, whose result is
+    // exact for any tree: the predicted state keeps the slots of s and reuses
+    // its tree, the walk widening its boxes by the predictor's displacement.
+    // Gravity's multipole sums depend on the tree, so they get a new one.
+    const bool reuse = !p->gravity;
     pr = prof_begin(c, st, PH_INTEGRATE);
     timestep_reduce(c, s, *p, d[0], st);
-    pc_update(c, s, &q, d[0], 0.5, mt, *p, st);
+    if (reuse) cudaMemsetAsync(B.dmove, 0, sizeof(unsigned long long), st);
+    pc_update(c, s, &q, d[0], 0.5, mt, *p, st, reuse ? B.dmove : nullptr);
     prof_end(c, st, pr);
-    rhs_all(c, &q, mt, *p, d[1], st);
+    if (reuse) {
+      pr = prof_begin(c, st, PH_TREE);
+      pack_f32(c, &q, st);
+      prof_end(c, st, pr);
+      partners_gravity_passes(c, &q, mt, *p, d[1], st, B.dmove);
+    } else {
+      rhs_all(c, &q, mt, *p, d[1], st);
+    }
     pr = prof_begin(c, st, PH_INTEGRATE);
     pc_update(c, s, s, d[1], 1.0, mt, *p, st);
     prof_end(c, st, pr);

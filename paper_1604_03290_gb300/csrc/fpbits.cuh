@@ -174,16 +174,43 @@ __host__ __device__ __forceinline__ bool positive_finite_bits(double v) {
 }
 
 #ifdef __CUDACC__
+// FP64 fallbacks for values outside the helpers' domain.  They are kept out
+// of line: inlined, the compiler would evaluate them unconditionally (as
+// predicated code) and the FP64 unit would be busy for every value again.
+static __device__ __noinline__ float f32_rn_slow(double v, double scale) { return __double2float_rn(v * scale); }
+static __device__ __noinline__ float f32_rd_slow(double v, double scale) { return __double2float_rd(v * scale); }
+static __device__ __noinline__ float f32_ru_slow(double v, double scale) { return __double2float_ru(v * scale); }
+static __device__ __noinline__ float2 f32_split_slow(double v, double scale) {
+  const double X = v * scale;
+  const float hi = __double2float_rn(X);
+  return make_float2(hi, __double2float_rn(X - (double)hi));
+}
+static __device__ __noinline__ double f64_slow(float f, double scale) { return (double)f * scale; }
+
 // v * 2^k as a float (nearest even); `scale` = 2^k for the FP64 fallback.
 __device__ __forceinline__ float to_f32_scaled(double v, int k, double scale) {
   float f;
-  if (!f32_rn_scaled(v, k, f)) f = __double2float_rn(v * scale);
+  if (!f32_rn_scaled(v, k, f)) f = f32_rn_slow(v, scale);
   return f;
+}
+// float(v * 2^k) rounded down (up = false) or up
+__device__ __forceinline__ float to_f32_dir_scaled(double v, int k, bool up, double scale) {
+  float f;
+  if (!f32_dir_scaled(v, k, up, f)) f = up ? f32_ru_slow(v, scale) : f32_rd_slow(v, scale);
+  return f;
+}
+// hi = float(v * 2^k), lo = float(v * 2^k - hi)
+__device__ __forceinline__ void to_f32_split_scaled(double v, int k, double scale, float &hi, float &lo) {
+  if (!f32_split_scaled(v, k, hi, lo)) {
+    const float2 r = f32_split_slow(v, scale);
+    hi = r.x;
+    lo = r.y;
+  }
 }
 // (double)f * 2^k, exact; `scale` = 2^k for the fallback.
 __device__ __forceinline__ double to_f64_scaled(float f, int k, double scale) {
   double d;
-  if (!f64_scaled(f, k, d)) d = (double)f * scale;
+  if (!f64_scaled(f, k, d)) d = f64_slow(f, scale);
   return d;
 }
 // a <= b and a >= 0 for doubles that are not NaN, on the integer pipe

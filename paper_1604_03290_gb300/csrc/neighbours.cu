@@ -17,6 +17,7 @@
 // relative band of 6e-5 around h_ab^2 - far wider than the FP32 error of
 // about 2e-6 - are decided by the FP64 expression.  The result is therefore
 // bit-identical to the FP64 definition.
+#include "fpbits.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -43,7 +44,9 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_partners(Tree T, PackedF32 pk
                                                             const double *__restrict__ z,
                                                             const double *__restrict__ h, int dim, int kmax,
                                                             int32_t *__restrict__ nb_idx, int32_t *__restrict__ nb_cnt,
-                                                            int64_t ld, int walk_leaf, int32_t *err) {
+                                                            int64_t ld, int walk_leaf, int32_t *err,
+                                                            const unsigned long long *__restrict__ grow,
+                                                            const Units *__restrict__ U) {
   __shared__ float4 sc[kNbWarps][kMaxLeaf];
   __shared__ int32_t sb[kNbWarps][kMaxLeaf];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -52,6 +55,11 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_partners(Tree T, PackedF32 pk
   // and culls their whole particle range: any stopping rule gives the same set.
   const int L = max(T.leaf_size, walk_leaf), B = T.max_depth;
   const int nnodes = *T.nnodes;
+  // Node boxes are those of the tree the walk runs on; when the particles have
+  // moved since it was built (by at most `grow` per axis), widening the
+  // group's box by that much keeps every node that may hold a partner.
+  float gw = 0.f;
+  if (grow) gw = to_f32_dir_scaled(bitsd(*grow), pow2_exp(U->invL), true, U->invL);
   for (int g = blockIdx.x * kNbWarps + w; g < ngroups; g += gridDim.x * kNbWarps) {
     const int32_t s0 = T.grp_start[g], s1 = T.grp_end[g], inst = T.grp_inst[g];
     const int32_t slot = s0 + lane;
@@ -82,7 +90,7 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_partners(Tree T, PackedF32 pk
       hg = fmaxf(hg, __shfl_xor_sync(0xffffffffu, hg, o));
     }
     float mag = fmaxf(fmaxf(fabsf(gh[0]), fabsf(gh[1])), fabsf(gh[2]));
-    float slack = 1e-6f * mag;
+    float slack = 1e-6f * mag + gw * (1.0f + 1e-6f);
     for (int ax = 0; ax < 3; ++ax) {
       gl[ax] -= slack;
       gh[ax] += slack;
@@ -164,11 +172,12 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_partners(Tree T, PackedF32 pk
   }
 }
 
-void find_partners(sph_ctx *c, const sph_state *s, cudaStream_t st) {
+void find_partners(sph_ctx *c, const sph_state *s, cudaStream_t st, const unsigned long long *grow) {
   if (s->n == 0) return;
   int blocks = c->num_sms * c->tune.walk_blocks_per_sm;
   { k_partners<<<blocks, kNbWarps * 32, 0, st>>>(c->tree, c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim, c->kmax,
-                                              c->nb_idx, c->nb_cnt, c->cap_n, c->tune.walk_leaf, c->d_err); ++sph::g_launches; }
+                                              c->nb_idx, c->nb_cnt, c->cap_n, c->tune.walk_leaf, c->d_err, grow,
+                                              c->units); ++sph::g_launches; }
 }
 
 // ---------------------------------------------------------------------------

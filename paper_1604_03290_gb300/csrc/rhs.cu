@@ -641,8 +641,7 @@ __global__ void k_repack_rho(const double *__restrict__ rho, const double *__res
   float4 v = pk.pv[i], w = pk.pvl[i];
   // as in the packing after the tree build: rho scaled by its power-of-two
   // unit, and the volume m / rho from the FP32 views
-  float rf;
-  if (!f32_rn_scaled(rho[i], pow2_exp(U->invrho), rf)) rf = __double2float_rn(rho[i] * U->invrho);
+  const float rf = to_f32_scaled(rho[i], pow2_exp(U->invrho), U->invrho);
   v.w = rf;
   w.w = __fdiv_rn(pk.pxl[i].w, rf);
   pk.pv[i] = v;

@@ -114,6 +114,7 @@ struct StepBufs {
   double *d_x[2][3], *d_v[2][3], *d_rho[2], *d_u[2], *d_S[2], *d_dmg[2], *d_cs[2];
   int32_t *d_nact[2];
   unsigned long long *dt_enc;  // per instance, ordered encoding for atomicMin
+  unsigned long long *dmove;   // bits of the predictor's largest per-axis displacement
   double *dt;                  // per instance
   double *gather;              // reorder scratch (n doubles)
   int32_t *gather_i;
@@ -269,7 +270,9 @@ void tree_build(sph_ctx *c, const sph_state *s, int leaf_size, int max_depth, cu
 void tree_reorder_state(sph_ctx *c, sph_state *s, cudaStream_t st);
 void pack_f32(sph_ctx *c, const sph_state *s, cudaStream_t st);
 // neighbours.cu
-void find_partners(sph_ctx *c, const sph_state *s, cudaStream_t st);
+// grow (device, may be NULL): bits of a displacement bound by which every
+// particle may have left the node boxes of the current tree, per axis
+void find_partners(sph_ctx *c, const sph_state *s, cudaStream_t st, const unsigned long long *grow = nullptr);
 void partners_to_csr(sph_ctx *c, const sph_state *s, int64_t *off, int32_t *idx, int64_t cap, cudaStream_t st);
 // rhs.cu
 void rhs_passes(sph_ctx *c, sph_state *s, const MatTable &mt, const sph_params &p, const sph_derivs &out,
@@ -285,7 +288,10 @@ void pc_update_adjoint(sph_ctx *c, const sph_state *base, const sph_derivs &d, c
                        sph_derivs *fbar, double *param_bar, cudaStream_t st);
 // step.cu
 void timestep_reduce(sph_ctx *c, const sph_state *s, const sph_params &p, const sph_derivs &d, cudaStream_t st);
+// dmove (device, may be NULL): receives the bits of max over particles and
+// axes of |out.x - base.x|; non-finite output or rho <= 0 then raises the
+// non-finite error bit, as a tree build over `out` would
 void pc_update(sph_ctx *c, const sph_state *base, sph_state *out, const sph_derivs &d, double frac,
-               const MatTable &mt, const sph_params &p, cudaStream_t st);
+               const MatTable &mt, const sph_params &p, cudaStream_t st, unsigned long long *dmove = nullptr);
 
 }  // namespace sph

@@ -51,6 +51,16 @@ __device__ __forceinline__ float screen_f32(double v, bool &risky) {
 
 __device__ __forceinline__ bool bits_nonzero(double v) { return ((unsigned long long)__double_as_longlong(v) << 1) != 0ULL; }
 
+// c_accel sqrt(h / |dv/dt|), or `none` for zero acceleration.  Out of line
+// so that the compiler branches around it rather than predicating it.
+static __device__ __noinline__ double accel_limit(int dim, double h, double a0, double a1, double a2v, double c,
+                                           double none) {
+  double a2 = a0 * a0;
+  a2 += a1 * a1;
+  if (dim == 3) a2 += a2v * a2v;
+  return a2 > 0.0 ? c * sqrt(h / sqrt(a2)) : none;
+}
+
 // The limits of one particle.  Every limit is first estimated in FP32 (within
 // about 1e-6 relative); the FP64 expression is then evaluated only for limits
 // whose estimate lies within 2^-12 of the smallest estimate, or whose inputs
@@ -173,13 +183,7 @@ __device__ double particle_dt(const DtArgs &A, int64_t a) {
     if (ok && (int64_t)db > 0 && db <= 0x7ff0000000000000ULL)  // den > 0 (NaN excluded)
       dt = fmin(dt, c * (bitsd(qb) + fl) / bitsd(db));
   }
-  if (pick & 2u) {
-    double a2 = 0.0;
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax)
-      if (ax < A.dim) a2 += dvd[ax] * dvd[ax];
-    if (a2 > 0.0) dt = fmin(dt, P.c_accel * sqrt(h / sqrt(a2)));
-  }
+  if (pick & 2u) dt = fmin(dt, accel_limit(A.dim, h, dvd[0], dvd[1], dvd[2], P.c_accel, dt));
   return dt;
 }
 
@@ -288,18 +292,32 @@ struct PcArgs {
   double frac;
   MatTable mt;
   int density_sum;
+  unsigned long long *dmove;  // NULL, or max |out.x - base.x| (bits of a non-negative double)
+  int32_t *err;
 };
 
-__global__ void k_pc(PcArgs A) {
-  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= A.n) return;
+// Update of particle a; returns the bits of max_axis |out.x - base.x| when
+// A.dmove is set (else 0).
+__device__ __forceinline__ unsigned long long pc_particle(const PcArgs &A, int64_t a) {
   const int inst = inst_of(A.inst_off, A.ninst, a);
   const double dt = A.frac * A.dt[inst];
+  unsigned long long mv = 0ULL;  // bits of max |ox - bx| (non-negative doubles order as integers)
+  bool bad = false;
   for (int ax = 0; ax < A.dim; ++ax) {
-    A.ox[ax][a] = A.bx[ax][a] + dt * A.dx[ax][a];
-    A.ov[ax][a] = A.bv[ax][a] + dt * A.dv[ax][a];
+    const double bx = A.bx[ax][a], ox = bx + dt * A.dx[ax][a], ov = A.bv[ax][a] + dt * A.dv[ax][a];
+    A.ox[ax][a] = ox;
+    A.ov[ax][a] = ov;
+    if (A.dmove) {
+      const unsigned long long m = dbits(ox - bx) & 0x7fffffffffffffffULL;
+      mv = m > mv ? m : mv;
+      bad |= !finite_bits(ox) || !finite_bits(ov);
+    }
   }
   A.orho[a] = A.density_sum ? A.brho[a] : A.brho[a] + dt * A.drho[a];
+  if (A.dmove) {
+    bad |= !positive_finite_bits(A.orho[a]);
+    if (bad) raise_err(A.err, ERR_NONFINITE);
+  }
   A.ou[a] = A.bu[a] + dt * A.du[a];
   const int mi = A.mat ? A.mat[a] : 0;
   const sph_material &M = A.mt.m[(mi >= 0 && mi < A.mt.nmat) ? mi : 0];
@@ -338,10 +356,24 @@ __global__ void k_pc(PcArgs A) {
     }
     A.odmg[a] = fmin(nd, 1.0);
   }
+  return mv;
+}
+
+__global__ void k_pc(PcArgs A) {
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long mv = 0ULL;
+  if (a < A.n) mv = pc_particle(A, a);
+  if (A.dmove) {  // every lane of the warp arrives here
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long w = __shfl_xor_sync(0xffffffffu, mv, o);
+      mv = w > mv ? w : mv;
+    }
+    if ((threadIdx.x & 31) == 0 && mv != 0ULL) atomicMax(A.dmove, mv);
+  }
 }
 
 void pc_update(sph_ctx *c, const sph_state *base, sph_state *out, const sph_derivs &d, double frac,
-               const MatTable &mt, const sph_params &p, cudaStream_t st) {
+               const MatTable &mt, const sph_params &p, cudaStream_t st, unsigned long long *dmove) {
   if (base->n == 0) return;
   PcArgs A;
   memset(&A, 0, sizeof(A));
@@ -377,6 +409,8 @@ void pc_update(sph_ctx *c, const sph_state *base, sph_state *out, const sph_deri
   A.frac = frac;
   A.mt = mt;
   A.density_sum = p.density_sum;
+  A.dmove = dmove;
+  A.err = c->d_err;
   { k_pc<<<nblk(base->n, 256), 256, 0, st>>>(A); ++sph::g_launches; }
 }
 

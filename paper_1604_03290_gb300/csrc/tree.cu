@@ -297,22 +297,13 @@ __global__ void k_pack(const double *__restrict__ x, const double *__restrict__ 
                        dim == 3 ? __dsub_rn(z[i], ilo[3 * inst + 2]) : 0.0};
   const double V[3] = {vx[i], vy[i], dim == 3 ? vz[i] : 0.0};
   float xh[3], xl[3], vh[3], vl[3];
+#pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
-    if (!f32_split_scaled(X[ax], kL, xh[ax], xl[ax])) {
-      const double Xs = X[ax] * U->invL;
-      xh[ax] = __double2float_rn(Xs);
-      xl[ax] = __double2float_rn(Xs - (double)xh[ax]);
-    }
-    if (!f32_split_scaled(V[ax], kV, vh[ax], vl[ax])) {
-      const double Vs = V[ax] * U->invV;
-      vh[ax] = __double2float_rn(Vs);
-      vl[ax] = __double2float_rn(Vs - (double)vh[ax]);
-    }
+    to_f32_split_scaled(X[ax], kL, U->invL, xh[ax], xl[ax]);
+    to_f32_split_scaled(V[ax], kV, U->invV, vh[ax], vl[ax]);
   }
-  float hf, mf, rf;
-  if (!f32_rn_scaled(h[i], kL, hf)) hf = __double2float_rn(h[i] * U->invL);
-  if (!f32_rn_scaled(m[i], kM, mf)) mf = __double2float_rn(m[i] * U->invM);
-  if (!f32_rn_scaled(rho[i], kR, rf)) rf = __double2float_rn(rho[i] * U->invrho);
+  const float hf = to_f32_scaled(h[i], kL, U->invL), mf = to_f32_scaled(m[i], kM, U->invM);
+  const float rf = to_f32_scaled(rho[i], kR, U->invrho);
   pk.px[i] = make_float4(xh[0], xh[1], xh[2], hf);
   pk.pxl[i] = make_float4(xl[0], xl[1], xl[2], mf);
   pk.pv[i] = make_float4(vh[0], vh[1], vh[2], rf);
@@ -817,19 +808,15 @@ __global__ void k_moments(Tree T, const double *__restrict__ x, const double *__
         if (ax >= dim) break;
         const double dl = __dsub_rn(blo[ax], ilo[ax]), dh = __dsub_rn(bhi[ax], ilo[ax]);
         const double dc = __dsub_rn(com[ax], ilo[ax]);
-        if (!f32_dir_scaled(dl, kL, false, bl[ax])) bl[ax] = __double2float_rd(dl * U->invL);
-        if (!f32_dir_scaled(dh, kL, true, bh[ax])) bh[ax] = __double2float_ru(dh * U->invL);
-        if (!f32_split_scaled(dc, kL, ch[ax], cl[ax])) {
-          const double Xc = dc * U->invL;
-          ch[ax] = __double2float_rn(Xc);
-          cl[ax] = __double2float_rn(Xc - (double)ch[ax]);
-        }
+        bl[ax] = to_f32_dir_scaled(dl, kL, false, U->invL);
+        bh[ax] = to_f32_dir_scaled(dh, kL, true, U->invL);
+        to_f32_split_scaled(dc, kL, U->invL, ch[ax], cl[ax]);
       }
-      float hf, mf, ef;
-      if (!f32_dir_scaled(hmax, kL, true, hf)) hf = __double2float_ru(hmax * U->invL);
-      if (!f32_rn_scaled(M, kM, mf)) mf = __double2float_rn(M * U->invM);
+      const float hf = to_f32_dir_scaled(hmax, kL, true, U->invL), mf = to_f32_scaled(M, kM, U->invM);
       const int lev = T.level[node];
-      if (!f32_rn_scaled(T.inst_s0[inst], kL - lev, ef)) ef = __double2float_rn(ldexp(T.inst_s0[inst], -lev) * U->invL);
+      // edge s0 / 2^level in code units: one exponent shift (the fallback's
+      // scale 2^(kL - level) is built from its bits)
+      const float ef = to_f32_scaled(T.inst_s0[inst], kL - lev, bitsd((uint64_t)(1023 + kL - lev) << 52));
       T.fbox_lo[node] = make_float4(bl[0], bl[1], bl[2], hf);
       T.fbox_hi[node] = make_float4(bh[0], bh[1], bh[2], 0.f);
       T.fcom_hi[node] = make_float4(ch[0], ch[1], ch[2], mf);

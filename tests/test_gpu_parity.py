@@ -136,6 +136,16 @@ def _small_impact(seed=31):
     return ps
 
 
+def _fast_impact(seed=33):
+    # a fixed step long enough that the predictor half-step moves the projectile
+    # by about half its support radius: the predictor evaluation's partner
+    # search must still find every partner
+    ps = wl.measurement_1m(seed=seed, n_side=14)
+    hp = ps.h[ps.v[2] < -1000.0].min()
+    ps.params = replace(ps.params, dt_fixed=2 * 0.5 * hp / 7000.0)
+    return ps
+
+
 def _small_cloud():
     ps = wl.cloud_collapse(seed=3, n=6000)
     return ps
@@ -155,6 +165,7 @@ CASES = {
     "solid2d": lambda: _random_solid(1, 2, n_side=30),
     "rings": lambda: wl.rings_2d(artificial_stress=True),
     "impact": _small_impact,
+    "impact_fast": _fast_impact,
     "cloud": _small_cloud,
     "batch": _small_batch,
 }
@@ -233,7 +244,8 @@ def _by_id(d, ids):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("case,nsteps,fixed", [("solid3d", 3, True), ("solid3d", 2, False), ("rings", 4, True),
-                                               ("impact", 2, False), ("batch", 2, False), ("cloud", 2, False)])
+                                               ("impact", 2, False), ("impact_fast", 2, True), ("batch", 2, False),
+                                               ("cloud", 2, False)])
 def test_steps_match_oracle(orc, S, case, nsteps, fixed, prec):
     ps = CASES[case]()
     if fixed:
