@@ -198,9 +198,9 @@ sph_status sph_neighbours(sph_ctx *ctx, const sph_state *state, int32_t leaf_siz
  * packed positions and partner columns live in one array of
  * SPH_STATIC_SCRATCH_BYTES bytes inside the library's device code; every
  * device that loads the library holds it until the process exits.  A call
- * needs about 570 + 4 * max_neighbours bytes per particle and at least
- * 0.9 MiB, so the array holds about 60 000 particles at max_neighbours =
- * 128; larger n returns SPH_ERR_CAPACITY, before touching the device, with a
+ * needs about 600 + 4 * max_neighbours bytes per particle and at least
+ * 1 MiB, so the array holds about 60 000 particles at max_neighbours = 128;
+ * larger n returns SPH_ERR_CAPACITY, before touching the device, with a
  * message that gives the bytes needed.  The call itself allocates nothing:
  * no cudaMalloc, cudaFree or other allocating routine.
  *

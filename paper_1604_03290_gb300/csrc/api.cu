@@ -106,6 +106,7 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   T.nchild = ctx_alloc<int32_t>(c, cn, ok);
   T.arrived = ctx_alloc<int32_t>(c, cn, ok);
   T.child = ctx_alloc<int32_t>(c, 8 * cn, ok);
+  T.nrec = ctx_alloc<int4>(c, cn, ok);
   T.level = ctx_alloc<int32_t>(c, cn, ok);
   T.cell = ctx_alloc<unsigned long long>(c, cn, ok);
   T.mass = ctx_alloc<double>(c, cn, ok);
@@ -130,10 +131,10 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   T.grp_end = ctx_alloc<int32_t>(c, T.cap_groups, ok);
   T.grp_inst = ctx_alloc<int32_t>(c, T.cap_groups, ok);
   T.ngroups = ctx_alloc<int32_t>(c, 1, ok);
-  c->pk.px = ctx_alloc<float4>(c, N, ok);
-  c->pk.pxl = ctx_alloc<float4>(c, N, ok);
-  c->pk.pv = ctx_alloc<float4>(c, N, ok);
-  c->pk.pvl = ctx_alloc<float4>(c, N, ok);
+  c->pk.px_ = ctx_alloc<float4>(c, N, ok);
+  c->pk.pxl_ = ctx_alloc<float4>(c, N, ok);
+  c->pk.pv_ = ctx_alloc<float4>(c, N, ok);
+  c->pk.pvl_ = ctx_alloc<float4>(c, N, ok);
   c->nb_idx = ctx_alloc<int32_t>(c, (int64_t)max_neighbours * N, ok);
   c->nb_cnt = ctx_alloc<int32_t>(c, N, ok);
   c->csr_total = ctx_alloc<int64_t>(c, 1, ok);

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kGrWarps * 32) k_gravity(GravArgs A) {
     const unsigned long long ka = act ? T.skey[slot] : 0ULL;
     double xa[3] = {0, 0, 0};
     for (int ax = 0; ax < dim; ++ax) xa[ax] = A.x[ax][a];
-    const float4 Pa = A.pk.px[a], Qa = A.pk.pxl[a];
+    const float4 Pa = A.pk.px(a), Qa = A.pk.pxl(a);
     const double e = MIXED ? A.eps * (double)Pa.w : A.eps * A.h[a];
     const R eps2 = (R)(e * e);
     const double s0r = T.inst_s0[inst];
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kGrWarps * 32) k_gravity(GravArgs A) {
           const int c = min(e1 - base, kMaxLeaf);
           if (lane < c) {
             const int32_t b = T.perm[base + lane];
-            const float4 pb = A.pk.px[b], qb = A.pk.pxl[b];
+            const float4 pb = A.pk.px(b), qb = A.pk.pxl(b);
             sh_hi[w][lane] = make_float4(pb.x, pb.y, pb.z, (float)0);
             sh_lo[w][lane] = make_float4(qb.x, qb.y, qb.z, qb.w);  // .w = m as float
             sh_b[w][lane] = b;

@@ -23,6 +23,12 @@
 namespace sph {
 
 constexpr int kNbWarps = 4;
+// resident blocks per SM the walk is compiled for: 8 (64 registers) was the
+// fastest of 4..12 on GB300, the walk being latency- and issue-bound
+#ifndef SPH_WALK_MIN_BLOCKS
+#define SPH_WALK_MIN_BLOCKS 8
+#endif
+#define SPH_WALK_BOUNDS __launch_bounds__(kNbWarps * 32, SPH_WALK_MIN_BLOCKS)
 constexpr float kBand = 6e-5f;
 
 __device__ __forceinline__ bool exact_partner(const double *__restrict__ x, const double *__restrict__ y,
@@ -39,21 +45,21 @@ __device__ __forceinline__ bool exact_partner(const double *__restrict__ x, cons
   return r2 < __dmul_rn(hab, hab);
 }
 
-__global__ void __launch_bounds__(kNbWarps * 32) k_partners(Tree T, PackedF32 pk, const double *__restrict__ x,
+__global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *__restrict__ x,
                                                             const double *__restrict__ y,
                                                             const double *__restrict__ z,
                                                             const double *__restrict__ h, int dim, int kmax,
                                                             int32_t *__restrict__ nb_idx, int32_t *__restrict__ nb_cnt,
-                                                            int64_t ld, int walk_leaf, int32_t *err,
+                                                            int64_t ld, int32_t *err,
                                                             const unsigned long long *__restrict__ grow,
                                                             const Units *__restrict__ U) {
   __shared__ float4 sc[kNbWarps][kMaxLeaf];
   __shared__ int32_t sb[kNbWarps][kMaxLeaf];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ngroups = *T.ngroups;
-  // The walk stops at nodes of at most walk_leaf particles (or tree leaves)
+  // The walk stops at nodes flagged in their box word (at most
+  // max(leaf_size, walk_leaf) particles, or depth B; set by the tree build)
   // and culls their whole particle range: any stopping rule gives the same set.
-  const int L = max(T.leaf_size, walk_leaf), B = T.max_depth;
   const int nnodes = *T.nnodes;
   // Node boxes are those of the tree the walk runs on; when the particles have
   // moved since it was built (by at most `grow` per axis), widening the
@@ -64,15 +70,16 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_partners(Tree T, PackedF32 pk
     const int32_t s0 = T.grp_start[g], s1 = T.grp_end[g], inst = T.grp_inst[g];
     const int32_t slot = s0 + lane;
     const bool act = slot < s1;
-    const int32_t a = act ? T.perm[slot] : -1;
-    float4 P = act ? pk.px[a] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 Q = act ? pk.pxl[a] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int32_t a = act ? (T.perm_identity ? slot : T.perm[slot]) : -1;
+    float4 P = act ? pk.px(a) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 Q = act ? pk.pxl(a) : make_float4(0.f, 0.f, 0.f, 0.f);
     // reference point: lane 0's position
     const float cx = __shfl_sync(0xffffffffu, P.x, 0), cy = __shfl_sync(0xffffffffu, P.y, 0),
                 cz = __shfl_sync(0xffffffffu, P.z, 0);
     const float lx = __shfl_sync(0xffffffffu, Q.x, 0), ly = __shfl_sync(0xffffffffu, Q.y, 0),
                 lz = __shfl_sync(0xffffffffu, Q.z, 0);
     const float rax = (P.x - cx) + (Q.x - lx), ray = (P.y - cy) + (Q.y - ly), raz = (P.z - cz) + (Q.z - lz);
+    const float hha = 0.5f * P.w;
     // group box (hi coordinates, for the node test) and largest h
     float gl[3] = {act ? P.x : 3e38f, act ? P.y : 3e38f, act ? P.z : 3e38f};
     float gh[3] = {act ? P.x : -3e38f, act ? P.y : -3e38f, act ? P.z : -3e38f};
@@ -102,30 +109,35 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_partners(Tree T, PackedF32 pk
     const int32_t stop = root >= 0 ? T.skip[root] : root;
     int cnt = 0;
     int iter = 0;
+    // Stackless pre-order walk over the node box words: (lo, +-hmax) and
+    // (hi, skip), the sign of hmax marking the nodes where the walk stops.
     for (int32_t nd = root; nd < stop && iter <= nnodes; ++iter) {
       const float4 bl = __ldg(&T.fbox_lo[nd]), bh = __ldg(&T.fbox_hi[nd]);
+      const float hw = fabsf(bl.w);
       float gx = fmaxf(0.f, fmaxf(bl.x - gh[0], gl[0] - bh.x));
       float gy = fmaxf(0.f, fmaxf(bl.y - gh[1], gl[1] - bh.y));
       float gz = fmaxf(0.f, fmaxf(bl.z - gh[2], gl[2] - bh.z));
       float d2 = gx * gx + gy * gy + gz * gz;
-      float thr = 0.5f * (hg + bl.w) * (1.0f + 1e-5f);
+      float thr = 0.5f * (hg + hw) * (1.0f + 1e-5f);
+      bool enter = false;
       if (d2 <= thr * thr) {
-        const int32_t f = __ldg(&T.first[nd]), e = __ldg(&T.end[nd]);
-        if (e - f <= L || __ldg(&T.level[nd]) == B) {
+        if (__float_as_uint(bl.w) >> 31) {  // the walk stops here: cull its particles
+          const int4 nr = __ldg(&T.nrec[nd]);
+          const int32_t f = nr.x, e = nr.y;
           for (int32_t base = f; base < e; base += kMaxLeaf) {  // leaves at full depth may exceed 32
             // stage the candidates that come within reach of the group's box
             bool keep = false;
             float4 cand = make_float4(0.f, 0.f, 0.f, 0.f);
             int32_t b = -1;
             if (base + lane < e) {
-              b = __ldg(&T.perm[base + lane]);
-              float4 Pb = __ldg(&pk.px[b]), Qb = __ldg(&pk.pxl[b]);
+              b = T.perm_identity ? base + lane : __ldg(&T.perm[base + lane]);
+              float4 Pb = __ldg(&pk.px(b)), Qb = __ldg(&pk.pxl(b));
               cand = make_float4((Pb.x - cx) + (Qb.x - lx), (Pb.y - cy) + (Qb.y - ly), (Pb.z - cz) + (Qb.z - lz),
-                                 Pb.w);
+                                 0.5f * Pb.w);  // half support radius: h_ab = h_a / 2 + h_b / 2
               float qx = fmaxf(0.f, fmaxf(rl[0] - cand.x, cand.x - rh[0]));
               float qy = fmaxf(0.f, fmaxf(rl[1] - cand.y, cand.y - rh[1]));
               float qz = fmaxf(0.f, fmaxf(rl[2] - cand.z, cand.z - rh[2]));
-              float reach = 0.5f * (hg + cand.w) * (1.0f + 1e-5f) + rslack;
+              float reach = (0.5f * hg + cand.w) * (1.0f + 1e-5f) + rslack;
               keep = qx * qx + qy * qy + qz * qz <= reach * reach;
             }
             const unsigned km = __ballot_sync(0xffffffffu, keep);
@@ -142,7 +154,7 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_partners(Tree T, PackedF32 pk
                 const int32_t b = sb[w][k];
                 float dx = rax - cb.x, dy = ray - cb.y, dz = raz - cb.z;
                 float r2 = dx * dx + dy * dy + dz * dz;
-                float hab = 0.5f * (P.w + cb.w);
+                float hab = hha + cb.w;
                 float h2 = hab * hab;
                 bool in;
                 if (r2 < h2 * (1.0f - kBand)) in = true;
@@ -156,13 +168,11 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_partners(Tree T, PackedF32 pk
             }
             __syncwarp();
           }
-          nd = __ldg(&T.skip[nd]);
         } else {
-          nd = nd + 1;
+          enter = true;
         }
-      } else {
-        nd = __ldg(&T.skip[nd]);
       }
+      nd = enter ? nd + 1 : __float_as_int(bh.w);
     }
     if (iter > nnodes) raise_err(err, ERR_TIMEOUT);
     if (act) {
@@ -176,7 +186,7 @@ void find_partners(sph_ctx *c, const sph_state *s, cudaStream_t st, const unsign
   if (s->n == 0) return;
   int blocks = c->num_sms * c->tune.walk_blocks_per_sm;
   { k_partners<<<blocks, kNbWarps * 32, 0, st>>>(c->tree, c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim, c->kmax,
-                                              c->nb_idx, c->nb_cnt, c->cap_n, c->tune.walk_leaf, c->d_err, grow,
+                                              c->nb_idx, c->nb_cnt, c->cap_n, c->d_err, grow,
                                               c->units); ++sph::g_launches; }
 }
 

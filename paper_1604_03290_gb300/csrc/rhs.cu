@@ -70,6 +70,14 @@ __device__ __forceinline__ double rsqrt_or_zero<double>(double r2) {
   return r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
 }
 
+// resident blocks per SM the neighbour passes are compiled for (register
+// budget); by default the compiler chooses
+#ifdef SPH_PASS_MIN_BLOCKS
+#define SPH_PASS_BOUNDS __launch_bounds__(128, SPH_PASS_MIN_BLOCKS)
+#else
+#define SPH_PASS_BOUNDS __launch_bounds__(128)
+#endif
+
 // 1 / x, correctly rounded: the same value as the division
 template <class R>
 __device__ __forceinline__ R rcp_rn(R x);
@@ -119,17 +127,17 @@ struct Own<true> {
   float4 P, Q, V, W;
   float h, rho, m;
   __device__ void load(const RhsArgs &A, int64_t a) {
-    P = A.pk.px[a];
-    Q = A.pk.pxl[a];
-    V = A.pk.pv[a];
-    W = A.pk.pvl[a];
+    P = A.pk.px(a);
+    Q = A.pk.pxl(a);
+    V = A.pk.pv(a);
+    W = A.pk.pvl(a);
     h = P.w;
     rho = V.w;
     m = Q.w;
   }
   __device__ __forceinline__ void pair(const RhsArgs &A, int32_t b, float d[3], float w[3], float &hb, float &rhob,
                                        float &mb, float &vol) const {
-    const float4 Pb = A.pk.px[b], Qb = A.pk.pxl[b], Vb = A.pk.pv[b], Wb = A.pk.pvl[b];
+    const float4 Pb = A.pk.px(b), Qb = A.pk.pxl(b), Vb = A.pk.pv(b), Wb = A.pk.pvl(b);
     d[0] = (P.x - Pb.x) + (Q.x - Qb.x);
     d[1] = (P.y - Pb.y) + (Q.y - Qb.y);
     d[2] = (P.z - Pb.z) + (Q.z - Qb.z);
@@ -262,7 +270,7 @@ __device__ __forceinline__ void sym_eigen(int dim, R A[3][3], R w[3], R V[3][3])
 // Pass A + per-particle update
 // ---------------------------------------------------------------------------
 template <bool MIXED, int DIM>
-__global__ void __launch_bounds__(128) k_passA(RhsArgs A) {
+__global__ void SPH_PASS_BOUNDS k_passA(RhsArgs A) {
   using R = typename std::conditional<MIXED, float, double>::type;
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= A.n) return;
@@ -553,7 +561,7 @@ __device__ __forceinline__ R ipow(R f, R n) {
 }
 
 template <bool MIXED, bool AS, int DIM>
-__global__ void __launch_bounds__(128) k_passB(RhsArgs A) {
+__global__ void SPH_PASS_BOUNDS k_passB(RhsArgs A) {
   using R = typename std::conditional<MIXED, float, double>::type;
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= A.n) return;
@@ -638,14 +646,14 @@ __global__ void k_repack_rho(const double *__restrict__ rho, const double *__res
                              const Units *__restrict__ U) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  float4 v = pk.pv[i], w = pk.pvl[i];
+  float4 v = pk.pv(i), w = pk.pvl(i);
   // as in the packing after the tree build: rho scaled by its power-of-two
   // unit, and the volume m / rho from the FP32 views
   const float rf = to_f32_scaled(rho[i], pow2_exp(U->invrho), U->invrho);
   v.w = rf;
-  w.w = __fdiv_rn(pk.pxl[i].w, rf);
-  pk.pv[i] = v;
-  pk.pvl[i] = w;
+  w.w = __fdiv_rn(pk.pxl(i).w, rf);
+  pk.pv(i) = v;
+  pk.pvl(i) = w;
 }
 
 void rhs_passes(sph_ctx *c, sph_state *s, const MatTable &mt, const sph_params &p, const sph_derivs &out,

@@ -37,11 +37,16 @@ constexpr int kMaxLeaf = 32;
 // Per-particle FP32 views used by the walks and the mixed-precision passes.
 // Positions are split X = x - corner into hi = float(X), lo = float(X - hi)
 // so that differences of neighbours keep ~48 bits; velocities likewise.
+// Four separate arrays (structure of arrays): the lanes of a warp gather
+// nearby neighbours, whose words then share few 128-byte lines per load; an
+// interleaved 64-byte record per particle measured slower in the passes
+// (more lines, i.e. L1 wavefronts, per gather instruction).
 struct PackedF32 {
-  float4 *px;   // (x_hi, y_hi, z_hi, h)
-  float4 *pxl;  // (x_lo, y_lo, z_lo, m)
-  float4 *pv;   // (vx_hi, vy_hi, vz_hi, rho)
-  float4 *pvl;  // (vx_lo, vy_lo, vz_lo, m/rho)
+  float4 *px_, *pxl_, *pv_, *pvl_;
+  __host__ __device__ float4 &px(int64_t i) const { return px_[i]; }    // (x_hi, y_hi, z_hi, h)
+  __host__ __device__ float4 &pxl(int64_t i) const { return pxl_[i]; }  // (x_lo, y_lo, z_lo, m)
+  __host__ __device__ float4 &pv(int64_t i) const { return pv_[i]; }    // (vx_hi, vy_hi, vz_hi, rho)
+  __host__ __device__ float4 &pvl(int64_t i) const { return pvl_[i]; }  // (vx_lo, vy_lo, vz_lo, m/rho)
 };
 
 struct Tree {
@@ -63,12 +68,14 @@ struct Tree {
   int32_t *nnodes;     // device scalar
   int32_t *first, *end, *skip, *parent, *nchild, *arrived, *level;
   int32_t *child;      // up to 8 child ids per node, in arrival order
+  int4 *nrec;          // (first, end, skip, level) per node, for the walks
   unsigned long long *cell;  // level prefix of the key (instance bits included)
   double *mass, *com;  // com: 3 * cap_nodes, component-major
   double *bblo, *bbhi; // tight particle box, 3 * cap_nodes each
   double *hmax;
-  float4 *fbox_lo;     // (lo xyz relative to instance corner, rounded down; hmax rounded up)
-  float4 *fbox_hi;     // (hi xyz, rounded up)
+  float4 *fbox_lo;     // (lo xyz relative to instance corner, rounded down; +-hmax rounded up, negative
+                       //  where the partner walk stops: at most max(leaf_size, walk_leaf) particles or depth B)
+  float4 *fbox_hi;     // (hi xyz, rounded up; skip[] as int bits)
   float4 *fcom_hi;     // (com hi xyz relative to instance corner, mass)
   float4 *fcom_lo;     // (com lo xyz, edge s0 / 2^level)
   // per instance
@@ -84,6 +91,7 @@ struct Tree {
   int64_t cap_groups;
   int leaf_size, max_depth, dim, ninst;
   int64_t n;
+  int perm_identity;   // host flag: the state is in tree order (perm[i] = i)
 };
 
 struct MatTable {

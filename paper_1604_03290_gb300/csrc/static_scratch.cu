@@ -77,6 +77,7 @@ void layout(sph_ctx *c, Carve &k, int64_t n, int ninst, int leaf_size, int kmax)
   T.nchild = k.take<int32_t>(cn);
   T.arrived = k.take<int32_t>(cn);
   T.child = k.take<int32_t>(8 * cn);
+  T.nrec = k.take<int4>(cn);
   T.level = k.take<int32_t>(cn);
   T.cell = k.take<unsigned long long>(cn);
   T.mass = k.take<double>(cn);
@@ -100,10 +101,10 @@ void layout(sph_ctx *c, Carve &k, int64_t n, int ninst, int leaf_size, int kmax)
   T.grp_end = k.take<int32_t>(T.cap_groups);
   T.grp_inst = k.take<int32_t>(T.cap_groups);
   T.ngroups = k.take<int32_t>(1);
-  c->pk.px = k.take<float4>(N);
-  c->pk.pxl = k.take<float4>(N);
-  c->pk.pv = k.take<float4>(N);
-  c->pk.pvl = k.take<float4>(N);
+  c->pk.px_ = k.take<float4>(N);
+  c->pk.pxl_ = k.take<float4>(N);
+  c->pk.pv_ = k.take<float4>(N);
+  c->pk.pvl_ = k.take<float4>(N);
   c->nb_idx = k.take<int32_t>((int64_t)kmax * N);
   c->nb_cnt = k.take<int32_t>(N);
   c->cap_n = N;

@@ -304,10 +304,10 @@ __global__ void k_pack(const double *__restrict__ x, const double *__restrict__ 
   }
   const float hf = to_f32_scaled(h[i], kL, U->invL), mf = to_f32_scaled(m[i], kM, U->invM);
   const float rf = to_f32_scaled(rho[i], kR, U->invrho);
-  pk.px[i] = make_float4(xh[0], xh[1], xh[2], hf);
-  pk.pxl[i] = make_float4(xl[0], xl[1], xl[2], mf);
-  pk.pv[i] = make_float4(vh[0], vh[1], vh[2], rf);
-  pk.pvl[i] = make_float4(vl[0], vl[1], vl[2], __fdiv_rn(mf, rf));
+  pk.px(i) = make_float4(xh[0], xh[1], xh[2], hf);
+  pk.pxl(i) = make_float4(xl[0], xl[1], xl[2], mf);
+  pk.pv(i) = make_float4(vh[0], vh[1], vh[2], rf);
+  pk.pvl(i) = make_float4(vl[0], vl[1], vl[2], __fdiv_rn(mf, rf));
 }
 
 // ---------------------------------------------------------------------------
@@ -624,6 +624,7 @@ __global__ void k_node_emit(KeyLevels K, int64_t n, int L, const int64_t *__rest
       T.level[id] = l;
       T.cell[id] = K.prefix(i, l);
       T.skip[id] = min((int64_t)nstart[end], T.cap_nodes);
+      T.nrec[id] = make_int4((int32_t)i, (int32_t)end, T.skip[id], l);
       T.parent[id] = parent;
       if (parent >= 0) {
         const int r = atomicAdd(&T.nchild[parent], 1);
@@ -750,7 +751,8 @@ __global__ void k_group_emit(Tree T, const int32_t *__restrict__ gstart, const i
 __global__ void k_moments(Tree T, const double *__restrict__ x, const double *__restrict__ y,
                           const double *__restrict__ z, const double *__restrict__ m, const double *__restrict__ h,
                           int dim, int L, const int64_t *__restrict__ inst_off, int ninst,
-                          const Units *__restrict__ U) {
+                          const Units *__restrict__ U, int walk_leaf) {
+  const int Lw = max(L, walk_leaf);
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= *T.nleaf) return;
   const int64_t id = T.ncount[tid];  // one thread per leaf
@@ -817,8 +819,10 @@ __global__ void k_moments(Tree T, const double *__restrict__ x, const double *__
       // edge s0 / 2^level in code units: one exponent shift (the fallback's
       // scale 2^(kL - level) is built from its bits)
       const float ef = to_f32_scaled(T.inst_s0[inst], kL - lev, bitsd((uint64_t)(1023 + kL - lev) << 52));
-      T.fbox_lo[node] = make_float4(bl[0], bl[1], bl[2], hf);
-      T.fbox_hi[node] = make_float4(bh[0], bh[1], bh[2], 0.f);
+      const int32_t nf = T.first[node], ne = T.end[node];
+      const bool stop = ne - nf <= Lw || lev == T.max_depth;
+      T.fbox_lo[node] = make_float4(bl[0], bl[1], bl[2], stop ? -hf : hf);
+      T.fbox_hi[node] = make_float4(bh[0], bh[1], bh[2], __int_as_float(T.skip[node]));
       T.fcom_hi[node] = make_float4(ch[0], ch[1], ch[2], mf);
       T.fcom_lo[node] = make_float4(cl[0], cl[1], cl[2], ef);
     }
@@ -889,6 +893,7 @@ void tree_build(sph_ctx *c, const sph_state *s, int leaf_size, int max_depth, cu
   const int dim = s->dim;
   T.leaf_size = leaf_size;
   T.max_depth = max_depth;
+  T.perm_identity = 0;
   T.dim = dim;
   T.ninst = ninst;
   T.n = n;
@@ -922,7 +927,8 @@ void tree_build(sph_ctx *c, const sph_state *s, int leaf_size, int max_depth, cu
   cudaMemsetAsync(T.nleaf, 0, sizeof(int32_t), st);
   { k_node_emit<<<nblk(n + 1, 256), 256, 0, st>>>(K, n, leaf_size, s->inst_off, ninst, T.nstart, T, c->d_err); ++sph::g_launches; }
   { k_moments<<<nblk(std::max<int64_t>(n, 1), 256), 256, 0, st>>>(
-      T, s->x[0], s->x[1], s->x[2], s->m, s->h, dim, leaf_size, s->inst_off, ninst, c->units); ++sph::g_launches; }
+      T, s->x[0], s->x[1], s->x[2], s->m, s->h, dim, leaf_size, s->inst_off, ninst, c->units,
+      c->tune.walk_leaf); ++sph::g_launches; }
   { k_inst_roots<<<nblk(ninst, 128), 128, 0, st>>>(s->inst_off, ninst, n, T.nstart, T); ++sph::g_launches; }
   { k_group_count<<<nblk(T.cap_nodes + 1, 256), 256, 0, st>>>(T, T.gcnt); ++sph::g_launches; }
   scan_excl_i32(T.gcnt, T.gstart, T.cap_nodes + 1, T.scan_tmp, st);
@@ -932,50 +938,82 @@ void tree_build(sph_ctx *c, const sph_state *s, int leaf_size, int max_depth, cu
 // ---------------------------------------------------------------------------
 // In-place reorder of the caller's state along the tree
 // ---------------------------------------------------------------------------
-__global__ void k_gather_d(const double *__restrict__ src, double *__restrict__ dst, const int32_t *__restrict__ perm,
-                           int64_t n) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = src[perm[i]];
-}
-__global__ void k_gather_i(const int32_t *__restrict__ src, int32_t *__restrict__ dst,
-                           const int32_t *__restrict__ perm, int64_t n) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = src[perm[i]];
-}
 __global__ void k_iota(int32_t *p, int64_t n) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = (int32_t)i;
 }
 
+// All fields at once: dst_f[i] = src_f[perm[i]] (gather) or dst_f[i] = src_f[i]
+// (copy back), doubles then ints.
+constexpr int kMaxFields = 20;
+struct FieldSet {
+  const double *dsrc[kMaxFields];
+  double *ddst[kMaxFields];
+  const int32_t *isrc[2];
+  int32_t *idst[2];
+  int nd, ni;
+};
+
+__global__ void k_gather_fields(FieldSet F, const int32_t *__restrict__ perm, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t j = perm ? perm[i] : i;
+#pragma unroll 4
+  for (int f = 0; f < F.nd; ++f) F.ddst[f][i] = F.dsrc[f][j];
+  for (int f = 0; f < F.ni; ++f) F.idst[f][i] = F.isrc[f][j];
+}
+
 void tree_reorder_state(sph_ctx *c, sph_state *s, cudaStream_t st) {
   const int64_t n = s->n;
   if (n == 0) return;
-  const int32_t *perm = c->tree.perm;
-  double *buf = c->st.gather;
-  auto gd = [&](double *f) {
+  // scratch: the predicted-state and derivative buffers, free at this point
+  StepBufs &B = c->st;
+  double *scratch[kMaxFields] = {B.x[0], B.x[1], B.x[2], B.v[0], B.v[1], B.v[2], B.rho, B.u, B.dmg,
+                                 B.d_x[0][0], B.d_x[0][1], B.d_x[0][2], B.d_v[0][0], B.d_v[0][1],
+                                 B.d_v[0][2], B.d_rho[0], B.d_u[0], B.d_dmg[0], B.d_cs[0], B.gather};
+  FieldSet G, R;
+  memset(&G, 0, sizeof(G));
+  auto add = [&](double *f) {
     if (!f) return;
-    { k_gather_d<<<nblk(n, 256), 256, 0, st>>>(f, buf, perm, n); ++sph::g_launches; }
-    cudaMemcpyAsync(f, buf, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
-  };
-  auto gi = [&](int32_t *f) {
-    if (!f) return;
-    { k_gather_i<<<nblk(n, 256), 256, 0, st>>>(f, c->st.gather_i, perm, n); ++sph::g_launches; }
-    cudaMemcpyAsync(f, c->st.gather_i, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st);
+    G.dsrc[G.nd] = f;
+    G.ddst[G.nd] = scratch[G.nd];
+    ++G.nd;
   };
   for (int ax = 0; ax < s->dim; ++ax) {
-    gd(s->x[ax]);
-    gd(s->v[ax]);
+    add(s->x[ax]);
+    add(s->v[ax]);
   }
-  gd(s->rho);
-  gd(s->u);
-  gd(s->m);
-  gd(s->h);
-  gd(s->dmg);
+  add(s->rho);
+  add(s->u);
+  add(s->m);
+  add(s->h);
+  add(s->dmg);
   if (s->S)
-    for (int k = 0; k < nsym(s->dim); ++k) gd(s->S + (int64_t)k * n);
-  gi(s->mat);
-  gi(s->id);
+    for (int k = 0; k < nsym(s->dim); ++k) add(s->S + (int64_t)k * n);
+  int32_t *iscr[2] = {B.gather_i, B.d_nact[0]};
+  if (s->mat) {
+    G.isrc[G.ni] = s->mat;
+    G.idst[G.ni] = iscr[G.ni];
+    ++G.ni;
+  }
+  if (s->id) {
+    G.isrc[G.ni] = s->id;
+    G.idst[G.ni] = iscr[G.ni];
+    ++G.ni;
+  }
+  R = G;
+  for (int f = 0; f < G.nd; ++f) {
+    R.dsrc[f] = G.ddst[f];
+    R.ddst[f] = const_cast<double *>(G.dsrc[f]);
+  }
+  for (int f = 0; f < G.ni; ++f) {
+    R.isrc[f] = G.idst[f];
+    R.idst[f] = const_cast<int32_t *>(G.isrc[f]);
+  }
+  { k_gather_fields<<<nblk(n, 256), 256, 0, st>>>(G, c->tree.perm, n); ++sph::g_launches; }
+  { k_gather_fields<<<nblk(n, 256), 256, 0, st>>>(R, nullptr, n); ++sph::g_launches; }
   { k_iota<<<nblk(n, 256), 256, 0, st>>>(c->tree.perm, n); ++sph::g_launches; }
+  c->tree.perm_identity = 1;
   pack_f32(c, s, st);
 }
 
