@@ -70,12 +70,18 @@ __device__ __forceinline__ double rsqrt_or_zero<double>(double r2) {
   return r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
 }
 
-// resident blocks per SM the neighbour passes are compiled for (register
-// budget); by default the compiler chooses
-#ifdef SPH_PASS_MIN_BLOCKS
-#define SPH_PASS_BOUNDS __launch_bounds__(128, SPH_PASS_MIN_BLOCKS)
+// Resident blocks per SM the neighbour passes are compiled for (register
+// budget).  Measured on GB300 with the partner prefetch below: pass A is
+// fastest at 6 (capped registers) in mixed precision, pass B with the
+// compiler's own choice.
+#ifndef SPH_PASSA_MIN_BLOCKS
+#define SPH_PASSA_MIN_BLOCKS 6
+#endif
+#define SPH_PASSA_BOUNDS __launch_bounds__(128, MIXED ? SPH_PASSA_MIN_BLOCKS : 1)  // FP64: uncapped
+#ifdef SPH_PASSB_MIN_BLOCKS
+#define SPH_PASSB_BOUNDS __launch_bounds__(128, SPH_PASSB_MIN_BLOCKS)
 #else
-#define SPH_PASS_BOUNDS __launch_bounds__(128)
+#define SPH_PASSB_BOUNDS __launch_bounds__(128)
 #endif
 
 // 1 / x, correctly rounded: the same value as the division
@@ -120,6 +126,15 @@ struct Own<false> {
     mb = A.m[b];
     vol = mb / rhob;
   }
+  // the same split into the loads of b (issued ahead) and the arithmetic
+  struct Raw {
+    int32_t b;
+  };
+  __device__ __forceinline__ Raw fetch(const RhsArgs &, int32_t b) const { return Raw{b}; }
+  __device__ __forceinline__ void from(const RhsArgs &A, const Raw &r, double d[3], double w[3], double &hb,
+                                       double &rhob, double &mb, double &vol) const {
+    pair(A, r.b, d, w, hb, rhob, mb, vol);
+  }
 };
 
 template <>
@@ -135,9 +150,22 @@ struct Own<true> {
     rho = V.w;
     m = Q.w;
   }
+  struct Raw {
+    float4 P, Q, V, W;
+  };
+  __device__ __forceinline__ Raw fetch(const RhsArgs &A, int32_t b) const {
+    return Raw{A.pk.px(b), A.pk.pxl(b), A.pk.pv(b), A.pk.pvl(b)};
+  }
+  __device__ __forceinline__ void from(const RhsArgs &, const Raw &r, float d[3], float w[3], float &hb,
+                                       float &rhob, float &mb, float &vol) const {
+    unpack(r.P, r.Q, r.V, r.W, d, w, hb, rhob, mb, vol);
+  }
   __device__ __forceinline__ void pair(const RhsArgs &A, int32_t b, float d[3], float w[3], float &hb, float &rhob,
                                        float &mb, float &vol) const {
-    const float4 Pb = A.pk.px(b), Qb = A.pk.pxl(b), Vb = A.pk.pv(b), Wb = A.pk.pvl(b);
+    unpack(A.pk.px(b), A.pk.pxl(b), A.pk.pv(b), A.pk.pvl(b), d, w, hb, rhob, mb, vol);
+  }
+  __device__ __forceinline__ void unpack(const float4 Pb, const float4 Qb, const float4 Vb, const float4 Wb, float d[3],
+                                         float w[3], float &hb, float &rhob, float &mb, float &vol) const {
     d[0] = (P.x - Pb.x) + (Q.x - Qb.x);
     d[1] = (P.y - Pb.y) + (Q.y - Qb.y);
     d[2] = (P.z - Pb.z) + (Q.z - Qb.z);
@@ -148,6 +176,61 @@ struct Own<true> {
     rhob = Vb.w;
     mb = Qb.w;
     vol = Wb.w;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Partner cursor: the column-major list of particle a, read with the index
+// two pairs ahead and the neighbour's data one pair ahead, so that the
+// gathers of pair k + 1 are in flight while pair k is evaluated.
+// ---------------------------------------------------------------------------
+#ifndef SPH_PASS_PREFETCH
+#define SPH_PASS_PREFETCH 1
+#endif
+
+template <bool MIXED, bool WITH_T = false>
+struct PartnerCursor {
+  using Raw = typename Own<MIXED>::Raw;
+  static constexpr bool kT = MIXED && WITH_T;  // also the neighbour's T words (pass B, mixed)
+  const int32_t *col;
+  int64_t ld;
+  int cnt;
+  int32_t b1, b2;
+  Raw r1;
+  float4 t0, t1;
+  __device__ __forceinline__ void start(const RhsArgs &A, const Own<MIXED> &o, int64_t a, int n) {
+    col = A.nb_idx + a;
+    ld = A.ld;
+    cnt = n;
+    b1 = n > 0 ? col[0] : 0;
+    b2 = n > 1 ? col[ld] : 0;
+    if (n > 0) {
+      r1 = o.fetch(A, b1);
+      if constexpr (kT) {
+        t0 = A.Tf[b1];
+        t1 = A.Tf[A.ld + b1];
+      }
+    }
+  }
+  // the pair k: its index, its raw data and (kT) its T words
+  __device__ __forceinline__ int32_t next(const RhsArgs &A, const Own<MIXED> &o, int k, Raw &cur, float4 &ct0,
+                                          float4 &ct1) {
+    const int32_t b = b1;
+    cur = r1;
+    if constexpr (kT) {
+      ct0 = t0;
+      ct1 = t1;
+    }
+    b1 = b2;
+    if (k + 2 < cnt) b2 = col[(int64_t)(k + 2) * ld];
+    if (k + 1 < cnt) {
+      r1 = o.fetch(A, b1);
+      if constexpr (kT) {
+        t0 = A.Tf[b1];
+        t1 = A.Tf[A.ld + b1];
+      }
+    }
+    return b;
   }
 };
 
@@ -270,7 +353,7 @@ __device__ __forceinline__ void sym_eigen(int dim, R A[3][3], R w[3], R V[3][3])
 // Pass A + per-particle update
 // ---------------------------------------------------------------------------
 template <bool MIXED, int DIM>
-__global__ void SPH_PASS_BOUNDS k_passA(RhsArgs A) {
+__global__ void SPH_PASSA_BOUNDS k_passA(RhsArgs A) {
   using R = typename std::conditional<MIXED, float, double>::type;
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= A.n) return;
@@ -286,10 +369,21 @@ __global__ void SPH_PASS_BOUNDS k_passA(RhsArgs A) {
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) L[i][j] = G[i][j] = R(0);
   const int cnt = A.nb_cnt[a];
+#if SPH_PASS_PREFETCH
+  PartnerCursor<MIXED> cur;
+  cur.start(A, o, a, cnt);
+#endif
   for (int k = 0; k < cnt; ++k) {
-    const int32_t b = A.nb_idx[(int64_t)k * A.ld + a];
     R d[3], w[3], hb, rhob, mb, vol;
+#if SPH_PASS_PREFETCH
+    typename Own<MIXED>::Raw raw;
+    float4 t0, t1;
+    cur.next(A, o, k, raw, t0, t1);
+    o.from(A, raw, d, w, hb, rhob, mb, vol);
+#else
+    const int32_t b = A.nb_idx[(int64_t)k * A.ld + a];
     o.pair(A, b, d, w, hb, rhob, mb, vol);
+#endif
     const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     const R rinv = rsqrt_or_zero(r2);
     const R r = r2 * rinv;
@@ -561,7 +655,7 @@ __device__ __forceinline__ R ipow(R f, R n) {
 }
 
 template <bool MIXED, bool AS, int DIM>
-__global__ void SPH_PASS_BOUNDS k_passB(RhsArgs A) {
+__global__ void SPH_PASSB_BOUNDS k_passB(RhsArgs A) {
   using R = typename std::conditional<MIXED, float, double>::type;
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= A.n) return;
@@ -579,12 +673,34 @@ __global__ void SPH_PASS_BOUNDS k_passB(RhsArgs A) {
   const R dmpd = (R)(P.dmpd * (MIXED ? A.U->invL : 1.0));
   KahanT<R> acc[3], du;
   const int cnt = A.nb_cnt[a];
+#if SPH_PASS_PREFETCH
+  PartnerCursor<MIXED, true> cur;
+  cur.start(A, o, a, cnt);
+#endif
   for (int k = 0; k < cnt; ++k) {
-    const int32_t b = A.nb_idx[(int64_t)k * A.ld + a];
     R d[3], w[3], hb, rhob, mb, vol;
-    o.pair(A, b, d, w, hb, rhob, mb, vol);
     R Tb[6], csb;
+#if SPH_PASS_PREFETCH
+    typename Own<MIXED>::Raw raw;
+    float4 t0, t1;
+    const int32_t b = cur.next(A, o, k, raw, t0, t1);
+    o.from(A, raw, d, w, hb, rhob, mb, vol);
+    if constexpr (MIXED) {
+      Tb[0] = t0.x;
+      Tb[1] = t0.y;
+      Tb[2] = t0.z;
+      Tb[3] = t0.w;
+      Tb[4] = t1.x;
+      Tb[5] = t1.y;
+      csb = t1.z;
+    } else {
+      load_T<MIXED>(A, b, ns, Tb, csb);
+    }
+#else
+    const int32_t b = A.nb_idx[(int64_t)k * A.ld + a];
+    o.pair(A, b, d, w, hb, rhob, mb, vol);
     load_T<MIXED>(A, b, ns, Tb, csb);
+#endif
     const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     const R rinv = rsqrt_or_zero(r2);
     const R r = r2 * rinv;
