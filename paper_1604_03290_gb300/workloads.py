@@ -409,7 +409,11 @@ def batched_impacts(seed=5, ninst=256, nmin=2000, nmax=50000, dx=1e-3, vmin=3000
     x = np.concatenate(xs, axis=1)
     v = np.concatenate(vs, axis=1)
     n = x.shape[1]
-    params = Params(dim=3, alpha=1.0, beta=2.0, dmpd=dx, u_floor=1e3, S_floor=1e5)
+    # the Morton key holds 3 * max_depth cell bits plus ceil(log2(ninst))
+    # instance bits in 64
+    ibits = max(int(ninst - 1).bit_length(), 0)
+    params = Params(dim=3, alpha=1.0, beta=2.0, dmpd=dx, u_floor=1e3, S_floor=1e5,
+                    max_depth=min(21, (64 - ibits) // 3))
     ps = _finish(3, x, v, np.full(n, mat.rho0 * dx ** 3), np.full(n, 2.4 * dx), np.full(n, mat.rho0), np.zeros(n),
                  np.zeros(n, np.int32), [mat], params, with_dmg=True, name="batched_%d" % ninst,
                  inst_off=np.asarray(off, np.int64))

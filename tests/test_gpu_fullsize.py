@@ -1,0 +1,152 @@
+"""Parity at the full sizes of the benchmarked configurations, in the launch
+configuration the bench times (max_neighbours 128, the workloads' own leaf
+size and depth): every particle's right-hand side against the FP64 oracle
+(1M-particle aluminium impact as measured, the 64^3 cube + sphere, the 2M
+cloud and the 2 x 1M Ceres pair without their gravity), a predictor-corrector
+step at 1M and over the 256 batched impacts (3.9M particles), and the
+Barnes-Hut accelerations of the 2M-particle configurations on a seeded sample
+of particles the oracle evaluates one by one."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+from paper_1604_03290_gb300 import workloads as wl
+from parity_util import compare_rhs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "mixed": 1e-5}
+KMAX = 128
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1604_03290_gb300 import sph
+    return sph
+
+
+def _ctx(S, ps):
+    return S.Context(ps.dim, ps.n, max_instances=max(ps.ninst, 1), max_neighbours=KMAX,
+                     leaf_size=ps.params.leaf_size)
+
+
+def _gpu_rhs(S, ctx, ps, prec):
+    ds = S.DeviceState(ps)
+    out = S.rhs(ctx, ds, ps.materials, replace(ps.params, precision=prec))
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    g["rho"] = ds.rho.cpu().numpy()
+    return g
+
+
+def _check_rhs(S, orc, ps, precs=("fp64", "mixed")):
+    o = orc.rhs(ps, ps.materials, ps.params)
+    ctx = _ctx(S, ps)
+    for prec in precs:
+        g = _gpu_rhs(S, ctx, ps, prec)
+        np.testing.assert_array_equal(g["nnb"], o["nnb"])
+        fields = ("drho", "dv", "du", "dS", "dxdt", "p", "cs")
+        if ps.params.density_sum:
+            fields = fields + ("rho",)
+        if ps.S is None:
+            fields = tuple(f for f in fields if f != "dS")
+        errs = compare_rhs(ps, o, g, TOL[prec], fields=fields, prec=prec)
+        print(ps.name, prec, errs)
+        if ps.dmg is not None:
+            same = g["n_act"] == o["n_act"]
+            assert same.all() if prec == "fp64" else same.mean() > 0.999
+
+
+@pytest.fixture(scope="module")
+def m1():
+    return wl.measurement_1m(seed=11, n_side=100)
+
+
+def test_rhs_measured_1m_every_particle(S, orc, m1):
+    _check_rhs(S, orc, m1)
+
+
+def test_rhs_cube_64_and_sphere_every_particle(S, orc):
+    _check_rhs(S, orc, wl.al_impact())
+
+
+def _by_id(d):
+    order = np.argsort(d["id"])
+    return {k: (None if v is None else v[..., order]) for k, v in d.items()}
+
+
+def _check_step(S, orc, ps, nsteps=1, tol=2e-5):
+    ost, olog = orc.step(ps, ps.materials, ps.params, nsteps)
+    ctx = _ctx(S, ps)
+    ds = S.DeviceState(ps)
+    dt = S.step(ctx, ds, ps.materials, replace(ps.params, precision="mixed"), nsteps).cpu().numpy()
+    np.testing.assert_allclose(dt, olog[-1], rtol=1e-4)
+    g = _by_id(ds.to_numpy())
+    for f in ("x", "v", "rho", "u", "S", "dmg"):
+        if ost.get(f) is None:
+            continue
+        init = getattr(ps, f)
+        change = np.abs(ost[f] - init).max()
+        scale = change + 1e-300
+        if f == "x":
+            scale = max(change, 1e-6 * np.abs(init).max())
+        err = np.abs(g[f] - ost[f]).max() / scale
+        print(ps.name, f, err)
+        assert err <= tol, (f, err)
+
+
+def test_step_measured_1m(S, orc, m1):
+    _check_step(S, orc, m1)
+
+
+def test_step_256_batched_impacts(S, orc):
+    ps = wl.batched_impacts(seed=5)
+    assert ps.ninst == 256
+    _check_step(S, orc, ps)
+
+
+def _grav_scale_sampled(x, m, h, G, eg, idx, chunk=8):
+    """Per sampled particle: G sum_b m_b r_ab / (r_ab^2 + (eg h_a)^2)^(3/2), the
+    magnitude sum of the direct softened sum."""
+    out = np.zeros(len(idx))
+    for s in range(0, len(idx), chunk):
+        ii = idx[s:s + chunk]
+        d = x[:, ii, None] - x[:, None, :]
+        r2 = (d ** 2).sum(0)
+        q = r2 + (eg * h[ii, None]) ** 2
+        q[np.arange(len(ii)), ii] = np.inf
+        out[s:s + chunk] = G * (m[None, :] * np.sqrt(r2) / q ** 1.5).sum(1)
+    return out
+
+
+def _check_gravity(S, orc, ps, nsample=128):
+    rng = np.random.default_rng(77)
+    idx = np.sort(rng.choice(ps.n, size=nsample, replace=False))
+    P = ps.params
+    o = orc.gravity_bh(ps.x, ps.m, ps.h, ps.dim, P.G, P.theta, P.eps_grav, P.leaf_size, P.max_depth, sample=idx)
+    sc = _grav_scale_sampled(ps.x, ps.m, ps.h, P.G, P.eps_grav, idx)
+    ctx = _ctx(S, ps)
+    for prec in ("fp64", "mixed"):
+        g = S.gravity(ctx, S.DeviceState(ps), replace(P, precision=prec)).cpu().numpy()[:, idx]
+        err = (np.abs(g - o) / sc).max()
+        print(ps.name, "gravity", prec, err)
+        assert err <= TOL[prec], (prec, err)
+
+
+def test_cloud_2m_rhs_and_sampled_gravity(S, orc):
+    ps = wl.cloud_collapse(seed=3)
+    assert ps.n > 1_900_000
+    _check_gravity(S, orc, ps)
+    ps.params = replace(ps.params, gravity=False)
+    _check_rhs(S, orc, ps)
+
+
+def test_ceres_pair_rhs_and_sampled_gravity(S, orc):
+    ps = wl.ceres_pair(seed=4)
+    assert ps.n > 1_900_000
+    _check_gravity(S, orc, ps)
+    ps.params = replace(ps.params, gravity=False)
+    _check_rhs(S, orc, ps, precs=("mixed",))
