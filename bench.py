@@ -104,13 +104,19 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # Byte model of the kernels (algorithmic bytes per particle, mixed mode)
 # ----------------------------------------------------------------------------
-# DRAM bytes per particle of one launch, from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum) as summarised under profiles/; per-particle so that a
-# capture on a smaller case scales to the full launch.  Kernels without an
-# entry report traffic null.
-NCU_TRAFFIC_PER_PARTICLE = {
-    "partners": 298.0,  # profiles/k_partners_al_impact_514k.md
+# Per particle and launch, from one ncu capture of the kernels as built (the
+# first right-hand side of the warm-up step, after the state is put in tree
+# order, of the 514,109-particle case of this workload, n_side 80; profiles/
+# holds the summary): warp instructions issued (smsp__inst_executed.sum) and DRAM bytes
+# (dram__bytes_read.sum + dram__bytes_write.sum).  Both scale with the
+# particle count at this density.  Set to None when a kernel changes and the
+# capture has not been repeated.
+NCU_PER_PARTICLE = {
+    "partners": {"inst": 703.47, "dram": 297.87, "fp32_pipe": 0.265, "issue": 0.650},
+    "passA": {"inst": 365.57, "dram": 506.52, "fp32_pipe": 0.378, "issue": 0.597},
+    "passB": {"inst": 395.24, "dram": 348.77, "fp32_pipe": 0.440, "issue": 0.628},
 }
+ISSUE_SLOTS_PER_SM = 4  # one warp instruction per clock per SM sub-partition
 
 
 def algorithmic_bytes(phase, K, n_flaw_mean, dim=3):
@@ -234,24 +240,60 @@ def main():
         ms = float(t.item())
     value = world * n * args.steps / (ms * 1e-3)
 
-    # ---- roofline of the dominant kernel ----
+    # ---- rooflines ----
+    # The partner walk is bound by instruction issue (latency and ALU work of
+    # an irregular tree walk): its roofline is warp instructions issued per
+    # second against SMs x 4 issue slots x the SM clock seen under load.  The
+    # neighbour passes are reported against HBM with their algorithmic bytes
+    # (each array once), and against issue the same way.  Launch times are the
+    # library's CUDA events on the launching stream over the timed region.
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm_peak, peak_src = 6800.0, "fallback 6.8 TB/s"
     if os.path.exists(peaks_path):
         with open(peaks_path) as f:
             hbm_peak = float(json.load(f)["hbm_gbs"])
         peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)"
-    timed = {p: v for p, v in phases.items() if v[1] > 0 and p in ("passA", "passB", "partners")}
-    dom = max(timed, key=lambda p: timed[p][0]) if timed else "passB"
-    per_launch_ms = timed[dom][0] / timed[dom][1] if timed else float("nan")
-    bytes_per_launch = algorithmic_bytes(dom, K, n_flaw) * n
-    achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": achieved / hbm_peak,
-            "traffic": (NCU_TRAFFIC_PER_PARTICLE[dom] * n) if dom in NCU_TRAFFIC_PER_PARTICLE else None,
-            "peak_source": peak_src,
-            "bytes_per_particle": algorithmic_bytes(dom, K, n_flaw), "mean_partners": K,
-            "avg_launch_ms": per_launch_ms}
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    issue_peak = nsm * ISSUE_SLOTS_PER_SM * sm_mhz * 1e6 / 1e9  # G warp-instructions / s
+
+    def kernel_roof(phase):
+        calls = phases.get(phase, (0.0, 0))
+        if calls[1] == 0:
+            return None
+        launch_ms = calls[0] / calls[1]
+        ab = algorithmic_bytes(phase, K, n_flaw) * n
+        r = {"avg_launch_ms": launch_ms,
+             "hbm": {"achieved": ab / (launch_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": ab / (launch_ms * 1e-3) / 1e9 / hbm_peak,
+                     "bytes_per_particle": algorithmic_bytes(phase, K, n_flaw)}}
+        c = NCU_PER_PARTICLE.get(phase)
+        if c:
+            ginst = c["inst"] * n / (launch_ms * 1e-3) / 1e9
+            r["issue"] = {"achieved": ginst, "peak": issue_peak, "unit": "G warp-instructions/s",
+                          "frac": ginst / issue_peak, "inst_per_particle_ncu": c["inst"]}
+            r["dram_bytes_ncu"] = c["dram"] * n
+            r["fp32_pipe_frac_ncu"] = c["fp32_pipe"]
+        return r
+
+    kr = {p: kernel_roof(p) for p in ("partners", "passA", "passB")}
+    timed = {p: phases[p][0] for p in kr if kr[p] is not None}
+    dom = max(timed, key=timed.get) if timed else "partners"
+    d = kr[dom]
+    if dom == "partners" and "issue" in d:
+        roof = {"bound": "alu", "kernel": dom, "achieved": d["issue"]["achieved"], "peak": issue_peak,
+                "unit": "G warp-instructions/s", "frac": d["issue"]["frac"],
+                "traffic": d.get("dram_bytes_ncu"),
+                "peak_source": "%d SMs x %d issue slots x %.0f MHz (median SM clock under load)" %
+                               (nsm, ISSUE_SLOTS_PER_SM, sm_mhz),
+                "avg_launch_ms": d["avg_launch_ms"], "hbm_frac_algorithmic": d["hbm"]["frac"],
+                "fp32_pipe_frac_ncu": d.get("fp32_pipe_frac_ncu")}
+    else:
+        roof = {"bound": "hbm", "kernel": dom, "achieved": d["hbm"]["achieved"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": d["hbm"]["frac"], "traffic": d.get("dram_bytes_ncu"), "peak_source": peak_src,
+                "avg_launch_ms": d["avg_launch_ms"]}
+    roof["mean_partners"] = K
+    roof["kernels"] = kr
     total_ms = sum(v[0] for v in phases.values())
     phase_report = {p: {"ms_per_step": v[0] / args.steps, "share": v[0] / total_ms if total_ms else None,
                         "launch_ms": v[0] / v[1] if v[1] else None}
