@@ -61,14 +61,18 @@ static __device__ __noinline__ double accel_limit(int dim, double h, double a0, 
   return a2 > 0.0 ? c * sqrt(h / sqrt(a2)) : none;
 }
 
-// The limits of one particle.  Every limit is first estimated in FP32 (within
-// about 1e-6 relative); the FP64 expression is then evaluated only for limits
-// whose estimate lies within 2^-12 of the smallest estimate, or whose inputs
-// the FP32 view does not trust.  Any limit skipped is larger than the one that
-// wins, so the minimum equals the all-FP64 minimum bit for bit, at about one
-// FP64 division per particle instead of eleven.
-__device__ double particle_dt(const DtArgs &A, int64_t a) {
+// The limits of one particle, called by every thread of a block.  Every limit
+// is first estimated in FP32 (within about 1e-6 relative); the FP64 expression
+// is then evaluated only for limits whose estimate lies within 2^-12 of the
+// smallest estimate of the block (of the warp or the lane, when those span
+// several instances: `scope` 2, 1, 0), or whose inputs the FP32 view does not
+// trust.  Any limit skipped is larger than the one that attains that minimum,
+// so the minimum over the scope equals the all-FP64 minimum bit for bit, at
+// about one FP64 division per block.  The result for one thread is only
+// meaningful through that minimum.
+__device__ double particle_dt(const DtArgs &A, int64_t a_in, bool valid, int scope) {
   const sph_params &P = A.prm;
+  const int64_t a = valid ? a_in : A.n - 1;  // lanes past the end read the last particle, then drop out
   const float inf = __int_as_float(0x7f800000);
   float est[11];
   unsigned risky = 0;
@@ -133,10 +137,23 @@ __device__ double particle_dt(const DtArgs &A, int64_t a) {
     if ((long long)__double_as_longlong(dq) > 0) est[10] = A.f_quantity * (qf + A.f_dmg_floor) * __frcp_rn(df);
     if (rr) risky |= 1024u;
   }
+  if (!valid) {
+    risky = 0;
+#pragma unroll
+    for (int i = 0; i < 11; ++i) est[i] = inf;
+  }
   float best = A.f_dt_max;
 #pragma unroll
   for (int i = 0; i < 11; ++i)
     if (!((risky >> i) & 1u)) best = fminf(best, est[i]);
+  if (scope >= 1)
+    for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if (scope == 2) {
+    __shared__ float bmin[32];
+    if ((threadIdx.x & 31) == 0) bmin[threadIdx.x >> 5] = best;
+    __syncthreads();
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) best = fminf(best, bmin[k]);
+  }
   const float thr = best * (1.f + 1.f / 4096.f);
   unsigned pick = risky;
 #pragma unroll
@@ -187,48 +204,62 @@ __device__ double particle_dt(const DtArgs &A, int64_t a) {
   return dt;
 }
 
+__device__ __forceinline__ unsigned long long warp_min_ord(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w < v ? w : v;
+  }
+  return v;
+}
+
 __global__ void k_dt(DtArgs A) {
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const sph_params &P = A.prm;
-  double dt = P.dt_max;
-  int inst = 0;
-  if (a < A.n) {
-    inst = inst_of(A.inst_off, A.ninst, a);
-    dt = particle_dt(A, a);
-  }
-  // warp-level min when the warp lies in one instance, else per lane; then one
-  // atomic per run of equal instances among the block's warps
+  const bool valid = a < A.n;
+  const int inst = valid ? inst_of(A.inst_off, A.ninst, a) : 0;
+  // the widest scope lying in one instance: block (2), warp (1) or lane (0)
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __shared__ double wmin[32];
+  __shared__ int binst;
+  if (threadIdx.x == 0) binst = inst;
+  __syncthreads();
+  const int inst0 = __shfl_sync(full, inst, 0);
+  const bool wsame = __all_sync(full, inst == inst0 || !valid);
+  const bool bsame = __syncthreads_and(inst == binst || !valid);
+  const int scope = bsame ? 2 : (wsame ? 1 : 0);
+  const double dt = particle_dt(A, a, valid, scope);
+  // minima as order-preserving integers (integer pipe): per lane when the warp
+  // spans instances, else per warp, then one atomic per run of equal instances
+  // among the block's warps
+  unsigned long long o = valid ? dbl_to_ord(dt) : dbl_to_ord(P.dt_max);
+  __shared__ unsigned long long wmin[32];
   __shared__ int winst[32];
-  int inst0 = __shfl_sync(full, inst, 0);
-  bool same = __all_sync(full, inst == inst0 || a >= A.n);
-  if (same) {
-    for (int o = 16; o > 0; o >>= 1) dt = fmin(dt, __shfl_xor_sync(full, dt, o));
+  if (wsame) {
+    o = warp_min_ord(o);
   } else {
-    if (a < A.n) atomicMin(&A.enc[inst], dbl_to_ord(dt));
-    dt = P.dt_max;  // already reported
+    if (valid) atomicMin(&A.enc[inst], o);
+    o = dbl_to_ord(P.dt_max);  // already reported
   }
   if (lane == 0) {
-    wmin[w] = dt;
+    wmin[w] = o;
     winst[w] = inst0;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
+    const unsigned long long none = dbl_to_ord(P.dt_max);
     const int nw = blockDim.x >> 5;
-    double cur = wmin[0];
+    unsigned long long cur = wmin[0];
     int ci = winst[0];
     for (int k = 1; k < nw; ++k) {
       if (winst[k] == ci) {
-        cur = fmin(cur, wmin[k]);
+        cur = wmin[k] < cur ? wmin[k] : cur;
       } else {
-        if (cur < P.dt_max) atomicMin(&A.enc[ci], dbl_to_ord(cur));
+        if (cur < none) atomicMin(&A.enc[ci], cur);
         cur = wmin[k];
         ci = winst[k];
       }
     }
-    if (cur < P.dt_max) atomicMin(&A.enc[ci], dbl_to_ord(cur));
+    if (cur < none) atomicMin(&A.enc[ci], cur);
   }
 }
 

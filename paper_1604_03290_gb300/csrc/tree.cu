@@ -237,7 +237,7 @@ __device__ __forceinline__ double pow2_floor(double v) { return (v > 0.0 && isfi
 
 __global__ void k_units(const double *__restrict__ h, const double *__restrict__ m, int64_t n, int dim,
                         double vscale, MatTable mt, Units *U) {
-  if (threadIdx.x != 0) return;
+  // every lane forms the (power-of-two) base units; lane i converts material i
   const double L = pow2_floor(n > 0 ? h[0] : 1.0), M = pow2_floor(n > 0 ? m[0] : 1.0);
   const double T = pow2_floor(L / (vscale > 0.0 ? vscale : 1.0));
   Units u;
@@ -257,9 +257,10 @@ __global__ void k_units(const double *__restrict__ h, const double *__restrict__
   u.invE = 1.0 / u.E;
   u.acc = L / (T * T);
   u.Gs = 0.0;
-  for (int i = 0; i < SPH_MAX_MATERIALS; ++i) {
+  const int i = threadIdx.x;
+  if (i < SPH_MAX_MATERIALS) {
     const sph_material &a = mt.m[i < mt.nmat ? i : 0];
-    float *f = u.matf[i];
+    float *f = U->matf[i];
     f[MF_RHO0] = (float)(a.rho0 * u.invrho);
     f[MF_CS] = (float)(a.cs * u.invV);
     f[MF_K0] = (float)(a.K0 * u.invsig);
@@ -277,7 +278,25 @@ __global__ void k_units(const double *__restrict__ h, const double *__restrict__
     f[MF_MU] = (float)(a.mu * u.invsig);
     f[MF_Y0] = (float)(a.Y0 * u.invsig);
   }
-  *U = u;
+  if (threadIdx.x == 0) {
+    // base fields only: the material rows are written by their lanes
+    U->L = u.L;
+    U->M = u.M;
+    U->T = u.T;
+    U->invL = u.invL;
+    U->invM = u.invM;
+    U->invT = u.invT;
+    U->rho = u.rho;
+    U->invrho = u.invrho;
+    U->V = u.V;
+    U->invV = u.invV;
+    U->sig = u.sig;
+    U->invsig = u.invsig;
+    U->E = u.E;
+    U->invE = u.invE;
+    U->acc = u.acc;
+    U->Gs = u.Gs;
+  }
 }
 
 // FP32 views of the state (see PackedF32), in code units.
@@ -330,39 +349,6 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const unsigned long
   }
   __syncthreads();
   hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = hs[threadIdx.x];
-}
-
-// Exclusive scan of m unsigned ints in place, one block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_scan_u32_1blk(uint32_t *d, int64_t m) {
-  __shared__ uint32_t ws[32];
-  int64_t chunk = (m + 1023) / 1024;
-  int64_t b = threadIdx.x * chunk, e = min(m, b + chunk);
-  uint32_t s = 0;
-  for (int64_t i = b; i < e; ++i) s += d[i];
-  // block exclusive scan of s
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t v = s;
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += t;
-  }
-  if (lane == 31) ws[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    uint32_t t = ws[lane];
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t u = __shfl_up_sync(0xffffffffu, t, o);
-      if (lane >= o) t += u;
-    }
-    ws[lane] = t;
-  }
-  __syncthreads();
-  uint32_t off = v - s + (w > 0 ? ws[w - 1] : 0);
-  for (int64_t i = b; i < e; ++i) {
-    uint32_t t = d[i];
-    d[i] = off;
-    off += t;
-  }
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const unsigned long long *__restrict__ kin,
@@ -748,23 +734,20 @@ __global__ void k_group_emit(Tree T, const int32_t *__restrict__ gstart, const i
 // Node moments, bottom-up
 // ---------------------------------------------------------------------------
 
+// Bottom-up sums, one thread per leaf: mass, the mass-weighted position sum
+// (kept in T.com until k_node_finish divides it), the particle box and h_max.
+// The last child to arrive combines its parent's children in id order, so the
+// sums are deterministic.  Extrema are kept as order-preserving integers and
+// h_max as the bits of a positive double: only the sums use the FP64 unit.
 __global__ void k_moments(Tree T, const double *__restrict__ x, const double *__restrict__ y,
                           const double *__restrict__ z, const double *__restrict__ m, const double *__restrict__ h,
-                          int dim, int L, const int64_t *__restrict__ inst_off, int ninst,
-                          const Units *__restrict__ U, int walk_leaf) {
-  const int Lw = max(L, walk_leaf);
+                          int dim) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= *T.nleaf) return;
   const int64_t id = T.ncount[tid];  // one thread per leaf
   int32_t f = T.first[id], e = T.end[id];
   const double *X[3] = {x, y, z};
   const int64_t cap = T.cap_nodes;
-  int inst = inst_of(inst_off, ninst, f);
-  const double ilo[3] = {T.inst_lo[3 * inst], T.inst_lo[3 * inst + 1], T.inst_lo[3 * inst + 2]};
-  const int kL = pow2_exp(U->invL), kM = pow2_exp(U->invM);
-  // Sums stay FP64.  Extrema are kept as order-preserving integers and h_max
-  // as the bits of a positive double, so that comparisons, like the scaled
-  // FP32 conversions below, stay off the FP64 unit.
   double M = 0.0, mx[3] = {0, 0, 0};
   unsigned long long lo[3] = {~0ULL, ~0ULL, ~0ULL}, hi[3] = {0ULL, 0ULL, 0ULL};
   unsigned long long hm = 0ULL;
@@ -786,45 +769,14 @@ __global__ void k_moments(Tree T, const double *__restrict__ x, const double *__
   }
   int64_t node = id;
   for (int depth = 0; depth < 64; ++depth) {
-    const double iM = 1.0 / M;
-    double com[3], blo[3], bhi[3];
+    T.mass[node] = M;
+    T.hmax[node] = bitsd(hm);
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
       const bool use = ax < dim;
-      com[ax] = use ? mx[ax] * iM : 0.0;
-      blo[ax] = use ? of_ord(lo[ax]) : 0.0;
-      bhi[ax] = use ? of_ord(hi[ax]) : 0.0;
-      T.com[ax * cap + node] = com[ax];
-      T.bblo[ax * cap + node] = blo[ax];
-      T.bbhi[ax * cap + node] = bhi[ax];
-    }
-    const double hmax = bitsd(hm);
-    T.mass[node] = M;
-    T.hmax[node] = hmax;
-    {
-      // FP32 box rounded outwards and the COM as hi + lo, relative to the
-      // instance corner, in code units
-      float bl[3] = {0.f, 0.f, 0.f}, bh[3] = {0.f, 0.f, 0.f}, ch[3] = {0.f, 0.f, 0.f}, cl[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-      for (int ax = 0; ax < 3; ++ax) {
-        if (ax >= dim) break;
-        const double dl = __dsub_rn(blo[ax], ilo[ax]), dh = __dsub_rn(bhi[ax], ilo[ax]);
-        const double dc = __dsub_rn(com[ax], ilo[ax]);
-        bl[ax] = to_f32_dir_scaled(dl, kL, false, U->invL);
-        bh[ax] = to_f32_dir_scaled(dh, kL, true, U->invL);
-        to_f32_split_scaled(dc, kL, U->invL, ch[ax], cl[ax]);
-      }
-      const float hf = to_f32_dir_scaled(hmax, kL, true, U->invL), mf = to_f32_scaled(M, kM, U->invM);
-      const int lev = T.level[node];
-      // edge s0 / 2^level in code units: one exponent shift (the fallback's
-      // scale 2^(kL - level) is built from its bits)
-      const float ef = to_f32_scaled(T.inst_s0[inst], kL - lev, bitsd((uint64_t)(1023 + kL - lev) << 52));
-      const int32_t nf = T.first[node], ne = T.end[node];
-      const bool stop = ne - nf <= Lw || lev == T.max_depth;
-      T.fbox_lo[node] = make_float4(bl[0], bl[1], bl[2], stop ? -hf : hf);
-      T.fbox_hi[node] = make_float4(bh[0], bh[1], bh[2], __int_as_float(T.skip[node]));
-      T.fcom_hi[node] = make_float4(ch[0], ch[1], ch[2], mf);
-      T.fcom_lo[node] = make_float4(cl[0], cl[1], cl[2], ef);
+      T.com[ax * cap + node] = use ? mx[ax] : 0.0;
+      T.bblo[ax * cap + node] = use ? of_ord(lo[ax]) : 0.0;
+      T.bbhi[ax * cap + node] = use ? of_ord(hi[ax]) : 0.0;
     }
     int32_t p = T.parent[node];
     if (p < 0) return;
@@ -858,14 +810,13 @@ __global__ void k_moments(Tree T, const double *__restrict__ x, const double *__
     for (int k = 0; k < 8; ++k) {
       if (k >= nc) break;
       const int32_t cc = ch[k];
-      double mc = __ldcg(&T.mass[cc]);
-      M += mc;
+      M += __ldcg(&T.mass[cc]);
       const unsigned long long hb = dbits(__ldcg(&T.hmax[cc]));
       hm = hb > hm ? hb : hm;
 #pragma unroll
       for (int ax = 0; ax < 3; ++ax) {
         if (ax >= dim) break;
-        mx[ax] += mc * __ldcg(&T.com[ax * cap + cc]);
+        mx[ax] += __ldcg(&T.com[ax * cap + cc]);
         const unsigned long long ol = ord_of(__ldcg(&T.bblo[ax * cap + cc]));
         const unsigned long long oh = ord_of(__ldcg(&T.bbhi[ax * cap + cc]));
         lo[ax] = ol < lo[ax] ? ol : lo[ax];
@@ -874,6 +825,45 @@ __global__ void k_moments(Tree T, const double *__restrict__ x, const double *__
     }
     node = p;
   }
+}
+
+// Per node, all warps full: centre of mass from the sums, and the FP32 words
+// of the walks in code units relative to the instance corner - the box rounded
+// outwards with +-h_max (negative where the partner walk stops: at most
+// max(L, walk_leaf) particles or depth B) and skip[], and the COM as hi + lo
+// with the mass and the cell edge s0 / 2^level.
+__global__ void k_node_finish(Tree T, int dim, int L, const int64_t *__restrict__ inst_off, int ninst,
+                              const Units *__restrict__ U, int walk_leaf) {
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= *T.nnodes) return;
+  const int Lw = max(L, walk_leaf);
+  const int64_t cap = T.cap_nodes;
+  const int32_t nf = T.first[node], ne = T.end[node];
+  const int inst = inst_of(inst_off, ninst, nf);
+  const int kL = pow2_exp(U->invL), kM = pow2_exp(U->invM);
+  const double M = T.mass[node], iM = 1.0 / M, hmax = T.hmax[node];
+  float bl[3] = {0.f, 0.f, 0.f}, bh[3] = {0.f, 0.f, 0.f}, chi[3] = {0.f, 0.f, 0.f}, clo[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    if (ax >= dim) break;
+    const double ilo = T.inst_lo[3 * inst + ax];
+    const double com = T.com[ax * cap + node] * iM;
+    T.com[ax * cap + node] = com;
+    const double dl = __dsub_rn(T.bblo[ax * cap + node], ilo), dh = __dsub_rn(T.bbhi[ax * cap + node], ilo);
+    bl[ax] = to_f32_dir_scaled(dl, kL, false, U->invL);
+    bh[ax] = to_f32_dir_scaled(dh, kL, true, U->invL);
+    to_f32_split_scaled(__dsub_rn(com, ilo), kL, U->invL, chi[ax], clo[ax]);
+  }
+  const float hf = to_f32_dir_scaled(hmax, kL, true, U->invL), mf = to_f32_scaled(M, kM, U->invM);
+  const int lev = T.level[node];
+  // edge s0 / 2^level: one exponent shift (the fallback's scale 2^(kL - level)
+  // is built from its bits)
+  const float ef = to_f32_scaled(T.inst_s0[inst], kL - lev, bitsd((uint64_t)(1023 + kL - lev) << 52));
+  const bool stop = ne - nf <= Lw || lev == T.max_depth;
+  T.fbox_lo[node] = make_float4(bl[0], bl[1], bl[2], stop ? -hf : hf);
+  T.fbox_hi[node] = make_float4(bh[0], bh[1], bh[2], __int_as_float(T.skip[node]));
+  T.fcom_hi[node] = make_float4(chi[0], chi[1], chi[2], mf);
+  T.fcom_lo[node] = make_float4(clo[0], clo[1], clo[2], ef);
 }
 
 // ---------------------------------------------------------------------------
@@ -926,9 +916,10 @@ void tree_build(sph_ctx *c, const sph_state *s, int leaf_size, int max_depth, cu
   cudaMemsetAsync(T.arrived, 0, sizeof(int32_t) * T.cap_nodes, st);
   cudaMemsetAsync(T.nleaf, 0, sizeof(int32_t), st);
   { k_node_emit<<<nblk(n + 1, 256), 256, 0, st>>>(K, n, leaf_size, s->inst_off, ninst, T.nstart, T, c->d_err); ++sph::g_launches; }
-  { k_moments<<<nblk(std::max<int64_t>(n, 1), 256), 256, 0, st>>>(
-      T, s->x[0], s->x[1], s->x[2], s->m, s->h, dim, leaf_size, s->inst_off, ninst, c->units,
-      c->tune.walk_leaf); ++sph::g_launches; }
+  { k_moments<<<nblk(std::max<int64_t>(n, 1), 256), 256, 0, st>>>(T, s->x[0], s->x[1], s->x[2], s->m, s->h,
+                                                                   dim); ++sph::g_launches; }
+  { k_node_finish<<<nblk(T.cap_nodes, 256), 256, 0, st>>>(T, dim, leaf_size, s->inst_off, ninst, c->units,
+                                                        c->tune.walk_leaf); ++sph::g_launches; }
   { k_inst_roots<<<nblk(ninst, 128), 128, 0, st>>>(s->inst_off, ninst, n, T.nstart, T); ++sph::g_launches; }
   { k_group_count<<<nblk(T.cap_nodes + 1, 256), 256, 0, st>>>(T, T.gcnt); ++sph::g_launches; }
   scan_excl_i32(T.gcnt, T.gstart, T.cap_nodes + 1, T.scan_tmp, st);
