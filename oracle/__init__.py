@@ -93,6 +93,7 @@ def lib():
             L.orc_neighbours_brute.restype = C.c_int64
             L.orc_neighbours_grid.restype = C.c_int64
             L.orc_neighbours_one.restype = C.c_int32
+            L.orc_adapt_h.restype = C.c_int32
             L.orc_tree_nodes.restype = C.c_int64
             L.orc_gravity_bh.restype = C.c_int32
             L.orc_rhs.restype = C.c_int32
@@ -259,6 +260,20 @@ def neighbours_one(x, h, dim, a, cap=4096):
                                  _p(out, _ip), C.c_int32(cap))
     assert c <= cap
     return out[:c].copy()
+
+
+def adapt_h(x, h, dim, n_des, tol=0, max_iter=10, inst_off=None):
+    """Variable smoothing length iteration (Sect. 4.2).  Returns (h, counts,
+    number of updates); the input h is not modified."""
+    x, px, py, pz = _xyz(x, dim)
+    n = x.shape[1]
+    hh = np.array(h, dtype=np.float64, copy=True)
+    cnt = np.zeros(max(n, 1), np.int32)
+    io = None if inst_off is None else np.ascontiguousarray(inst_off, dtype=np.int64)
+    ninst = 1 if io is None else len(io) - 1
+    it = lib().orc_adapt_h(C.c_int32(dim), C.c_int64(n), px, py, pz, _p(hh), _p(io, _lp), C.c_int32(ninst),
+                           C.c_double(n_des), C.c_int32(tol), C.c_int32(max_iter), _p(cnt, _ip))
+    return hh, cnt[:n], int(it)
 
 
 def cell_coords(x, dim, max_depth=21):

@@ -100,6 +100,14 @@ int64_t orc_neighbours_grid(int32_t dim, int64_t n, const double *x, const doubl
 int32_t orc_neighbours_one(int32_t dim, int64_t n, const double *x, const double *y, const double *z,
                            const double *h, int64_t a, int32_t *out, int32_t cap);
 
+/* Variable smoothing length (Sect. 4.2): h <- h (1 + (n_des/n_a)^(1/D)) / 2 for all
+ * particles at once, n_a = #{b != a in a's instance : r_ab^2 < h_a^2}; repeated until
+ * every |n_a - n_des| <= tol or max_iter updates.  n_a = 0 doubles h.  h in place;
+ * counts[n] = the last n_a; returns the number of updates.  inst_off may be NULL. */
+int32_t orc_adapt_h(int32_t dim, int64_t n, const double *x, const double *y, const double *z, double *h,
+                    const int64_t *inst_off, int32_t ninst, double n_des, int32_t tol, int32_t max_iter,
+                    int32_t *counts);
+
 /* Octree (Sect. 3.5.1 root cube and subdivision; bucket leaves of <= leaf_size).
  * Writes per node: level, integer cell coordinates, particle count, mass, COM.
  * Returns the node count, or -1 if it exceeds cap. */

@@ -261,6 +261,83 @@ int64_t orc_neighbours_grid(int32_t dim, int64_t n, const double *x, const doubl
 }
 
 /* ------------------------------------------------------------------------ */
+/* Variable smoothing length, Sect. 4.2 (after Hernquist & Katz 1989): every */
+/* particle's h is replaced by h (1 + (n_des / n_a)^(1/D)) / 2, where n_a is  */
+/* the number of other particles of its instance closer than its own h,      */
+/* ((dx dx + dy dy) + dz dz) < h_a h_a; all particles at once, repeated until */
+/* every |n_a - n_des| <= tol or max_iter updates have been made.  A particle */
+/* without partners doubles its h.  Returns the number of updates; counts    */
+/* receives n_a of the last count.                                           */
+/* ------------------------------------------------------------------------ */
+static int within_own_h(int dim, const double *x, const double *y, const double *z, const double *h, int64_t a,
+                        int64_t b) {
+  double dx = x[a] - x[b];
+  double dy = y[a] - y[b];
+  double r2 = dx * dx + dy * dy;
+  if (dim == 3) {
+    double dz = z[a] - z[b];
+    r2 = r2 + dz * dz;
+  }
+  return r2 < h[a] * h[a];
+}
+
+/* n_a for every particle of one instance (arrays offset to its first particle) */
+static void count_own_h(int dim, int64_t n, const double *x, const double *y, const double *z, const double *h,
+                        int32_t *counts) {
+  if (n == 0) return;
+  cellgrid g;
+  grid_build(&g, dim, n, x, y, z, h); /* cells no smaller than max h >= h_a */
+  const double *X[3] = {x, y, z};
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+  for (int64_t a = 0; a < n; ++a) {
+    int64_t c0[3] = {0, 0, 0};
+    for (int ax = 0; ax < dim; ++ax) c0[ax] = grid_coord(&g, ax, X[ax][a]);
+    int32_t cnt = 0;
+    int zr = dim == 3 ? 1 : 0;
+    for (int64_t dz = -zr; dz <= zr; ++dz)
+      for (int64_t dy = -1; dy <= 1; ++dy)
+        for (int64_t dx = -1; dx <= 1; ++dx) {
+          int64_t cx = c0[0] + dx, cy = c0[1] + dy, cz = c0[2] + dz;
+          if (cx < 0 || cy < 0 || cz < 0 || cx >= g.nc[0] || cy >= g.nc[1] || cz >= g.nc[2]) continue;
+          int64_t c = (cz * g.nc[1] + cy) * g.nc[0] + cx;
+          for (int64_t k = g.start[c]; k < g.start[c + 1]; ++k) {
+            int64_t b = g.items[k];
+            if (b != a && within_own_h(dim, x, y, z, h, a, b)) ++cnt;
+          }
+        }
+    counts[a] = cnt;
+  }
+  grid_free(&g);
+}
+
+int32_t orc_adapt_h(int32_t dim, int64_t n, const double *x, const double *y, const double *z, double *h,
+                    const int64_t *inst_off, int32_t ninst, double n_des, int32_t tol, int32_t max_iter,
+                    int32_t *counts) {
+  int32_t it = 0;
+  if (ninst < 1 || !inst_off) ninst = 1;
+  for (;;) {
+    for (int32_t i = 0; i < ninst; ++i) {
+      int64_t lo = ninst > 1 ? inst_off[i] : 0, hi = ninst > 1 ? inst_off[i + 1] : n;
+      count_own_h(dim, hi - lo, x + lo, y + lo, z ? z + lo : NULL, h + lo, counts + lo);
+    }
+    int done = 1;
+    for (int64_t a = 0; a < n; ++a)
+      if (fabs((double)counts[a] - n_des) > (double)tol) done = 0;
+    if (done || it >= max_iter) return it;
+    for (int64_t a = 0; a < n; ++a) {
+      if (counts[a] == 0) {
+        h[a] = 2.0 * h[a];
+      } else {
+        double q = n_des / (double)counts[a];
+        double r = dim == 3 ? cbrt(q) : (dim == 2 ? sqrt(q) : q);
+        h[a] = h[a] * 0.5 * (1.0 + r);
+      }
+    }
+    ++it;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Octree, Sect. 3.5.1.  Root cube: lower corner at the per-axis minimum,    */
 /* edge s0 = max_axis(extent) * (1 + 2^-20) so the particle at the maximum   */
 /* lies inside; a node at depth d has edge s0 / 2^d.  Cell index of a        */
