@@ -87,6 +87,9 @@ typedef struct {
   double G, theta, eps_grav;      /* gravity constant; opening angle; softening/h  */
   double c_courant, c_accel, c_quantity;          /* time step factors (Sect. 3.4.1) */
   double u_floor, S_floor, dmg_floor, dt_max, dt_fixed;
+  double n_des;         /* > 0: sph_step adapts h at the start of each step to
+                           about n_des partners (sph_adapt_h, Sect. 4.2)      */
+  int32_t h_tol, h_iter;  /* its count tolerance and most updates (<= 64)     */
 } sph_params;
 
 /* Particle state (device pointers).  S and dmg may be NULL.  Flaw thresholds
@@ -215,6 +218,18 @@ sph_status sph_neighbours(sph_ctx *ctx, const sph_state *state, int32_t leaf_siz
 sph_status sph_neighbours_static(const sph_state *state, int32_t leaf_size, int32_t max_depth,
                                  int32_t max_neighbours, int64_t *nb_offset, int32_t *nb_index,
                                  int64_t nb_capacity, char *msg, int32_t msg_len, void *stream);
+
+/* Variable smoothing length (Sect. 4.2, after Hernquist & Katz): starting
+ * from state->h, every particle's support radius is replaced by
+ * h (1 + (n_des / n_a)^(1/D)) / 2, with n_a = #{b != a in a's instance :
+ * ((dx^2 + dy^2) + dz^2) < h_a^2} evaluated exactly in FP64 (the particle's
+ * own h), all particles at once, until every |n_a - n_des| <= tol or
+ * max_iter (<= 64) updates have been made; n_a = 0 doubles h.  state->h is
+ * updated in place.  counts (device int32[n], may be NULL) receives n_a of the
+ * last count; *updates (host, may be NULL) the number of updates made.  Builds
+ * the tree itself (no reorder); blocks on `stream` at the end. */
+sph_status sph_adapt_h(sph_ctx *ctx, sph_state *state, int32_t leaf_size, int32_t max_depth, double n_des,
+                       int32_t tol, int32_t max_iter, int32_t *counts, int32_t *updates, void *stream);
 
 /* One right-hand side: tree, partners, (density sum), the neighbour pass for
  * continuity / velocity gradient / XSPH, the per-particle constitutive update

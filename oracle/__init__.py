@@ -56,7 +56,8 @@ class Params(C.Structure):
                 ("G", C.c_double), ("theta", C.c_double), ("eps_grav", C.c_double),
                 ("c_courant", C.c_double), ("c_accel", C.c_double), ("c_quantity", C.c_double),
                 ("u_floor", C.c_double), ("S_floor", C.c_double), ("dmg_floor", C.c_double),
-                ("dt_max", C.c_double), ("dt_fixed", C.c_double)]
+                ("dt_max", C.c_double), ("dt_fixed", C.c_double), ("n_des", C.c_double),
+                ("h_tol", C.c_int32), ("h_iter", C.c_int32)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -141,7 +142,8 @@ def params_struct(p) -> Params:
     s = Params()
     for k, _ in Params._fields_:
         v = getattr(p, k)
-        setattr(s, k, int(v) if k in ("dim", "density_sum", "consistency", "gravity", "leaf_size", "max_depth") else float(v))
+        setattr(s, k, int(v) if k in ("dim", "density_sum", "consistency", "gravity", "leaf_size", "max_depth",
+                                     "h_tol", "h_iter") else float(v))
     return s
 
 
@@ -157,7 +159,7 @@ class _StateArrays:
         self.rho = cp(_f64(ps.rho))
         self.u = cp(_f64(ps.u))
         self.m = _f64(ps.m)
-        self.h = _f64(ps.h)
+        self.h = cp(_f64(ps.h))
         self.S = cp(_f64(ps.S))
         self.dmg = cp(_f64(ps.dmg))
         self.mat = np.ascontiguousarray(ps.mat, dtype=np.int32)
@@ -183,7 +185,7 @@ class _StateArrays:
         self.struct = s
 
     def as_dict(self):
-        return {"x": self.x, "v": self.v, "rho": self.rho, "u": self.u, "S": self.S, "dmg": self.dmg}
+        return {"x": self.x, "v": self.v, "rho": self.rho, "u": self.u, "S": self.S, "dmg": self.dmg, "h": self.h}
 
 
 def _derivs(dim, n, ns):

@@ -47,6 +47,8 @@ typedef struct {
   double G, theta, eps_grav;      /* gravity constant, opening angle, softening / h */
   double c_courant, c_accel, c_quantity;
   double u_floor, S_floor, dmg_floor, dt_max, dt_fixed;
+  double n_des;                   /* > 0: variable h (Sect. 4.2) at the start of each step */
+  int32_t h_tol, h_iter;          /* its count tolerance and most updates   */
 } orc_params;
 
 /* Particle state, structure of arrays.  Tensors S are symmetric and stored

@@ -1465,7 +1465,11 @@ int32_t orc_step(orc_state *s, const orc_material *mats, int32_t nmat, const orc
   dstore_alloc(&d0, dim, n);
   dstore_alloc(&d1, dim, n);
   int rc = 0;
+  int32_t *hcnt = P->n_des > 0.0 ? (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t)) : NULL;
   for (int32_t st = 0; st < nsteps && rc == 0; ++st) {
+    /* variable smoothing length: iterate from the last step's h (Sect. 4.2) */
+    if (hcnt)
+      orc_adapt_h(dim, n, s->x, s->y, s->z, s->h, s->inst_off, ninst, P->n_des, P->h_tol, P->h_iter, hcnt);
     rc = orc_rhs(s, mats, nmat, P, &d0.d);
     if (rc) break;
     orc_timestep(s, mats, nmat, P, &d0.d, dt_inst);
@@ -1478,5 +1482,6 @@ int32_t orc_step(orc_state *s, const orc_material *mats, int32_t nmat, const orc
   dstore_free(&d0);
   dstore_free(&d1);
   free(buf);
+  free(hcnt);
   return rc;
 }

@@ -138,6 +138,7 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   c->nb_idx = ctx_alloc<int32_t>(c, (int64_t)max_neighbours * N, ok);
   c->nb_cnt = ctx_alloc<int32_t>(c, N, ok);
   c->csr_total = ctx_alloc<int64_t>(c, 1, ok);
+  c->hflags = ctx_alloc<int32_t>(c, kMaxHIter + 3, ok);
   c->T = ctx_alloc<double>(c, 8 * N, ok);
   c->zeta = ctx_alloc<double>(c, 8 * N, ok);
   c->cs = ctx_alloc<double>(c, N, ok);
@@ -250,6 +251,8 @@ static sph_status check_params(sph_ctx *c, const sph_state *s, const sph_materia
   if (p->dim != s->dim) return fail(c, SPH_ERR_INVALID, "params.dim differs from the state's");
   if (p->precision != SPH_FP64 && p->precision != SPH_MIXED) return fail(c, SPH_ERR_INVALID, "bad precision");
   if (p->eps_s > 0.0 && !(p->dmpd > 0.0)) return fail(c, SPH_ERR_INVALID, "artificial stress needs dmpd > 0");
+  if (p->n_des > 0.0 && (p->h_tol < 0 || p->h_iter < 0 || p->h_iter > kMaxHIter))
+    return fail(c, SPH_ERR_INVALID, "variable h needs h_tol >= 0 and 0 <= h_iter <= 64");
   memset(&mt, 0, sizeof(mt));
   for (int i = 0; i < nmat; ++i) {
     mt.m[i] = mats[i];
@@ -366,6 +369,26 @@ sph_status sph_neighbours(sph_ctx *c, const sph_state *s, int32_t leaf_size, int
   return sph_sync_status(c, stream);
 }
 
+sph_status sph_adapt_h(sph_ctx *c, sph_state *s, int32_t leaf_size, int32_t max_depth, double n_des, int32_t tol,
+                       int32_t max_iter, int32_t *counts, int32_t *updates, void *stream) {
+  sph_status r = check_state(c, s);
+  if (r != SPH_OK) return r;
+  if ((r = check_tree_args(c, s, leaf_size, max_depth)) != SPH_OK) return r;
+  if (!(n_des > 0.0) || tol < 0 || max_iter < 0 || max_iter > kMaxHIter)
+    return fail(c, SPH_ERR_INVALID, "need n_des > 0, tol >= 0 and 0 <= max_iter <= 64");
+  cudaStream_t st = (cudaStream_t)stream;
+  set_materials(c, nullptr);
+  tree_build(c, s, leaf_size, max_depth, st);  // positions only: the counts use the current h
+  adapt_h(c, s, n_des, tol, max_iter, c->hflags, st);
+  if (counts && s->n > 0) cudaMemcpyAsync(counts, c->nb_cnt, sizeof(int32_t) * s->n, cudaMemcpyDeviceToDevice, st);
+  int32_t u = 0;
+  cudaMemcpyAsync(&u, c->hflags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if ((r = cuda_check(c, "sph_adapt_h")) != SPH_OK) return r;
+  if ((r = sph_sync_status(c, stream)) != SPH_OK) return r;
+  if (updates) *updates = u;
+  return SPH_OK;
+}
+
 sph_status sph_rhs(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t nmat, const sph_params *p,
                    sph_derivs *out, void *stream) {
   sph_status r = check_state(c, s);
@@ -434,6 +457,12 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
     d[j].n_act = B.d_nact[j];
   }
   for (int it = 0; it < nsteps; ++it) {
+    if (p->n_des > 0.0) {  // variable smoothing length from the last step's h (Sect. 4.2)
+      int pa = prof_begin(c, st, PH_PARTNERS);
+      tree_build(c, s, p->leaf_size, p->max_depth, st);
+      adapt_h(c, s, p->n_des, p->h_tol, p->h_iter, c->hflags, st);
+      prof_end(c, st, pa);
+    }
     // order the state along the tree once per step (coalesced partner gathers)
     timed_tree(c, s, *p, st);
     int pr = prof_begin(c, st, PH_REORDER);

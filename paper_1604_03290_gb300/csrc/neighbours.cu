@@ -45,14 +45,37 @@ __device__ __forceinline__ bool exact_partner(const double *__restrict__ x, cons
   return r2 < __dmul_rn(hab, hab);
 }
 
+// The same predicate with the particle's own support radius, for the
+// variable smoothing length iteration: ((dx^2 + dy^2) + dz^2) < h_a^2.
+__device__ __forceinline__ bool exact_within_own_h(const double *__restrict__ x, const double *__restrict__ y,
+                                                   const double *__restrict__ z, const double *__restrict__ h,
+                                                   int dim, int64_t a, int64_t b) {
+  double dx = __dsub_rn(x[a], x[b]);
+  double dy = __dsub_rn(y[a], y[b]);
+  double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+  if (dim == 3) {
+    double dz = __dsub_rn(z[a], z[b]);
+    r2 = __dadd_rn(r2, __dmul_rn(dz, dz));
+  }
+  return r2 < __dmul_rn(h[a], h[a]);
+}
+
+// OWN_H = false: interaction partners (h_ab), lists and counts.  OWN_H = true:
+// only the number of particles within each particle's own h (the current h
+// of the state, not the packed one), plus the count of particles whose number
+// lies farther than tol from n_des (*unconverged); the walk is skipped once
+// *done is set.
+template <bool OWN_H>
 __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *__restrict__ x,
-                                                            const double *__restrict__ y,
-                                                            const double *__restrict__ z,
-                                                            const double *__restrict__ h, int dim, int kmax,
-                                                            int32_t *__restrict__ nb_idx, int32_t *__restrict__ nb_cnt,
-                                                            int64_t ld, int32_t *err,
-                                                            const unsigned long long *__restrict__ grow,
-                                                            const Units *__restrict__ U) {
+                                           const double *__restrict__ y, const double *__restrict__ z,
+                                           const double *__restrict__ h, int dim, int kmax,
+                                           int32_t *__restrict__ nb_idx, int32_t *__restrict__ nb_cnt, int64_t ld,
+                                           int32_t *err, const unsigned long long *__restrict__ grow,
+                                           const Units *__restrict__ U, const int32_t *__restrict__ done,
+                                           int32_t *__restrict__ unconverged, double n_des, int tol) {
+  if constexpr (OWN_H) {
+    if (*done) return;
+  }
   __shared__ float4 sc[kNbWarps][kMaxLeaf];
   __shared__ int32_t sb[kNbWarps][kMaxLeaf];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -80,10 +103,13 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
                 lz = __shfl_sync(0xffffffffu, Q.z, 0);
     const float rax = (P.x - cx) + (Q.x - lx), ray = (P.y - cy) + (Q.y - ly), raz = (P.z - cz) + (Q.z - lz);
     const float hha = 0.5f * P.w;
+    // own support radius in code units (OWN_H): from the state's current h
+    float hown = 0.f;
+    if constexpr (OWN_H) hown = act ? to_f32_scaled(h[a], pow2_exp(U->invL), U->invL) : 0.f;
     // group box (hi coordinates, for the node test) and largest h
     float gl[3] = {act ? P.x : 3e38f, act ? P.y : 3e38f, act ? P.z : 3e38f};
     float gh[3] = {act ? P.x : -3e38f, act ? P.y : -3e38f, act ? P.z : -3e38f};
-    float hg = act ? P.w : 0.f;
+    float hg = act ? (OWN_H ? hown : P.w) : 0.f;
     // the same box relative to the reference point, for culling candidates
     float rl[3] = {act ? rax : 3e38f, act ? ray : 3e38f, act ? raz : 3e38f};
     float rh[3] = {act ? rax : -3e38f, act ? ray : -3e38f, act ? raz : -3e38f};
@@ -118,7 +144,7 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
       float gy = fmaxf(0.f, fmaxf(bl.y - gh[1], gl[1] - bh.y));
       float gz = fmaxf(0.f, fmaxf(bl.z - gh[2], gl[2] - bh.z));
       float d2 = gx * gx + gy * gy + gz * gz;
-      float thr = 0.5f * (hg + hw) * (1.0f + 1e-5f);
+      float thr = (OWN_H ? hg : 0.5f * (hg + hw)) * (1.0f + 1e-5f);
       bool enter = false;
       if (d2 <= thr * thr) {
         if (__float_as_uint(bl.w) >> 31) {  // the walk stops here: cull its particles
@@ -137,7 +163,7 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
               float qx = fmaxf(0.f, fmaxf(rl[0] - cand.x, cand.x - rh[0]));
               float qy = fmaxf(0.f, fmaxf(rl[1] - cand.y, cand.y - rh[1]));
               float qz = fmaxf(0.f, fmaxf(rl[2] - cand.z, cand.z - rh[2]));
-              float reach = (0.5f * hg + cand.w) * (1.0f + 1e-5f) + rslack;
+              float reach = (OWN_H ? hg : 0.5f * hg + cand.w) * (1.0f + 1e-5f) + rslack;
               keep = qx * qx + qy * qy + qz * qz <= reach * reach;
             }
             const unsigned km = __ballot_sync(0xffffffffu, keep);
@@ -154,14 +180,15 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
                 const int32_t b = sb[w][k];
                 float dx = rax - cb.x, dy = ray - cb.y, dz = raz - cb.z;
                 float r2 = dx * dx + dy * dy + dz * dz;
-                float hab = hha + cb.w;
+                float hab = OWN_H ? hown : hha + cb.w;
                 float h2 = hab * hab;
                 bool in;
                 if (r2 < h2 * (1.0f - kBand)) in = true;
                 else if (r2 > h2 * (1.0f + kBand)) in = false;
-                else in = exact_partner(x, y, z, h, dim, a, b);
+                else in = OWN_H ? exact_within_own_h(x, y, z, h, dim, a, b) : exact_partner(x, y, z, h, dim, a, b);
                 if (in && b != a) {
-                  if (cnt < kmax) nb_idx[(int64_t)cnt * ld + a] = b;
+                  if constexpr (!OWN_H)
+                    if (cnt < kmax) nb_idx[(int64_t)cnt * ld + a] = b;
                   ++cnt;
                 }
               }
@@ -175,7 +202,12 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
       nd = enter ? nd + 1 : __float_as_int(bh.w);
     }
     if (iter > nnodes) raise_err(err, ERR_TIMEOUT);
-    if (act) {
+    if constexpr (OWN_H) {
+      if (act) {
+        nb_cnt[a] = cnt;
+        if (fabs((double)cnt - n_des) > (double)tol) atomicAdd(unconverged, 1);
+      }
+    } else if (act) {
       nb_cnt[a] = min(cnt, kmax);
       if (cnt > kmax) raise_err(err, ERR_NB_OVERFLOW);
     }
@@ -185,9 +217,51 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
 void find_partners(sph_ctx *c, const sph_state *s, cudaStream_t st, const unsigned long long *grow) {
   if (s->n == 0) return;
   int blocks = c->num_sms * c->tune.walk_blocks_per_sm;
-  { k_partners<<<blocks, kNbWarps * 32, 0, st>>>(c->tree, c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim, c->kmax,
-                                              c->nb_idx, c->nb_cnt, c->cap_n, c->d_err, grow,
-                                              c->units); ++sph::g_launches; }
+  { k_partners<false><<<blocks, kNbWarps * 32, 0, st>>>(c->tree, c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim,
+                                                     c->kmax, c->nb_idx, c->nb_cnt, c->cap_n, c->d_err, grow,
+                                                     c->units, nullptr, nullptr, 0.0, 0); ++sph::g_launches; }
+}
+
+// ---------------------------------------------------------------------------
+// Variable smoothing length (Sect. 4.2): count with the own h, then
+// h <- (h / 2) (1 + (n_des / n_a)^(1/D)) for every particle when any count lies
+// farther than tol from n_des (else the iteration is done)
+// ---------------------------------------------------------------------------
+__global__ void k_h_update(double *__restrict__ h, const int32_t *__restrict__ cnt, int64_t n, int dim,
+                           double n_des, const int32_t *__restrict__ unconverged, int32_t *__restrict__ done,
+                           int32_t *__restrict__ updates) {
+  if (*done) return;
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (*unconverged == 0) {
+    if (a == 0) *done = 1;
+    return;
+  }
+  if (a == 0) atomicAdd(updates, 1);
+  if (a >= n) return;
+  const int32_t na = cnt[a];
+  if (na == 0) {
+    h[a] = 2.0 * h[a];
+  } else {
+    const double q = n_des / (double)na;
+    const double r = dim == 3 ? cbrt(q) : (dim == 2 ? sqrt(q) : q);
+    h[a] = h[a] * 0.5 * (1.0 + r);
+  }
+}
+
+void adapt_h(sph_ctx *c, sph_state *s, double n_des, int tol, int max_iter, int32_t *flags, cudaStream_t st) {
+  // flags: [0] done, [1] updates, [2 + i] particles off target at count i
+  const int64_t n = s->n;
+  cudaMemsetAsync(flags, 0, sizeof(int32_t) * (max_iter + 3), st);
+  if (n == 0) return;
+  const int blocks = c->num_sms * c->tune.walk_blocks_per_sm;
+  for (int i = 0; i <= max_iter; ++i) {
+    { k_partners<true><<<blocks, kNbWarps * 32, 0, st>>>(c->tree, c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim,
+                                                        c->kmax, c->nb_idx, c->nb_cnt, c->cap_n, c->d_err, nullptr,
+                                                        c->units, flags, flags + 2 + i, n_des, tol); ++sph::g_launches; }
+    if (i == max_iter) break;
+    { k_h_update<<<nblk(n, 256), 256, 0, st>>>(s->h, c->nb_cnt, n, s->dim, n_des, flags + 2 + i, flags,
+                                             flags + 1); ++sph::g_launches; }
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -33,6 +33,7 @@ enum : int32_t {
 
 constexpr int kWarp = 32;
 constexpr int kMaxLeaf = 32;
+constexpr int kMaxHIter = 64;  // most updates of one variable smoothing length iteration
 
 // Per-particle FP32 views used by the walks and the mixed-precision passes.
 // Positions are split X = x - corner into hi = float(X), lo = float(X - hi)
@@ -147,6 +148,7 @@ struct sph_ctx {
   int32_t *nb_idx;
   int32_t *nb_cnt;
   int64_t *csr_total;   // device scalar for sph_neighbours
+  int32_t *hflags;      // variable-h iteration: done, updates, off-target count per pass
   // pass A -> pass B per-particle data
   void *T;              // nsym * cap_n of double (FP64) or float (mixed)
   void *zeta;
@@ -281,6 +283,8 @@ void pack_f32(sph_ctx *c, const sph_state *s, cudaStream_t st);
 // grow (device, may be NULL): bits of a displacement bound by which every
 // particle may have left the node boxes of the current tree, per axis
 void find_partners(sph_ctx *c, const sph_state *s, cudaStream_t st, const unsigned long long *grow = nullptr);
+// variable smoothing length iteration; flags: device int32[max_iter + 3]
+void adapt_h(sph_ctx *c, sph_state *s, double n_des, int tol, int max_iter, int32_t *flags, cudaStream_t st);
 void partners_to_csr(sph_ctx *c, const sph_state *s, int64_t *off, int32_t *idx, int64_t cap, cudaStream_t st);
 // rhs.cu
 void rhs_passes(sph_ctx *c, sph_state *s, const MatTable &mt, const sph_params &p, const sph_derivs &out,

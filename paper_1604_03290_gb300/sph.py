@@ -52,7 +52,8 @@ class Params(C.Structure):
                 ("G", C.c_double), ("theta", C.c_double), ("eps_grav", C.c_double),
                 ("c_courant", C.c_double), ("c_accel", C.c_double), ("c_quantity", C.c_double),
                 ("u_floor", C.c_double), ("S_floor", C.c_double), ("dmg_floor", C.c_double),
-                ("dt_max", C.c_double), ("dt_fixed", C.c_double)]
+                ("dt_max", C.c_double), ("dt_fixed", C.c_double), ("n_des", C.c_double),
+                ("h_tol", C.c_int32), ("h_iter", C.c_int32)]
 
 
 _vp = C.c_void_p
@@ -96,6 +97,8 @@ def lib():
             L.sph_rhs.argtypes = [_vp, C.POINTER(State), C.POINTER(Material), C.c_int32, C.POINTER(Params),
                                   C.POINTER(Derivs), _vp]
             L.sph_gravity.argtypes = [_vp, C.POINTER(State), C.POINTER(Params), _vp, _vp, _vp, _vp]
+            L.sph_adapt_h.argtypes = [_vp, C.POINTER(State), C.c_int32, C.c_int32, C.c_double, C.c_int32,
+                                      C.c_int32, _vp, C.POINTER(C.c_int32), _vp]
             L.sph_neighbours_static.argtypes = [C.POINTER(State), C.c_int32, C.c_int32, C.c_int32, _vp, _vp,
                                                 C.c_int64, C.c_char_p, C.c_int32, _vp]
             L.sph_step.argtypes = [_vp, C.POINTER(State), C.POINTER(Material), C.c_int32, C.POINTER(Params), _vp,
@@ -115,7 +118,7 @@ def lib():
             L.sph_launch_count.argtypes = []
             L.sph_launch_count.restype = C.c_int64
             for f in ("sph_create", "sph_sync_status", "sph_build_tree", "sph_tree_nodes", "sph_neighbours",
-                      "sph_neighbours_static",
+                      "sph_neighbours_static", "sph_adapt_h",
                       "sph_rhs", "sph_gravity", "sph_step", "sph_measure_fma_peak", "sph_profile_enable",
                       "sph_profile_read", "sph_get_tuning", "sph_set_tuning", "sph_rhs_adjoint", "sph_pc_update",
                       "sph_pc_update_adjoint"):
@@ -150,7 +153,7 @@ def material_struct(m: wl.Material) -> Material:
 
 def params_struct(p: wl.Params, check: bool = True) -> Params:
     s = Params()
-    ints = ("dim", "density_sum", "consistency", "gravity", "leaf_size", "max_depth")
+    ints = ("dim", "density_sum", "consistency", "gravity", "leaf_size", "max_depth", "h_tol", "h_iter")
     for k, _ in Params._fields_:
         if k == "precision":
             s.precision = PRECISION[p.precision]
@@ -355,6 +358,17 @@ def neighbours(ctx: Context, ds: DeviceState, leaf_size=16, max_depth=21, capaci
     ctx.check(ctx._lib.sph_neighbours(ctx.h, C.byref(st), int(leaf_size), int(max_depth), _ptr(off), _ptr(idx),
                                       int(cap), _stream(stream)), "sph_neighbours")
     return off, idx[: int(off[-1].item())]
+
+
+def adapt_h(ctx: Context, ds: DeviceState, n_des, tol=0, max_iter=10, leaf_size=16, max_depth=21, stream=None):
+    """Variable smoothing length iteration (Sect. 4.2) on ds.h in place.
+    Returns (counts of the last pass, number of updates)."""
+    cnt = torch.zeros(max(ds.n, 1), dtype=torch.int32, device=ds.x.device)
+    upd = C.c_int32(0)
+    st = ds.struct()
+    ctx.check(ctx._lib.sph_adapt_h(ctx.h, C.byref(st), int(leaf_size), int(max_depth), float(n_des), int(tol),
+                                   int(max_iter), _ptr(cnt), C.byref(upd), _stream(stream)), "sph_adapt_h")
+    return cnt[: ds.n], upd.value
 
 
 def neighbours_static(ds: DeviceState, leaf_size=16, max_depth=21, max_neighbours=128, capacity=None,

@@ -90,6 +90,9 @@ class Params:
     dmg_floor: float = 1e-2
     dt_max: float = 1e30
     dt_fixed: float = 0.0
+    n_des: float = 0.0           # > 0: variable h at each step start (Sect. 4.2)
+    h_tol: int = 0
+    h_iter: int = 8
     precision: str = "fp64"      # fp64 | mixed
 
 

@@ -151,6 +151,16 @@ def _small_cloud():
     return ps
 
 
+def _cloud_variable_h():
+    # variable smoothing length at each step start (Sect. 4.2), from a
+    # perturbed h so that the first iteration has work to do
+    ps = wl.cloud_collapse(seed=3, n=6000)
+    rng = np.random.default_rng(13)
+    ps.h = ps.h * rng.uniform(0.7, 1.4, ps.n)
+    ps.params = replace(ps.params, n_des=50.0, h_tol=2, h_iter=6)
+    return ps
+
+
 def _small_batch():
     ps = wl.batched_impacts(seed=5, ninst=3, nmin=400, nmax=1500)
     rng = np.random.default_rng(9)
@@ -167,6 +177,7 @@ CASES = {
     "impact": _small_impact,
     "impact_fast": _fast_impact,
     "cloud": _small_cloud,
+    "cloud_vh": _cloud_variable_h,
     "batch": _small_batch,
 }
 
@@ -245,7 +256,7 @@ def _by_id(d, ids):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("case,nsteps,fixed", [("solid3d", 3, True), ("solid3d", 2, False), ("rings", 4, True),
                                                ("impact", 2, False), ("impact_fast", 2, True), ("batch", 2, False),
-                                               ("cloud", 2, False)])
+                                               ("cloud", 2, False), ("cloud_vh", 1, False)])
 def test_steps_match_oracle(orc, S, case, nsteps, fixed, prec):
     ps = CASES[case]()
     if fixed:
@@ -259,8 +270,8 @@ def test_steps_match_oracle(orc, S, case, nsteps, fixed, prec):
     g = ds.to_numpy()
     g = _by_id(g, g["id"])
     tol = 1e-9 if prec == "fp64" else 2e-5
-    for f in ("x", "v", "rho", "u", "S", "dmg"):
-        if ost.get(f) is None:
+    for f in ("x", "v", "rho", "u", "S", "dmg", "h"):
+        if ost.get(f) is None or (f == "h" and not ps.params.n_des > 0):
             continue
         init = getattr(ps, f)
         change = np.abs(ost[f] - init).max()
