@@ -99,6 +99,7 @@ def lib():
             L.orc_gravity_bh.restype = C.c_int32
             L.orc_rhs.restype = C.c_int32
             L.orc_step.restype = C.c_int32
+            L.orc_step_rk3.restype = C.c_int32
             L.orc_get_threads.restype = C.c_int32
             L.orc_eos.argtypes = [C.POINTER(Material), C.c_double, C.c_double, _dp, _dp, _dp, _dp]
             L.orc_sym_eig.argtypes = [C.c_int32, _dp, _dp, _dp]
@@ -373,6 +374,24 @@ def timestep(ps, materials, params, derivs):
     lib().orc_timestep(C.byref(st.struct), _mats(materials), C.c_int32(len(materials)),
                        C.byref(params_struct(params)), C.byref(d), _p(dt))
     return dt
+
+
+def step_rk3(ps, materials, params, eps_des, nsteps, dt=None, t=None):
+    """nsteps embedded Runge-Kutta attempts (Sect. 3.4.2) on a copy.  dt, t: per
+    instance (None: dt from the predictor-corrector limit, t = 0).  Returns
+    (state dict, dt, t, error log [nsteps, ninst], accepted log [nsteps, ninst])."""
+    st = _StateArrays(ps)
+    ninst = max(ps.ninst, 1)
+    dtv = np.zeros(ninst) if dt is None else np.array(dt, dtype=np.float64, copy=True)
+    tv = np.zeros(ninst) if t is None else np.array(t, dtype=np.float64, copy=True)
+    err = np.zeros((max(nsteps, 1), ninst))
+    acc = np.zeros((max(nsteps, 1), ninst), np.int32)
+    rc = lib().orc_step_rk3(C.byref(st.struct), _mats(materials), C.c_int32(len(materials)),
+                            C.byref(params_struct(params)), C.c_double(eps_des), C.c_int32(nsteps), _p(dtv),
+                            _p(tv), _p(err), _p(acc, _ip))
+    if rc != 0:
+        raise RuntimeError("oracle rk3 step failed: %d" % rc)
+    return st.as_dict(), dtv, tv, err[:nsteps], acc[:nsteps]
 
 
 def step(ps, materials, params, nsteps):

@@ -110,6 +110,17 @@ int32_t orc_adapt_h(int32_t dim, int64_t n, const double *x, const double *y, co
                     const int64_t *inst_off, int32_t ninst, double n_des, int32_t tol, int32_t max_iter,
                     int32_t *counts);
 
+/* Embedded Runge-Kutta steps (Sect. 3.4.2), nsteps attempts: k1 = f(q), k2 = f(q + dt/2 k1),
+ * k3 = f(q - dt k1 + 2 dt k2); error per instance = max over particles and components of
+ * dt |2 k2 - k1 - k3| / 6 / (|q + dt k1| + floor) (floors: h for x, c_s for v, 0 for rho,
+ * u_floor, S_floor, dmg_floor); err < eps_des accepts q + dt (k1 + 4 k2 + k3)/6 and sets
+ * dt <- dt (eps_des/err)^0.3 (dt_max for err = 0), else q is kept and dt <- 0.9 dt
+ * (eps_des/err)^(1/4); dt <= dt_max.  dt_inst[ninst] in/out (<= 0: the predictor-corrector
+ * limit of k1); t_inst (may be NULL) += dt of accepted steps; err_log, acc_log (may be NULL):
+ * [nsteps][ninst]. */
+int32_t orc_step_rk3(orc_state *s, const orc_material *mats, int32_t nmat, const orc_params *P, double eps_des,
+                     int32_t nsteps, double *dt_inst, double *t_inst, double *err_log, int32_t *acc_log);
+
 /* Octree (Sect. 3.5.1 root cube and subdivision; bucket leaves of <= leaf_size).
  * Writes per node: level, integer cell coordinates, particle count, mass, COM.
  * Returns the node count, or -1 if it exceeds cap. */

@@ -1437,6 +1437,180 @@ static void pc_update(const orc_state *base, orc_state *out, const orc_derivs *d
   }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Embedded Runge-Kutta step, Sect. 3.4.2.  k1 = f(q), k2 = f(q + dt/2 k1),  */
+/* k3 = f(q - dt k1 + 2 dt k2); q_rk3 = q + dt (k1 + 4 k2 + k3)/6 and the    */
+/* midpoint value q + dt k2 differ by dt (2 k2 - k1 - k3)/6.  The error of   */
+/* an instance is the largest ratio of that difference to the Euler value    */
+/* |q + dt k1| over its particles and integrated components; a floor is      */
+/* added to the denominator (h for positions, c_s for velocities, the        */
+/* limiter floors for u, S and d^1/3, none for rho).  err < eps_des accepts  */
+/* the step (q <- q_rk3, t += dt, dt <- dt (eps_des/err)^0.3, or dt_max for  */
+/* err = 0); otherwise the instance keeps q and dt <- 0.9 dt                 */
+/* (eps_des/err)^(1/4).  dt never exceeds dt_max.  Every state formed (the  */
+/* two stage states and q_rk3) gets the yield and damage limits of the       */
+/* predictor-corrector update, with n_act of the last derivative used.       */
+/* ------------------------------------------------------------------------ */
+static void rk_combine(const orc_state *base, orc_state *out, const orc_derivs *k[3], const double c[3],
+                       const double *dt_inst, const int32_t *mask, const orc_material *mats, int nmat,
+                       const orc_params *P) {
+  const int dim = P->dim;
+  const int64_t n = base->n;
+  const int ns = nsym(dim);
+  int last = 0;
+  for (int j = 0; j < 3; ++j)
+    if (c[j] != 0.0) last = j;
+  /* D = c1 k1 + c2 k2 + c3 k3, in that order */
+#define RK_D(field, i) ((c[0] * k[0]->field[i] + c[1] * (c[1] != 0.0 ? k[1]->field[i] : 0.0)) + \
+                        c[2] * (c[2] != 0.0 ? k[2]->field[i] : 0.0))
+  double *Xb[3] = {base->x, base->y, base->z}, *Xo[3] = {out->x, out->y, out->z};
+  double *Vb[3] = {base->vx, base->vy, base->vz}, *Vo[3] = {out->vx, out->vy, out->vz};
+  for (int64_t a = 0; a < n; ++a) {
+    const int32_t ii = inst_of(base, a);
+    if (mask && !mask[ii]) continue;
+    const double dt = dt_inst[ii];
+    for (int ax = 0; ax < dim; ++ax) {
+      double dX = ax == 0 ? RK_D(dxdt, a) : (ax == 1 ? RK_D(dydt, a) : RK_D(dzdt, a));
+      double dV = ax == 0 ? RK_D(dvx, a) : (ax == 1 ? RK_D(dvy, a) : RK_D(dvz, a));
+      Xo[ax][a] = Xb[ax][a] + dt * dX;
+      Vo[ax][a] = Vb[ax][a] + dt * dV;
+    }
+    if (!P->density_sum) out->rho[a] = base->rho[a] + dt * RK_D(drho, a);
+    else out->rho[a] = base->rho[a];
+    out->u[a] = base->u[a] + dt * RK_D(du, a);
+    const orc_material *M = mat_of(base, mats, nmat, a);
+    if (base->S) {
+      double S[3][3];
+      for (int kk = 0; kk < ns; ++kk) {
+        int64_t i = (int64_t)kk * n + a;
+        out->S[i] = base->S[i] + dt * RK_D(dS, i);
+      }
+      if (M->strength) {
+        sym_load(dim, out->S, n, a, S);
+        double fY = yield_factor(dim, M, S);
+        for (int kk = 0; kk < ns; ++kk) out->S[(int64_t)kk * n + a] *= fY;
+      }
+    }
+    if (base->dmg) {
+      const double dd = RK_D(ddmg, a);
+      double nd = base->dmg[a] + dt * dd;
+      if (dd > 0.0) {
+        int64_t id = base->id ? base->id[a] : a;
+        int64_t ntot = base->flaw_off[id + 1] - base->flaw_off[id];
+        double cap = cbrt((double)k[last]->n_act[a] / (double)ntot);
+        if (nd > cap) nd = cap;
+      }
+      if (nd > 1.0) nd = 1.0;
+      out->dmg[a] = nd;
+    }
+  }
+#undef RK_D
+}
+
+static double rk_ratio(double q, double k1, double k2, double k3, double dt, double floor) {
+  double num = fabs(2.0 * k2 - k1 - k3) * dt / 6.0;
+  double den = fabs(q + dt * k1) + floor;
+  return den > 0.0 ? num / den : (num > 0.0 ? INFINITY : 0.0);
+}
+
+int32_t orc_step_rk3(orc_state *s, const orc_material *mats, int32_t nmat, const orc_params *P, double eps_des,
+                     int32_t nsteps, double *dt_inst, double *t_inst, double *err_log, int32_t *acc_log) {
+  const int dim = P->dim;
+  const int64_t n = s->n;
+  const int ns = nsym(dim);
+  int32_t ninst = s->ninst > 0 ? s->ninst : 1;
+  orc_state q = *s;
+  double *buf = (double *)calloc((size_t)((8 + ns + 2) * n) + 1, sizeof(double));
+  double *p = buf;
+  q.x = p; p += n;
+  q.y = p; p += n;
+  q.z = p; p += n;
+  q.vx = p; p += n;
+  q.vy = p; p += n;
+  q.vz = p; p += n;
+  q.rho = p; p += n;
+  q.u = p; p += n;
+  q.S = s->S ? p : NULL; p += ns * n;
+  q.dmg = s->dmg ? p : NULL; p += n;
+  if (dim == 2) {
+    q.z = NULL;
+    q.vz = NULL;
+  }
+  dstore d[3];
+  for (int j = 0; j < 3; ++j) dstore_alloc(&d[j], dim, n);
+  const orc_derivs *k[3] = {&d[0].d, &d[1].d, &d[2].d};
+  double *lim = (double *)malloc((size_t)ninst * sizeof(double));
+  double *err = (double *)malloc((size_t)ninst * sizeof(double));
+  int32_t *acc = (int32_t *)malloc((size_t)ninst * sizeof(int32_t));
+  int rc = 0;
+  for (int32_t st = 0; st < nsteps && rc == 0; ++st) {
+    rc = orc_rhs(s, mats, nmat, P, &d[0].d);
+    if (rc) break;
+    orc_timestep(s, mats, nmat, P, &d[0].d, lim); /* first step size where none is given */
+    for (int32_t i = 0; i < ninst; ++i)
+      if (!(dt_inst[i] > 0.0)) dt_inst[i] = lim[i];
+    const double c2[3] = {0.5, 0.0, 0.0}, c3[3] = {-1.0, 2.0, 0.0}, cf[3] = {1.0 / 6.0, 4.0 / 6.0, 1.0 / 6.0};
+    rk_combine(s, &q, k, c2, dt_inst, NULL, mats, nmat, P);
+    rc = orc_rhs(&q, mats, nmat, P, &d[1].d);
+    if (rc) break;
+    rk_combine(s, &q, k, c3, dt_inst, NULL, mats, nmat, P);
+    rc = orc_rhs(&q, mats, nmat, P, &d[2].d);
+    if (rc) break;
+    /* error of each instance */
+    for (int32_t i = 0; i < ninst; ++i) err[i] = 0.0;
+    const double *Xs[3] = {s->x, s->y, s->z}, *Vs[3] = {s->vx, s->vy, s->vz};
+    for (int64_t a = 0; a < n; ++a) {
+      const int32_t ii = inst_of(s, a);
+      const double dt = dt_inst[ii];
+      double e = 0.0, r;
+      const double *K1x[3] = {k[0]->dxdt, k[0]->dydt, k[0]->dzdt}, *K2x[3] = {k[1]->dxdt, k[1]->dydt, k[1]->dzdt},
+                   *K3x[3] = {k[2]->dxdt, k[2]->dydt, k[2]->dzdt};
+      const double *K1v[3] = {k[0]->dvx, k[0]->dvy, k[0]->dvz}, *K2v[3] = {k[1]->dvx, k[1]->dvy, k[1]->dvz},
+                   *K3v[3] = {k[2]->dvx, k[2]->dvy, k[2]->dvz};
+      for (int ax = 0; ax < dim; ++ax) {
+        r = rk_ratio(Xs[ax][a], K1x[ax][a], K2x[ax][a], K3x[ax][a], dt, s->h[a]);
+        if (r > e) e = r;
+        r = rk_ratio(Vs[ax][a], K1v[ax][a], K2v[ax][a], K3v[ax][a], dt, k[0]->cs[a]);
+        if (r > e) e = r;
+      }
+      if (!P->density_sum) {
+        r = rk_ratio(s->rho[a], k[0]->drho[a], k[1]->drho[a], k[2]->drho[a], dt, 0.0);
+        if (r > e) e = r;
+      }
+      r = rk_ratio(s->u[a], k[0]->du[a], k[1]->du[a], k[2]->du[a], dt, P->u_floor);
+      if (r > e) e = r;
+      if (s->S)
+        for (int kk = 0; kk < ns; ++kk) {
+          int64_t i = (int64_t)kk * n + a;
+          r = rk_ratio(s->S[i], k[0]->dS[i], k[1]->dS[i], k[2]->dS[i], dt, P->S_floor);
+          if (r > e) e = r;
+        }
+      if (s->dmg) {
+        r = rk_ratio(s->dmg[a], k[0]->ddmg[a], k[1]->ddmg[a], k[2]->ddmg[a], dt, P->dmg_floor);
+        if (r > e) e = r;
+      }
+      if (e > err[ii]) err[ii] = e;
+    }
+    for (int32_t i = 0; i < ninst; ++i) acc[i] = err[i] < eps_des;
+    rk_combine(s, s, k, cf, dt_inst, acc, mats, nmat, P);
+    for (int32_t i = 0; i < ninst; ++i) {
+      if (t_inst && acc[i]) t_inst[i] += dt_inst[i];
+      double dn;
+      if (acc[i]) dn = err[i] > 0.0 ? dt_inst[i] * pow(eps_des / err[i], 0.3) : P->dt_max;
+      else dn = 0.9 * dt_inst[i] * pow(eps_des / err[i], 0.25);
+      dt_inst[i] = dn < P->dt_max ? dn : P->dt_max;
+      if (err_log) err_log[(int64_t)st * ninst + i] = err[i];
+      if (acc_log) acc_log[(int64_t)st * ninst + i] = acc[i];
+    }
+  }
+  for (int j = 0; j < 3; ++j) dstore_free(&d[j]);
+  free(buf);
+  free(lim);
+  free(err);
+  free(acc);
+  return rc;
+}
+
 int32_t orc_step(orc_state *s, const orc_material *mats, int32_t nmat, const orc_params *P, int32_t nsteps,
                  double *dt_inst, double *dt_log) {
   const int dim = P->dim;

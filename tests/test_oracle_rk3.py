@@ -1,0 +1,95 @@
+"""Pins of the oracle's embedded Runge-Kutta step (Sect. 3.4.2) by properties
+of the method rather than by its formulas: third-order convergence on a smooth
+problem (the predictor-corrector is second order), the error estimate shrinking
+as dt^3, exact motion of free particles with a zero error estimate (dt grows to
+dt_max), and a rejected step that leaves the state untouched and shrinks dt."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+from paper_1604_03290_gb300 import workloads as wl
+
+
+def _smooth_block(dim=2):
+    # elastic lattice block with a smooth velocity field; no viscosity switches,
+    # so the solution is smooth in time
+    ps = wl.lattice_block(seed=2, nx=10, ny=10, nz=10 if dim == 3 else 1, dim=dim, jitter=0.05)
+    x = ps.x
+    ps.v = 0.02 * np.stack([np.sin(0.4 * x[1]), np.cos(0.3 * x[0])] + ([np.sin(0.2 * x[0])] if dim == 3 else []))
+    ps.S = np.zeros((ps.nsym, ps.n))
+    ps.params = replace(ps.params, alpha=0.0, beta=0.0, xsph=0.0)
+    return ps
+
+
+def _run_rk3(orc, ps, T, nsteps):
+    dt = T / nsteps
+    prm = replace(ps.params, dt_max=dt)
+    st, dtv, tv, err, acc = orc.step_rk3(ps, ps.materials, prm, eps_des=np.inf, nsteps=nsteps, dt=[dt])
+    assert acc.all() and abs(tv[0] - T) <= 1e-12 * T
+    return st
+
+
+def _run_pc(orc, ps, T, nsteps):
+    prm = replace(ps.params, dt_fixed=T / nsteps)
+    st, _ = orc.step(ps, ps.materials, prm, nsteps)
+    return st
+
+
+def _err(a, b):
+    return max(np.abs(a["x"] - b["x"]).max(), np.abs(a["v"] - b["v"]).max())
+
+
+def test_third_order_convergence(orc):
+    ps = _smooth_block()
+    T = 3.0
+    ref = _run_rk3(orc, ps, T, 96)
+    e = [_err(_run_rk3(orc, ps, T, n), ref) for n in (6, 12, 24)]
+    r1, r2 = e[0] / e[1], e[1] / e[2]
+    print("rk3 error ratios", r1, r2)
+    assert 6.0 < r1 < 11.0 and 6.5 < r2 < 10.0
+    # the predictor-corrector on the same problem is second order
+    pref = _run_pc(orc, ps, T, 96)
+    p = [_err(_run_pc(orc, ps, T, n), pref) for n in (12, 24)]
+    assert 3.0 < p[0] / p[1] < 5.0
+
+
+def test_error_estimate_scales_as_dt_cubed(orc):
+    ps = _smooth_block()
+    errs = []
+    for dt in (0.05, 0.025, 0.0125):
+        _, _, _, err, _ = orc.step_rk3(ps, ps.materials, replace(ps.params, dt_max=1.0), eps_des=np.inf,
+                                       nsteps=1, dt=[dt])
+        errs.append(err[0, 0])
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    print("error estimate ratios", r1, r2)
+    # asymptotically 8 (the estimate is the dt^3 difference of the midpoint and
+    # the third-order values; measured 7.26, 7.59); a first-order mistake gives ~2
+    assert 6.5 < r1 < 9.0 and 6.5 < r2 < 9.0
+
+
+def test_free_particles_move_exactly(orc):
+    # three particles far apart: no partners, constant velocity, k1 = k2 = k3
+    x = np.array([[0.0, 100.0, 200.0], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    v = np.array([[1.5, -2.0, 0.25], [0.5, 0.0, 1.0], [0.0, 3.0, 0.0]])
+    n = 3
+    ps = wl.ParticleSet(dim=3, x=x, v=v, rho=np.ones(n), u=np.ones(n), m=np.ones(n), h=np.ones(n),
+                        mat=np.zeros(n, np.int32), id=np.arange(n, dtype=np.int32),
+                        materials=[wl.Material(eos="linear", rho0=1.0, cs=1.0)],
+                        params=wl.Params(dim=3, dt_max=8.0, alpha=0.0, beta=0.0, xsph=0.0, consistency=False))
+    st, dtv, tv, err, acc = orc.step_rk3(ps, ps.materials, ps.params, eps_des=1e-6, nsteps=3, dt=[0.5])
+    assert acc.all() and (err == 0.0).all()
+    # dt 0.5 accepted, then dt_max = 8 twice: t = 16.5
+    assert tv[0] == 16.5 and dtv[0] == 8.0
+    np.testing.assert_allclose(st["x"], x + 16.5 * v, rtol=1e-15, atol=0)  # the weights 1/6, 4/6 round
+    np.testing.assert_array_equal(st["v"], v)
+
+
+def test_rejected_step_keeps_the_state(orc):
+    ps = _smooth_block()
+    st, dtv, tv, err, acc = orc.step_rk3(ps, ps.materials, replace(ps.params, dt_max=1.0), eps_des=1e-30,
+                                         nsteps=1, dt=[0.3])
+    assert not acc.any() and tv[0] == 0.0
+    np.testing.assert_array_equal(st["x"], ps.x)
+    np.testing.assert_array_equal(st["v"], ps.v)
+    assert 0.0 < dtv[0] < 0.9 * 0.3
