@@ -259,6 +259,26 @@ sph_status sph_gravity(sph_ctx *ctx, const sph_state *state, const sph_params *p
 sph_status sph_step(sph_ctx *ctx, sph_state *state, const sph_material *mats, int32_t nmat, const sph_params *params,
                     double *dt, int32_t nsteps, void *stream);
 
+/* Embedded Runge-Kutta steps with adaptive step size (Sect. 3.4.2), nsteps
+ * attempts: k1 = f(q), k2 = f(q + dt/2 k1), k3 = f(q - dt k1 + 2 dt k2) with
+ * each stage state limited as in the predictor-corrector (yield, damage
+ * cap); per instance the error estimate is the largest
+ * dt |2 k2 - k1 - k3| / 6 / (|q + dt k1| + floor) over its particles and
+ * integrated components (floors: h for positions, c_s of k1 for velocities,
+ * 0 for rho, params u_floor, S_floor, dmg_floor), the difference of the
+ * midpoint and third-order values relative to the Euler value.  err < eps_des
+ * accepts q + dt (k1 + 4 k2 + k3)/6 (limited) and sets dt <- dt
+ * (eps_des/err)^0.3 (dt_max for err = 0); otherwise the instance keeps its
+ * state and dt <- 0.9 dt (eps_des/err)^(1/4); dt <= dt_max.
+ * dt: device double[ninst], in/out (<= 0: start from the predictor-corrector
+ * limit of k1); t (device double[ninst], may be NULL) += dt of accepted steps;
+ * err_log, acc_log (device double / int32 [nsteps][ninst], may be NULL).
+ * State reordered along the tree as in sph_step.  Variable h (params.n_des)
+ * as in sph_step. */
+sph_status sph_step_rk3(sph_ctx *ctx, sph_state *state, const sph_material *mats, int32_t nmat,
+                        const sph_params *params, double eps_des, double *dt, double *t, int32_t nsteps,
+                        double *err_log, int32_t *acc_log, void *stream);
+
 /* Reverse-mode derivative of sph_rhs at `state` (FP64, any requested
  * precision is evaluated in FP64), with the partner lists and the damage of
  * that evaluation held fixed and every branch (artificial viscosity on/off,

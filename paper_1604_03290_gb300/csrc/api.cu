@@ -156,7 +156,7 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   S.u = ctx_alloc<double>(c, N, ok);
   S.S = ctx_alloc<double>(c, 6 * N, ok);
   S.dmg = ctx_alloc<double>(c, N, ok);
-  for (int s = 0; s < 2; ++s) {
+  for (int s = 0; s < 3; ++s) {
     for (int k = 0; k < 3; ++k) {
       S.d_x[s][k] = ctx_alloc<double>(c, N, ok);
       S.d_v[s][k] = ctx_alloc<double>(c, N, ok);
@@ -169,6 +169,8 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
     S.d_nact[s] = ctx_alloc<int32_t>(c, N, ok);
   }
   S.dt_enc = ctx_alloc<unsigned long long>(c, ci, ok);
+  S.rk_err = ctx_alloc<unsigned long long>(c, ci, ok);
+  S.rk_acc = ctx_alloc<int32_t>(c, ci, ok);
   S.dmove = ctx_alloc<unsigned long long>(c, 1, ok);
   S.dt = ctx_alloc<double>(c, ci, ok);
   S.gather = ctx_alloc<double>(c, N, ok);
@@ -493,6 +495,86 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
   }
   if (dt && nsteps > 0) cudaMemcpyAsync(dt, B.dt, sizeof(double) * ninst, cudaMemcpyDeviceToDevice, st);
   return finish(c, p, st, "sph_step");
+}
+
+sph_status sph_step_rk3(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t nmat, const sph_params *p,
+                        double eps_des, double *dt, double *t, int32_t nsteps, double *err_log, int32_t *acc_log,
+                        void *stream) {
+  sph_status r = check_state(c, s);
+  if (r != SPH_OK) return r;
+  MatTable mt;
+  if ((r = check_params(c, s, mats, nmat, p, mt)) != SPH_OK) return r;
+  if (nsteps < 0 || !dt || !(eps_des > 0.0)) return fail(c, SPH_ERR_INVALID, "need dt, eps_des > 0, nsteps >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  set_materials(c, &mt);
+  StepBufs &B = c->st;
+  const int ninst = s->ninst > 0 ? s->ninst : 1;
+  // stage states share m, h, mat, id, flaws and instances with s
+  sph_state q = *s;
+  for (int k = 0; k < 3; ++k) {
+    q.x[k] = s->x[k] ? B.x[k] : nullptr;
+    q.v[k] = s->v[k] ? B.v[k] : nullptr;
+  }
+  q.rho = B.rho;
+  q.u = B.u;
+  q.S = s->S ? B.S : nullptr;
+  q.dmg = s->dmg ? B.dmg : nullptr;
+  sph_derivs d[3];
+  for (int j = 0; j < 3; ++j) {
+    memset(&d[j], 0, sizeof(sph_derivs));
+    for (int k = 0; k < 3; ++k) {
+      d[j].dx[k] = B.d_x[j][k];
+      d[j].dv[k] = B.d_v[j][k];
+    }
+    d[j].drho = B.d_rho[j];
+    d[j].du = B.d_u[j];
+    d[j].dS = B.d_S[j];
+    d[j].ddmg = B.d_dmg[j];
+    d[j].cs = B.d_cs[j];
+    d[j].n_act = B.d_nact[j];
+  }
+  const sph_derivs *k1[1] = {&d[0]}, *k12[2] = {&d[0], &d[1]}, *k123[3] = {&d[0], &d[1], &d[2]};
+  const double c2[1] = {0.5}, c3[2] = {-1.0, 2.0}, cf[3] = {1.0 / 6.0, 4.0 / 6.0, 1.0 / 6.0};
+  const bool reuse = !p->gravity;  // stage states keep the slots of s and use its tree (as in sph_step)
+  auto stage = [&](const sph_derivs *const *k, const double *coef, int nd, sph_derivs &out) {
+    int pr = prof_begin(c, st, PH_INTEGRATE);
+    if (reuse) cudaMemsetAsync(B.dmove, 0, sizeof(unsigned long long), st);
+    combine_update(c, s, &q, k, coef, nd, nullptr, mt, *p, st, reuse ? B.dmove : nullptr);
+    prof_end(c, st, pr);
+    if (reuse) {
+      pr = prof_begin(c, st, PH_TREE);
+      pack_f32(c, &q, st);
+      prof_end(c, st, pr);
+      partners_gravity_passes(c, &q, mt, *p, out, st, B.dmove);
+    } else {
+      rhs_all(c, &q, mt, *p, out, st);
+    }
+  };
+  for (int it = 0; it < nsteps; ++it) {
+    if (p->n_des > 0.0) {  // variable smoothing length from the last step's h (Sect. 4.2)
+      int pa = prof_begin(c, st, PH_PARTNERS);
+      tree_build(c, s, p->leaf_size, p->max_depth, st);
+      adapt_h(c, s, p->n_des, p->h_tol, p->h_iter, c->hflags, st);
+      prof_end(c, st, pa);
+    }
+    timed_tree(c, s, *p, st);
+    int pr = prof_begin(c, st, PH_REORDER);
+    tree_reorder_state(c, s, st);
+    prof_end(c, st, pr);
+    partners_gravity_passes(c, s, mt, *p, d[0], st);  // k1
+    pr = prof_begin(c, st, PH_INTEGRATE);
+    timestep_reduce(c, s, *p, d[0], st);  // the limit, for a first step size
+    rk_set_dt(c, s, dt, st);
+    prof_end(c, st, pr);
+    stage(k1, c2, 1, d[1]);    // k2 = f(q + dt/2 k1)
+    stage(k12, c3, 2, d[2]);   // k3 = f(q - dt k1 + 2 dt k2)
+    pr = prof_begin(c, st, PH_INTEGRATE);
+    rk_error_control(c, s, k123, *p, eps_des, dt, t, err_log ? err_log + (int64_t)it * ninst : nullptr,
+                     acc_log ? acc_log + (int64_t)it * ninst : nullptr, st);
+    combine_update(c, s, s, k123, cf, 3, B.rk_acc, mt, *p, st);  // q + dt (k1 + 4 k2 + k3)/6 where accepted
+    prof_end(c, st, pr);
+  }
+  return finish(c, p, st, "sph_step_rk3");
 }
 
 sph_status sph_rhs_adjoint(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t nmat, const sph_params *p,

@@ -119,9 +119,12 @@ struct Units {
 struct StepBufs {
   // predicted state
   double *x[3], *v[3], *rho, *u, *S, *dmg;
-  // two derivative sets
-  double *d_x[2][3], *d_v[2][3], *d_rho[2], *d_u[2], *d_S[2], *d_dmg[2], *d_cs[2];
-  int32_t *d_nact[2];
+  // three derivative sets (two for the predictor-corrector, three for the
+  // embedded Runge-Kutta step)
+  double *d_x[3][3], *d_v[3][3], *d_rho[3], *d_u[3], *d_S[3], *d_dmg[3], *d_cs[3];
+  int32_t *d_nact[3];
+  unsigned long long *rk_err;  // per instance, bits of the error estimate (non-negative)
+  int32_t *rk_acc;             // per instance, step accepted
   unsigned long long *dt_enc;  // per instance, ordered encoding for atomicMin
   unsigned long long *dmove;   // bits of the predictor's largest per-axis displacement
   double *dt;                  // per instance
@@ -305,5 +308,13 @@ void timestep_reduce(sph_ctx *c, const sph_state *s, const sph_params &p, const 
 // non-finite error bit, as a tree build over `out` would
 void pc_update(sph_ctx *c, const sph_state *base, sph_state *out, const sph_derivs &d, double frac,
                const MatTable &mt, const sph_params &p, cudaStream_t st, unsigned long long *dmove = nullptr);
+// out = base + dt (coef_0 d_0 + ...), nd <= 3 sets, where mask[inst] (NULL: all)
+void combine_update(sph_ctx *c, const sph_state *base, sph_state *out, const sph_derivs *const *d, const double *coef,
+                    int nd, const int32_t *mask, const MatTable &mt, const sph_params &p, cudaStream_t st,
+                    unsigned long long *dmove = nullptr);
+// embedded Runge-Kutta: step size of the attempt (c->st.dt), error and control
+void rk_set_dt(sph_ctx *c, const sph_state *s, double *dt_io, cudaStream_t st);
+void rk_error_control(sph_ctx *c, const sph_state *s, const sph_derivs *const *k, const sph_params &p, double eps_des,
+                      double *dt_io, double *t_io, double *err_log, int32_t *acc_log, cudaStream_t st);
 
 }  // namespace sph

@@ -309,33 +309,56 @@ void timestep_reduce(sph_ctx *c, const sph_state *s, const sph_params &p, const 
 // ---------------------------------------------------------------------------
 // out = base + frac * dt * deriv, then S <- f_Y S and the damage cap
 // ---------------------------------------------------------------------------
+// One derivative set (device arrays, layout of sph_derivs)
+struct DSet {
+  const double *dx[3], *dv[3], *drho, *du, *dS, *ddmg;
+};
+
+// out = base + dt_inst (c_0 d_0 + c_1 d_1 + c_2 d_2), nd sets (the
+// predictor-corrector: one set, c_0 = 1/2 or 1; the Runge-Kutta stages:
+// up to three), then the yield and damage limits.
 struct PcArgs {
   int dim;
   int64_t n;
   const double *bx[3], *bv[3], *brho, *bu, *bS, *bdmg;
   double *ox[3], *ov[3], *orho, *ou, *oS, *odmg;
-  const double *dx[3], *dv[3], *drho, *du, *dS, *ddmg;
-  const int32_t *nact, *mat, *id;
+  DSet d[3];
+  double coef[3];
+  int nd;
+  const int32_t *mask;  // per instance: update only where set (NULL: all)
+  const int32_t *nact, *mat, *id;  // nact: of the last set
   const int64_t *flaw_off;
   const int64_t *inst_off;
   int ninst;
   const double *dt;
-  double frac;
   MatTable mt;
   int density_sum;
   unsigned long long *dmove;  // NULL, or max |out.x - base.x| (bits of a non-negative double)
   int32_t *err;
 };
 
+// The combined derivative c_0 d_0[i] + c_1 d_1[i] + c_2 d_2[i], in that
+// order (for one set, c_0 = 1/2 or 1 scales exactly)
+__device__ __forceinline__ double comb(const PcArgs &A, const double *p0, const double *p1, const double *p2,
+                                       int64_t i) {
+  double v = A.coef[0] * p0[i];
+  if (A.nd > 1) v += A.coef[1] * p1[i];
+  if (A.nd > 2) v += A.coef[2] * p2[i];
+  return v;
+}
+
 // Update of particle a; returns the bits of max_axis |out.x - base.x| when
 // A.dmove is set (else 0).
 __device__ __forceinline__ unsigned long long pc_particle(const PcArgs &A, int64_t a) {
   const int inst = inst_of(A.inst_off, A.ninst, a);
-  const double dt = A.frac * A.dt[inst];
+  if (A.mask && !A.mask[inst]) return 0ULL;
+  const double dt = A.dt[inst];
   unsigned long long mv = 0ULL;  // bits of max |ox - bx| (non-negative doubles order as integers)
   bool bad = false;
   for (int ax = 0; ax < A.dim; ++ax) {
-    const double bx = A.bx[ax][a], ox = bx + dt * A.dx[ax][a], ov = A.bv[ax][a] + dt * A.dv[ax][a];
+    const double bx = A.bx[ax][a];
+    const double ox = bx + dt * comb(A, A.d[0].dx[ax], A.d[1].dx[ax], A.d[2].dx[ax], a);
+    const double ov = A.bv[ax][a] + dt * comb(A, A.d[0].dv[ax], A.d[1].dv[ax], A.d[2].dv[ax], a);
     A.ox[ax][a] = ox;
     A.ov[ax][a] = ov;
     if (A.dmove) {
@@ -344,12 +367,12 @@ __device__ __forceinline__ unsigned long long pc_particle(const PcArgs &A, int64
       bad |= !finite_bits(ox) || !finite_bits(ov);
     }
   }
-  A.orho[a] = A.density_sum ? A.brho[a] : A.brho[a] + dt * A.drho[a];
+  A.orho[a] = A.density_sum ? A.brho[a] : A.brho[a] + dt * comb(A, A.d[0].drho, A.d[1].drho, A.d[2].drho, a);
   if (A.dmove) {
     bad |= !positive_finite_bits(A.orho[a]);
     if (bad) raise_err(A.err, ERR_NONFINITE);
   }
-  A.ou[a] = A.bu[a] + dt * A.du[a];
+  A.ou[a] = A.bu[a] + dt * comb(A, A.d[0].du, A.d[1].du, A.d[2].du, a);
   const int mi = A.mat ? A.mat[a] : 0;
   const sph_material &M = A.mt.m[(mi >= 0 && mi < A.mt.nmat) ? mi : 0];
   if (A.bS) {
@@ -358,7 +381,7 @@ __device__ __forceinline__ unsigned long long pc_particle(const PcArgs &A, int64
     double J2 = 0.0;
     for (int k = 0; k < ns; ++k) {
       int64_t i = (int64_t)k * A.n + a;
-      S[k] = A.bS[i] + dt * A.dS[i];
+      S[k] = A.bS[i] + dt * comb(A, A.d[0].dS, A.d[1].dS, A.d[2].dS, i);
       J2 += (k < A.dim ? 1.0 : 2.0) * S[k] * S[k];  // off-diagonal terms appear twice in S:S
     }
     J2 *= 0.5;
@@ -373,7 +396,7 @@ __device__ __forceinline__ unsigned long long pc_particle(const PcArgs &A, int64
     for (int k = 0; k < ns; ++k) A.oS[(int64_t)k * A.n + a] = S[k];
   }
   if (A.bdmg) {
-    const double dd = A.ddmg[a];
+    const double dd = comb(A, A.d[0].ddmg, A.d[1].ddmg, A.d[2].ddmg, a);
     double nd = A.bdmg[a] + dt * dd;
     if (dd > 0.0) {
       const int64_t idp = A.id ? A.id[a] : a;
@@ -403,8 +426,22 @@ __global__ void k_pc(PcArgs A) {
   }
 }
 
-void pc_update(sph_ctx *c, const sph_state *base, sph_state *out, const sph_derivs &d, double frac,
-               const MatTable &mt, const sph_params &p, cudaStream_t st, unsigned long long *dmove) {
+static DSet dset_of(const sph_derivs &d) {
+  DSet r;
+  for (int k = 0; k < 3; ++k) {
+    r.dx[k] = d.dx[k];
+    r.dv[k] = d.dv[k];
+  }
+  r.drho = d.drho;
+  r.du = d.du;
+  r.dS = d.dS;
+  r.ddmg = d.ddmg;
+  return r;
+}
+
+void combine_update(sph_ctx *c, const sph_state *base, sph_state *out, const sph_derivs *const *d, const double *coef,
+                    int nd, const int32_t *mask, const MatTable &mt, const sph_params &p, cudaStream_t st,
+                    unsigned long long *dmove) {
   if (base->n == 0) return;
   PcArgs A;
   memset(&A, 0, sizeof(A));
@@ -415,8 +452,6 @@ void pc_update(sph_ctx *c, const sph_state *base, sph_state *out, const sph_deri
     A.bv[k] = base->v[k];
     A.ox[k] = out->x[k];
     A.ov[k] = out->v[k];
-    A.dx[k] = d.dx[k];
-    A.dv[k] = d.dv[k];
   }
   A.brho = base->rho;
   A.bu = base->u;
@@ -426,23 +461,163 @@ void pc_update(sph_ctx *c, const sph_state *base, sph_state *out, const sph_deri
   A.ou = out->u;
   A.oS = out->S;
   A.odmg = out->dmg;
-  A.drho = d.drho;
-  A.du = d.du;
-  A.dS = d.dS;
-  A.ddmg = d.ddmg;
-  A.nact = d.n_act;
+  A.nd = nd;
+  for (int j = 0; j < nd; ++j) {
+    A.d[j] = dset_of(*d[j]);
+    A.coef[j] = coef[j];
+  }
+  A.nact = d[nd - 1]->n_act;
+  A.mask = mask;
   A.mat = base->mat;
   A.id = base->id;
   A.flaw_off = base->flaw_off;
   A.inst_off = base->inst_off;
   A.ninst = base->ninst > 0 ? base->ninst : 1;
   A.dt = c->st.dt;
-  A.frac = frac;
   A.mt = mt;
   A.density_sum = p.density_sum;
   A.dmove = dmove;
   A.err = c->d_err;
   { k_pc<<<nblk(base->n, 256), 256, 0, st>>>(A); ++sph::g_launches; }
+}
+
+void pc_update(sph_ctx *c, const sph_state *base, sph_state *out, const sph_derivs &d, double frac,
+               const MatTable &mt, const sph_params &p, cudaStream_t st, unsigned long long *dmove) {
+  const sph_derivs *dd[1] = {&d};
+  combine_update(c, base, out, dd, &frac, 1, nullptr, mt, p, st, dmove);
+}
+
+// ---------------------------------------------------------------------------
+// Embedded Runge-Kutta step (Sect. 3.4.2): error estimate and step control
+// ---------------------------------------------------------------------------
+struct RkErrArgs {
+  int dim;
+  int64_t n;
+  const double *x[3], *v[3], *rho, *u, *S, *dmg, *h;
+  DSet k[3];
+  const double *cs;  // of k1
+  const int64_t *inst_off;
+  int ninst;
+  const double *dt;
+  double u_floor, S_floor, dmg_floor;
+  int density_sum;
+  unsigned long long *err;  // per instance
+};
+
+// largest |2 k2 - k1 - k3| / (|q + dt k1| + floor) of one particle, tracked as
+// a (numerator, denominator) pair by cross-multiplication so that only the
+// winner is divided
+__device__ __forceinline__ void rk_track(double q, double k1, double k2, double k3, double dt, double fl, double &bn,
+                                         double &bd) {
+  const double num = fabs(2.0 * k2 - k1 - k3), den = fabs(q + dt * k1) + fl;
+  if (num * bd > bn * den) {
+    bn = num;
+    bd = den;
+  }
+}
+
+__global__ void k_rk_error(RkErrArgs A) {
+  const int64_t a_in = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = a_in < A.n;
+  const int64_t a = valid ? a_in : A.n - 1;  // lanes past the end read the last particle, then drop out
+  const int inst = inst_of(A.inst_off, A.ninst, a);
+  const double dt = A.dt[inst];
+  double bn = 0.0, bd = 1.0;
+  for (int ax = 0; ax < A.dim; ++ax) {
+    rk_track(A.x[ax][a], A.k[0].dx[ax][a], A.k[1].dx[ax][a], A.k[2].dx[ax][a], dt, A.h[a], bn, bd);
+    rk_track(A.v[ax][a], A.k[0].dv[ax][a], A.k[1].dv[ax][a], A.k[2].dv[ax][a], dt, A.cs[a], bn, bd);
+  }
+  if (!A.density_sum) rk_track(A.rho[a], A.k[0].drho[a], A.k[1].drho[a], A.k[2].drho[a], dt, 0.0, bn, bd);
+  rk_track(A.u[a], A.k[0].du[a], A.k[1].du[a], A.k[2].du[a], dt, A.u_floor, bn, bd);
+  if (A.S)
+    for (int k = 0; k < nsym(A.dim); ++k) {
+      const int64_t i = (int64_t)k * A.n + a;
+      rk_track(A.S[i], A.k[0].dS[i], A.k[1].dS[i], A.k[2].dS[i], dt, A.S_floor, bn, bd);
+    }
+  if (A.dmg) rk_track(A.dmg[a], A.k[0].ddmg[a], A.k[1].ddmg[a], A.k[2].ddmg[a], dt, A.dmg_floor, bn, bd);
+  const double num = bn * dt / 6.0;
+  const double e = bd > 0.0 ? num / bd : (num > 0.0 ? __longlong_as_double(0x7ff0000000000000LL) : 0.0);
+  // non-negative doubles order as their bits: a warp maximum when the warp lies
+  // in one instance, then one atomic
+  unsigned long long o = valid ? (unsigned long long)__double_as_longlong(e) : 0ULL;
+  const int inst0 = __shfl_sync(0xffffffffu, inst, 0);
+  if (__all_sync(0xffffffffu, inst == inst0)) {
+    for (int k = 16; k > 0; k >>= 1) {
+      const unsigned long long w = __shfl_xor_sync(0xffffffffu, o, k);
+      o = w > o ? w : o;
+    }
+    if ((threadIdx.x & 31) == 0 && o != 0ULL) atomicMax(&A.err[inst0], o);
+  } else if (o != 0ULL) {
+    atomicMax(&A.err[inst], o);
+  }
+}
+
+// per instance: accept where err < eps_des (t += dt), then the new step size
+__global__ void k_rk_control(const unsigned long long *__restrict__ err, int32_t *__restrict__ acc,
+                             double *__restrict__ dt_io, const double *__restrict__ dt_used, double *__restrict__ t_io,
+                             int ninst, double eps_des, double dt_max, double *__restrict__ err_log,
+                             int32_t *__restrict__ acc_log) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ninst) return;
+  const double e = __longlong_as_double((long long)err[i]), dt = dt_used[i];
+  const int ok = e < eps_des;
+  acc[i] = ok;
+  if (t_io && ok) t_io[i] += dt;
+  double dn;
+  if (ok) dn = e > 0.0 ? dt * pow(eps_des / e, 0.3) : dt_max;
+  else dn = 0.9 * dt * pow(eps_des / e, 0.25);
+  dt_io[i] = dn < dt_max ? dn : dt_max;
+  if (err_log) err_log[i] = e;
+  if (acc_log) acc_log[i] = ok;
+}
+
+// the step size of this attempt: the caller's where positive, else the
+// predictor-corrector limit just computed into dt_used
+__global__ void k_rk_dt(double *__restrict__ dt_io, double *__restrict__ dt_used, int ninst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ninst) return;
+  const double v = dt_io[i] > 0.0 ? dt_io[i] : dt_used[i];
+  dt_io[i] = v;
+  dt_used[i] = v;
+}
+
+void rk_error_control(sph_ctx *c, const sph_state *s, const sph_derivs *const *k, const sph_params &p, double eps_des,
+                      double *dt_io, double *t_io, double *err_log, int32_t *acc_log, cudaStream_t st) {
+  const int ninst = s->ninst > 0 ? s->ninst : 1;
+  cudaMemsetAsync(c->st.rk_err, 0, sizeof(unsigned long long) * ninst, st);
+  if (s->n > 0) {
+    RkErrArgs A;
+    memset(&A, 0, sizeof(A));
+    A.dim = s->dim;
+    A.n = s->n;
+    for (int ax = 0; ax < 3; ++ax) {
+      A.x[ax] = s->x[ax];
+      A.v[ax] = s->v[ax];
+    }
+    A.rho = s->rho;
+    A.u = s->u;
+    A.S = s->S;
+    A.dmg = s->dmg;
+    A.h = s->h;
+    for (int j = 0; j < 3; ++j) A.k[j] = dset_of(*k[j]);
+    A.cs = k[0]->cs;
+    A.inst_off = s->inst_off;
+    A.ninst = ninst;
+    A.dt = c->st.dt;
+    A.u_floor = p.u_floor;
+    A.S_floor = p.S_floor;
+    A.dmg_floor = p.dmg_floor;
+    A.density_sum = p.density_sum;
+    A.err = c->st.rk_err;
+    { k_rk_error<<<nblk(s->n, 256), 256, 0, st>>>(A); ++sph::g_launches; }
+  }
+  { k_rk_control<<<nblk(ninst, 128), 128, 0, st>>>(c->st.rk_err, c->st.rk_acc, dt_io, c->st.dt, t_io, ninst, eps_des,
+                                                  p.dt_max, err_log, acc_log); ++sph::g_launches; }
+}
+
+void rk_set_dt(sph_ctx *c, const sph_state *s, double *dt_io, cudaStream_t st) {
+  const int ninst = s->ninst > 0 ? s->ninst : 1;
+  { k_rk_dt<<<nblk(ninst, 128), 128, 0, st>>>(dt_io, c->st.dt, ninst); ++sph::g_launches; }
 }
 
 }  // namespace sph

@@ -97,6 +97,8 @@ def lib():
             L.sph_rhs.argtypes = [_vp, C.POINTER(State), C.POINTER(Material), C.c_int32, C.POINTER(Params),
                                   C.POINTER(Derivs), _vp]
             L.sph_gravity.argtypes = [_vp, C.POINTER(State), C.POINTER(Params), _vp, _vp, _vp, _vp]
+            L.sph_step_rk3.argtypes = [_vp, C.POINTER(State), C.POINTER(Material), C.c_int32, C.POINTER(Params),
+                                       C.c_double, _vp, _vp, C.c_int32, _vp, _vp, _vp]
             L.sph_adapt_h.argtypes = [_vp, C.POINTER(State), C.c_int32, C.c_int32, C.c_double, C.c_int32,
                                       C.c_int32, _vp, C.POINTER(C.c_int32), _vp]
             L.sph_neighbours_static.argtypes = [C.POINTER(State), C.c_int32, C.c_int32, C.c_int32, _vp, _vp,
@@ -118,7 +120,7 @@ def lib():
             L.sph_launch_count.argtypes = []
             L.sph_launch_count.restype = C.c_int64
             for f in ("sph_create", "sph_sync_status", "sph_build_tree", "sph_tree_nodes", "sph_neighbours",
-                      "sph_neighbours_static", "sph_adapt_h",
+                      "sph_neighbours_static", "sph_adapt_h", "sph_step_rk3",
                       "sph_rhs", "sph_gravity", "sph_step", "sph_measure_fma_peak", "sph_profile_enable",
                       "sph_profile_read", "sph_get_tuning", "sph_set_tuning", "sph_rhs_adjoint", "sph_pc_update",
                       "sph_pc_update_adjoint"):
@@ -418,6 +420,26 @@ def step(ctx: Context, ds: DeviceState, materials, params: wl.Params, nsteps: in
     ctx.check(ctx._lib.sph_step(ctx.h, C.byref(st), M, len(materials), C.byref(P), _ptr(dt), int(nsteps),
                                 _stream(stream)), "sph_step")
     return dt
+
+
+def step_rk3(ctx: Context, ds: DeviceState, materials, params: wl.Params, eps_des: float, nsteps: int, dt=None,
+             t=None, check=True, stream=None):
+    """nsteps embedded Runge-Kutta attempts (Sect. 3.4.2).  dt, t: per-instance
+    device tensors, updated in place (None: new ones; dt <= 0 starts from the
+    predictor-corrector limit).  Returns (dt, t, error log, accepted log), the
+    logs of shape (nsteps, ninst)."""
+    ninst = max(ds.ninst, 1)
+    dev = ds.x.device
+    dt = dt if dt is not None else torch.zeros(ninst, dtype=torch.float64, device=dev)
+    t = t if t is not None else torch.zeros(ninst, dtype=torch.float64, device=dev)
+    err = torch.zeros((max(nsteps, 1), ninst), dtype=torch.float64, device=dev)
+    acc = torch.zeros((max(nsteps, 1), ninst), dtype=torch.int32, device=dev)
+    st = ds.struct()
+    P = params_struct(params, check)
+    M = materials_array(materials)
+    ctx.check(ctx._lib.sph_step_rk3(ctx.h, C.byref(st), M, len(materials), C.byref(P), float(eps_des), _ptr(dt),
+                                    _ptr(t), int(nsteps), _ptr(err), _ptr(acc), _stream(stream)), "sph_step_rk3")
+    return dt, t, err[:nsteps], acc[:nsteps]
 
 
 def launch_count() -> int:
