@@ -99,6 +99,8 @@ def lib():
             L.orc_gravity_bh.restype = C.c_int32
             L.orc_rhs.restype = C.c_int32
             L.orc_step.restype = C.c_int32
+            L.orc_flaws.restype = C.c_int64
+            L.orc_fof.restype = C.c_int64
             L.orc_step_rk3.restype = C.c_int32
             L.orc_get_threads.restype = C.c_int32
             L.orc_eos.argtypes = [C.POINTER(Material), C.c_double, C.c_double, _dp, _dp, _dp, _dp]
@@ -277,6 +279,63 @@ def adapt_h(x, h, dim, n_des, tol=0, max_iter=10, inst_off=None):
     it = lib().orc_adapt_h(C.c_int32(dim), C.c_int64(n), px, py, pz, _p(hh), _p(io, _lp), C.c_int32(ninst),
                            C.c_double(n_des), C.c_int32(tol), C.c_int32(max_iter), _p(cnt, _ip))
     return hh, cnt[:n], int(it)
+
+
+def philox4x64(ctr, key):
+    """One Philox4x64-10 block: four 64-bit words (Python ints)."""
+    c = (C.c_uint64 * 4)(*[int(v) & (2 ** 64 - 1) for v in ctr])
+    k = (C.c_uint64 * 2)(*[int(v) & (2 ** 64 - 1) for v in key])
+    out = (C.c_uint64 * 4)()
+    lib().orc_philox4x64(c, k, out)
+    return [int(v) for v in out]
+
+
+def flaws(ps, weibull_k=None, weibull_m=None, seed=0):
+    """Weibull activation thresholds (Sect. 3.2) of the particle set's brittle
+    groups (instance x material).  weibull_k, weibull_m default to the
+    materials' own.  Returns (flaw_off int64[n+1] by id, flaw_eps float32)."""
+    n = ps.n
+    nmat = len(ps.materials)
+    wk = np.array([m.weibull_k for m in ps.materials] if weibull_k is None else weibull_k, np.float64)
+    wm = np.array([m.weibull_m for m in ps.materials] if weibull_m is None else weibull_m, np.float64)
+    mats = _mats(ps.materials)
+    ids = np.ascontiguousarray(ps.id, np.int32)
+    mat = np.ascontiguousarray(ps.mat, np.int32)
+    m = _f64(ps.m)
+    io = None if ps.inst_off is None else np.ascontiguousarray(ps.inst_off, np.int64)
+    ninst = 1 if io is None else len(io) - 1
+    off = np.zeros(n + 1, np.int64)
+    cap = int(n * (np.log(max(n, 2)) + 12)) + 64
+    while True:
+        eps = np.zeros(max(cap, 1), np.float32)
+        tot = lib().orc_flaws(C.c_int64(n), _p(ids, _ip), _p(mat, _ip), _p(m), _p(io, _lp), C.c_int32(ninst),
+                              mats, C.c_int32(nmat), _p(wk), _p(wm), C.c_uint64(seed), _p(off, _lp),
+                              _p(eps, _fp), C.c_int64(cap))
+        if tot < 0:
+            raise ValueError("ids are not a permutation of 0..n-1")
+        if tot <= cap:
+            return off, eps[:tot]
+        cap = tot
+
+
+def fof(x, h0, m, dim, b=1.01, d_remove=1.0, min_size=3, dmg=None, inst_off=None):
+    """Friends-of-friends fragments (Sect. 4).  Returns (label int32[n],
+    count int32[nf], mass float64[nf])."""
+    x, px, py, pz = _xyz(x, dim)
+    n = x.shape[1]
+    h0 = _f64(h0)
+    m = _f64(m)
+    dm = None if dmg is None else _f64(dmg)
+    io = None if inst_off is None else np.ascontiguousarray(inst_off, np.int64)
+    ninst = 1 if io is None else len(io) - 1
+    label = np.zeros(max(n, 1), np.int32)
+    cap = max(n, 1)
+    cnt = np.zeros(cap, np.int32)
+    mass = np.zeros(cap)
+    nf = lib().orc_fof(C.c_int32(dim), C.c_int64(n), px, py, pz, _p(h0), _p(dm), _p(m), _p(io, _lp),
+                       C.c_int32(ninst), C.c_double(b), C.c_double(d_remove), C.c_int32(min_size), _p(label, _ip),
+                       _p(cnt, _ip), _p(mass), C.c_int64(cap))
+    return label[:n], cnt[:nf], mass[:nf]
 
 
 def cell_coords(x, dim, max_depth=21):

@@ -164,6 +164,28 @@ void orc_timestep(const orc_state *s, const orc_material *mats, int32_t nmat, co
 int32_t orc_step(orc_state *s, const orc_material *mats, int32_t nmat, const orc_params *prm,
                  int32_t nsteps, double *dt_inst, double *dt_log);
 
+/* Philox4x64-10 block: out = the ten-round cipher of ctr under key. */
+void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
+
+/* Weibull activation thresholds (Sect. 3.2): per group of the brittle particles of one instance and
+ * material (damage set, weibull_k > 0, weibull_m > 0; group g = instance * nmat + material, members in
+ * ascending id, volume V = sum m / rho0), flaw j = 1, 2, ... goes to member floor(w_j N / 2^64), w_j the
+ * draw (word (j-1) mod 4 of Philox4x64-10 with counter ((j-1)/4, 0, 0, 0) and key (seed, g)), with
+ * threshold (j / (k V))^(1/m) as float, until every member holds one.  flaw_off[n+1] by id; flaw_eps
+ * (ascending per particle) written when the total fits in cap.  Returns the total, -1 for invalid ids. */
+int64_t orc_flaws(int64_t n, const int32_t *id, const int32_t *mat, const double *m, const int64_t *inst_off,
+                  int32_t ninst, const orc_material *mats, int32_t nmat, const double *weibull_k,
+                  const double *weibull_m, uint64_t seed, int64_t *flaw_off, float *flaw_eps, int64_t cap);
+
+/* Friends-of-friends fragments (Sect. 4): particles with dmg >= d_remove removed (dmg may be NULL);
+ * friends = partners (same instance) with smoothing lengths b h0; fragments = connected components of
+ * at least min_size particles, numbered by decreasing count, ties by smallest member index; label[n]
+ * = fragment or -1; frag_count, frag_mass up to cap.  Returns the number of fragments. */
+int64_t orc_fof(int32_t dim, int64_t n, const double *x, const double *y, const double *z, const double *h0,
+                const double *dmg, const double *m, const int64_t *inst_off, int32_t ninst, double b,
+                double d_remove, int32_t min_size, int32_t *label, int32_t *frag_count, double *frag_mass,
+                int64_t cap);
+
 void orc_set_threads(int32_t nthreads);
 int32_t orc_get_threads(void);
 

@@ -1659,3 +1659,252 @@ int32_t orc_step(orc_state *s, const orc_material *mats, int32_t nmat, const orc
   free(hcnt);
   return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Counter-based random numbers: Philox4x64-10 (Salmon, Moraes, Dror and     */
+/* Shaw 2011, "Parallel random numbers: as easy as 1, 2, 3").  Each of the   */
+/* ten rounds multiplies counter words 0 and 2 by the two round multipliers  */
+/* (full 128-bit products); the new counter is (hi(2)^c1^k0, lo(2),           */
+/* hi(0)^c3^k1, lo(0)); the key gains the two Weyl increments (golden ratio  */
+/* and sqrt(3) - 1 in 64-bit fixed point) before every round but the first.  */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+  uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint64_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B97F4A7C15ULL;
+      k1 += 0xBB67AE8584CAA73BULL;
+    }
+    unsigned __int128 p0 = (unsigned __int128)0xD2E7470EE14C6C93ULL * c0;
+    unsigned __int128 p2 = (unsigned __int128)0xCA5A826395121157ULL * c2;
+    uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+    uint64_t hi2 = (uint64_t)(p2 >> 64), lo2 = (uint64_t)p2;
+    c0 = hi2 ^ c1 ^ k0;
+    c1 = lo2;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+/* Draw j >= 1 of group g: word (j - 1) mod 4 of the block with counter   */
+/* ((j - 1) / 4, 0, 0, 0) and key (seed, g); a member index in [0, N) is     */
+/* the high word of draw * N (multiply-shift).                               */
+static uint64_t flaw_draw(uint64_t seed, uint64_t g, uint64_t j) {
+  uint64_t ctr[4] = {(j - 1) >> 2, 0, 0, 0}, key[2] = {seed, g}, out[4];
+  orc_philox4x64(ctr, key, out);
+  return out[(j - 1) & 3];
+}
+
+typedef struct {
+  int32_t id;
+  int64_t a;
+} id_idx;
+
+static int cmp_id_idx(const void *p, const void *q) {
+  int32_t a = ((const id_idx *)p)->id, b = ((const id_idx *)q)->id;
+  return (a > b) - (a < b);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Weibull activation thresholds, Sect. 3.2 (after Benz & Asphaug 1995).    */
+/* The brittle particles of each instance and material form a group of N    */
+/* particles (ascending id) with volume V = sum m / rho0.  Flaw j = 1, 2, ... */
+/* goes to a uniformly drawn member and has the threshold strain             */
+/* (j / (k V))^(1/m); flaws are handed out until every member holds one.     */
+/* Group g = instance * nmat + material; brittle: damage set, k > 0, m > 0.  */
+/* flaw_off[0..n] (indexed by id, ids a permutation of 0..n-1) receives the  */
+/* CSR offsets; flaw_eps the thresholds (float, ascending per particle) when */
+/* the total fits in cap.  Returns the total, or -1 for invalid ids.         */
+/* ------------------------------------------------------------------------ */
+int64_t orc_flaws(int64_t n, const int32_t *id, const int32_t *mat, const double *m, const int64_t *inst_off,
+                  int32_t ninst, const orc_material *mats, int32_t nmat, const double *weibull_k,
+                  const double *weibull_m, uint64_t seed, int64_t *flaw_off, float *flaw_eps, int64_t cap) {
+  if (ninst < 1) ninst = 1;
+  int64_t *cnt = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+  int64_t *owner = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t)); /* id -> index */
+  for (int64_t a = 0; a < n; ++a) owner[a] = -1;
+  for (int64_t a = 0; a < n; ++a) {
+    if (id[a] < 0 || id[a] >= n || owner[id[a]] >= 0) {
+      free(cnt);
+      free(owner);
+      return -1;
+    }
+    owner[id[a]] = a;
+  }
+  /* draws of every group, in order: (member particle index, j) */
+  int64_t ndraw = 0, capd = 1024;
+  int64_t *dpart = (int64_t *)malloc((size_t)capd * sizeof(int64_t));
+  uint64_t *dj = (uint64_t *)malloc((size_t)capd * sizeof(uint64_t));
+  double *dkv = (double *)malloc((size_t)capd * sizeof(double)), *dinvm = (double *)malloc((size_t)capd * sizeof(double));
+  id_idx *mem = (id_idx *)malloc((size_t)(n > 0 ? n : 1) * sizeof(id_idx));
+  char *covered = (char *)malloc((size_t)(n > 0 ? n : 1));
+  for (int32_t i = 0; i < ninst; ++i) {
+    int64_t b0 = (ninst > 1 && inst_off) ? inst_off[i] : 0, b1 = (ninst > 1 && inst_off) ? inst_off[i + 1] : n;
+    for (int32_t mt = 0; mt < nmat; ++mt) {
+      if (!mats[mt].damage || !(weibull_k[mt] > 0.0) || !(weibull_m[mt] > 0.0)) continue;
+      int64_t N = 0;
+      for (int64_t a = b0; a < b1; ++a)
+        if (mat[a] == mt) {
+          mem[N].id = id[a];
+          mem[N].a = a;
+          ++N;
+        }
+      if (N <= 0) continue;
+      qsort(mem, (size_t)N, sizeof(id_idx), cmp_id_idx);
+      double V = 0.0;
+      for (int64_t k = 0; k < N; ++k) V = V + m[mem[k].a] / mats[mt].rho0;
+      const double kV = weibull_k[mt] * V, invm = 1.0 / weibull_m[mt];
+      const uint64_t g = (uint64_t)i * (uint64_t)nmat + (uint64_t)mt;
+      memset(covered, 0, (size_t)N);
+      int64_t left = N;
+      for (uint64_t j = 1; left > 0; ++j) {
+        uint64_t w = flaw_draw(seed, g, j);
+        int64_t k = (int64_t)(((unsigned __int128)w * (uint64_t)N) >> 64);
+        if (!covered[k]) {
+          covered[k] = 1;
+          --left;
+        }
+        if (ndraw == capd) {
+          capd *= 2;
+          dpart = (int64_t *)realloc(dpart, (size_t)capd * sizeof(int64_t));
+          dj = (uint64_t *)realloc(dj, (size_t)capd * sizeof(uint64_t));
+          dkv = (double *)realloc(dkv, (size_t)capd * sizeof(double));
+          dinvm = (double *)realloc(dinvm, (size_t)capd * sizeof(double));
+        }
+        dpart[ndraw] = mem[k].a;
+        dj[ndraw] = j;
+        dkv[ndraw] = kV;
+        dinvm[ndraw] = invm;
+        ++ndraw;
+        cnt[id[mem[k].a] + 1]++;
+      }
+    }
+  }
+  for (int64_t k = 0; k < n; ++k) cnt[k + 1] += cnt[k];
+  memcpy(flaw_off, cnt, (size_t)(n + 1) * sizeof(int64_t));
+  if (ndraw <= cap) {
+    /* draws are in ascending j within a group, so each particle's list stays ascending */
+    int64_t *fill = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    memcpy(fill, cnt, (size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    for (int64_t d = 0; d < ndraw; ++d) {
+      double eps = pow((double)dj[d] / dkv[d], dinvm[d]);
+      flaw_eps[fill[id[dpart[d]]]++] = (float)eps;
+    }
+    free(fill);
+  }
+  free(cnt);
+  free(owner);
+  free(dpart);
+  free(dj);
+  free(dkv);
+  free(dinvm);
+  free(mem);
+  free(covered);
+  return ndraw;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Fragments by friends-of-friends (Sect. 4, fragment analysis of the       */
+/* impact experiment): particles with dmg >= d_remove are removed; two of    */
+/* the rest in the same instance are friends when they would be interaction  */
+/* partners with smoothing lengths b h0 (r_ab^2 < h'_ab^2, h' = b h0 rounded */
+/* to double); fragments are the connected components of the friendship     */
+/* graph with at least min_size particles, numbered by decreasing particle  */
+/* count, ties by smallest member index.  label[n]: fragment or -1.         */
+/* frag_count, frag_mass (sum of m in ascending index) up to cap entries.    */
+/* dmg may be NULL (nothing removed).  Returns the number of fragments.     */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int64_t count, first;
+} frag_key;
+
+static int cmp_frag(const void *p, const void *q) {
+  const frag_key *a = (const frag_key *)p, *b = (const frag_key *)q;
+  if (a->count != b->count) return a->count > b->count ? -1 : 1;
+  return (a->first > b->first) - (a->first < b->first);
+}
+
+int64_t orc_fof(int32_t dim, int64_t n, const double *x, const double *y, const double *z, const double *h0,
+                const double *dmg, const double *m, const int64_t *inst_off, int32_t ninst, double b,
+                double d_remove, int32_t min_size, int32_t *label, int32_t *frag_count, double *frag_mass,
+                int64_t cap) {
+  if (ninst < 1) ninst = 1;
+  double *hb = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+  for (int64_t a = 0; a < n; ++a) hb[a] = b * h0[a];
+  int64_t *comp = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t)); /* smallest member index */
+  int64_t *stack = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+  for (int64_t a = 0; a < n; ++a) comp[a] = -1;
+  for (int32_t i = 0; i < ninst; ++i) {
+    int64_t b0 = (ninst > 1 && inst_off) ? inst_off[i] : 0, b1 = (ninst > 1 && inst_off) ? inst_off[i + 1] : n;
+    int64_t ni = b1 - b0;
+    if (ni <= 0) continue;
+    const double *xi = x + b0, *yi = y + b0, *zi = dim == 3 ? z + b0 : NULL;
+    int64_t *off = (int64_t *)malloc((size_t)(ni + 1) * sizeof(int64_t));
+    int64_t capn = 64 * ni + 1024;
+    int32_t *nb = NULL;
+    for (;;) {
+      nb = (int32_t *)malloc((size_t)capn * sizeof(int32_t));
+      if (orc_neighbours_grid(dim, ni, xi, yi, zi, hb + b0, off, nb, capn) >= 0) break;
+      free(nb);
+      capn = off[ni] + 1;
+    }
+    /* depth-first search from each unvisited surviving particle, in index order */
+    for (int64_t s0 = 0; s0 < ni; ++s0) {
+      int64_t a0 = b0 + s0;
+      if (comp[a0] >= 0 || (dmg && dmg[a0] >= d_remove)) continue;
+      int64_t top = 0;
+      stack[top++] = s0;
+      comp[a0] = a0;
+      while (top > 0) {
+        int64_t s = stack[--top];
+        for (int64_t k = off[s]; k < off[s + 1]; ++k) {
+          int64_t t = nb[k], at = b0 + t;
+          if (comp[at] >= 0 || (dmg && dmg[at] >= d_remove)) continue;
+          comp[at] = a0;
+          stack[top++] = t;
+        }
+      }
+    }
+    free(off);
+    free(nb);
+  }
+  /* sizes of the components, keyed by their smallest member */
+  int64_t *size = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+  for (int64_t a = 0; a < n; ++a)
+    if (comp[a] >= 0) size[comp[a]]++;
+  int64_t nf = 0;
+  for (int64_t a = 0; a < n; ++a)
+    if (comp[a] == a && size[a] >= min_size) ++nf;
+  frag_key *fk = (frag_key *)malloc((size_t)(nf > 0 ? nf : 1) * sizeof(frag_key));
+  nf = 0;
+  for (int64_t a = 0; a < n; ++a)
+    if (comp[a] == a && size[a] >= min_size) {
+      fk[nf].count = size[a];
+      fk[nf].first = a;
+      ++nf;
+    }
+  qsort(fk, (size_t)nf, sizeof(frag_key), cmp_frag);
+  int64_t *rank = stack; /* reuse: rank of a component by its smallest member */
+  for (int64_t a = 0; a < n; ++a) rank[a] = -1;
+  for (int64_t f = 0; f < nf; ++f) rank[fk[f].first] = f;
+  for (int64_t f = 0; f < nf && f < cap; ++f) {
+    frag_count[f] = (int32_t)fk[f].count;
+    frag_mass[f] = 0.0;
+  }
+  for (int64_t a = 0; a < n; ++a) {
+    int64_t f = comp[a] >= 0 ? rank[comp[a]] : -1;
+    label[a] = (int32_t)f;
+    if (f >= 0 && f < cap) frag_mass[f] = frag_mass[f] + m[a];
+  }
+  free(hb);
+  free(comp);
+  free(stack);
+  free(size);
+  free(fk);
+  return nf;
+}
