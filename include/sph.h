@@ -279,6 +279,51 @@ sph_status sph_step_rk3(sph_ctx *ctx, sph_state *state, const sph_material *mats
                         const sph_params *params, double eps_des, double *dt, double *t, int32_t nsteps,
                         double *err_log, int32_t *acc_log, void *stream);
 
+/* Weibull activation thresholds (Sect. 3.2, after Benz & Asphaug): the
+ * brittle particles (mats[mat].damage set, weibull_k[mat] > 0 and
+ * weibull_m[mat] > 0) of each instance and material form a group of N
+ * particles, listed by ascending id, with volume V = sum m / rho0.  Flaw
+ * j = 1, 2, ... goes to member floor(w_j N / 2^64) with threshold strain
+ * (j / (k V))^(1/m), until every member holds one; w_j is word (j-1) mod 4
+ * of the Philox4x64-10 block (Salmon et al. 2011) with counter
+ * ((j-1)/4, 0, 0, 0) and key (seed, instance * nmat + material).
+ * state: n, ninst/inst_off, mat, id (a permutation of 0..n-1) and m are
+ * read.  weibull_k, weibull_m: host double[nmat].
+ * flaw_off: device int64[n+1] (may be NULL: count only), CSR offsets by id,
+ * as sph_state.flaw_off expects; flaw_eps: device float[eps_capacity] (may
+ * be NULL), thresholds ascending per particle.  *nflaws (host) receives
+ * the total.  Blocking.  SPH_ERR_CAPACITY when the total exceeds
+ * eps_capacity (offsets and *nflaws are still written) or 2^31;
+ * SPH_ERR_INVALID for an id or material index out of range.  The result
+ * depends only on seed and the state, not on the particle order within an
+ * instance; it equals the sequential procedure's up to the rounding of V
+ * (a sum in a different order) and of pow. */
+sph_status sph_flaws(sph_ctx *ctx, const sph_state *state, const sph_material *mats, int32_t nmat,
+                     const double *weibull_k, const double *weibull_m, uint64_t seed, int64_t *flaw_off,
+                     float *flaw_eps, int64_t eps_capacity, int64_t *nflaws, void *stream);
+
+/* Fragments by friends-of-friends (Sect. 4, fragment analysis of an
+ * impact): particles with dmg >= d_remove are removed (state.dmg NULL:
+ * none); two remaining particles of one instance are friends when
+ * r_ab^2 < ((h'_a + h'_b)/2)^2 with h' = link * h0 (the partner rule of
+ * sph_neighbours at smoothing lengths h'; the paper links at 1.01 times the
+ * original smoothing length); fragments are the connected components with
+ * at least min_size particles (the paper drops those below 3), numbered by
+ * decreasing particle count, ties by smallest member index.
+ * h0: device double[n], the original smoothing lengths (NULL: state.h).
+ * label: device int32[n], fragment number or -1 (removed, or in a smaller
+ * component).  frag_count (int32), frag_mass (double, sum of m): device
+ * arrays of frag_capacity entries (may be NULL); masses are summed with
+ * atomics, so their last bits may differ between runs.  *nfrag (host)
+ * receives the number of fragments.  Blocking.  Uses the context's partner
+ * lists: SPH_ERR_CAPACITY when a particle has more than max_neighbours
+ * friends, or more fragments than frag_capacity (labels and *nfrag are
+ * complete then). */
+sph_status sph_fragments(sph_ctx *ctx, const sph_state *state, const double *h0, double link, double d_remove,
+                         int32_t min_size, int32_t leaf_size, int32_t max_depth, int32_t *label,
+                         int32_t *frag_count, double *frag_mass, int64_t frag_capacity, int64_t *nfrag,
+                         void *stream);
+
 /* Reverse-mode derivative of sph_rhs at `state` (FP64, any requested
  * precision is evaluated in FP64), with the partner lists and the damage of
  * that evaluation held fixed and every branch (artificial viscosity on/off,

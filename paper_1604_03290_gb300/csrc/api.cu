@@ -49,7 +49,7 @@ static T *ctx_alloc(sph_ctx *c, int64_t count, bool &ok) {
   if (!ok) return nullptr;
   void *p = nullptr;
   size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
-  if (cudaMalloc(&p, bytes) != cudaSuccess || c->nallocs >= 128) {
+  if (cudaMalloc(&p, bytes) != cudaSuccess || c->nallocs >= 256) {
     ok = false;
     return nullptr;
   }
@@ -175,6 +175,18 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   S.dt = ctx_alloc<double>(c, ci, ok);
   S.gather = ctx_alloc<double>(c, N, ok);
   S.gather_i = ctx_alloc<int32_t>(c, N, ok);
+  FlawBufs &F = c->fl;
+  F.cap_groups = (int64_t)ci * SPH_MAX_MATERIALS;
+  F.cap_plan = (int)F.cap_groups;
+  F.goff = ctx_alloc<int32_t>(c, F.cap_groups + 1, ok);
+  F.kv = ctx_alloc<double>(c, F.cap_groups, ok);
+  F.invm = ctx_alloc<double>(c, F.cap_groups, ok);
+  F.J = ctx_alloc<uint32_t>(c, F.cap_groups, ok);
+  F.unc = ctx_alloc<int32_t>(c, F.cap_groups, ok);
+  F.plan_grp = ctx_alloc<int32_t>(c, F.cap_groups, ok);
+  F.plan_b0 = ctx_alloc<int64_t>(c, F.cap_groups, ok);
+  F.plan_pre = ctx_alloc<int64_t>(c, F.cap_groups + 1, ok);
+  F.bad = ctx_alloc<int32_t>(c, 1, ok);
   if (ok) ok = cudaMemset(c->d_err, 0, sizeof(int32_t)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -388,6 +400,52 @@ sph_status sph_adapt_h(sph_ctx *c, sph_state *s, int32_t leaf_size, int32_t max_
   if ((r = cuda_check(c, "sph_adapt_h")) != SPH_OK) return r;
   if ((r = sph_sync_status(c, stream)) != SPH_OK) return r;
   if (updates) *updates = u;
+  return SPH_OK;
+}
+
+sph_status sph_flaws(sph_ctx *c, const sph_state *s, const sph_material *mats, int32_t nmat, const double *weibull_k,
+                     const double *weibull_m, uint64_t seed, int64_t *flaw_off, float *flaw_eps,
+                     int64_t eps_capacity, int64_t *nflaws, void *stream) {
+  if (!c || !s) return SPH_ERR_INVALID;
+  if (s->n < 0 || s->n > c->cap_n) return fail(c, SPH_ERR_INVALID, "n exceeds the context capacity");
+  const int ninst = s->ninst > 0 ? s->ninst : 1;
+  if (ninst > c->cap_inst) return fail(c, SPH_ERR_INVALID, "ninst exceeds the context capacity");
+  if (ninst > 1 && !s->inst_off) return fail(c, SPH_ERR_INVALID, "inst_off is required when ninst > 1");
+  if (!mats || nmat < 1 || nmat > SPH_MAX_MATERIALS || !weibull_k || !weibull_m || !nflaws)
+    return fail(c, SPH_ERR_INVALID, "need materials (1..8), weibull_k, weibull_m and nflaws");
+  if (s->n > 0 && (!s->mat || !s->id || !s->m)) return fail(c, SPH_ERR_INVALID, "need mat, id and m");
+  if (eps_capacity < 0 || (flaw_eps && !flaw_off)) return fail(c, SPH_ERR_INVALID, "bad flaw output");
+  for (int k = 0; k < nmat; ++k)
+    if (mats[k].damage && weibull_k[k] > 0.0 && weibull_m[k] > 0.0 && !(mats[k].rho0 > 0.0))
+      return fail(c, SPH_ERR_INVALID, "a brittle material needs rho0 > 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  sph_status r = flaws_generate(c, s, mats, nmat, weibull_k, weibull_m, seed, flaw_off, flaw_eps, eps_capacity,
+                                nflaws, st);
+  if (r == SPH_ERR_CUDA) {
+    const sph_status e = cuda_check(c, "sph_flaws");
+    return e != SPH_OK ? e : fail(c, r, "sph_flaws: stream synchronisation failed");
+  }
+  if (r != SPH_OK) return r;
+  if ((r = cuda_check(c, "sph_flaws")) != SPH_OK) return r;
+  return sph_sync_status(c, stream);
+}
+
+sph_status sph_fragments(sph_ctx *c, const sph_state *s, const double *h0, double link, double d_remove,
+                         int32_t min_size, int32_t leaf_size, int32_t max_depth, int32_t *label, int32_t *frag_count,
+                         double *frag_mass, int64_t frag_capacity, int64_t *nfrag, void *stream) {
+  sph_status r = check_state(c, s);
+  if (r != SPH_OK) return r;
+  if ((r = check_tree_args(c, s, leaf_size, max_depth)) != SPH_OK) return r;
+  if (!(link > 0.0) || min_size < 1 || frag_capacity < 0 || !nfrag || (s->n > 0 && !label))
+    return fail(c, SPH_ERR_INVALID, "need link > 0, min_size >= 1, label and nfrag");
+  cudaStream_t st = (cudaStream_t)stream;
+  set_materials(c, nullptr);
+  fragments_fof(c, s, h0, link, d_remove, min_size, leaf_size, max_depth, label, frag_count, frag_mass,
+                frag_capacity, nfrag, st);
+  if ((r = cuda_check(c, "sph_fragments")) != SPH_OK) return r;
+  if ((r = sph_sync_status(c, stream)) != SPH_OK) return r;
+  if (*nfrag > frag_capacity)
+    return fail(c, SPH_ERR_CAPACITY, "more fragments than frag_capacity (labels and nfrag are complete)");
   return SPH_OK;
 }
 

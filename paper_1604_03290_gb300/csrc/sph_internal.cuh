@@ -132,6 +132,19 @@ struct StepBufs {
   int32_t *gather_i;
 };
 
+// Per-group scratch of the flaw generator (group = instance x material).
+struct FlawBufs {
+  int64_t cap_groups;
+  int32_t *goff;       // cap_groups + 1: first sorted position of each group
+  double *kv, *invm;   // k V and 1/m per group
+  uint32_t *J;         // number of flaws per group
+  int32_t *unc;        // members not yet hit
+  int32_t *plan_grp;   // draw plan of one round
+  int64_t *plan_b0, *plan_pre;
+  int cap_plan;
+  int32_t *bad;        // set when an id or material index is out of range
+};
+
 }  // namespace sph
 
 struct sph_ctx {
@@ -170,8 +183,9 @@ struct sph_ctx {
   cudaEvent_t *prof_ev;       // 2 * kMaxProfEvents
   int32_t *prof_phase;        // kMaxProfEvents
   sph::StepBufs st;
+  sph::FlawBufs fl;
   // allocation list
-  void *allocs[128];
+  void *allocs[256];
   int nallocs;
 };
 
@@ -301,6 +315,14 @@ void rhs_adjoint(sph_ctx *c, const sph_state *s, const MatTable &mt, const sph_p
 void pc_update_adjoint(sph_ctx *c, const sph_state *base, const sph_derivs &d, const double *dt, double frac,
                        const MatTable &mt, const sph_params &p, const sph_state *obar, sph_state *gbar,
                        sph_derivs *fbar, double *param_bar, cudaStream_t st);
+// flaws.cu: Weibull thresholds (Sect. 3.2); *total receives the number of flaws
+sph_status flaws_generate(sph_ctx *c, const sph_state *s, const sph_material *mats, int nmat, const double *wk,
+                          const double *wm, uint64_t seed, int64_t *flaw_off, float *flaw_eps, int64_t cap,
+                          int64_t *total, cudaStream_t st);
+// fof.cu: friends-of-friends fragments (Sect. 4); blocking (*nfrag on return)
+void fragments_fof(sph_ctx *c, const sph_state *s, const double *h0, double b, double d_remove, int min_size,
+                   int leaf_size, int max_depth, int32_t *label, int32_t *frag_count, double *frag_mass, int64_t cap,
+                   int64_t *nfrag, cudaStream_t st);
 // step.cu
 void timestep_reduce(sph_ctx *c, const sph_state *s, const sph_params &p, const sph_derivs &d, cudaStream_t st);
 // dmove (device, may be NULL): receives the bits of max over particles and

@@ -416,6 +416,18 @@ static void radix_sort(sph_ctx *c, int64_t n, int bits, cudaStream_t st) {
   T.perm = T.vals[src];
 }
 
+// Sorts (keys[0], vals[0]) of the tree's sort buffers; the result is left
+// in (skey, perm).  Used outside the tree build by the flaw generator and the
+// fragment finder, which do not need the tree afterwards.
+void sort_pairs(sph_ctx *c, int64_t n, int bits, cudaStream_t st) {
+  if (n > 0) {
+    radix_sort(c, n, bits, st);
+  } else {
+    c->tree.skey = c->tree.keys[0];
+    c->tree.perm = c->tree.vals[0];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Exclusive scan of int32 counts (length m), three phases.
 // ---------------------------------------------------------------------------

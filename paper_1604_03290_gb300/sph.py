@@ -105,6 +105,10 @@ def lib():
                                                 C.c_int64, C.c_char_p, C.c_int32, _vp]
             L.sph_step.argtypes = [_vp, C.POINTER(State), C.POINTER(Material), C.c_int32, C.POINTER(Params), _vp,
                                    C.c_int32, _vp]
+            L.sph_flaws.argtypes = [_vp, C.POINTER(State), C.POINTER(Material), C.c_int32, _vp, _vp, C.c_uint64,
+                                    _vp, _vp, C.c_int64, C.POINTER(C.c_int64), _vp]
+            L.sph_fragments.argtypes = [_vp, C.POINTER(State), _vp, C.c_double, C.c_double, C.c_int32, C.c_int32,
+                                        C.c_int32, _vp, _vp, _vp, C.c_int64, C.POINTER(C.c_int64), _vp]
             L.sph_measure_fma_peak.argtypes = [C.c_int32, C.POINTER(C.c_double)]
             L.sph_profile_enable.argtypes = [_vp, C.c_int32]
             L.sph_profile_read.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_int32]
@@ -120,7 +124,7 @@ def lib():
             L.sph_launch_count.argtypes = []
             L.sph_launch_count.restype = C.c_int64
             for f in ("sph_create", "sph_sync_status", "sph_build_tree", "sph_tree_nodes", "sph_neighbours",
-                      "sph_neighbours_static", "sph_adapt_h", "sph_step_rk3",
+                      "sph_neighbours_static", "sph_adapt_h", "sph_step_rk3", "sph_flaws", "sph_fragments",
                       "sph_rhs", "sph_gravity", "sph_step", "sph_measure_fma_peak", "sph_profile_enable",
                       "sph_profile_read", "sph_get_tuning", "sph_set_tuning", "sph_rhs_adjoint", "sph_pc_update",
                       "sph_pc_update_adjoint"):
@@ -371,6 +375,43 @@ def adapt_h(ctx: Context, ds: DeviceState, n_des, tol=0, max_iter=10, leaf_size=
     ctx.check(ctx._lib.sph_adapt_h(ctx.h, C.byref(st), int(leaf_size), int(max_depth), float(n_des), int(tol),
                                    int(max_iter), _ptr(cnt), C.byref(upd), _stream(stream)), "sph_adapt_h")
     return cnt[: ds.n], upd.value
+
+
+def flaws(ctx: Context, ds: DeviceState, materials, weibull_k=None, weibull_m=None, seed=0, stream=None):
+    """Weibull activation thresholds (Sect. 3.2) of the brittle particles of
+    ds.  weibull_k, weibull_m default to the materials' own.  Returns
+    (flaw_off int64[n+1] by id, flaw_eps float32) as device tensors; assign
+    them to ds.flaw_off / ds.flaw_eps to use them in the damage model."""
+    mats, nmat = materials_array(materials), len(materials)
+    wk = np.ascontiguousarray([m.weibull_k for m in materials] if weibull_k is None else weibull_k, np.float64)
+    wm = np.ascontiguousarray([m.weibull_m for m in materials] if weibull_m is None else weibull_m, np.float64)
+    off = torch.zeros(ds.n + 1, dtype=torch.int64, device=ds.x.device)
+    tot = C.c_int64(0)
+    st = ds.struct()
+    seed = int(seed) & (2 ** 64 - 1)
+    args = (ctx.h, C.byref(st), mats, nmat, wk.ctypes.data_as(_vp), wm.ctypes.data_as(_vp), seed)
+    ctx.check(ctx._lib.sph_flaws(*args, None, None, 0, C.byref(tot), _stream(stream)), "sph_flaws")
+    eps = torch.empty(max(tot.value, 1), dtype=torch.float32, device=ds.x.device)
+    ctx.check(ctx._lib.sph_flaws(*args, _ptr(off), _ptr(eps), int(tot.value), C.byref(tot), _stream(stream)),
+              "sph_flaws")
+    return off, eps[: tot.value]
+
+
+def fragments(ctx: Context, ds: DeviceState, h0=None, link=1.01, d_remove=1.0, min_size=3, leaf_size=16,
+              max_depth=21, stream=None):
+    """Friends-of-friends fragments (Sect. 4).  Returns (label int32[n],
+    count int32[nf], mass float64[nf]) as device tensors."""
+    dev = ds.x.device
+    label = torch.empty(max(ds.n, 1), dtype=torch.int32, device=dev)
+    cap = max(ds.n, 1)
+    cnt = torch.empty(cap, dtype=torch.int32, device=dev)
+    mass = torch.empty(cap, dtype=torch.float64, device=dev)
+    nf = C.c_int64(0)
+    st = ds.struct()
+    ctx.check(ctx._lib.sph_fragments(ctx.h, C.byref(st), _ptr(h0), float(link), float(d_remove), int(min_size),
+                                     int(leaf_size), int(max_depth), _ptr(label), _ptr(cnt), _ptr(mass), int(cap),
+                                     C.byref(nf), _stream(stream)), "sph_fragments")
+    return label[: ds.n], cnt[: nf.value], mass[: nf.value]
 
 
 def neighbours_static(ds: DeviceState, leaf_size=16, max_depth=21, max_neighbours=128, capacity=None,

@@ -426,6 +426,33 @@ def batched_impacts(seed=5, ninst=256, nmin=2000, nmax=50000, dx=1e-3, vmin=3000
     return ps
 
 
+def fragmented_body(seed=21, n_side=100, ncracks=10, dx=1e-3, jitter=0.05, d_spot=0.05) -> ParticleSet:
+    """A basalt cube (n_side^3 jittered lattice, h = 2.4 dx) as an impact
+    leaves it: fully damaged slabs of half-width 1.3 dx around `ncracks`
+    random planes (wider than the 1.01 h linking length, so they cut the body
+    into pieces), a fraction d_spot of scattered fully damaged particles, and
+    d ~ U[0, 0.95) elsewhere.  The input of the fragment analysis."""
+    rng = np.random.default_rng(seed)
+    side = n_side * dx
+    x = _lattice_box(n_side, n_side, n_side, dx, origin=(-side / 2, -side / 2, -side / 2))
+    x += rng.uniform(-jitter, jitter, size=x.shape) * dx
+    n = x.shape[1]
+    dmg = rng.uniform(0.0, 0.95, n)
+    for _ in range(ncracks):
+        nrm = rng.normal(size=3)
+        nrm /= np.linalg.norm(nrm)
+        p0 = rng.uniform(-0.35, 0.35, 3) * side
+        dist = np.abs(nrm @ (x - p0[:, None]))
+        dmg[dist < 1.3 * dx] = 1.0
+    dmg[rng.uniform(size=n) < d_spot] = 1.0
+    mat = replace(basalt(), weibull_k=5e34, weibull_m=8.5)
+    params = Params(dim=3, alpha=1.0, beta=2.0, dmpd=dx, u_floor=1e3, S_floor=1e5)
+    ps = _finish(3, x, np.zeros((3, n)), np.full(n, mat.rho0 * dx ** 3), np.full(n, 2.4 * dx), np.full(n, mat.rho0),
+                 np.zeros(n), np.zeros(n, np.int32), [mat], params, with_dmg=True, name="fragmented_%d" % n)
+    ps.dmg = dmg
+    return ps
+
+
 def lattice_block(seed=0, nx=12, ny=12, nz=12, dx=1.0, jitter=0.2, h_factor=2.4, dim=3) -> ParticleSet:
     """A small jittered lattice block (unit density, linear EOS) for tests."""
     rng = np.random.default_rng(seed)
