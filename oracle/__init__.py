@@ -57,7 +57,7 @@ class Params(C.Structure):
                 ("c_courant", C.c_double), ("c_accel", C.c_double), ("c_quantity", C.c_double),
                 ("u_floor", C.c_double), ("S_floor", C.c_double), ("dmg_floor", C.c_double),
                 ("dt_max", C.c_double), ("dt_fixed", C.c_double), ("n_des", C.c_double),
-                ("h_tol", C.c_int32), ("h_iter", C.c_int32)]
+                ("h_tol", C.c_int32), ("h_iter", C.c_int32), ("tree_reuse", C.c_int32), ("pad2", C.c_int32)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -144,9 +144,11 @@ def material_struct(m) -> Material:
 def params_struct(p) -> Params:
     s = Params()
     for k, _ in Params._fields_:
+        if k == "pad2":
+            continue
         v = getattr(p, k)
         setattr(s, k, int(v) if k in ("dim", "density_sum", "consistency", "gravity", "leaf_size", "max_depth",
-                                     "h_tol", "h_iter") else float(v))
+                                     "h_tol", "h_iter", "tree_reuse") else float(v))
     return s
 
 
@@ -373,6 +375,18 @@ def gravity_direct(x, m, h, dim, G, eps_grav):
     lib().orc_gravity_direct(C.c_int32(dim), C.c_int64(n), px, py, pz, _p(_f64(m)), _p(_f64(h)),
                              C.c_double(G), C.c_double(eps_grav), _p(a[0]), _p(a[1]), _p(a[2]))
     return a[:dim]
+
+
+def gravity_bh_reuse(xb, x, m, h, dim, G, theta, eps_grav, leaf_size, max_depth=21):
+    """Barnes-Hut accelerations at x with the tree and pseudo-particles of xb."""
+    xb, pxb, pyb, pzb = _xyz(xb, dim)
+    x, px, py, pz = _xyz(x, dim)
+    n = x.shape[1]
+    out = np.zeros((3, n))
+    lib().orc_gravity_bh_reuse(C.c_int32(dim), C.c_int64(n), pxb, pyb, pzb, px, py, pz, _p(_f64(m)), _p(_f64(h)),
+                               C.c_double(G), C.c_double(theta), C.c_double(eps_grav), C.c_int32(leaf_size),
+                               C.c_int32(max_depth), None, C.c_int64(0), _p(out[0]), _p(out[1]), _p(out[2]))
+    return out[:dim]
 
 
 def gravity_bh(x, m, h, dim, G, theta, eps_grav, leaf_size, max_depth=21, sample=None):

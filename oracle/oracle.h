@@ -49,6 +49,10 @@ typedef struct {
   double u_floor, S_floor, dmg_floor, dt_max, dt_fixed;
   double n_des;                   /* > 0: variable h (Sect. 4.2) at the start of each step */
   int32_t h_tol, h_iter;          /* its count tolerance and most updates   */
+  int32_t tree_reuse;             /* > 0: with gravity, one tree (and its pseudo-particles) serves the
+                                     evaluations of this many consecutive steps (Sect. 5); 0: a tree per
+                                     evaluation */
+  int32_t pad2;
 } orc_params;
 
 /* Particle state, structure of arrays.  Tensors S are symmetric and stored
@@ -120,6 +124,14 @@ int32_t orc_adapt_h(int32_t dim, int64_t n, const double *x, const double *y, co
  * [nsteps][ninst]. */
 int32_t orc_step_rk3(orc_state *s, const orc_material *mats, int32_t nmat, const orc_params *P, double eps_des,
                      int32_t nsteps, double *dt_inst, double *t_inst, double *err_log, int32_t *acc_log);
+
+/* Barnes-Hut accelerations at positions (x, y, z) with the tree and pseudo-particles built at
+ * (xb, yb, zb): containment by the particle's current cell in the build's root cube, leaves summed
+ * over their members' current positions.  xb = x gives orc_gravity_bh. */
+int32_t orc_gravity_bh_reuse(int32_t dim, int64_t n, const double *xb, const double *yb, const double *zb,
+                             const double *x, const double *y, const double *z, const double *m, const double *h,
+                             double G, double theta, double eps_grav, int32_t leaf_size, int32_t max_depth,
+                             const int64_t *sample, int64_t nsample, double *ax, double *ay, double *az);
 
 /* Octree (Sect. 3.5.1 root cube and subdivision; bucket leaves of <= leaf_size).
  * Writes per node: level, integer cell coordinates, particle count, mass, COM.

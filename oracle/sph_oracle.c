@@ -573,13 +573,13 @@ void orc_gravity_direct(int32_t dim, int64_t n, const double *x, const double *y
 /* distance to the node's centre of mass) and its cube does not contain a;   */
 /* otherwise a leaf is summed particle by particle (self skipped) and an     */
 /* inner node is opened.                                                     */
-static void bh_walk(const otree *t, int64_t id, int64_t a, const double *const X[3], const double *m,
-                    double G, double theta, double eps2, double acc[3]) {
+static void bh_walk(const otree *t, int64_t id, int64_t a, const int64_t ka[3], const double *const X[3],
+                    const double *m, double G, double theta, double eps2, double acc[3]) {
   const onode *nd = &t->nodes[id];
   int dim = t->dim;
   int inside = 1;
   for (int ax = 0; ax < dim; ++ax)
-    if ((t->k[3 * a + ax] >> (t->B - nd->level)) != nd->cell[ax]) inside = 0;
+    if ((ka[ax] >> (t->B - nd->level)) != nd->cell[ax]) inside = 0;
   double xa[3] = {0, 0, 0};
   for (int ax = 0; ax < dim; ++ax) xa[ax] = X[ax][a];
   if (!inside) {
@@ -604,15 +604,21 @@ static void bh_walk(const otree *t, int64_t id, int64_t a, const double *const X
     }
     return;
   }
-  for (int c = 0; c < nd->nchild; ++c) bh_walk(t, nd->child[c], a, X, m, G, theta, eps2, acc);
+  for (int c = 0; c < nd->nchild; ++c) bh_walk(t, nd->child[c], a, ka, X, m, G, theta, eps2, acc);
 }
 
-int32_t orc_gravity_bh(int32_t dim, int64_t n, const double *x, const double *y, const double *z,
-                       const double *m, const double *h, double G, double theta, double eps_grav,
-                       int32_t leaf_size, int32_t max_depth, const int64_t *sample, int64_t nsample,
-                       double *ax, double *ay, double *az) {
+/* Barnes-Hut accelerations at positions (x, y, z) from the tree built at    */
+/* (xb, yb, zb): the pseudo-particles (node mass and centre of mass), node   */
+/* cubes and leaf membership are those of the build; each particle's cell   */
+/* comes from its current position in the build's root cube (clamped, as in */
+/* the build), and leaves are summed over their members' current positions. */
+/* With xb = x this is the plain Barnes-Hut sum.                             */
+static void gravity_bh_at(int32_t dim, int64_t n, const double *xb, const double *yb, const double *zb,
+                          const double *x, const double *y, const double *z, const double *m, const double *h,
+                          double G, double theta, double eps_grav, int32_t leaf_size, int32_t max_depth,
+                          const int64_t *sample, int64_t nsample, double *ax, double *ay, double *az) {
   otree t;
-  tree_build(&t, dim, n, x, y, z, m, leaf_size, max_depth);
+  tree_build(&t, dim, n, xb, yb, zb, m, leaf_size, max_depth);
   const double *X[3] = {x, y, z};
   double *A[3] = {ax, ay, az};
   int64_t cnt = sample ? nsample : n;
@@ -620,11 +626,30 @@ int32_t orc_gravity_bh(int32_t dim, int64_t n, const double *x, const double *y,
   for (int64_t i = 0; i < cnt; ++i) {
     int64_t a = sample ? sample[i] : i;
     double acc[3] = {0, 0, 0};
+    int64_t ka[3] = {0, 0, 0};
+    for (int k = 0; k < dim; ++k) ka[k] = cell_index(&t.rc, k, X[k][a], max_depth);
     double e = eps_grav * h[a];
-    if (n > 0) bh_walk(&t, 0, a, X, m, G, theta, e * e, acc);
+    if (n > 0) bh_walk(&t, 0, a, ka, X, m, G, theta, e * e, acc);
     for (int k = 0; k < dim; ++k) A[k][i] = acc[k];
   }
   tree_free(&t);
+}
+
+int32_t orc_gravity_bh(int32_t dim, int64_t n, const double *x, const double *y, const double *z,
+                       const double *m, const double *h, double G, double theta, double eps_grav,
+                       int32_t leaf_size, int32_t max_depth, const int64_t *sample, int64_t nsample,
+                       double *ax, double *ay, double *az) {
+  gravity_bh_at(dim, n, x, y, z, x, y, z, m, h, G, theta, eps_grav, leaf_size, max_depth, sample, nsample, ax, ay,
+                az);
+  return 0;
+}
+
+int32_t orc_gravity_bh_reuse(int32_t dim, int64_t n, const double *xb, const double *yb, const double *zb,
+                             const double *x, const double *y, const double *z, const double *m, const double *h,
+                             double G, double theta, double eps_grav, int32_t leaf_size, int32_t max_depth,
+                             const int64_t *sample, int64_t nsample, double *ax, double *ay, double *az) {
+  gravity_bh_at(dim, n, xb, yb, zb, x, y, z, m, h, G, theta, eps_grav, leaf_size, max_depth, sample, nsample, ax,
+                ay, az);
   return 0;
 }
 
@@ -865,7 +890,10 @@ static int flaw_count_below(const float *eps, int64_t n, double e) {
 /* Conditioning of a kernel term at the support edge (see oracle.h). */
 static double edge_kappa(double q) { return q >= 0.5 ? q / (1.0 - q) : 1.0; }
 
-static int rhs_instance(orc_state *s, const orc_material *mats, int nmat, const orc_params *P, orc_derivs *d) {
+/* xb (may be NULL): positions at which the gravity tree was built, when its */
+/* pseudo-particles are reused (tree_reuse); NULL builds it at s's positions. */
+static int rhs_instance(orc_state *s, const orc_material *mats, int nmat, const orc_params *P, orc_derivs *d,
+                        const double *const *xb) {
   const int dim = P->dim;
   const int64_t n = s->n;
   if (n == 0) return 0;
@@ -1161,8 +1189,12 @@ static int rhs_instance(orc_state *s, const orc_material *mats, int nmat, const 
   if (P->gravity) {
     double *ag[3];
     for (int ax = 0; ax < 3; ++ax) ag[ax] = (double *)calloc((size_t)n, sizeof(double));
-    orc_gravity_bh(dim, n, s->x, s->y, s->z, s->m, s->h, P->G, P->theta, P->eps_grav, P->leaf_size,
-                   P->max_depth, NULL, 0, ag[0], ag[1], ag[2]);
+    if (xb)
+      orc_gravity_bh_reuse(dim, n, xb[0], xb[1], xb[2], s->x, s->y, s->z, s->m, s->h, P->G, P->theta, P->eps_grav,
+                           P->leaf_size, P->max_depth, NULL, 0, ag[0], ag[1], ag[2]);
+    else
+      orc_gravity_bh(dim, n, s->x, s->y, s->z, s->m, s->h, P->G, P->theta, P->eps_grav, P->leaf_size,
+                     P->max_depth, NULL, 0, ag[0], ag[1], ag[2]);
     double *DV[3] = {d->dvx, d->dvy, d->dvz};
     double *AG[3] = {d->agx, d->agy, d->agz};
     for (int ax = 0; ax < dim; ++ax)
@@ -1239,9 +1271,10 @@ static orc_derivs derivs_view(const orc_derivs *d, int64_t lo) {
 
 /* Component-major tensors cannot be shifted by a pointer offset, so an      */
 /* instance's tensors are copied into and out of contiguous scratch.         */
-int32_t orc_rhs(orc_state *s, const orc_material *mats, int32_t nmat, const orc_params *P, orc_derivs *d) {
+static int32_t rhs_at(orc_state *s, const orc_material *mats, int32_t nmat, const orc_params *P, orc_derivs *d,
+                      const double *const *xb) {
   int32_t ninst = s->ninst > 0 ? s->ninst : 1;
-  if (ninst == 1 || !s->inst_off) return rhs_instance(s, mats, nmat, P, d);
+  if (ninst == 1 || !s->inst_off) return rhs_instance(s, mats, nmat, P, d, xb);
   const int ns = nsym(P->dim);
   const int nd2 = P->dim * P->dim;
   int64_t N = s->n;
@@ -1264,7 +1297,10 @@ int32_t orc_rhs(orc_state *s, const orc_material *mats, int32_t nmat, const orc_
       gv = (double *)calloc((size_t)(nd2 * n), sizeof(double));
       dv.gradv = gv;
     }
-    int rc = rhs_instance(&v, mats, nmat, P, &dv);
+    const double *xbv[3] = {NULL, NULL, NULL};
+    if (xb)
+      for (int k = 0; k < 3; ++k) xbv[k] = xb[k] ? xb[k] + lo : NULL;
+    int rc = rhs_instance(&v, mats, nmat, P, &dv, xb ? xbv : NULL);
     if (dS)
       for (int k = 0; k < ns; ++k) memcpy(d->dS + k * N + lo, dS + k * n, (size_t)n * sizeof(double));
     if (gv)
@@ -1275,6 +1311,10 @@ int32_t orc_rhs(orc_state *s, const orc_material *mats, int32_t nmat, const orc_
     if (rc) return rc;
   }
   return 0;
+}
+
+int32_t orc_rhs(orc_state *s, const orc_material *mats, int32_t nmat, const orc_params *P, orc_derivs *d) {
+  return rhs_at(s, mats, nmat, P, d, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1640,23 +1680,41 @@ int32_t orc_step(orc_state *s, const orc_material *mats, int32_t nmat, const orc
   dstore_alloc(&d1, dim, n);
   int rc = 0;
   int32_t *hcnt = P->n_des > 0.0 ? (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t)) : NULL;
+  /* Decoupled self-gravity (tree_reuse = R > 0, Sect. 5): the tree built at */
+  /* the start of a step serves every evaluation of R consecutive steps; its */
+  /* pseudo-particles are reused (positions of the build kept in xb).  With  */
+  /* variable h every step builds.  A call starts with a build.             */
+  const int reuse = P->gravity && P->tree_reuse > 0;
+  double *xbuf = reuse ? (double *)malloc((size_t)(3 * n + 1) * sizeof(double)) : NULL;
+  const double *xb[3] = {NULL, NULL, NULL};
+  if (reuse) {
+    for (int k = 0; k < dim; ++k) xb[k] = xbuf + k * n;
+  }
+  int32_t age = 0;
   for (int32_t st = 0; st < nsteps && rc == 0; ++st) {
     /* variable smoothing length: iterate from the last step's h (Sect. 4.2) */
     if (hcnt)
       orc_adapt_h(dim, n, s->x, s->y, s->z, s->h, s->inst_off, ninst, P->n_des, P->h_tol, P->h_iter, hcnt);
-    rc = orc_rhs(s, mats, nmat, P, &d0.d);
+    if (reuse && (age == 0 || hcnt)) {
+      const double *X[3] = {s->x, s->y, s->z};
+      for (int k = 0; k < dim; ++k) memcpy(xbuf + k * n, X[k], (size_t)n * sizeof(double));
+      age = 0;
+    }
+    rc = rhs_at(s, mats, nmat, P, &d0.d, reuse ? xb : NULL);
     if (rc) break;
     orc_timestep(s, mats, nmat, P, &d0.d, dt_inst);
     if (dt_log) memcpy(dt_log + (int64_t)st * ninst, dt_inst, (size_t)ninst * sizeof(double));
     pc_update(s, &q, &d0.d, dt_inst, 0.5, mats, nmat, P);
-    rc = orc_rhs(&q, mats, nmat, P, &d1.d);
+    rc = rhs_at(&q, mats, nmat, P, &d1.d, reuse ? xb : NULL);
     if (rc) break;
     pc_update(s, s, &d1.d, dt_inst, 1.0, mats, nmat, P);
+    if (reuse) age = (age + 1) % P->tree_reuse;
   }
   dstore_free(&d0);
   dstore_free(&d1);
   free(buf);
   free(hcnt);
+  free(xbuf);
   return rc;
 }
 

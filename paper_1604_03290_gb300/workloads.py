@@ -93,6 +93,7 @@ class Params:
     n_des: float = 0.0           # > 0: variable h at each step start (Sect. 4.2)
     h_tol: int = 0
     h_iter: int = 8
+    tree_reuse: int = 0          # > 0: one tree serves this many steps (decoupled self-gravity)
     precision: str = "fp64"      # fp64 | mixed
 
 
