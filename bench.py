@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--cpu-side", type=int, default=100, help="cube side of the CPU-baseline sample")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-aux", action="store_true", help="skip timing the flaw and fragment steps")
+    ap.add_argument("--only-aux", action="store_true", help="time only the flaw and fragment steps")
     return ap.parse_args()
 
 
@@ -136,6 +138,50 @@ def algorithmic_bytes(phase, K, n_flaw_mean, dim=3):
 
 
 # ----------------------------------------------------------------------------
+# Steps on either side of the damage path, timed outside the step: the Weibull
+# flaw distribution of the measured configuration (Sect. 3.2) and the
+# friends-of-friends fragments of a 1M-particle fragmented body (Sect. 4).
+# ----------------------------------------------------------------------------
+def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3):
+    import torch
+
+    def timed(fn):
+        fn()  # warm-up
+        ctx.sync_status()
+        ctx.profile(True)
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            out = fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        ph = ctx.profile_read()
+        ctx.profile(False)
+        phases = {k: v[0] / reps for k, v in ph.items() if v[1] > 0}
+        return statistics.median(ts), phases, out
+
+    ds = sph.DeviceState(ps)
+    ms_f, ph_f, (off, eps) = timed(lambda: sph.flaws(ctx, ds, ps.materials, seed=12345))
+    nfl = int(eps.numel())
+    flaws = {"workload": "Weibull flaws of the measured configuration (%d particles, k = %g, m = %g, seed 12345)"
+                         % (ps.n, ps.materials[0].weibull_k, ps.materials[0].weibull_m),
+             "ms": ms_f, "flaws": nfl, "value": nfl / (ms_f * 1e-3), "unit": "flaws/s", "phases_ms": ph_f,
+             # output bytes: thresholds (4 B each) and offsets (8 B per particle)
+             "hbm_frac_output_bytes": (4 * nfl + 8 * ps.n) / (ms_f * 1e-3) / 1e9 / hbm_peak}
+    del ds, off, eps
+    fb = wl.fragmented_body(seed=21)
+    dsf = sph.DeviceState(fb)
+    ms_g, ph_g, (lab, cnt, mass) = timed(lambda: sph.fragments(ctx, dsf, link=1.01, d_remove=1.0, min_size=3))
+    frag = {"workload": "friends-of-friends of the fragmented body (%d particles, 10 damaged slabs, link 1.01 h)"
+                        % fb.n,
+            "ms": ms_g, "fragments": int(cnt.numel()), "value": fb.n / (ms_g * 1e-3), "unit": "particles/s",
+            "phases_ms": ph_g}
+    return {"flaws": flaws, "fragments": frag}
+
+
+# ----------------------------------------------------------------------------
 # CPU oracle as a baseline (the oracle as it stands, all host cores)
 # ----------------------------------------------------------------------------
 def cpu_baseline(n_side, steps=1):
@@ -200,6 +246,16 @@ def main():
     prm = replace(ps.params, precision="mixed")
     ctx = sph.Context(3, n, max_neighbours=128, leaf_size=prm.leaf_size)
     stream = torch.cuda.current_stream()
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm_peak, peak_src = 6800.0, "fallback 6.8 TB/s"
+    if os.path.exists(peaks_path):
+        with open(peaks_path) as f:
+            hbm_peak = float(json.load(f)["hbm_gbs"])
+        peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)"
+    if args.only_aux:
+        if rank == 0:
+            print(json.dumps({"next_rows": aux_rows(sph, wl, ctx, ps, stream, hbm_peak)}), flush=True)
+        return
 
     # mean partner count and flaw count for the byte model (outside timing)
     ds = sph.DeviceState(ps)
@@ -247,12 +303,6 @@ def main():
     # neighbour passes are reported against HBM with their algorithmic bytes
     # (each array once), and against issue the same way.  Launch times are the
     # library's CUDA events on the launching stream over the timed region.
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    hbm_peak, peak_src = 6800.0, "fallback 6.8 TB/s"
-    if os.path.exists(peaks_path):
-        with open(peaks_path) as f:
-            hbm_peak = float(json.load(f)["hbm_gbs"])
-        peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)"
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
     issue_peak = nsm * ISSUE_SLOTS_PER_SM * sm_mhz * 1e6 / 1e9  # G warp-instructions / s
@@ -342,6 +392,8 @@ def main():
     e2e = {"value": world * n * e2e_steps / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
 
+    aux = aux_rows(sph, wl, ctx, ps, stream, hbm_peak) if not args.no_aux else None
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         b = cpu_baseline(args.cpu_side, steps=1)
@@ -358,7 +410,7 @@ def main():
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "fp64": fp64,
                 "speedup_mixed_over_fp64": (value / world / fp64["value"]) if fp64 else None,
-                "phases": phase_report}
+                "phases": phase_report, "next_rows": aux}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

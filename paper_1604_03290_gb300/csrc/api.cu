@@ -187,6 +187,12 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   F.plan_b0 = ctx_alloc<int64_t>(c, F.cap_groups, ok);
   F.plan_pre = ctx_alloc<int64_t>(c, F.cap_groups + 1, ok);
   F.bad = ctx_alloc<int32_t>(c, 1, ok);
+  F.cap_chunks = (int)(N / 4096 + F.cap_groups + 1);  // chunks of 4096 members
+  F.ck_g = ctx_alloc<int32_t>(c, F.cap_chunks, ok);
+  F.ck_lo = ctx_alloc<int32_t>(c, F.cap_chunks, ok);
+  F.ck_hi = ctx_alloc<int32_t>(c, F.cap_chunks, ok);
+  F.ck_sum = ctx_alloc<double>(c, F.cap_chunks, ok);
+  F.g_ck = ctx_alloc<int32_t>(c, F.cap_groups + 1, ok);
   if (ok) ok = cudaMemset(c->d_err, 0, sizeof(int32_t)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();

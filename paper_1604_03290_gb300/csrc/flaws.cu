@@ -18,6 +18,7 @@
 //      thresholds, and sort each particle's (short) list.
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "sph_internal.cuh"
@@ -89,17 +90,20 @@ __global__ void k_flaw_bounds(const unsigned long long *__restrict__ skey, int64
   for (int64_t q = gp + 1; q <= g && q <= G; ++q) goff[q] = (int32_t)p;
 }
 
-// k V and 1/m per group; V = sum over members of m / rho0 (fixed-shape
-// reduction, so the result does not change between runs)
-__global__ void __launch_bounds__(256) k_flaw_volume(const int32_t *__restrict__ goff, const int32_t *__restrict__ perm,
-                                                     const double *__restrict__ m, FlawMats M, double *kv,
-                                                     double *invm) {
-  const int g = blockIdx.x;
-  const int mt = g % M.nmat;
-  const int32_t b = goff[g], e = goff[g + 1];
+// V = sum over the members of m / rho0, in two deterministic steps: chunks
+// of kVolChunk consecutive members (one block each, fixed reduction shape),
+// then the chunks of a group in order.  log2(k V) and 1/m per group.
+constexpr int kVolChunk = 4096;
+
+__global__ void __launch_bounds__(256) k_flaw_vol_chunks(const int32_t *__restrict__ ck_g,
+                                                         const int32_t *__restrict__ ck_lo,
+                                                         const int32_t *__restrict__ ck_hi,
+                                                         const int32_t *__restrict__ perm,
+                                                         const double *__restrict__ m, FlawMats M, double *ck_sum) {
+  const int k = blockIdx.x;
+  const double rho0 = M.rho0[ck_g[k] % M.nmat];
   double s = 0.0;
-  if ((M.brittle >> mt) & 1)
-    for (int32_t p = b + threadIdx.x; p < e; p += blockDim.x) s += m[perm[p]] / M.rho0[mt];
+  for (int32_t p = ck_lo[k] + threadIdx.x; p < ck_hi[k]; p += blockDim.x) s += m[perm[p]] / rho0;
   __shared__ double red[256];
   red[threadIdx.x] = s;
   __syncthreads();
@@ -107,10 +111,18 @@ __global__ void __launch_bounds__(256) k_flaw_volume(const int32_t *__restrict__
     if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    kv[g] = M.k[mt] * red[0];
-    invm[g] = M.m[mt] > 0.0 ? 1.0 / M.m[mt] : 0.0;
-  }
+  if (threadIdx.x == 0) ck_sum[k] = red[0];
+}
+
+__global__ void k_flaw_vol_groups(const int32_t *__restrict__ g_ck, const double *__restrict__ ck_sum, int64_t G,
+                                  FlawMats M, double *lkv, double *invm) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  const int mt = (int)(g % M.nmat);
+  double V = 0.0;
+  for (int32_t k = g_ck[g]; k < g_ck[g + 1]; ++k) V += ck_sum[k];
+  lkv[g] = log2(M.k[mt] * V);
+  invm[g] = M.m[mt] > 0.0 ? 1.0 / M.m[mt] : 0.0;
 }
 
 // One batch of Philox blocks per listed group: entry e covers blocks
@@ -139,7 +151,7 @@ template <int MODE>
 __global__ void k_flaw_draws(DrawPlan P, uint64_t seed, const int32_t *__restrict__ goff,
                              const uint32_t *__restrict__ J, const int32_t *__restrict__ perm,
                              const int32_t *__restrict__ id, uint32_t *first_hit, int32_t *cnt,
-                             const int32_t *__restrict__ start, float *eps, const double *__restrict__ kv,
+                             const int32_t *__restrict__ start, float *eps, const double *__restrict__ lkv,
                              const double *__restrict__ invm) {
   const int64_t total = P.pre[P.nplan];
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
@@ -164,22 +176,32 @@ __global__ void k_flaw_draws(DrawPlan P, uint64_t seed, const int32_t *__restric
           atomicAdd(&cnt[d], 1);
         } else {
           const int32_t slot = start[d] + atomicAdd(&cnt[d], 1);
-          eps[slot] = (float)pow((double)j / kv[g], invm[g]);
+          // (j / (k V))^(1/m) as 2^((log2 j - log2(k V)) / m): within ~1e-15 of
+          // the power in FP64, so the float rounds as the power's does except
+          // at near-ties
+          eps[slot] = (float)exp2(invm[g] * (log2((double)j) - lkv[g]));
         }
       }
     }
   }
 }
 
-// per group: members not yet hit, and the largest first hit
+// per group: members not yet hit, and the largest first hit.  Members of
+// a group are consecutive, so the lanes of a warp mostly share it: they
+// combine first and one lane per group does the atomics.
 __global__ void k_flaw_cover_stats(const unsigned long long *__restrict__ skey, const uint32_t *__restrict__ first_hit,
                                    int32_t nb, int32_t *unc, uint32_t *J) {
   const int32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= nb) return;
-  const int g = (int)(skey[p] >> kIdBits);
-  const uint32_t f = first_hit[p];
-  if (f == kNoHit) atomicAdd(&unc[g], 1);
-  else atomicMax(&J[g], f);
+  const bool valid = p < nb;
+  const int g = valid ? (int)(skey[p] >> kIdBits) : -1;
+  const uint32_t f = valid ? first_hit[p] : 0u;
+  const unsigned peers = __match_any_sync(0xffffffffu, g);
+  const unsigned nun = __reduce_add_sync(peers, (valid && f == kNoHit) ? 1u : 0u);
+  const unsigned mx = __reduce_max_sync(peers, (valid && f != kNoHit) ? f : 0u);
+  if (valid && (threadIdx.x & 31) == __ffs(peers) - 1) {
+    if (nun) atomicAdd(&unc[g], (int32_t)nun);
+    if (mx) atomicMax(&J[g], mx);
+  }
 }
 
 __global__ void k_flaw_offsets(const int32_t *__restrict__ start, int64_t n, int64_t *off) {
@@ -237,7 +259,6 @@ sph_status flaws_generate(sph_ctx *c, const sph_state *s, const sph_material *ma
                                               F.bad); ++g_launches; }
   sort_pairs(c, n, kIdBits + gbits, st);
   { k_flaw_bounds<<<nblk(n + 1, 256), 256, 0, st>>>(T.skey, n, G, F.goff); ++g_launches; }
-  { k_flaw_volume<<<(int)G, 256, 0, st>>>(F.goff, T.perm, s->m, M, F.kv, F.invm); ++g_launches; }
   std::vector<int32_t> goff(G + 1);
   int32_t bad = 0;
   cudaMemcpyAsync(goff.data(), F.goff, sizeof(int32_t) * (G + 1), cudaMemcpyDeviceToHost, st);
@@ -247,6 +268,29 @@ sph_status flaws_generate(sph_ctx *c, const sph_state *s, const sph_material *ma
     snprintf(c->err, sizeof(c->err), "sph_flaws: id outside 0..n-1 or material outside 0..nmat-1");
     return SPH_ERR_INVALID;
   }
+  // group volumes from chunks of members
+  std::vector<int32_t> ck_g, ck_lo, ck_hi, g_ck(G + 1, 0);
+  for (int64_t g = 0; g < G; ++g) {
+    g_ck[g] = (int32_t)ck_g.size();
+    for (int32_t lo = goff[g]; lo < goff[g + 1]; lo += kVolChunk) {
+      ck_g.push_back((int32_t)g);
+      ck_lo.push_back(lo);
+      ck_hi.push_back(std::min(lo + kVolChunk, goff[g + 1]));
+    }
+  }
+  g_ck[G] = (int32_t)ck_g.size();
+  const int nck = (int)ck_g.size();
+  if (nck > F.cap_chunks) {
+    snprintf(c->err, sizeof(c->err), "sph_flaws: too many volume chunks");
+    return SPH_ERR_CAPACITY;
+  }
+  cudaMemcpyAsync(F.ck_g, ck_g.data(), sizeof(int32_t) * nck, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(F.ck_lo, ck_lo.data(), sizeof(int32_t) * nck, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(F.ck_hi, ck_hi.data(), sizeof(int32_t) * nck, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(F.g_ck, g_ck.data(), sizeof(int32_t) * (G + 1), cudaMemcpyHostToDevice, st);
+  if (nck > 0)
+    { k_flaw_vol_chunks<<<nck, 256, 0, st>>>(F.ck_g, F.ck_lo, F.ck_hi, T.perm, s->m, M, F.ck_sum); ++g_launches; }
+  { k_flaw_vol_groups<<<nblk(G, 128), 128, 0, st>>>(F.g_ck, F.ck_sum, G, M, F.kv, F.invm); ++g_launches; }
   const int32_t nb = goff[G];  // brittle particles
   uint32_t *first_hit = reinterpret_cast<uint32_t *>(c->st.gather_i);
   cudaMemsetAsync(first_hit, 0xff, sizeof(uint32_t) * nb, st);
@@ -292,10 +336,12 @@ sph_status flaws_generate(sph_ctx *c, const sph_state *s, const sph_material *ma
     cudaMemcpyAsync(F.plan_b0, pb0.data(), sizeof(int64_t) * np, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(F.plan_pre, ppre.data(), sizeof(int64_t) * (np + 1), cudaMemcpyHostToDevice, st);
     DrawPlan P{F.plan_grp, F.plan_b0, F.plan_pre, np};
+    const int pr = prof_begin(c, st, PH_FLAW_DRAWS);
     { k_flaw_draws<DRAW_COVER><<<draw_blocks(c), 256, 0, st>>>(P, seed, F.goff, nullptr, nullptr, nullptr, first_hit,
                                                                nullptr, nullptr, nullptr, nullptr, nullptr); ++g_launches; }
     cudaMemsetAsync(F.unc, 0, sizeof(int32_t) * G, st);
     { k_flaw_cover_stats<<<nblk(nb, 256), 256, 0, st>>>(T.skey, first_hit, nb, F.unc, F.J); ++g_launches; }
+    prof_end(c, st, pr);
     cudaMemcpyAsync(unc.data(), F.unc, sizeof(int32_t) * G, cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return SPH_ERR_CUDA;
   }
@@ -327,11 +373,13 @@ sph_status flaws_generate(sph_ctx *c, const sph_state *s, const sph_material *ma
   cudaMemcpyAsync(F.plan_pre, ppre.data(), sizeof(int64_t) * (np + 1), cudaMemcpyHostToDevice, st);
   DrawPlan P{F.plan_grp, F.plan_b0, F.plan_pre, np};
   int32_t *cnt = T.ncount, *start = T.nstart;
+  int pr = prof_begin(c, st, PH_FLAW_DRAWS);
   cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), st);
   { k_flaw_draws<DRAW_COUNT><<<draw_blocks(c), 256, 0, st>>>(P, seed, F.goff, F.J, T.perm, s->id, nullptr, cnt,
                                                              nullptr, nullptr, nullptr, nullptr); ++g_launches; }
   scan_counts(c, cnt, start, n + 1, st);
   { k_flaw_offsets<<<nblk(n + 1, 256), 256, 0, st>>>(start, n, flaw_off); ++g_launches; }
+  prof_end(c, st, pr);
   if (!flaw_eps || tot > cap) {
     // the host vectors above must outlive the copies
     if (cudaStreamSynchronize(st) != cudaSuccess) return SPH_ERR_CUDA;
@@ -342,10 +390,12 @@ sph_status flaws_generate(sph_ctx *c, const sph_state *s, const sph_material *ma
     }
     return SPH_OK;
   }
+  pr = prof_begin(c, st, PH_FLAW_FILL);
   cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), st);
   { k_flaw_draws<DRAW_FILL><<<draw_blocks(c), 256, 0, st>>>(P, seed, F.goff, F.J, T.perm, s->id, nullptr, cnt, start,
                                                             flaw_eps, F.kv, F.invm); ++g_launches; }
   { k_flaw_sort<<<nblk(n, 128), 128, 0, st>>>(start, n, flaw_eps); ++g_launches; }
+  prof_end(c, st, pr);
   if (cudaStreamSynchronize(st) != cudaSuccess) return SPH_ERR_CUDA;
   return SPH_OK;
 }

@@ -51,14 +51,21 @@ __global__ void k_fof_union(int32_t *parent, const int32_t *__restrict__ nb_idx,
   if (a >= n || __ldcg(parent + a) < 0) return;
   const int k = nb_cnt[a];
   int steps = 0;
+  // a's representative is kept across its pairs.  It may go stale (hooked
+  // by another thread); a hook on it then fails and it is found again, and
+  // hooking a root under it is still a union with a's set.
+  int32_t ra = fof_rep(parent, (int32_t)a, steps);
   for (int i = 0; i < k; ++i) {
     const int32_t b = nb_idx[(int64_t)i * ld + a];
     if (b <= a || __ldcg(parent + b) < 0) continue;  // each pair once, survivors only
-    int32_t ra = fof_rep(parent, (int32_t)a, steps), rb = fof_rep(parent, b, steps);
+    int32_t rb = fof_rep(parent, b, steps);
     while (ra != rb && steps <= kFindLimit) {
       const int32_t hi = ra > rb ? ra : rb, lo = ra > rb ? rb : ra;
       const int32_t old = atomicCAS(parent + hi, hi, lo);
-      if (old == hi) break;  // hooked
+      if (old == hi) {  // hooked: lo now represents both sets
+        ra = lo;
+        break;
+      }
       // hi was hooked elsewhere meanwhile: continue from its new representative
       ++steps;
       if (hi == ra) ra = fof_rep(parent, old, steps);
@@ -150,8 +157,13 @@ void fragments_fof(sph_ctx *c, const sph_state *s, const double *h0, double b, d
   { k_fof_init<<<nblk(n, 256), 256, 0, st>>>(h0 ? h0 : s->h, s->dmg, n, b, d_remove, hq, parent); ++g_launches; }
   sph_state q = *s;
   q.h = hq;
+  int pr = prof_begin(c, st, PH_TREE);
   tree_build(c, &q, leaf_size, max_depth, st);
+  prof_end(c, st, pr);
+  pr = prof_begin(c, st, PH_PARTNERS);
   find_partners(c, &q, st);
+  prof_end(c, st, pr);
+  pr = prof_begin(c, st, PH_FOF_LINKS);
   { k_fof_union<<<nblk(n, 128), 128, 0, st>>>(parent, c->nb_idx, c->nb_cnt, c->cap_n, n, c->d_err); ++g_launches; }
   cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), st);
   cudaMemsetAsync(mass, 0, sizeof(double) * n, st);
@@ -160,6 +172,7 @@ void fragments_fof(sph_ctx *c, const sph_state *s, const double *h0, double b, d
   scan_counts(c, pos, pos, n + 1, st);
   int32_t nf = 0;
   cudaMemcpyAsync(&nf, pos + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  prof_end(c, st, pr);
   { k_fof_compact<<<nblk(n, 256), 256, 0, st>>>(parent, cnt, pos, n, min_size, c->tree.keys[0], c->tree.vals[0]); ++g_launches; }
   cudaStreamSynchronize(st);
   *nfrag = nf;

@@ -17,7 +17,8 @@ namespace sph {
 extern std::atomic<int64_t> g_launches;
 
 // Phases timed by the optional profiler (CUDA events on the launch stream).
-enum { PH_TREE = 0, PH_REORDER, PH_PARTNERS, PH_DENSITY, PH_PASSA, PH_PASSB, PH_GRAVITY, PH_INTEGRATE, PH_COUNT };
+enum { PH_TREE = 0, PH_REORDER, PH_PARTNERS, PH_DENSITY, PH_PASSA, PH_PASSB, PH_GRAVITY, PH_INTEGRATE,
+       PH_FLAW_DRAWS, PH_FLAW_FILL, PH_FOF_LINKS, PH_COUNT };
 constexpr int kMaxProfEvents = 8192;
 
 // ---------------------------------------------------------------------------
@@ -136,13 +137,17 @@ struct StepBufs {
 struct FlawBufs {
   int64_t cap_groups;
   int32_t *goff;       // cap_groups + 1: first sorted position of each group
-  double *kv, *invm;   // k V and 1/m per group
+  double *kv, *invm;   // log2(k V) and 1/m per group
   uint32_t *J;         // number of flaws per group
   int32_t *unc;        // members not yet hit
   int32_t *plan_grp;   // draw plan of one round
   int64_t *plan_b0, *plan_pre;
   int cap_plan;
   int32_t *bad;        // set when an id or material index is out of range
+  // volume chunks: group, member range, partial sum; first chunk of each group
+  int32_t *ck_g, *ck_lo, *ck_hi, *g_ck;
+  double *ck_sum;
+  int cap_chunks;
 };
 
 }  // namespace sph

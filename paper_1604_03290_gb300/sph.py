@@ -26,7 +26,8 @@ SPH_OK, SPH_ERR_INVALID, SPH_ERR_CAPACITY, SPH_ERR_NONFINITE, SPH_ERR_TIMEOUT, S
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "CAPACITY", 3: "NONFINITE", 4: "TIMEOUT", 5: "CUDA"}
 EOS = {"linear": 0, "murnaghan": 1, "tillotson": 2, "isothermal": 3}
 PRECISION = {"fp64": 0, "mixed": 1}
-PHASES = ("tree", "reorder", "partners", "density", "passA", "passB", "gravity", "integrate")
+PHASES = ("tree", "reorder", "partners", "density", "passA", "passB", "gravity", "integrate", "flaw_draws",
+          "flaw_fill", "fof_links")
 
 
 class SphError(RuntimeError):
