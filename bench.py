@@ -144,6 +144,7 @@ def algorithmic_bytes(phase, K, n_flaw_mean, dim=3):
 # ----------------------------------------------------------------------------
 def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3):
     import torch
+    from dataclasses import replace
 
     def timed(fn):
         fn()  # warm-up
@@ -178,7 +179,35 @@ def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3):
                         % fb.n,
             "ms": ms_g, "fragments": int(cnt.numel()), "value": fb.n / (ms_g * 1e-3), "unit": "particles/s",
             "phases_ms": ph_g}
-    return {"flaws": flaws, "fragments": frag}
+    del dsf, lab, cnt, mass
+
+    # gravity/hydro decoupling (Sect. 5): the 2M-particle collapsing cloud,
+    # steps that build a tree per evaluation against steps that reuse one
+    # tree (and its pseudo-particles) over 4 steps
+    cl = wl.cloud_collapse(seed=3)
+    cctx = sph.Context(3, cl.n, max_neighbours=128, leaf_size=cl.params.leaf_size)
+    dec = {"workload": "rotating cloud collapse, %d particles, Barnes-Hut theta %g, mixed precision" %
+                       (cl.n, cl.params.theta)}
+    for R in (0, 4):
+        prm = replace(cl.params, precision="mixed", tree_reuse=R)
+        dsc = sph.DeviceState(cl)
+        sph.step(cctx, dsc, cl.materials, prm, 1, check=False)
+        cctx.sync_status()
+        cctx.profile(True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sph.step(cctx, dsc, cl.materials, prm, 2 * 4, check=False)  # two windows of 4 steps in one call
+        b.record(stream)
+        b.synchronize()
+        ph = cctx.profile_read()
+        cctx.profile(False)
+        cctx.sync_status()
+        dec["tree_reuse_%d" % R] = {"ms_per_step": a.elapsed_time(b) / 8,
+                                    "phases_ms_per_step": {k: v[0] / 8 for k, v in ph.items() if v[1] > 0}}
+        del dsc
+    dec["speedup"] = dec["tree_reuse_0"]["ms_per_step"] / dec["tree_reuse_4"]["ms_per_step"]
+    del cctx
+    return {"flaws": flaws, "fragments": frag, "decoupled_gravity": dec}
 
 
 # ----------------------------------------------------------------------------

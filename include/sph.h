@@ -90,6 +90,14 @@ typedef struct {
   double n_des;         /* > 0: sph_step adapts h at the start of each step to
                            about n_des partners (sph_adapt_h, Sect. 4.2)      */
   int32_t h_tol, h_iter;  /* its count tolerance and most updates (<= 64)     */
+  int32_t tree_reuse;     /* sph_step: > 0 lets the tree built at a step start
+                             serve every evaluation of this many consecutive
+                             steps (gravity from its pseudo-particles: the
+                             gravity/hydro decoupling of Sect. 5; partners stay
+                             exact); 0: with gravity, a tree per evaluation.
+                             Variable h builds every step; each call starts
+                             with a build.                                  */
+  int32_t pad2;
 } sph_params;
 
 /* Particle state (device pointers).  S and dmg may be NULL.  Flaw thresholds

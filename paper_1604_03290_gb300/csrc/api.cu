@@ -172,6 +172,8 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   S.rk_err = ctx_alloc<unsigned long long>(c, ci, ok);
   S.rk_acc = ctx_alloc<int32_t>(c, ci, ok);
   S.dmove = ctx_alloc<unsigned long long>(c, 1, ok);
+  S.dbuild = ctx_alloc<unsigned long long>(c, 1, ok);
+  S.dgrow = ctx_alloc<unsigned long long>(c, 1, ok);
   S.dt = ctx_alloc<double>(c, ci, ok);
   S.gather = ctx_alloc<double>(c, N, ok);
   S.gather_i = ctx_alloc<int32_t>(c, N, ok);
@@ -271,6 +273,7 @@ static sph_status check_params(sph_ctx *c, const sph_state *s, const sph_materia
   if (p->dim != s->dim) return fail(c, SPH_ERR_INVALID, "params.dim differs from the state's");
   if (p->precision != SPH_FP64 && p->precision != SPH_MIXED) return fail(c, SPH_ERR_INVALID, "bad precision");
   if (p->eps_s > 0.0 && !(p->dmpd > 0.0)) return fail(c, SPH_ERR_INVALID, "artificial stress needs dmpd > 0");
+  if (p->tree_reuse < 0) return fail(c, SPH_ERR_INVALID, "tree_reuse must be >= 0");
   if (p->n_des > 0.0 && (p->h_tol < 0 || p->h_iter < 0 || p->h_iter > kMaxHIter))
     return fail(c, SPH_ERR_INVALID, "variable h needs h_tol >= 0 and 0 <= h_iter <= 64");
   memset(&mt, 0, sizeof(mt));
@@ -324,15 +327,17 @@ static void timed_tree(sph_ctx *c, const sph_state *s, const sph_params &p, cuda
   prof_end(c, st, pr);
 }
 
+// grow: displacement bound since the tree build (NULL: built at s);
+// greuse: gravity from the pseudo-particles of an earlier build
 static void partners_gravity_passes(sph_ctx *c, sph_state *s, const MatTable &mt, const sph_params &p,
                                     const sph_derivs &out, cudaStream_t st,
-                                    const unsigned long long *grow = nullptr) {
+                                    const unsigned long long *grow = nullptr, bool greuse = false) {
   int pr = prof_begin(c, st, PH_PARTNERS);
   find_partners(c, s, st, grow);
   prof_end(c, st, pr);
   if (p.gravity) {
     pr = prof_begin(c, st, PH_GRAVITY);
-    gravity_walk(c, s, p, c->ag, c->ag + c->cap_n, c->ag + 2 * c->cap_n, st);
+    gravity_walk(c, s, p, c->ag, c->ag + c->cap_n, c->ag + 2 * c->cap_n, st, greuse);
     prof_end(c, st, pr);
   }
   rhs_passes(c, s, mt, p, out, st);
@@ -522,39 +527,64 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
     d[j].cs = B.d_cs[j];
     d[j].n_act = B.d_nact[j];
   }
+  // Trees: without gravity the tree only serves the partner search, whose
+  // result is exact for any tree, so the predicted state keeps the slots of s
+  // and reuses its tree, the walk widening its boxes by the displacement
+  // since the build.  Gravity's multipole sums depend on the tree: each
+  // evaluation builds one, unless tree_reuse = R > 0 (the gravity/hydro
+  // decoupling of Sect. 5), when the tree of a step start serves every
+  // evaluation of R consecutive steps with its pseudo-particles (and, for the
+  // partner search, boxes widened by the summed displacement bounds).
+  const int R = p->tree_reuse > 0 ? p->tree_reuse : 0;
+  const bool reuse_pred = !p->gravity || R > 0;
+  int age = 0;
   for (int it = 0; it < nsteps; ++it) {
-    if (p->n_des > 0.0) {  // variable smoothing length from the last step's h (Sect. 4.2)
+    const bool vh = p->n_des > 0.0;
+    if (vh) {  // variable smoothing length from the last step's h (Sect. 4.2)
       int pa = prof_begin(c, st, PH_PARTNERS);
       tree_build(c, s, p->leaf_size, p->max_depth, st);
       adapt_h(c, s, p->n_des, p->h_tol, p->h_iter, c->hflags, st);
       prof_end(c, st, pa);
     }
-    // order the state along the tree once per step (coalesced partner gathers)
-    timed_tree(c, s, *p, st);
-    int pr = prof_begin(c, st, PH_REORDER);
-    tree_reorder_state(c, s, st);
-    prof_end(c, st, pr);
-    partners_gravity_passes(c, s, mt, *p, d[0], st);
-    // Without gravity the tree only serves the partner search, whose result is
-    // exact for any tree: the predicted state keeps the slots of s and reuses
-    // its tree, the walk widening its boxes by the predictor's displacement.
-    // Gravity's multipole sums depend on the tree, so they get a new one.
-    const bool reuse = !p->gravity;
+    const bool build = R == 0 || age == 0 || vh;  // h changes invalidate the node boxes
+    int pr;
+    if (build) {
+      // order the state along the tree once per build (coalesced partner gathers)
+      timed_tree(c, s, *p, st);
+      pr = prof_begin(c, st, PH_REORDER);
+      tree_reorder_state(c, s, st);
+      prof_end(c, st, pr);
+      if (R > 0) cudaMemsetAsync(B.dbuild, 0, sizeof(unsigned long long), st);
+      partners_gravity_passes(c, s, mt, *p, d[0], st);
+    } else {
+      pr = prof_begin(c, st, PH_TREE);
+      pack_f32(c, s, st);
+      prof_end(c, st, pr);
+      partners_gravity_passes(c, s, mt, *p, d[0], st, B.dbuild, p->gravity);
+    }
     pr = prof_begin(c, st, PH_INTEGRATE);
     timestep_reduce(c, s, *p, d[0], st);
-    if (reuse) cudaMemsetAsync(B.dmove, 0, sizeof(unsigned long long), st);
-    pc_update(c, s, &q, d[0], 0.5, mt, *p, st, reuse ? B.dmove : nullptr);
+    if (reuse_pred) cudaMemsetAsync(B.dmove, 0, sizeof(unsigned long long), st);
+    pc_update(c, s, &q, d[0], 0.5, mt, *p, st, reuse_pred ? B.dmove : nullptr);
+    if (reuse_pred && !build) bound_add(B.dgrow, B.dbuild, B.dmove, st);
     prof_end(c, st, pr);
-    if (reuse) {
+    if (reuse_pred) {
       pr = prof_begin(c, st, PH_TREE);
       pack_f32(c, &q, st);
       prof_end(c, st, pr);
-      partners_gravity_passes(c, &q, mt, *p, d[1], st, B.dmove);
+      partners_gravity_passes(c, &q, mt, *p, d[1], st, build ? B.dmove : B.dgrow, p->gravity);
     } else {
       rhs_all(c, &q, mt, *p, d[1], st);
     }
     pr = prof_begin(c, st, PH_INTEGRATE);
-    pc_update(c, s, s, d[1], 1.0, mt, *p, st);
+    if (R > 0) {  // the corrector's displacement joins the bound of the reused tree
+      cudaMemsetAsync(B.dmove, 0, sizeof(unsigned long long), st);
+      pc_update(c, s, s, d[1], 1.0, mt, *p, st, B.dmove);
+      bound_add(B.dbuild, B.dbuild, B.dmove, st);
+      age = (age + 1) % R;
+    } else {
+      pc_update(c, s, s, d[1], 1.0, mt, *p, st);
+    }
     prof_end(c, st, pr);
   }
   if (dt && nsteps > 0) cudaMemcpyAsync(dt, B.dt, sizeof(double) * ninst, cudaMemcpyDeviceToDevice, st);

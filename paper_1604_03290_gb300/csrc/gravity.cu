@@ -13,12 +13,19 @@
 // (the paper's Eq. gravitational_force read as attractive, with Plummer
 // softening).
 //
+// Reused tree (gravity/hydro decoupling, Sect. 5): the pseudo-particles,
+// node cubes and leaf membership are those of the build, the particle's cell
+// is recomputed from its current position in the build's root cube, and
+// leaves are summed at the members' current positions (the packed views are
+// refreshed before the walk).
+//
 // Mixed precision: distances from hi/lo split coordinates in FP32, the
 // acceptance test in FP32 with a relative band of 1e-4 around the threshold
 // inside which the FP64 expression decides, FP32 monopole terms summed with
 // Kahan compensation.
 #include <type_traits>
 
+#include "morton.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -35,6 +42,7 @@ struct GravArgs {
   double *out[3];
   const Units *U;
   int32_t *err;
+  int reuse;  // the tree was built at earlier positions: locate each particle anew
 };
 
 __device__ __forceinline__ double r2_fp64(int dim, const double xa[3], const double c[3]) {
@@ -68,9 +76,13 @@ __global__ void __launch_bounds__(kGrWarps * 32) k_gravity(GravArgs A) {
     const int32_t slot = s0 + lane;
     const bool act = slot < s1;
     const int32_t a = act ? T.perm[slot] : 0;
-    const unsigned long long ka = act ? T.skey[slot] : 0ULL;
     double xa[3] = {0, 0, 0};
     for (int ax = 0; ax < dim; ++ax) xa[ax] = A.x[ax][a];
+    // the cell of the particle's current position (the key of the build
+    // unless the tree is reused); node cubes are those of the build
+    const unsigned long long ka =
+        !act ? 0ULL
+             : (A.reuse ? morton_key(xa, dim, B, inst, T.inst_lo, T.inst_s0[inst], T.inst_rs0[inst]) : T.skey[slot]);
     const float4 Pa = A.pk.px(a), Qa = A.pk.pxl(a);
     const double e = MIXED ? A.eps * (double)Pa.w : A.eps * A.h[a];
     const R eps2 = (R)(e * e);
@@ -175,7 +187,7 @@ __global__ void __launch_bounds__(kGrWarps * 32) k_gravity(GravArgs A) {
 }
 
 void gravity_walk(sph_ctx *c, const sph_state *s, const sph_params &p, double *ax, double *ay, double *az,
-                  cudaStream_t st) {
+                  cudaStream_t st, bool reuse) {
   if (s->n == 0) return;
   GravArgs A;
   memset(&A, 0, sizeof(A));
@@ -193,6 +205,7 @@ void gravity_walk(sph_ctx *c, const sph_state *s, const sph_params &p, double *a
   A.out[2] = az;
   A.U = c->units;
   A.err = c->d_err;
+  A.reuse = reuse ? 1 : 0;
   int blocks = c->num_sms * 8;
   if (p.precision == SPH_MIXED) { k_gravity<true><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
   else { k_gravity<false><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }

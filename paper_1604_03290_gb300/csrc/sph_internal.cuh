@@ -128,6 +128,8 @@ struct StepBufs {
   int32_t *rk_acc;             // per instance, step accepted
   unsigned long long *dt_enc;  // per instance, ordered encoding for atomicMin
   unsigned long long *dmove;   // bits of the predictor's largest per-axis displacement
+  unsigned long long *dbuild;  // bits of a bound on every displacement since the last tree build
+  unsigned long long *dgrow;   // dbuild + dmove
   double *dt;                  // per instance
   double *gather;              // reorder scratch (n doubles)
   int32_t *gather_i;
@@ -312,8 +314,9 @@ void partners_to_csr(sph_ctx *c, const sph_state *s, int64_t *off, int32_t *idx,
 void rhs_passes(sph_ctx *c, sph_state *s, const MatTable &mt, const sph_params &p, const sph_derivs &out,
                 cudaStream_t st);
 // gravity.cu
+// reuse: the tree was built at earlier positions (pseudo-particles reused)
 void gravity_walk(sph_ctx *c, const sph_state *s, const sph_params &p, double *ax, double *ay, double *az,
-                  cudaStream_t st);
+                  cudaStream_t st, bool reuse = false);
 // adjoint.cu
 void rhs_adjoint(sph_ctx *c, const sph_state *s, const MatTable &mt, const sph_params &p, const sph_derivs &dbar,
                  sph_state *sbar, double *param_bar, cudaStream_t st);
@@ -341,6 +344,8 @@ void combine_update(sph_ctx *c, const sph_state *base, sph_state *out, const sph
                     unsigned long long *dmove = nullptr);
 // embedded Runge-Kutta: step size of the attempt (c->st.dt), error and control
 void rk_set_dt(sph_ctx *c, const sph_state *s, double *dt_io, cudaStream_t st);
+// *out = a + b rounded up (bits of non-negative doubles)
+void bound_add(unsigned long long *out, const unsigned long long *a, const unsigned long long *b, cudaStream_t st);
 void rk_error_control(sph_ctx *c, const sph_state *s, const sph_derivs *const *k, const sph_params &p, double eps_des,
                       double *dt_io, double *t_io, double *err_log, int32_t *acc_log, cudaStream_t st);
 

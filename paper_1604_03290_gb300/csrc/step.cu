@@ -620,4 +620,14 @@ void rk_set_dt(sph_ctx *c, const sph_state *s, double *dt_io, cudaStream_t st) {
   { k_rk_dt<<<nblk(ninst, 128), 128, 0, st>>>(dt_io, c->st.dt, ninst); ++sph::g_launches; }
 }
 
+// Displacement bounds of a reused tree: the sum of per-update maxima, rounded
+// up, bounds every particle's displacement since the build.
+__global__ void k_bound_add(unsigned long long *out, const unsigned long long *a, const unsigned long long *b) {
+  *out = dbits(__dadd_ru(bitsd(*a), bitsd(*b)));
+}
+
+void bound_add(unsigned long long *out, const unsigned long long *a, const unsigned long long *b, cudaStream_t st) {
+  { k_bound_add<<<1, 1, 0, st>>>(out, a, b); ++g_launches; }
+}
+
 }  // namespace sph

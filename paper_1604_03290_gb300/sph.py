@@ -54,7 +54,7 @@ class Params(C.Structure):
                 ("c_courant", C.c_double), ("c_accel", C.c_double), ("c_quantity", C.c_double),
                 ("u_floor", C.c_double), ("S_floor", C.c_double), ("dmg_floor", C.c_double),
                 ("dt_max", C.c_double), ("dt_fixed", C.c_double), ("n_des", C.c_double),
-                ("h_tol", C.c_int32), ("h_iter", C.c_int32)]
+                ("h_tol", C.c_int32), ("h_iter", C.c_int32), ("tree_reuse", C.c_int32), ("pad2", C.c_int32)]
 
 
 _vp = C.c_void_p
@@ -160,12 +160,15 @@ def material_struct(m: wl.Material) -> Material:
 
 def params_struct(p: wl.Params, check: bool = True) -> Params:
     s = Params()
-    ints = ("dim", "density_sum", "consistency", "gravity", "leaf_size", "max_depth", "h_tol", "h_iter")
+    ints = ("dim", "density_sum", "consistency", "gravity", "leaf_size", "max_depth", "h_tol", "h_iter",
+            "tree_reuse")
     for k, _ in Params._fields_:
         if k == "precision":
             s.precision = PRECISION[p.precision]
         elif k == "check":
             s.check = int(check)
+        elif k == "pad2":
+            continue
         else:
             v = getattr(p, k)
             setattr(s, k, int(v) if k in ints else float(v))
