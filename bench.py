@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--cpu-side", type=int, default=100, help="cube side of the CPU-baseline sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-aux", action="store_true", help="skip timing the flaw and fragment steps")
-    ap.add_argument("--only-aux", action="store_true", help="time only the flaw and fragment steps")
+    ap.add_argument("--only-aux", action="store_true", help="time only the flaw, fragment and decoupling legs")
+    ap.add_argument("--cloud-n", type=int, default=2_000_000, help="particles of the decoupling leg's cloud")
     return ap.parse_args()
 
 
@@ -142,7 +143,7 @@ def algorithmic_bytes(phase, K, n_flaw_mean, dim=3):
 # flaw distribution of the measured configuration (Sect. 3.2) and the
 # friends-of-friends fragments of a 1M-particle fragmented body (Sect. 4).
 # ----------------------------------------------------------------------------
-def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3):
+def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3, cloud_n=2_000_000):
     import torch
     from dataclasses import replace
 
@@ -184,7 +185,7 @@ def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3):
     # gravity/hydro decoupling (Sect. 5): the 2M-particle collapsing cloud,
     # steps that build a tree per evaluation against steps that reuse one
     # tree (and its pseudo-particles) over 4 steps
-    cl = wl.cloud_collapse(seed=3)
+    cl = wl.cloud_collapse(seed=3, n=cloud_n)
     cctx = sph.Context(3, cl.n, max_neighbours=128, leaf_size=cl.params.leaf_size)
     dec = {"workload": "rotating cloud collapse, %d particles, Barnes-Hut theta %g, mixed precision" %
                        (cl.n, cl.params.theta)}
@@ -283,7 +284,8 @@ def main():
         peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)"
     if args.only_aux:
         if rank == 0:
-            print(json.dumps({"next_rows": aux_rows(sph, wl, ctx, ps, stream, hbm_peak)}), flush=True)
+            print(json.dumps({"next_rows": aux_rows(sph, wl, ctx, ps, stream, hbm_peak, cloud_n=args.cloud_n)}),
+                  flush=True)
         return
 
     # mean partner count and flaw count for the byte model (outside timing)
@@ -421,7 +423,7 @@ def main():
     e2e = {"value": world * n * e2e_steps / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
 
-    aux = aux_rows(sph, wl, ctx, ps, stream, hbm_peak) if not args.no_aux else None
+    aux = aux_rows(sph, wl, ctx, ps, stream, hbm_peak, cloud_n=args.cloud_n) if not args.no_aux else None
 
     cpu = None
     if rank == 0 and not args.no_cpu:

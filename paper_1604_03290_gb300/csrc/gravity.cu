@@ -32,6 +32,58 @@ namespace sph {
 
 constexpr int kGrWarps = 4;
 constexpr float kMacBand = 1e-4f;
+constexpr int kFlushTerms = 16;
+
+// Sum of the FP32 terms of one particle: a plain partial sum, added into a
+// compensated (Kahan) sum every kFlushTerms terms, so that the error stays
+// near that of a compensated sum (the partial sums are short) at a fraction
+// of its cost per term.
+struct GravSumF {
+  float px = 0.f, py = 0.f, pz = 0.f;
+  int n = 0;
+  KahanT<float> kx, ky, kz;
+  __device__ __forceinline__ void flush() {
+    kx.add(px);
+    ky.add(py);
+    kz.add(pz);
+    px = py = pz = 0.f;
+    n = 0;
+  }
+  __device__ __forceinline__ void add(float fx, float fy, float fz) {
+    px += fx;
+    py += fy;
+    pz += fz;
+    if (++n == kFlushTerms) flush();
+  }
+  __device__ __forceinline__ void value(double &x, double &y, double &z) {
+    flush();
+    x = kx.value();
+    y = ky.value();
+    z = kz.value();
+  }
+};
+
+struct GravSumD {
+  double sx = 0.0, sy = 0.0, sz = 0.0;
+  __device__ __forceinline__ void add(double fx, double fy, double fz) {
+    sx += fx;
+    sy += fy;
+    sz += fz;
+  }
+  __device__ __forceinline__ void value(double &x, double &y, double &z) {
+    x = sx;
+    y = sy;
+    z = sz;
+  }
+};
+
+// 1 / q^(3/2): from the reciprocal square root in FP32 (a few ulps, far below
+// the mixed form's tolerance), correctly rounded operations in FP64
+__device__ __forceinline__ float inv_q32(float q) {
+  const float r = rsqrtf(q);
+  return r * r * r;
+}
+__device__ __forceinline__ double inv_q32(double q) { return 1.0 / (q * sqrt(q)); }
 
 struct GravArgs {
   Tree T;
@@ -45,27 +97,29 @@ struct GravArgs {
   int reuse;  // the tree was built at earlier positions: locate each particle anew
 };
 
-__device__ __forceinline__ double r2_fp64(int dim, const double xa[3], const double c[3]) {
-  double dx = __dsub_rn(xa[0], c[0]);
-  double dy = __dsub_rn(xa[1], c[1]);
+template <int DIM>
+__device__ __forceinline__ double r2_fp64(const double xa[3], double cx, double cy, double cz) {
+  double dx = __dsub_rn(xa[0], cx);
+  double dy = __dsub_rn(xa[1], cy);
   double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-  if (dim == 3) {
-    double dz = __dsub_rn(xa[2], c[2]);
+  if (DIM == 3) {
+    double dz = __dsub_rn(xa[2], cz);
     r2 = __dadd_rn(r2, __dmul_rn(dz, dz));
   }
   return r2;
 }
 
-template <bool MIXED>
-__global__ void __launch_bounds__(kGrWarps * 32) k_gravity(GravArgs A) {
+template <bool MIXED, int DIM>
+__global__ void __launch_bounds__(kGrWarps * 32, 8) k_gravity(GravArgs A) {
   using R = typename std::conditional<MIXED, float, double>::type;
-  __shared__ float4 sh_hi[kGrWarps][kMaxLeaf];
+  __shared__ float4 sh_hi[kGrWarps][kMaxLeaf];  // (x_hi, y_hi, z_hi, G m_b) of leaf members
   __shared__ float4 sh_lo[kGrWarps][kMaxLeaf];
   __shared__ int32_t sh_b[kGrWarps][kMaxLeaf];
   const Tree &T = A.T;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ngroups = *T.ngroups;
-  const int L = T.leaf_size, B = T.max_depth, dim = A.dim;
+  constexpr int dim = DIM;
+  const int L = T.leaf_size, B = T.max_depth;
   const int nnodes = *T.nnodes;
   const int64_t cap = T.cap_nodes;
   const double Gs = MIXED ? A.G * A.U->M * A.U->T * A.U->T * A.U->invL * A.U->invL * A.U->invL : A.G;
@@ -89,14 +143,15 @@ __global__ void __launch_bounds__(kGrWarps * 32) k_gravity(GravArgs A) {
     const double s0r = T.inst_s0[inst];
     const double th = A.theta;
     const float th2f = (float)(th * th);
-    KahanT<R> acc[3];
+    typename std::conditional<MIXED, GravSumF, GravSumD>::type acc;
     int32_t skip_until = -1;
     const int32_t root = T.inst_root[inst];
     const int32_t stop = root >= 0 ? T.skip[root] : root;
     int iter = 0;
     for (int32_t nd = root; nd < stop && iter <= nnodes; ++iter) {
-      const int lev = T.level[nd];
-      const int32_t f = T.first[nd], e1 = T.end[nd], sk = T.skip[nd];
+      const int4 rec = T.nrec[nd];  // (first, end, skip, level)
+      const int32_t f = rec.x, e1 = rec.y, sk = rec.z;
+      const int lev = rec.w;
       const bool leaf = (e1 - f <= L) || lev == B;
       bool open = false, direct = false;
       if (act && nd >= skip_until) {
@@ -117,22 +172,23 @@ __global__ void __launch_bounds__(kGrWarps * 32) k_gravity(GravArgs A) {
             if (lhs < rhs * (1.0f - kMacBand)) accept = true;
             else if (lhs > rhs * (1.0f + kMacBand)) accept = false;
             else {
-              double c[3] = {T.com[nd], T.com[cap + nd], dim == 3 ? T.com[2 * cap + nd] : 0.0};
-              accept = ldexp(s0r, -lev) < th * sqrt(r2_fp64(dim, xa, c));
+              accept = ldexp(s0r, -lev) <
+                       th * sqrt(r2_fp64<DIM>(xa, T.com[nd], T.com[cap + nd], DIM == 3 ? T.com[2 * cap + nd] : 0.0));
             }
           } else {
             const double s = ldexp(s0r, -lev);
-            double c[3] = {T.com[nd], T.com[cap + nd], dim == 3 ? T.com[2 * cap + nd] : 0.0};
-            for (int ax = 0; ax < 3; ++ax) d[ax] = ax < dim ? xa[ax] - c[ax] : 0.0;
-            r2 = r2_fp64(dim, xa, c);
+            const double cx = T.com[nd], cy = T.com[cap + nd], cz = DIM == 3 ? T.com[2 * cap + nd] : 0.0;
+            d[0] = xa[0] - cx;
+            d[1] = xa[1] - cy;
+            d[2] = DIM == 3 ? xa[2] - cz : 0.0;
+            r2 = r2_fp64<DIM>(xa, cx, cy, cz);
             accept = s < th * sqrt(r2);
           }
         }
         if (accept) {
           const R mp = MIXED ? (R)mpf : (R)T.mass[nd];
-          const R q = r2 + eps2;
-          const R inv = R(1) / (q * sqrt(q));
-          for (int ax = 0; ax < dim; ++ax) acc[ax].add(-G * mp * d[ax] * inv);
+          const R gq = -G * mp * inv_q32(r2 + eps2);
+          acc.add(gq * d[0], gq * d[1], dim == 3 ? gq * d[2] : R(0));
           skip_until = sk;
         } else if (leaf) {
           direct = true;
@@ -148,8 +204,8 @@ __global__ void __launch_bounds__(kGrWarps * 32) k_gravity(GravArgs A) {
           if (lane < c) {
             const int32_t b = T.perm[base + lane];
             const float4 pb = A.pk.px(b), qb = A.pk.pxl(b);
-            sh_hi[w][lane] = make_float4(pb.x, pb.y, pb.z, (float)0);
-            sh_lo[w][lane] = make_float4(qb.x, qb.y, qb.z, qb.w);  // .w = m as float
+            sh_hi[w][lane] = make_float4(pb.x, pb.y, pb.z, -(float)G * qb.w);  // qb.w = m as float
+            sh_lo[w][lane] = make_float4(qb.x, qb.y, qb.z, qb.w);
             sh_b[w][lane] = b;
           }
           __syncwarp();
@@ -157,22 +213,22 @@ __global__ void __launch_bounds__(kGrWarps * 32) k_gravity(GravArgs A) {
             for (int k = 0; k < c; ++k) {
               const int32_t b = sh_b[w][k];
               if (b == a) continue;
-              R d[3], mb;
+              R d[3], gm;  // gm = -G m_b
               if constexpr (MIXED) {
                 const float4 ph = sh_hi[w][k], pl = sh_lo[w][k];
                 d[0] = (Pa.x - ph.x) + (Qa.x - pl.x);
                 d[1] = (Pa.y - ph.y) + (Qa.y - pl.y);
                 d[2] = (Pa.z - ph.z) + (Qa.z - pl.z);
-                mb = pl.w;
+                gm = ph.w;
               } else {
                 for (int ax = 0; ax < 3; ++ax) d[ax] = ax < dim ? xa[ax] - A.x[ax][b] : 0.0;
-                mb = A.m[b];
+                gm = -G * A.m[b];
               }
               const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
               const R q = r2 + eps2;
               if (!(q > R(0))) continue;
-              const R inv = R(1) / (q * sqrt(q));
-              for (int ax = 0; ax < dim; ++ax) acc[ax].add(-G * mb * d[ax] * inv);
+              const R gq = gm * inv_q32(q);
+              acc.add(gq * d[0], gq * d[1], dim == 3 ? gq * d[2] : R(0));
             }
           }
           __syncwarp();
@@ -181,8 +237,13 @@ __global__ void __launch_bounds__(kGrWarps * 32) k_gravity(GravArgs A) {
       nd = any_open ? nd + 1 : sk;
     }
     if (iter > nnodes) raise_err(A.err, ERR_TIMEOUT);
-    if (act)
-      for (int ax = 0; ax < dim; ++ax) A.out[ax][a] = acc[ax].value() * out_scale;
+    if (act) {
+      double gx, gy, gz;
+      acc.value(gx, gy, gz);
+      A.out[0][a] = gx * out_scale;
+      A.out[1][a] = gy * out_scale;
+      if (DIM == 3) A.out[2][a] = gz * out_scale;
+    }
   }
 }
 
@@ -207,8 +268,14 @@ void gravity_walk(sph_ctx *c, const sph_state *s, const sph_params &p, double *a
   A.err = c->d_err;
   A.reuse = reuse ? 1 : 0;
   int blocks = c->num_sms * 8;
-  if (p.precision == SPH_MIXED) { k_gravity<true><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
-  else { k_gravity<false><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
+  const bool mixed = p.precision == SPH_MIXED;
+  if (s->dim == 3) {
+    if (mixed) { k_gravity<true, 3><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
+    else { k_gravity<false, 3><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
+  } else {
+    if (mixed) { k_gravity<true, 2><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
+    else { k_gravity<false, 2><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
+  }
 }
 
 }  // namespace sph
