@@ -7,6 +7,7 @@ CUDA device is missing, the calls raise; there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import threading
 from dataclasses import dataclass
@@ -394,10 +395,15 @@ def flaws(ctx: Context, ds: DeviceState, materials, weibull_k=None, weibull_m=No
     st = ds.struct()
     seed = int(seed) & (2 ** 64 - 1)
     args = (ctx.h, C.byref(st), mats, nmat, wk.ctypes.data_as(_vp), wm.ctypes.data_as(_vp), seed)
-    ctx.check(ctx._lib.sph_flaws(*args, None, None, 0, C.byref(tot), _stream(stream)), "sph_flaws")
-    eps = torch.empty(max(tot.value, 1), dtype=torch.float32, device=ds.x.device)
-    ctx.check(ctx._lib.sph_flaws(*args, _ptr(off), _ptr(eps), int(tot.value), C.byref(tot), _stream(stream)),
-              "sph_flaws")
+    # a group of N particles takes about N (ln N + 0.58) flaws: size for more,
+    # and repeat with the exact total in the (rare) case it does not fit
+    cap = int(ds.n * (math.log(max(ds.n, 2)) + 8.0)) + 1024
+    eps = torch.empty(cap, dtype=torch.float32, device=ds.x.device)
+    r = ctx._lib.sph_flaws(*args, _ptr(off), _ptr(eps), cap, C.byref(tot), _stream(stream))
+    if r == SPH_ERR_CAPACITY and tot.value > cap:
+        eps = torch.empty(tot.value, dtype=torch.float32, device=ds.x.device)
+        r = ctx._lib.sph_flaws(*args, _ptr(off), _ptr(eps), int(tot.value), C.byref(tot), _stream(stream))
+    ctx.check(r, "sph_flaws")
     return off, eps[: tot.value]
 
 
