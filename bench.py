@@ -144,6 +144,7 @@ def algorithmic_bytes(phase, K, n_flaw_mean, dim=3):
 # friends-of-friends fragments of a 1M-particle fragmented body (Sect. 4).
 # ----------------------------------------------------------------------------
 def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3, cloud_n=2_000_000):
+    import numpy as np
     import torch
     from dataclasses import replace
 
@@ -208,7 +209,74 @@ def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3, cloud_n=2_000_000):
         del dsc
     dec["speedup"] = dec["tree_reuse_0"]["ms_per_step"] / dec["tree_reuse_4"]["ms_per_step"]
     del cctx
-    return {"flaws": flaws, "fragments": frag, "decoupled_gravity": dec}
+
+    # batched instances: the 256 impacts of uneven size in one concatenated
+    # state, 4 steps per launch sequence, replayed from a captured CUDA graph
+    # and launched directly
+    bt = wl.batched_impacts(seed=5)
+    bctx = sph.Context(3, bt.n, max_instances=bt.ninst, max_neighbours=128, leaf_size=bt.params.leaf_size)
+    bprm = replace(bt.params, precision="mixed")
+    dsb = sph.DeviceState(bt)
+    graph = sph.StepGraph(bctx, dsb, bt.materials, bprm, nsteps=4)
+    graph.replay()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gstream = graph.stream
+    a.record(gstream)
+    with torch.cuda.stream(gstream):
+        for _ in range(3):
+            graph.replay()
+    b.record(gstream)
+    b.synchronize()
+    ms_graph = a.elapsed_time(b) / 12
+    bctx.sync_status()
+    del graph
+    dsb = sph.DeviceState(bt)
+    sph.step(bctx, dsb, bt.materials, bprm, 1, check=False)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    sph.step(bctx, dsb, bt.materials, bprm, 12, check=False)
+    b.record(stream)
+    b.synchronize()
+    ms_plain = a.elapsed_time(b) / 12
+    bctx.sync_status()
+    batched = {"workload": "%d independent basalt impacts, %d particles in one state (targets 2k-50k log-uniform)" %
+                           (bt.ninst, bt.n),
+               "ms_per_step_graph": ms_graph, "ms_per_step_launched": ms_plain,
+               "value": bt.n / (ms_graph * 1e-3), "unit": "particle-updates/s"}
+    del dsb, bctx, bt
+
+    # adjoint of the right-hand side (FP64, damage off), 1M measured configuration
+    ad = wl.measurement_1m(seed=21, n_side=100, damage=False)
+    rng = np.random.default_rng(21)
+    ad.u = rng.uniform(0.0, 6e6, ad.n)
+    ad.S = rng.normal(0.0, 0.4 * ad.materials[0].Y0, (6, ad.n))
+    aprm = replace(ad.params, alpha=1.0, beta=2.0, xsph=0.5, precision="fp64")
+    actx = sph.Context(3, ad.n, max_neighbours=128, leaf_size=aprm.leaf_size)
+    dsa = sph.DeviceState(ad)
+    out = sph.rhs(actx, dsa, ad.materials, aprm, check=False)
+    dbar = sph.alloc_derivs(dsa)
+    for k in ("dxdt", "dv", "drho", "du", "dS"):
+        dbar[k].normal_()
+    sbar = dsa.zeros_like()
+    pbar = torch.zeros((1, 1, 3), dtype=torch.float64, device="cuda")
+    sph.rhs_adjoint(actx, dsa, ad.materials, aprm, dbar, sbar, pbar, check=False)
+    a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    a.record(stream)
+    for _ in range(3):
+        sph.rhs(actx, dsa, ad.materials, aprm, out=out, check=False)
+    b.record(stream)
+    for _ in range(3):
+        sph.rhs_adjoint(actx, dsa, ad.materials, aprm, dbar, sbar, pbar, check=False)
+    c.record(stream)
+    c.synchronize()
+    actx.sync_status()
+    adjoint = {"workload": "right-hand side and its adjoint, FP64, %d particles (measured configuration, damage off)" %
+                           ad.n,
+               "ms_rhs_fp64": a.elapsed_time(b) / 3, "ms_adjoint_fp64": b.elapsed_time(c) / 3}
+    adjoint["adjoint_over_rhs"] = adjoint["ms_adjoint_fp64"] / adjoint["ms_rhs_fp64"]
+    del dsa, actx, out, dbar, sbar
+    return {"flaws": flaws, "fragments": frag, "decoupled_gravity": dec, "batched": batched, "adjoint": adjoint}
 
 
 # ----------------------------------------------------------------------------
