@@ -117,7 +117,12 @@ __global__ void __launch_bounds__(kGrWarps * 32, 8) k_gravity(GravArgs A) {
   __shared__ int32_t sh_b[kGrWarps][kMaxLeaf];
   const Tree &T = A.T;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ngroups = *T.ngroups;
+  // Warps take groups of particles; acceptance is per particle, so any
+  // grouping gives the same sums.  One instance: full chunks of 32
+  // consecutive slots (Morton order keeps them close); several: the tree's
+  // groups, which never span instances.
+  const bool chunks = T.ninst <= 1;
+  const int ngroups = chunks ? (int)((T.n + 31) >> 5) : *T.ngroups;
   constexpr int dim = DIM;
   const int L = T.leaf_size, B = T.max_depth;
   const int nnodes = *T.nnodes;
@@ -126,7 +131,9 @@ __global__ void __launch_bounds__(kGrWarps * 32, 8) k_gravity(GravArgs A) {
   const R G = (R)Gs;
   const double out_scale = MIXED ? A.U->acc : 1.0;
   for (int g = blockIdx.x * kGrWarps + w; g < ngroups; g += gridDim.x * kGrWarps) {
-    const int32_t s0 = T.grp_start[g], s1 = T.grp_end[g], inst = T.grp_inst[g];
+    const int32_t s0 = chunks ? g * 32 : T.grp_start[g];
+    const int32_t s1 = chunks ? (int32_t)(((int64_t)s0 + 32 < T.n) ? (int64_t)s0 + 32 : T.n) : T.grp_end[g];
+    const int inst = chunks ? 0 : T.grp_inst[g];
     const int32_t slot = s0 + lane;
     const bool act = slot < s1;
     const int32_t a = act ? T.perm[slot] : 0;
