@@ -282,6 +282,23 @@ def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3, cloud_n=2_000_000):
 # ----------------------------------------------------------------------------
 # CPU oracle as a baseline (the oracle as it stands, all host cores)
 # ----------------------------------------------------------------------------
+def reduce_max_ms(ms, dist, device):
+    """The slowest rank's time: every rank runs its own replica, and the job
+    takes as long as the slowest (max over ranks; NCCL on GPUs, gloo on CPU)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world, units_per_rank, steps, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time."""
+    return world * units_per_rank * steps / (ms * 1e-3)
+
+
 def cpu_baseline(n_side, steps=1):
     import oracle
     from paper_1604_03290_gb300 import workloads as wl
@@ -389,11 +406,8 @@ def main():
     clk = clocks.stop() if rank == 0 else None
     barrier()
     ctx.sync_status()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n * args.steps / (ms * 1e-3)
+    ms = reduce_max_ms(ms, dist, "cuda")
+    value = replica_value(world, n, args.steps, ms)
 
     # ---- rooflines ----
     # The partner walk is bound by instruction issue (latency and ALU work of
@@ -484,11 +498,8 @@ def main():
     g1.record(stream)
     g1.synchronize()
     ms_e2e = g0.elapsed_time(g1)
-    if dist is not None:
-        t = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e = {"value": world * n * e2e_steps / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+    ms_e2e = reduce_max_ms(ms_e2e, dist, "cuda")
+    e2e = {"value": replica_value(world, n, e2e_steps, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
 
     aux = aux_rows(sph, wl, ctx, ps, stream, hbm_peak, cloud_n=args.cloud_n) if not args.no_aux else None
