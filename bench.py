@@ -282,6 +282,39 @@ def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3, cloud_n=2_000_000):
 # ----------------------------------------------------------------------------
 # CPU oracle as a baseline (the oracle as it stands, all host cores)
 # ----------------------------------------------------------------------------
+def host_steps(sph, ctx, ds, host, materials, prm, nsteps, stream):
+    """nsteps predictor-corrector steps of a state that lives in pinned host
+    memory (`host`: the fields of ds as pinned CPU tensors): every step uploads
+    all its inputs and downloads its result (every field, since the step
+    reorders the state along the tree).  The host link carries both
+    directions at once: a field's upload for the next step starts as soon as
+    its download has finished, while the other fields still come down.  The
+    work is enqueued on `stream` (and two copy streams); returns without
+    synchronising."""
+    import torch
+    outs = [k for k in ("x", "v", "rho", "u", "m", "h", "S", "dmg", "mat", "id") if host.get(k) is not None]
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
+    got = {k: torch.cuda.Event() for k in outs}
+    ready, done = torch.cuda.Event(), torch.cuda.Event()
+    up.wait_stream(stream)
+    for it in range(nsteps):
+        with torch.cuda.stream(up):
+            for k in outs:
+                if it > 0:
+                    up.wait_event(got[k])  # this field of the previous result is on the host
+                getattr(ds, k).copy_(host[k], non_blocking=True)
+            ready.record(up)
+        stream.wait_event(ready)
+        sph.step(ctx, ds, materials, prm, 1, check=False)
+        done.record(stream)
+        down.wait_event(done)
+        with torch.cuda.stream(down):
+            for k in outs:
+                host[k].copy_(getattr(ds, k), non_blocking=True)
+                got[k].record(down)
+    stream.wait_stream(down)
+
+
 def reduce_max_ms(ms, dist, device):
     """The slowest rank's time: every rank runs its own replica, and the job
     takes as long as the slowest (max over ranks; NCCL on GPUs, gloo on CPU)."""
@@ -484,17 +517,13 @@ def main():
             {"x": ds.x, "v": ds.v, "rho": ds.rho, "u": ds.u, "m": ds.m, "h": ds.h, "S": ds.S, "dmg": ds.dmg,
              "mat": ds.mat, "id": ds.id}.items()}
     h2d = sum(t.numel() * t.element_size() for t in host.values() if t is not None)
-    d2h = sum(host[k].numel() * host[k].element_size() for k in ("x", "v", "rho", "u", "S", "dmg", "id"))
+    # the step reorders every field along the tree, so the result is all of them
+    d2h = h2d
     e2e_steps = max(3, args.steps // 3)
     barrier()
     g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     g0.record(stream)
-    for _ in range(e2e_steps):
-        for k, t in host.items():
-            getattr(ds, k).copy_(t, non_blocking=True)
-        sph.step(ctx, ds, ps.materials, prm, 1, check=False)
-        for k in ("x", "v", "rho", "u", "S", "dmg", "id"):
-            host[k].copy_(getattr(ds, k), non_blocking=True)
+    host_steps(sph, ctx, ds, host, ps.materials, prm, e2e_steps, stream)
     g1.record(stream)
     g1.synchronize()
     ms_e2e = g0.elapsed_time(g1)
