@@ -31,6 +31,10 @@
 namespace sph {
 
 constexpr int kGrWarps = 4;
+// resident blocks per SM the walk is compiled for (register budget)
+#ifndef SPH_GRAV_MIN_BLOCKS
+#define SPH_GRAV_MIN_BLOCKS 8
+#endif
 constexpr float kMacBand = 1e-4f;
 constexpr int kFlushTerms = 16;
 
@@ -110,7 +114,7 @@ __device__ __forceinline__ double r2_fp64(const double xa[3], double cx, double 
 }
 
 template <bool MIXED, int DIM>
-__global__ void __launch_bounds__(kGrWarps * 32, 8) k_gravity(GravArgs A) {
+__global__ void __launch_bounds__(kGrWarps * 32, SPH_GRAV_MIN_BLOCKS) k_gravity(GravArgs A) {
   using R = typename std::conditional<MIXED, float, double>::type;
   __shared__ float4 sh_hi[kGrWarps][kMaxLeaf];  // (x_hi, y_hi, z_hi, G m_b) of leaf members
   __shared__ float4 sh_lo[kGrWarps][kMaxLeaf];
@@ -129,7 +133,6 @@ __global__ void __launch_bounds__(kGrWarps * 32, 8) k_gravity(GravArgs A) {
   const int64_t cap = T.cap_nodes;
   const double Gs = MIXED ? A.G * A.U->M * A.U->T * A.U->T * A.U->invL * A.U->invL * A.U->invL : A.G;
   const R G = (R)Gs;
-  const double out_scale = MIXED ? A.U->acc : 1.0;
   for (int g = blockIdx.x * kGrWarps + w; g < ngroups; g += gridDim.x * kGrWarps) {
     const int32_t s0 = chunks ? g * 32 : T.grp_start[g];
     const int32_t s1 = chunks ? (int32_t)(((int64_t)s0 + 32 < T.n) ? (int64_t)s0 + 32 : T.n) : T.grp_end[g];
@@ -179,8 +182,10 @@ __global__ void __launch_bounds__(kGrWarps * 32, 8) k_gravity(GravArgs A) {
             if (lhs < rhs * (1.0f - kMacBand)) accept = true;
             else if (lhs > rhs * (1.0f + kMacBand)) accept = false;
             else {
-              accept = ldexp(s0r, -lev) <
-                       th * sqrt(r2_fp64<DIM>(xa, T.com[nd], T.com[cap + nd], DIM == 3 ? T.com[2 * cap + nd] : 0.0));
+              // rare: the FP64 decision, from values reloaded here rather than kept live in the loop
+              const double xr[3] = {A.x[0][a], A.x[1][a], DIM == 3 ? A.x[2][a] : 0.0};
+              accept = ldexp(T.inst_s0[inst], -lev) <
+                       A.theta * sqrt(r2_fp64<DIM>(xr, T.com[nd], T.com[cap + nd], DIM == 3 ? T.com[2 * cap + nd] : 0.0));
             }
           } else {
             const double s = ldexp(s0r, -lev);
@@ -247,9 +252,10 @@ __global__ void __launch_bounds__(kGrWarps * 32, 8) k_gravity(GravArgs A) {
     if (act) {
       double gx, gy, gz;
       acc.value(gx, gy, gz);
-      A.out[0][a] = gx * out_scale;
-      A.out[1][a] = gy * out_scale;
-      if (DIM == 3) A.out[2][a] = gz * out_scale;
+      const double osc = MIXED ? A.U->acc : 1.0;
+      A.out[0][a] = gx * osc;
+      A.out[1][a] = gy * osc;
+      if (DIM == 3) A.out[2][a] = gz * osc;
     }
   }
 }
@@ -274,7 +280,7 @@ void gravity_walk(sph_ctx *c, const sph_state *s, const sph_params &p, double *a
   A.U = c->units;
   A.err = c->d_err;
   A.reuse = reuse ? 1 : 0;
-  int blocks = c->num_sms * 8;
+  int blocks = c->num_sms * SPH_GRAV_MIN_BLOCKS;  // persistent: the resident blocks, looping over groups
   const bool mixed = p.precision == SPH_MIXED;
   if (s->dim == 3) {
     if (mixed) { k_gravity<true, 3><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
