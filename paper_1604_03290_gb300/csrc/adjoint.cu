@@ -71,8 +71,9 @@ __device__ __forceinline__ KernelPair kernel_pair(int dim, double r, double hab)
   k.W = sig * hD * w;
   const double d2W = gnorm * sp * hinv;
   if (r > 0.0) {
-    k.phi = k.dWdr / r;
-    k.dphi_r = (d2W - k.phi) / (r * r);
+    const double ir = 1.0 / r;
+    k.phi = k.dWdr * ir;
+    k.dphi_r = (d2W - k.phi) * ir * ir;
   } else {
     k.phi = -2.0 * gnorm * hinv;  // limit of dW/dr / r at r = 0
     k.dphi_r = 0.0;
@@ -87,15 +88,12 @@ __device__ __forceinline__ KernelPair kernel_pair(int dim, double r, double hab)
 // of d = x_a - x_b, w = v_a - v_b, of B (symmetrised; it goes to T_a and T_b),
 // and half the cotangents of the pair's mean sound speed and density.
 // ---------------------------------------------------------------------------
-__device__ void pairB_adj(int dim, const double d[3], const double w[3], double hab, double rho_a, double rho_b,
-                          double cs_a, double cs_b, const double Ta[6], const double Tb[6], double mb,
-                          const double vb[3], double ub, const sph_params &P, double dbar[3], double wbar[3],
-                          double Bsym[6], double &cs_half, double &rho_half) {
+// K: the kernel factors of the pair (the same for both of its terms), r2 = |d|^2.
+__device__ void pairB_adj(int dim, const double d[3], const double w[3], double r2, const KernelPair &K, double hab,
+                          double rho_a, double rho_b, double cs_a, double cs_b, const double Ta[6],
+                          const double Tb[6], double mb, const double vb[3], double ub, const sph_params &P,
+                          double dbar[3], double wbar[3], double Bsym[6], double &cs_half, double &rho_half) {
   const int ns = nsym(dim);
-  double r2 = 0.0;
-  for (int i = 0; i < dim; ++i) r2 += d[i] * d[i];
-  const double r = sqrt(r2);
-  const KernelPair K = kernel_pair(dim, r, hab);
   double g[3] = {0, 0, 0};
   for (int i = 0; i < dim; ++i) g[i] = K.phi * d[i];
   double vx = 0.0;
@@ -200,9 +198,12 @@ __global__ void k_adj_passB(AdjArgs A) {
     load_T64(A, e, Te);
     const double he = A.h[e], re = A.rho[e], cse = A.cs[e], me = A.m[e];
     const double hab = 0.5 * (hc + he);
+    double r2 = 0.0;
+    for (int i = 0; i < dim; ++i) r2 += d[i] * d[i];
+    const KernelPair K = kernel_pair(dim, sqrt(r2), hab);
     double db[3], wb[3], Bs[6], csh, rh;
     // c's own term with partner e
-    pairB_adj(dim, d, w, hab, rc, re, csc, cse, Tc, Te, me, vbc, ubc, A.prm, db, wb, Bs, csh, rh);
+    pairB_adj(dim, d, w, r2, K, hab, rc, re, csc, cse, Tc, Te, me, vbc, ubc, A.prm, db, wb, Bs, csh, rh);
     for (int i = 0; i < dim; ++i) {
       gx[i] += db[i];
       gv[i] += wb[i];
@@ -212,7 +213,7 @@ __global__ void k_adj_passB(AdjArgs A) {
     rhobar += rh;
     // e's term with partner c, differentiated with respect to c
     double dn[3] = {-d[0], -d[1], -d[2]}, wn[3] = {-w[0], -w[1], -w[2]};
-    pairB_adj(dim, dn, wn, hab, re, rc, cse, csc, Te, Tc, mc, vbe, ube, A.prm, db, wb, Bs, csh, rh);
+    pairB_adj(dim, dn, wn, r2, K, hab, re, rc, cse, csc, Te, Tc, mc, vbe, ube, A.prm, db, wb, Bs, csh, rh);
     for (int i = 0; i < dim; ++i) {
       gx[i] -= db[i];
       gv[i] -= wb[i];
@@ -508,13 +509,10 @@ __global__ void k_adj_update(AdjArgs A) {
 //   sum_rho += vol_b w.g,  L -= vol_b d (x) g,  G -= vol_b w (x) g,
 //   xs -= 2 m_b/(rho_a + rho_b) W w,   vol_b = m_b / rho_b
 // ---------------------------------------------------------------------------
-__device__ void pairA_adj(int dim, const double d[3], const double w[3], double hab, double mb, double rho_a,
-                          double rho_b, const double *I, int64_t ld, int64_t a, double dbar[3], double wbar[3],
-                          double &rho_a_bar, double &rho_b_bar) {
-  double r2 = 0.0;
-  for (int i = 0; i < dim; ++i) r2 += d[i] * d[i];
-  const double r = sqrt(r2);
-  const KernelPair K = kernel_pair(dim, r, hab);
+// K: the kernel factors of the pair, r = |d|.
+__device__ void pairA_adj(int dim, const double d[3], const double w[3], double r, const KernelPair &K, double mb,
+                          double rho_a, double rho_b, const double *I, int64_t ld, int64_t a, double dbar[3],
+                          double wbar[3], double &rho_a_bar, double &rho_b_bar) {
   const double vol = mb / rho_b;
   double g[3] = {0, 0, 0};
   for (int i = 0; i < dim; ++i) g[i] = K.phi * d[i];
@@ -566,7 +564,7 @@ __device__ void pairA_adj(int dim, const double d[3], const double w[3], double 
     rho_a_bar += ccbar * dcc;
     rho_b_bar += ccbar * dcc;
     if (r > 0.0)
-      for (int i = 0; i < dim; ++i) dbar[i] += Wbar * K.dWdr * d[i] / r;
+      for (int i = 0; i < dim; ++i) dbar[i] += Wbar * K.phi * d[i];  // dW/dr d / r
   }
   double gd = 0.0;
   for (int i = 0; i < dim; ++i) gd += gbar[i] * d[i];
@@ -595,15 +593,19 @@ __global__ void k_adj_passA(AdjArgs A) {
     }
     const double he = A.h[e], re = A.rho[e], me = A.m[e];
     const double hab = 0.5 * (hc + he);
+    double r2 = 0.0;
+    for (int i = 0; i < dim; ++i) r2 += d[i] * d[i];
+    const double r = sqrt(r2);
+    const KernelPair K = kernel_pair(dim, r, hab);
     double db[3], wb[3], ra, rb;
-    pairA_adj(dim, d, w, hab, me, rc, re, A.inter, A.ld, c, db, wb, ra, rb);  // c's own term
+    pairA_adj(dim, d, w, r, K, me, rc, re, A.inter, A.ld, c, db, wb, ra, rb);  // c's own term
     for (int i = 0; i < dim; ++i) {
       gx[i] += db[i];
       gv[i] += wb[i];
     }
     grho += ra;
     double dn[3] = {-d[0], -d[1], -d[2]}, wn[3] = {-w[0], -w[1], -w[2]};
-    pairA_adj(dim, dn, wn, hab, mc, re, rc, A.inter, A.ld, e, db, wb, ra, rb);  // e's term, w.r.t. c
+    pairA_adj(dim, dn, wn, r, K, mc, re, rc, A.inter, A.ld, e, db, wb, ra, rb);  // e's term, w.r.t. c
     for (int i = 0; i < dim; ++i) {
       gx[i] -= db[i];
       gv[i] -= wb[i];
