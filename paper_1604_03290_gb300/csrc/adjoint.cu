@@ -88,28 +88,45 @@ __device__ __forceinline__ KernelPair kernel_pair(int dim, double r, double hab)
 // of d = x_a - x_b, w = v_a - v_b, of B (symmetrised; it goes to T_a and T_b),
 // and half the cotangents of the pair's mean sound speed and density.
 // ---------------------------------------------------------------------------
-// K: the kernel factors of the pair (the same for both of its terms), r2 = |d|^2.
-__device__ void pairB_adj(int dim, const double d[3], const double w[3], double r2, const KernelPair &K, double hab,
-                          double rho_a, double rho_b, double cs_a, double cs_b, const double Ta[6],
-                          const double Tb[6], double mb, const double vb[3], double ub, const sph_params &P,
+// Artificial viscosity of a pair and its partial derivatives; symmetric in
+// the two particles (v.r, the mean sound speed and density do not change when
+// they swap), so computed once for both terms of the pair.
+struct ViscPair {
+  double vx, Pi, dPi_dnu, dnu_dvx, dnu_dr2, dPi_dc, dPi_drb;
+};
+
+__device__ __forceinline__ ViscPair visc_pair(int dim, const double d[3], const double w[3], double r2, double hab,
+                                              double rho_a, double rho_b, double cs_a, double cs_b,
+                                              const sph_params &P) {
+  ViscPair V;
+  V.vx = 0.0;
+  for (int i = 0; i < dim; ++i) V.vx += w[i] * d[i];
+  V.Pi = V.dPi_dnu = V.dnu_dvx = V.dnu_dr2 = V.dPi_dc = V.dPi_drb = 0.0;
+  if (V.vx < 0.0) {
+    const double iQ = 1.0 / (r2 + P.eps_v * hab * hab);
+    const double nu = hab * V.vx * iQ;
+    const double cb = 0.5 * (cs_a + cs_b), irb = 1.0 / (0.5 * (rho_a + rho_b));
+    V.Pi = (-P.alpha * cb * nu + P.beta * nu * nu) * irb;
+    V.dPi_dnu = (-P.alpha * cb + 2.0 * P.beta * nu) * irb;
+    V.dnu_dvx = hab * iQ;
+    V.dnu_dr2 = -nu * iQ;
+    V.dPi_dc = -P.alpha * nu * irb;
+    V.dPi_drb = -V.Pi * irb;
+  }
+  return V;
+}
+
+// K: the kernel factors of the pair (the same for both of its terms); Vs: its
+// artificial viscosity (the same for both terms: v.r is unchanged when d and
+// w change sign together).
+__device__ void pairB_adj(int dim, const double d[3], const double w[3], const KernelPair &K, const ViscPair &Vs,
+                          const double Ta[6], const double Tb[6], double mb, const double vb[3], double ub,
                           double dbar[3], double wbar[3], double Bsym[6], double &cs_half, double &rho_half) {
   const int ns = nsym(dim);
   double g[3] = {0, 0, 0};
   for (int i = 0; i < dim; ++i) g[i] = K.phi * d[i];
-  double vx = 0.0;
-  for (int i = 0; i < dim; ++i) vx += w[i] * d[i];
-  double Pi = 0.0, dPi_dnu = 0.0, dnu_dvx = 0.0, dnu_dr2 = 0.0, dPi_dc = 0.0, dPi_drb = 0.0;
-  if (vx < 0.0) {
-    const double Q = r2 + P.eps_v * hab * hab;
-    const double nu = hab * vx / Q;
-    const double cb = 0.5 * (cs_a + cs_b), rb = 0.5 * (rho_a + rho_b);
-    Pi = (-P.alpha * cb * nu + P.beta * nu * nu) / rb;
-    dPi_dnu = (-P.alpha * cb + 2.0 * P.beta * nu) / rb;
-    dnu_dvx = hab / Q;
-    dnu_dr2 = -hab * vx / (Q * Q);
-    dPi_dc = -P.alpha * nu / rb;
-    dPi_drb = -Pi / rb;
-  }
+  const double vx = Vs.vx, Pi = Vs.Pi, dPi_dnu = Vs.dPi_dnu, dnu_dvx = Vs.dnu_dvx, dnu_dr2 = Vs.dnu_dr2,
+               dPi_dc = Vs.dPi_dc, dPi_drb = Vs.dPi_drb;
   double B[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
@@ -201,9 +218,10 @@ __global__ void k_adj_passB(AdjArgs A) {
     double r2 = 0.0;
     for (int i = 0; i < dim; ++i) r2 += d[i] * d[i];
     const KernelPair K = kernel_pair(dim, sqrt(r2), hab);
+    const ViscPair Vs = visc_pair(dim, d, w, r2, hab, rc, re, csc, cse, A.prm);
     double db[3], wb[3], Bs[6], csh, rh;
     // c's own term with partner e
-    pairB_adj(dim, d, w, r2, K, hab, rc, re, csc, cse, Tc, Te, me, vbc, ubc, A.prm, db, wb, Bs, csh, rh);
+    pairB_adj(dim, d, w, K, Vs, Tc, Te, me, vbc, ubc, db, wb, Bs, csh, rh);
     for (int i = 0; i < dim; ++i) {
       gx[i] += db[i];
       gv[i] += wb[i];
@@ -213,7 +231,7 @@ __global__ void k_adj_passB(AdjArgs A) {
     rhobar += rh;
     // e's term with partner c, differentiated with respect to c
     double dn[3] = {-d[0], -d[1], -d[2]}, wn[3] = {-w[0], -w[1], -w[2]};
-    pairB_adj(dim, dn, wn, r2, K, hab, re, rc, cse, csc, Te, Tc, mc, vbe, ube, A.prm, db, wb, Bs, csh, rh);
+    pairB_adj(dim, dn, wn, K, Vs, Te, Tc, mc, vbe, ube, db, wb, Bs, csh, rh);
     for (int i = 0; i < dim; ++i) {
       gx[i] -= db[i];
       gv[i] -= wb[i];
