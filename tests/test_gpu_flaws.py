@@ -1,8 +1,9 @@
 """Weibull flaw distribution (Sect. 3.2) on the GPU against the oracle: the
 CSR offsets bit for bit (they follow from the integer draws alone), the
-thresholds to one float ulp (V is summed in a different order and pow may
-round differently; almost all are bit-equal), on groups of mixed materials
-and instances (sizes 1, 2 and thousands, a non-brittle material, k = 0),
+thresholds to one float ulp (V is summed in a different order and the power
+is formed as 2^((log2 j - log2 kV)/m); almost all are bit-equal), on groups
+of mixed materials
+and instances (sizes 0, 1, 2 and thousands, a non-brittle material, k = 0),
 several seeds, a permuted particle order, the 1M-particle measured
 configuration and the 256 batched impacts; and the damage model fed with
 the GPU's flaws activates as many as with the oracle's."""
@@ -113,3 +114,13 @@ def test_damage_model_with_gpu_flaws(S, orc):
     ds.flaw_off, ds.flaw_eps = S.flaws(ctx, ds, ps.materials, seed=8)
     g = S.rhs(ctx, ds, ps.materials, replace(ps.params, precision="fp64"))
     np.testing.assert_array_equal(g["n_act"].cpu().numpy(), o["n_act"])
+
+
+def test_empty_and_single_particle(S, orc):
+    e = _set([0], lambda i, k: 0)
+    ctx = S.Context(3, 4)
+    off, eps = S.flaws(ctx, S.DeviceState(e), e.materials, seed=3)
+    assert off.cpu().tolist() == [0] and eps.numel() == 0
+    one = _set([1], lambda i, k: 2)
+    off, eps = _compare(S, orc, one, 3)
+    assert off.tolist() == [0, 1]

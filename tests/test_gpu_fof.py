@@ -4,7 +4,9 @@ fixed by count and smallest member), masses to the summation bound
 (n_members x 2^-52 relative: both are sums of positive values in different
 orders); clustered random sets in 2D and 3D with removed particles, lattice
 blocks at the linking length, overlapping instances, min_size 1, an
-explicit h0, everything removed, and the 1M-particle fragmented body."""
+explicit h0, everything removed, empty and one-particle sets, components all
+below min_size, a 2D lattice cut by a damaged line, and the 1M-particle
+fragmented body."""
 import numpy as np
 import pytest
 
@@ -95,3 +97,27 @@ def test_fragmented_body_1m(S, orc):
     assert ps.n == 1_000_000
     _, c, _ = _compare(S, orc, ps)
     assert len(c) > 30
+
+
+def test_empty_single_and_too_small(S, orc):
+    ctx = S.Context(3, 8)
+    e = _ps(np.zeros((3, 0)), np.zeros(0), np.zeros(0))
+    lab, cnt, mass = S.fragments(ctx, S.DeviceState(e))
+    assert lab.numel() == 0 and cnt.numel() == 0
+    one = _ps(np.zeros((3, 1)), np.ones(1), np.full(1, 2.0))
+    _, c, m = _compare(S, orc, one, min_size=1)
+    assert c.tolist() == [1] and m.tolist() == [2.0]
+    _, c, _ = _compare(S, orc, one)
+    assert len(c) == 0
+    # clusters of 5 with min_size 6: nothing qualifies
+    x = np.concatenate([np.random.default_rng(1).uniform(0, 0.5, (3, 5)) + 10.0 * k for k in range(6)], 1)
+    gl, c, _ = _compare(S, orc, _ps(x, np.ones(30), np.ones(30)), min_size=6)
+    assert len(c) == 0 and (gl == -1).all()
+
+
+def test_2d_damaged_lattice(S, orc):
+    g = np.meshgrid(np.arange(60, dtype=float), np.arange(40, dtype=float), indexing="ij")
+    x = np.stack([a.ravel() for a in g]) + np.random.default_rng(3).uniform(-0.05, 0.05, (2, 2400))
+    dmg = np.where(np.abs(x[0] - 1.3 * x[1] - 5.0) < 1.2, 1.0, 0.3)
+    _, c, _ = _compare(S, orc, _ps(x, np.full(2400, 1.2), np.ones(2400), dmg), depth=15)
+    assert len(c) >= 2
