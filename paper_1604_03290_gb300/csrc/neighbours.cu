@@ -22,7 +22,12 @@
 
 namespace sph {
 
-constexpr int kNbWarps = 4;
+// Warps (particle groups) per block; the grid keeps the warp count of 4-warp
+// blocks.  1, 2 and 4 measured within 3 % of each other on GB300.
+#ifndef SPH_WALK_WARPS
+#define SPH_WALK_WARPS 4
+#endif
+constexpr int kNbWarps = SPH_WALK_WARPS;
 // resident blocks per SM the walk is compiled for: 8 (64 registers) was the
 // fastest of 4..12 on GB300, the walk being latency- and issue-bound
 #ifndef SPH_WALK_MIN_BLOCKS
@@ -216,7 +221,7 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
 
 void find_partners(sph_ctx *c, const sph_state *s, cudaStream_t st, const unsigned long long *grow) {
   if (s->n == 0) return;
-  int blocks = c->num_sms * c->tune.walk_blocks_per_sm;
+  int blocks = c->num_sms * c->tune.walk_blocks_per_sm * (4 / kNbWarps);
   { k_partners<false><<<blocks, kNbWarps * 32, 0, st>>>(c->tree, c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim,
                                                      c->kmax, c->nb_idx, c->nb_cnt, c->cap_n, c->d_err, grow,
                                                      c->units, nullptr, nullptr, 0.0, 0); ++sph::g_launches; }
@@ -253,7 +258,7 @@ void adapt_h(sph_ctx *c, sph_state *s, double n_des, int tol, int max_iter, int3
   const int64_t n = s->n;
   cudaMemsetAsync(flags, 0, sizeof(int32_t) * (max_iter + 3), st);
   if (n == 0) return;
-  const int blocks = c->num_sms * c->tune.walk_blocks_per_sm;
+  const int blocks = c->num_sms * c->tune.walk_blocks_per_sm * (4 / kNbWarps);
   for (int i = 0; i <= max_iter; ++i) {
     { k_partners<true><<<blocks, kNbWarps * 32, 0, st>>>(c->tree, c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim,
                                                         c->kmax, c->nb_idx, c->nb_cnt, c->cap_n, c->d_err, nullptr,
