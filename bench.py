@@ -261,20 +261,25 @@ def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3, cloud_n=2_000_000):
     sbar = dsa.zeros_like()
     pbar = torch.zeros((1, 1, 3), dtype=torch.float64, device="cuda")
     sph.rhs_adjoint(actx, dsa, ad.materials, aprm, dbar, sbar, pbar, check=False)
-    a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-    a.record(stream)
-    for _ in range(3):
-        sph.rhs(actx, dsa, ad.materials, aprm, out=out, check=False)
-    b.record(stream)
-    for _ in range(3):
-        sph.rhs_adjoint(actx, dsa, ad.materials, aprm, dbar, sbar, pbar, check=False)
-    c.record(stream)
-    c.synchronize()
-    actx.sync_status()
-    adjoint = {"workload": "right-hand side and its adjoint, FP64, %d particles (measured configuration, damage off)" %
-                           ad.n,
-               "ms_rhs_fp64": a.elapsed_time(b) / 3, "ms_adjoint_fp64": b.elapsed_time(c) / 3}
-    adjoint["adjoint_over_rhs"] = adjoint["ms_adjoint_fp64"] / adjoint["ms_rhs_fp64"]
+    adjoint = {"workload": "right-hand side and its adjoint (damage off), %d particles, measured configuration" %
+                           ad.n}
+    for prec in ("fp64", "mixed"):
+        pp = replace(aprm, precision=prec)
+        sph.rhs_adjoint(actx, dsa, ad.materials, pp, dbar, sbar, pbar, check=False)
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        for _ in range(3):
+            sph.rhs(actx, dsa, ad.materials, pp, out=out, check=False)
+        b.record(stream)
+        for _ in range(3):
+            sph.rhs_adjoint(actx, dsa, ad.materials, pp, dbar, sbar, pbar, check=False)
+        c.record(stream)
+        c.synchronize()
+        actx.sync_status()
+        adjoint["ms_rhs_" + prec] = a.elapsed_time(b) / 3
+        adjoint["ms_adjoint_" + prec] = b.elapsed_time(c) / 3
+    adjoint["adjoint_over_rhs_fp64"] = adjoint["ms_adjoint_fp64"] / adjoint["ms_rhs_fp64"]
+    adjoint["adjoint_speedup_mixed_over_fp64"] = adjoint["ms_adjoint_fp64"] / adjoint["ms_adjoint_mixed"]
     del dsa, actx, out, dbar, sbar
     return {"flaws": flaws, "fragments": frag, "decoupled_gravity": dec, "batched": batched, "adjoint": adjoint}
 

@@ -332,8 +332,8 @@ sph_status sph_fragments(sph_ctx *ctx, const sph_state *state, const double *h0,
                          int32_t *frag_count, double *frag_mass, int64_t frag_capacity, int64_t *nfrag,
                          void *stream);
 
-/* Reverse-mode derivative of sph_rhs at `state` (FP64, any requested
- * precision is evaluated in FP64), with the partner lists and the damage of
+/* Reverse-mode derivative of sph_rhs at `state`, with the partner lists and
+ * the damage of
  * that evaluation held fixed and every branch (artificial viscosity on/off,
  * yield on/off, EOS branch, C = I fallback) at its forward side.  Given the
  * cotangents dbar of the outputs dx/dt, dv/dt, drho/dt, du/dt, dS/dt (device,
@@ -344,7 +344,12 @@ sph_status sph_fragments(sph_ctx *ctx, const sph_state *state, const double *h0,
  * mu, the yield stress Y0 and the bulk modulus K of each material and
  * instance; K scales K0, A_T and B_T together and is measured in units of the
  * largest of them.  Requires continuity density, no artificial stress and no
- * gravity (SPH_ERR_INVALID otherwise).  Builds the tree and partners itself. */
+ * gravity (SPH_ERR_INVALID otherwise).  Builds the tree and partners itself.
+ * Precision: SPH_FP64 evaluates the forward pass and every derivative in
+ * FP64; SPH_MIXED evaluates the forward pass in mixed precision and the pair
+ * terms of the derivative in FP32 (in the power-of-two code units of the
+ * forward pass, on hi/lo position and velocity differences, compensated sums),
+ * the constitutive reverse in FP64 (within ~1e-6 of the FP64 form). */
 sph_status sph_rhs_adjoint(sph_ctx *ctx, sph_state *state, const sph_material *mats, int32_t nmat,
                            const sph_params *params, const sph_derivs *dbar, sph_state *state_bar, double *param_bar,
                            void *stream);

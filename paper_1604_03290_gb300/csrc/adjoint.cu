@@ -40,43 +40,52 @@ struct AdjArgs {
   double *pbar;                       // scratch: 3 * ld (mu, Y0, K per particle)
   MatTable mt;
   sph_params prm;
+  // mixed mode: FP32 views and code units of the forward evaluation
+  PackedF32 pk;
+  const float4 *Tf;                   // forward pass A: (T0..T3), (T4, T5, c_s, 0) in code units
+  float4 *Bpk;                        // output cotangents of dv and du in code units (ld)
+  float4 *Apk;                        // cotangents of the pass-A sums in code units (6 * ld)
+  const Units *U;
 };
 
 __device__ __forceinline__ int sidx(int dim, int i, int j) { return symk(dim, i, j); }
 
 // Kernel radial factors for a pair: phi = dW/dr / r and phi'(r)/r, W, dW/dr.
-struct KernelPair {
-  double phi, dphi_r, W, dWdr;
+template <class R>
+struct KPair {
+  R phi, dphi_r, W, dWdr;
 };
+using KernelPair = KPair<double>;
 
-__device__ __forceinline__ KernelPair kernel_pair(int dim, double r, double hab) {
-  const double sig = kernel_sigma<double>(dim);
-  const double hinv = 1.0 / hab;
-  const double hD = hpow(hinv, dim);
-  const double gnorm = 6.0 * sig * hD * hinv;
-  const double q = r * hinv;
-  double s = 0.0, sp = 0.0, w = 0.0;
-  if (q < 0.5) {
-    s = 3.0 * q * q - 2.0 * q;
-    sp = 6.0 * q - 2.0;
-    w = 6.0 * q * q * q - 6.0 * q * q + 1.0;
-  } else if (q <= 1.0) {
-    const double t = 1.0 - q;
+template <class R>
+__device__ __forceinline__ KPair<R> kernel_pair(int dim, R r, R hab) {
+  const R sig = kernel_sigma<R>(dim);
+  const R hinv = R(1.0) / hab;
+  const R hD = hpow(hinv, dim);
+  const R gnorm = R(6.0) * sig * hD * hinv;
+  const R q = r * hinv;
+  R s = R(0.0), sp = R(0.0), w = R(0.0);
+  if (q < R(0.5)) {
+    s = R(3.0) * q * q - R(2.0) * q;
+    sp = R(6.0) * q - R(2.0);
+    w = R(6.0) * q * q * q - R(6.0) * q * q + R(1.0);
+  } else if (q <= R(1.0)) {
+    const R t = R(1.0) - q;
     s = -t * t;
-    sp = 2.0 * t;
-    w = 2.0 * t * t * t;
+    sp = R(2.0) * t;
+    w = R(2.0) * t * t * t;
   }
-  KernelPair k;
+  KPair<R> k;
   k.dWdr = gnorm * s;
   k.W = sig * hD * w;
-  const double d2W = gnorm * sp * hinv;
-  if (r > 0.0) {
-    const double ir = 1.0 / r;
+  const R d2W = gnorm * sp * hinv;
+  if (r > R(0.0)) {
+    const R ir = R(1.0) / r;
     k.phi = k.dWdr * ir;
     k.dphi_r = (d2W - k.phi) * ir * ir;
   } else {
-    k.phi = -2.0 * gnorm * hinv;  // limit of dW/dr / r at r = 0
-    k.dphi_r = 0.0;
+    k.phi = -R(2.0) * gnorm * hinv;  // limit of dW/dr / r at r = 0
+    k.dphi_r = R(0.0);
   }
   return k;
 }
@@ -91,26 +100,29 @@ __device__ __forceinline__ KernelPair kernel_pair(int dim, double r, double hab)
 // Artificial viscosity of a pair and its partial derivatives; symmetric in
 // the two particles (v.r, the mean sound speed and density do not change when
 // they swap), so computed once for both terms of the pair.
-struct ViscPair {
-  double vx, Pi, dPi_dnu, dnu_dvx, dnu_dr2, dPi_dc, dPi_drb;
+template <class R>
+struct VPair {
+  R vx, Pi, dPi_dnu, dnu_dvx, dnu_dr2, dPi_dc, dPi_drb;
 };
+using ViscPair = VPair<double>;
 
-__device__ __forceinline__ ViscPair visc_pair(int dim, const double d[3], const double w[3], double r2, double hab,
-                                              double rho_a, double rho_b, double cs_a, double cs_b,
+template <class R>
+__device__ __forceinline__ VPair<R> visc_pair(int dim, const R d[3], const R w[3], R r2, R hab,
+                                              R rho_a, R rho_b, R cs_a, R cs_b,
                                               const sph_params &P) {
-  ViscPair V;
-  V.vx = 0.0;
+  VPair<R> V;
+  V.vx = R(0.0);
   for (int i = 0; i < dim; ++i) V.vx += w[i] * d[i];
-  V.Pi = V.dPi_dnu = V.dnu_dvx = V.dnu_dr2 = V.dPi_dc = V.dPi_drb = 0.0;
-  if (V.vx < 0.0) {
-    const double iQ = 1.0 / (r2 + P.eps_v * hab * hab);
-    const double nu = hab * V.vx * iQ;
-    const double cb = 0.5 * (cs_a + cs_b), irb = 1.0 / (0.5 * (rho_a + rho_b));
-    V.Pi = (-P.alpha * cb * nu + P.beta * nu * nu) * irb;
-    V.dPi_dnu = (-P.alpha * cb + 2.0 * P.beta * nu) * irb;
+  V.Pi = V.dPi_dnu = V.dnu_dvx = V.dnu_dr2 = V.dPi_dc = V.dPi_drb = R(0.0);
+  if (V.vx < R(0.0)) {
+    const R iQ = R(1.0) / (r2 + R(P.eps_v) * hab * hab);
+    const R nu = hab * V.vx * iQ;
+    const R cb = R(0.5) * (cs_a + cs_b), irb = R(1.0) / (R(0.5) * (rho_a + rho_b));
+    V.Pi = (-R(P.alpha) * cb * nu + R(P.beta) * nu * nu) * irb;
+    V.dPi_dnu = (-R(P.alpha) * cb + R(2.0) * R(P.beta) * nu) * irb;
     V.dnu_dvx = hab * iQ;
     V.dnu_dr2 = -nu * iQ;
-    V.dPi_dc = -P.alpha * nu * irb;
+    V.dPi_dc = -R(P.alpha) * nu * irb;
     V.dPi_drb = -V.Pi * irb;
   }
   return V;
@@ -119,25 +131,26 @@ __device__ __forceinline__ ViscPair visc_pair(int dim, const double d[3], const 
 // K: the kernel factors of the pair (the same for both of its terms); Vs: its
 // artificial viscosity (the same for both terms: v.r is unchanged when d and
 // w change sign together).
-__device__ void pairB_adj(int dim, const double d[3], const double w[3], const KernelPair &K, const ViscPair &Vs,
-                          const double Ta[6], const double Tb[6], double mb, const double vb[3], double ub,
-                          double dbar[3], double wbar[3], double Bsym[6], double &cs_half, double &rho_half) {
+template <class R>
+__device__ void pairB_adj(int dim, const R d[3], const R w[3], const KPair<R> &K, const VPair<R> &Vs,
+                          const R Ta[6], const R Tb[6], R mb, const R vb[3], R ub,
+                          R dbar[3], R wbar[3], R Bsym[6], R &cs_half, R &rho_half) {
   const int ns = nsym(dim);
-  double g[3] = {0, 0, 0};
+  R g[3] = {0, 0, 0};
   for (int i = 0; i < dim; ++i) g[i] = K.phi * d[i];
-  const double vx = Vs.vx, Pi = Vs.Pi, dPi_dnu = Vs.dPi_dnu, dnu_dvx = Vs.dnu_dvx, dnu_dr2 = Vs.dnu_dr2,
+  const R vx = Vs.vx, Pi = Vs.Pi, dPi_dnu = Vs.dPi_dnu, dnu_dvx = Vs.dnu_dvx, dnu_dr2 = Vs.dnu_dr2,
                dPi_dc = Vs.dPi_dc, dPi_drb = Vs.dPi_drb;
-  double B[3][3];
+  R B[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
       if (i < dim && j < dim) {
         const int k = sidx(dim, i, j);
-        B[i][j] = Ta[k] + Tb[k] - (i == j ? Pi : 0.0);
+        B[i][j] = Ta[k] + Tb[k] - (i == j ? Pi : R(0.0));
       } else {
-        B[i][j] = 0.0;
+        B[i][j] = R(0.0);
       }
     }
-  double Bg[3] = {0, 0, 0}, Bw[3] = {0, 0, 0}, Bv[3] = {0, 0, 0};
+  R Bg[3] = {0, 0, 0}, Bw[3] = {0, 0, 0}, Bv[3] = {0, 0, 0};
   for (int i = 0; i < dim; ++i)
     for (int j = 0; j < dim; ++j) {
       Bg[i] += B[i][j] * g[j];
@@ -145,37 +158,37 @@ __device__ void pairB_adj(int dim, const double d[3], const double w[3], const K
       Bv[i] += B[i][j] * vb[j];
     }
   // cotangents of B (general matrix), g and w
-  double Bbar[3][3];
-  double trB = 0.0;
+  R Bbar[3][3];
+  R trB = R(0.0);
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      Bbar[i][j] = (i < dim && j < dim) ? mb * vb[i] * g[j] - 0.5 * mb * ub * w[i] * g[j] : 0.0;
+      Bbar[i][j] = (i < dim && j < dim) ? mb * vb[i] * g[j] - R(0.5) * mb * ub * w[i] * g[j] : R(0.0);
       if (i == j) trB += Bbar[i][j];
     }
-  double gbar[3] = {0, 0, 0};
+  R gbar[3] = {0, 0, 0};
   for (int i = 0; i < 3; ++i) {
-    gbar[i] = mb * Bv[i] - 0.5 * mb * ub * Bw[i];
-    wbar[i] = -0.5 * mb * ub * Bg[i];
-    dbar[i] = 0.0;
+    gbar[i] = mb * Bv[i] - R(0.5) * mb * ub * Bw[i];
+    wbar[i] = -R(0.5) * mb * ub * Bg[i];
+    dbar[i] = R(0.0);
   }
   for (int i = 0; i < dim; ++i)
-    for (int j = i; j < dim; ++j) Bsym[sidx(dim, i, j)] = 0.5 * (Bbar[i][j] + Bbar[j][i]);
-  for (int k = ns; k < 6; ++k) Bsym[k] = 0.0;
-  cs_half = 0.0;
-  rho_half = 0.0;
-  if (vx < 0.0) {
-    const double Pibar = -trB;
-    const double nubar = Pibar * dPi_dnu;
-    const double vxbar = nubar * dnu_dvx;
-    const double r2bar = nubar * dnu_dr2;
-    cs_half = 0.5 * Pibar * dPi_dc;
-    rho_half = 0.5 * Pibar * dPi_drb;
+    for (int j = i; j < dim; ++j) Bsym[sidx(dim, i, j)] = R(0.5) * (Bbar[i][j] + Bbar[j][i]);
+  for (int k = ns; k < 6; ++k) Bsym[k] = R(0.0);
+  cs_half = R(0.0);
+  rho_half = R(0.0);
+  if (vx < R(0.0)) {
+    const R Pibar = -trB;
+    const R nubar = Pibar * dPi_dnu;
+    const R vxbar = nubar * dnu_dvx;
+    const R r2bar = nubar * dnu_dr2;
+    cs_half = R(0.5) * Pibar * dPi_dc;
+    rho_half = R(0.5) * Pibar * dPi_drb;
     for (int i = 0; i < dim; ++i) {
       wbar[i] += vxbar * d[i];
-      dbar[i] += vxbar * w[i] + 2.0 * r2bar * d[i];
+      dbar[i] += vxbar * w[i] + R(2.0) * r2bar * d[i];
     }
   }
-  double gd = 0.0;
+  R gd = R(0.0);
   for (int i = 0; i < dim; ++i) gd += gbar[i] * d[i];
   for (int i = 0; i < dim; ++i) dbar[i] += K.phi * gbar[i] + K.dphi_r * gd * d[i];
 }
@@ -527,41 +540,53 @@ __global__ void k_adj_update(AdjArgs A) {
 //   sum_rho += vol_b w.g,  L -= vol_b d (x) g,  G -= vol_b w (x) g,
 //   xs -= 2 m_b/(rho_a + rho_b) W w,   vol_b = m_b / rho_b
 // ---------------------------------------------------------------------------
-// K: the kernel factors of the pair, r = |d|.
-__device__ void pairA_adj(int dim, const double d[3], const double w[3], double r, const KernelPair &K, double mb,
-                          double rho_a, double rho_b, const double *I, int64_t ld, int64_t a, double dbar[3],
-                          double wbar[3], double &rho_a_bar, double &rho_b_bar) {
-  const double vol = mb / rho_b;
-  double g[3] = {0, 0, 0};
-  for (int i = 0; i < dim; ++i) g[i] = K.phi * d[i];
-  const double sr = I[a];
-  double Lb[3][3], Gb[3][3], xb[3];
+// Cotangents of the pass-A sums of one particle: continuity sum, L, G, XSPH.
+template <class R>
+struct ACot {
+  R sr, Lb[3][3], Gb[3][3], xb[3];
+};
+
+__device__ __forceinline__ ACot<double> load_acot64(const double *I, int64_t ld, int64_t a) {
+  ACot<double> c;
+  c.sr = I[a];
   for (int i = 0; i < 3; ++i) {
     for (int j = 0; j < 3; ++j) {
-      Lb[i][j] = I[(1 + 3 * i + j) * ld + a];
-      Gb[i][j] = I[(10 + 3 * i + j) * ld + a];
+      c.Lb[i][j] = I[(1 + 3 * i + j) * ld + a];
+      c.Gb[i][j] = I[(10 + 3 * i + j) * ld + a];
     }
-    xb[i] = I[(19 + i) * ld + a];
+    c.xb[i] = I[(19 + i) * ld + a];
   }
-  double gbar[3] = {0, 0, 0}, wg = 0.0;
+  return c;
+}
+
+// K: the kernel factors of the pair, r = |d|; Ct: the cotangents of the sums
+// of the particle whose term this is.
+template <class R>
+__device__ void pairA_adj(int dim, const R d[3], const R w[3], R r, const KPair<R> &K, R mb, R rho_a, R rho_b,
+                          const ACot<R> &Ct, R dbar[3], R wbar[3], R &rho_a_bar, R &rho_b_bar) {
+  const R vol = mb / rho_b;
+  R g[3] = {0, 0, 0};
+  for (int i = 0; i < dim; ++i) g[i] = K.phi * d[i];
+  const R sr = Ct.sr;
+  R gbar[3] = {0, 0, 0}, wg = R(0);
   for (int i = 0; i < 3; ++i) {
-    dbar[i] = 0.0;
-    wbar[i] = 0.0;
+    dbar[i] = R(0);
+    wbar[i] = R(0);
   }
   for (int i = 0; i < dim; ++i) wg += w[i] * g[i];
-  double volbar = sr * wg;
+  R volbar = sr * wg;
   for (int i = 0; i < dim; ++i) {
     gbar[i] += sr * vol * w[i];
     wbar[i] += sr * vol * g[i];
   }
   // L and G
   for (int i = 0; i < dim; ++i) {
-    double Lg = 0.0, Gg = 0.0, LTd = 0.0, GTw = 0.0;
+    R Lg = R(0), Gg = R(0), LTd = R(0), GTw = R(0);
     for (int j = 0; j < dim; ++j) {
-      Lg += Lb[i][j] * g[j];
-      Gg += Gb[i][j] * g[j];
-      LTd += Lb[j][i] * d[j];
-      GTw += Gb[j][i] * w[j];
+      Lg += Ct.Lb[i][j] * g[j];
+      Gg += Ct.Gb[i][j] * g[j];
+      LTd += Ct.Lb[j][i] * d[j];
+      GTw += Ct.Gb[j][i] * w[j];
     }
     dbar[i] += -vol * Lg;
     wbar[i] += -vol * Gg;
@@ -569,22 +594,22 @@ __device__ void pairA_adj(int dim, const double d[3], const double w[3], double 
     volbar += -d[i] * Lg - w[i] * Gg;
   }
   // XSPH
-  rho_a_bar = 0.0;
-  rho_b_bar = 0.0;
-  double wx = 0.0;
-  for (int i = 0; i < dim; ++i) wx += w[i] * xb[i];
-  if (wx != 0.0) {
-    const double cc = 2.0 * mb / (rho_a + rho_b);
-    for (int i = 0; i < dim; ++i) wbar[i] += -cc * K.W * xb[i];
-    const double Wbar = -cc * wx;
-    const double ccbar = -K.W * wx;
-    const double dcc = -cc / (rho_a + rho_b);
+  rho_a_bar = R(0);
+  rho_b_bar = R(0);
+  R wx = R(0);
+  for (int i = 0; i < dim; ++i) wx += w[i] * Ct.xb[i];
+  if (wx != R(0)) {
+    const R cc = R(2) * mb / (rho_a + rho_b);
+    for (int i = 0; i < dim; ++i) wbar[i] += -cc * K.W * Ct.xb[i];
+    const R Wbar = -cc * wx;
+    const R ccbar = -K.W * wx;
+    const R dcc = -cc / (rho_a + rho_b);
     rho_a_bar += ccbar * dcc;
     rho_b_bar += ccbar * dcc;
-    if (r > 0.0)
+    if (r > R(0))
       for (int i = 0; i < dim; ++i) dbar[i] += Wbar * K.phi * d[i];  // dW/dr d / r
   }
-  double gd = 0.0;
+  R gd = R(0);
   for (int i = 0; i < dim; ++i) gd += gbar[i] * d[i];
   for (int i = 0; i < dim; ++i) dbar[i] += K.phi * gbar[i] + K.dphi_r * gd * d[i];
   rho_b_bar += -volbar * vol / rho_b;
@@ -600,6 +625,7 @@ __global__ void k_adj_passA(AdjArgs A) {
     vc[i] = A.v[i][c];
   }
   const double hc = A.h[c], rc = A.rho[c], mc = A.m[c];
+  const ACot<double> Cc = load_acot64(A.inter, A.ld, c);
   double gx[3] = {0, 0, 0}, gv[3] = {0, 0, 0}, grho = 0.0;
   const int cnt = A.nb_cnt[c];
   for (int k = 0; k < cnt; ++k) {
@@ -616,14 +642,15 @@ __global__ void k_adj_passA(AdjArgs A) {
     const double r = sqrt(r2);
     const KernelPair K = kernel_pair(dim, r, hab);
     double db[3], wb[3], ra, rb;
-    pairA_adj(dim, d, w, r, K, me, rc, re, A.inter, A.ld, c, db, wb, ra, rb);  // c's own term
+    pairA_adj(dim, d, w, r, K, me, rc, re, Cc, db, wb, ra, rb);  // c's own term
     for (int i = 0; i < dim; ++i) {
       gx[i] += db[i];
       gv[i] += wb[i];
     }
     grho += ra;
     double dn[3] = {-d[0], -d[1], -d[2]}, wn[3] = {-w[0], -w[1], -w[2]};
-    pairA_adj(dim, dn, wn, r, K, mc, re, rc, A.inter, A.ld, e, db, wb, ra, rb);  // e's term, w.r.t. c
+    const ACot<double> Ce = load_acot64(A.inter, A.ld, e);
+    pairA_adj(dim, dn, wn, r, K, mc, re, rc, Ce, db, wb, ra, rb);  // e's term, w.r.t. c
     for (int i = 0; i < dim; ++i) {
       gx[i] -= db[i];
       gv[i] -= wb[i];
@@ -664,6 +691,190 @@ __global__ void k_adj_params(const double *__restrict__ pbar, int64_t ld, const 
       for (int k = 0; k < 3; ++k) out[((int64_t)inst * nmat + mm) * 3 + k] += sh[0][k];
     __syncthreads();
   }
+}
+
+// ---------------------------------------------------------------------------
+// Mixed precision (requested precision SPH_MIXED): the pair terms of passes B
+// and A are differentiated in FP32, in the code units of the forward
+// evaluation (powers of two, so every conversion is exact), on differences of
+// the hi/lo-split positions and velocities as in the forward pass, with
+// Kahan-compensated FP32 sums; the constitutive update (k_adj_update) stays
+// FP64.  A quantity q in SI is q_code * U_q, so its cotangent in SI is the
+// code-unit cotangent divided by U_q, and a given output cotangent enters in
+// code units multiplied by U_q.
+// ---------------------------------------------------------------------------
+// Forward T and c_s back to FP64 SI for k_adj_update; output cotangents of
+// dv/dt and du/dt into code units for pass B.
+__global__ void k_adj_unpack32(AdjArgs A, double *T64, double *cs64) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= A.n) return;
+  const Units &U = *A.U;
+  const double uT = U.sig * U.invrho * U.invrho;  // T = sigma / rho^2
+  const float4 t0 = A.Tf[c], t1 = A.Tf[A.ld + c];
+  const float t[6] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y};
+  const int ns = nsym(A.dim);
+  for (int k = 0; k < 6; ++k) T64[(int64_t)k * A.ld + c] = k < ns ? (double)t[k] * uT : 0.0;
+  cs64[c] = (double)t1.z * U.V;
+  float vb[3] = {0.f, 0.f, 0.f};
+  for (int i = 0; i < A.dim; ++i)
+    if (A.bdv[i]) vb[i] = (float)(A.bdv[i][c] * U.acc);
+  const float ub = A.bdu ? (float)(A.bdu[c] * (U.E * U.invT)) : 0.f;
+  A.Bpk[c] = make_float4(vb[0], vb[1], vb[2], ub);
+}
+
+__device__ __forceinline__ void load_T32(const AdjArgs &A, int64_t b, float t[6], float &cs) {
+  const float4 t0 = A.Tf[b], t1 = A.Tf[A.ld + b];
+  t[0] = t0.x;
+  t[1] = t0.y;
+  t[2] = t0.z;
+  t[3] = t0.w;
+  t[4] = t1.x;
+  t[5] = t1.y;
+  cs = t1.z;
+}
+
+template <int DIM>
+__global__ void k_adj_passB32(AdjArgs A) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= A.n) return;
+  constexpr int dim = DIM;
+  const int ns = nsym(dim);
+  const float4 Pc = A.pk.px(c), Qc = A.pk.pxl(c), Vc = A.pk.pv(c), Wc = A.pk.pvl(c);
+  float Tc[6], csc;
+  load_T32(A, c, Tc, csc);
+  const float4 bc = A.Bpk[c];
+  const float vbc[3] = {bc.x, bc.y, bc.z};
+  KahanT<float> gx[3], gv[3], Tb[6], csb, rhb;
+  const int cnt = A.nb_cnt[c];
+  for (int k = 0; k < cnt; ++k) {
+    const int32_t e = A.nb_idx[(int64_t)k * A.ld + c];
+    const float4 Pe = A.pk.px(e), Qe = A.pk.pxl(e), Ve = A.pk.pv(e), We = A.pk.pvl(e);
+    float d[3] = {(Pc.x - Pe.x) + (Qc.x - Qe.x), (Pc.y - Pe.y) + (Qc.y - Qe.y),
+                  DIM == 3 ? (Pc.z - Pe.z) + (Qc.z - Qe.z) : 0.f};
+    float w[3] = {(Vc.x - Ve.x) + (Wc.x - We.x), (Vc.y - Ve.y) + (Wc.y - We.y),
+                  DIM == 3 ? (Vc.z - Ve.z) + (Wc.z - We.z) : 0.f};
+    float Te[6], cse;
+    load_T32(A, e, Te, cse);
+    const float4 be = A.Bpk[e];
+    const float vbe[3] = {be.x, be.y, be.z};
+    const float hab = 0.5f * (Pc.w + Pe.w);
+    float r2 = 0.f;
+    for (int i = 0; i < dim; ++i) r2 += d[i] * d[i];
+    const KPair<float> K = kernel_pair<float>(dim, sqrtf(r2), hab);
+    const VPair<float> Vs = visc_pair<float>(dim, d, w, r2, hab, Vc.w, Ve.w, csc, cse, A.prm);
+    float db[3], wb[3], Bs[6], csh, rh;
+    pairB_adj<float>(dim, d, w, K, Vs, Tc, Te, Qe.w, vbc, bc.w, db, wb, Bs, csh, rh);  // c's own term
+    for (int i = 0; i < dim; ++i) {
+      gx[i].add(db[i]);
+      gv[i].add(wb[i]);
+    }
+    for (int q = 0; q < ns; ++q) Tb[q].add(Bs[q]);
+    csb.add(csh);
+    rhb.add(rh);
+    const float dn[3] = {-d[0], -d[1], -d[2]}, wn[3] = {-w[0], -w[1], -w[2]};
+    pairB_adj<float>(dim, dn, wn, K, Vs, Te, Tc, Qc.w, vbe, be.w, db, wb, Bs, csh, rh);  // e's term, w.r.t. c
+    for (int i = 0; i < dim; ++i) {
+      gx[i].add(-db[i]);
+      gv[i].add(-wb[i]);
+    }
+    for (int q = 0; q < ns; ++q) Tb[q].add(Bs[q]);
+    csb.add(csh);
+    rhb.add(rh);
+  }
+  const Units &U = *A.U;
+  for (int i = 0; i < dim; ++i) {
+    A.gx[i][c] += gx[i].value() * U.invL;
+    A.gv[i][c] += gv[i].value() * U.invV;
+  }
+  A.grho[c] += rhb.value() * U.invrho;
+  const double uTinv = U.rho * U.rho * U.invsig;
+  for (int q = 0; q < 6; ++q) A.Tbar[(int64_t)q * A.ld + c] = q < ns ? Tb[q].value() * uTinv : 0.0;
+  A.csbar[c] = csb.value() * U.invV;
+}
+
+// Cotangents of the pass-A sums (FP64 SI, from k_adj_update) into code units:
+// the continuity sum and G are rates (1/T), L is a number, XSPH a velocity.
+__global__ void k_adj_pack_acot32(AdjArgs A) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= A.n) return;
+  const Units &U = *A.U;
+  const double *I = A.inter;
+  const int64_t ld = A.ld;
+  float v[24];
+  v[0] = (float)(I[c] * U.invT);
+  for (int k = 0; k < 9; ++k) {
+    v[1 + k] = (float)I[(1 + k) * ld + c];
+    v[10 + k] = (float)(I[(10 + k) * ld + c] * U.invT);
+  }
+  for (int i = 0; i < 3; ++i) v[19 + i] = (float)(I[(19 + i) * ld + c] * U.V);
+  v[22] = v[23] = 0.f;
+  for (int q = 0; q < 6; ++q) A.Apk[(int64_t)q * ld + c] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
+__device__ __forceinline__ ACot<float> load_acot32(const AdjArgs &A, int64_t a) {
+  float v[24];
+  for (int q = 0; q < 6; ++q) {
+    const float4 t = A.Apk[(int64_t)q * A.ld + a];
+    v[4 * q] = t.x;
+    v[4 * q + 1] = t.y;
+    v[4 * q + 2] = t.z;
+    v[4 * q + 3] = t.w;
+  }
+  ACot<float> c;
+  c.sr = v[0];
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) {
+      c.Lb[i][j] = v[1 + 3 * i + j];
+      c.Gb[i][j] = v[10 + 3 * i + j];
+    }
+    c.xb[i] = v[19 + i];
+  }
+  return c;
+}
+
+template <int DIM>
+__global__ void k_adj_passA32(AdjArgs A) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= A.n) return;
+  constexpr int dim = DIM;
+  const float4 Pc = A.pk.px(c), Qc = A.pk.pxl(c), Vc = A.pk.pv(c), Wc = A.pk.pvl(c);
+  const ACot<float> Cc = load_acot32(A, c);
+  KahanT<float> gx[3], gv[3], grho;
+  const int cnt = A.nb_cnt[c];
+  for (int k = 0; k < cnt; ++k) {
+    const int32_t e = A.nb_idx[(int64_t)k * A.ld + c];
+    const float4 Pe = A.pk.px(e), Qe = A.pk.pxl(e), Ve = A.pk.pv(e), We = A.pk.pvl(e);
+    float d[3] = {(Pc.x - Pe.x) + (Qc.x - Qe.x), (Pc.y - Pe.y) + (Qc.y - Qe.y),
+                  DIM == 3 ? (Pc.z - Pe.z) + (Qc.z - Qe.z) : 0.f};
+    float w[3] = {(Vc.x - Ve.x) + (Wc.x - We.x), (Vc.y - Ve.y) + (Wc.y - We.y),
+                  DIM == 3 ? (Vc.z - Ve.z) + (Wc.z - We.z) : 0.f};
+    const float hab = 0.5f * (Pc.w + Pe.w);
+    float r2 = 0.f;
+    for (int i = 0; i < dim; ++i) r2 += d[i] * d[i];
+    const float r = sqrtf(r2);
+    const KPair<float> K = kernel_pair<float>(dim, r, hab);
+    float db[3], wb[3], ra, rb;
+    pairA_adj<float>(dim, d, w, r, K, Qe.w, Vc.w, Ve.w, Cc, db, wb, ra, rb);  // c's own term
+    for (int i = 0; i < dim; ++i) {
+      gx[i].add(db[i]);
+      gv[i].add(wb[i]);
+    }
+    grho.add(ra);
+    const ACot<float> Ce = load_acot32(A, e);
+    const float dn[3] = {-d[0], -d[1], -d[2]}, wn[3] = {-w[0], -w[1], -w[2]};
+    pairA_adj<float>(dim, dn, wn, r, K, Qc.w, Ve.w, Vc.w, Ce, db, wb, ra, rb);  // e's term, w.r.t. c
+    for (int i = 0; i < dim; ++i) {
+      gx[i].add(-db[i]);
+      gv[i].add(-wb[i]);
+    }
+    grho.add(rb);
+  }
+  const Units &U = *A.U;
+  for (int i = 0; i < dim; ++i) {
+    A.gx[i][c] += gx[i].value() * U.invL;
+    A.gv[i][c] += gv[i].value() * U.invV;
+  }
+  A.grho[c] += grho.value() * U.invrho;
 }
 
 void rhs_adjoint(sph_ctx *c, const sph_state *s, const MatTable &mt, const sph_params &p, const sph_derivs &dbar,
@@ -708,9 +919,29 @@ void rhs_adjoint(sph_ctx *c, const sph_state *s, const MatTable &mt, const sph_p
   A.mt = mt;
   A.prm = p;
   const int T = 128;
-  { k_adj_passB<<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
-  { k_adj_update<<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
-  { k_adj_passA<<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+  if (p.precision == SPH_MIXED) {
+    A.pk = c->pk;
+    A.Tf = (const float4 *)c->T;
+    A.Bpk = c->adj32;
+    A.Apk = c->adj32 + c->cap_n;
+    A.U = c->units;
+    // FP64 SI copies of T and c_s for the constitutive reverse (the third
+    // derivative set of the step buffers is free here)
+    double *T64 = c->st.d_S[2], *cs64 = c->st.d_cs[2];
+    A.T = T64;
+    A.cs = cs64;
+    { k_adj_unpack32<<<nblk(n, 256), 256, 0, st>>>(A, T64, cs64); ++sph::g_launches; }
+    if (s->dim == 3) { k_adj_passB32<3><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    else { k_adj_passB32<2><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    { k_adj_update<<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    { k_adj_pack_acot32<<<nblk(n, 256), 256, 0, st>>>(A); ++sph::g_launches; }
+    if (s->dim == 3) { k_adj_passA32<3><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    else { k_adj_passA32<2><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+  } else {
+    { k_adj_passB<<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    { k_adj_update<<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    { k_adj_passA<<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+  }
   const int ninst = s->ninst > 0 ? s->ninst : 1;
   if (param_bar)
     { k_adj_params<<<ninst, 256, 0, st>>>(c->ag, c->cap_n, s->mat, s->inst_off, ninst, n, mt.nmat, param_bar); ++sph::g_launches; }

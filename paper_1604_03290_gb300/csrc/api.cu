@@ -146,6 +146,7 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   c->ag = ctx_alloc<double>(c, 3 * N, ok);
   c->units = ctx_alloc<Units>(c, 1, ok);
   c->adj_inter = ctx_alloc<double>(c, 22 * N, ok);
+  c->adj32 = ctx_alloc<float4>(c, 7 * N, ok);
   c->vscale = 1.0;
   StepBufs &S = c->st;
   for (int k = 0; k < 3; ++k) {
@@ -688,8 +689,8 @@ sph_status sph_rhs_adjoint(sph_ctx *c, sph_state *s, const sph_material *mats, i
   cudaStream_t st = (cudaStream_t)stream;
   set_materials(c, &mt);
   sph_params q = *p;
-  q.precision = SPH_FP64;
-  // forward evaluation in FP64: partner lists, T = sigma / rho^2 and c_s
+  // forward evaluation in the requested precision: partner lists, T = sigma /
+  // rho^2 and c_s (FP64 arrays, or the FP32 code-unit views of the mixed form)
   StepBufs &B = c->st;
   sph_derivs fwd;
   memset(&fwd, 0, sizeof(fwd));

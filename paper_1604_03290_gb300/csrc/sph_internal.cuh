@@ -179,6 +179,7 @@ struct sph_ctx {
   double *p;
   double *ag;           // gravity acceleration, 3 * cap_n
   double *adj_inter;    // adjoint scratch, 22 * cap_n
+  float4 *adj32;        // mixed adjoint scratch, 7 * cap_n float4
   sph::Units *units;    // device
   double vscale;        // host: velocity scale for the time unit
   sph::MatTable mt;     // host copy of the materials of the current call

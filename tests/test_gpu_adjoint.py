@@ -112,14 +112,18 @@ def _depth_numpy(x, m, proj, inst_off):
     return np.array(out)
 
 
-def test_step_adjoint_matches_finite_differences(S, orc):
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_step_adjoint_matches_finite_differences(S, orc, prec):
+    # mixed: the rollout and its adjoint in mixed precision, against the oracle's
+    # FP64 finite differences (finite differences of the mixed trajectory itself
+    # would be FP32 rounding noise)
     import torch
     from paper_1604_03290_gb300 import adjoint
     ps = _batch()
     nsteps, every = 12, 5
     cmax = np.sqrt(ps.materials[0].A_T / ps.materials[0].rho0)
     dt = 0.25 * ps.h.min() / (cmax + 6000.0)
-    prm = replace(ps.params, dt_fixed=dt)
+    prm = replace(ps.params, dt_fixed=dt, precision=prec)
     ctx = S.Context(3, ps.n, max_instances=4, max_neighbours=160)
     runner = adjoint.Runner(ctx, ps, prm, dt, nsteps, every=every)
     proj = (ps.v[2] < 0).astype(float)
@@ -149,8 +153,10 @@ def test_step_adjoint_matches_finite_differences(S, orc):
         q = ps.copy()
         if v is not None:
             q.v = v
-        st, _ = orc.step(q, mats or ps.materials, prm, nsteps)
+        st, _ = orc.step(q, mats or ps.materials, replace(prm, precision="fp64"), nsteps)
         return _depth_numpy(st["x"], ps.m, proj, ps.inst_off)
+
+    fp64 = prec == "fp64"
 
     fd_gpu, fd_orc = [], []
     for i in range(ps.ninst):
@@ -158,10 +164,12 @@ def test_step_adjoint_matches_finite_differences(S, orc):
         sel = (inst == i) & (proj > 0)
         dV = 1e-6 * np.abs(ps.v[2][sel]).max()  # steps small enough not to cross branch switches
         dv[2][sel] = -dV  # increase the speed
-        fd_gpu.append((J_gpu(ps.v + dv)[i] - J_gpu(ps.v - dv)[i]) / (2 * dV))
+        if fp64:
+            fd_gpu.append((J_gpu(ps.v + dv)[i] - J_gpu(ps.v - dv)[i]) / (2 * dV))
         fd_orc.append((J_orc(ps.v + dv)[i] - J_orc(ps.v - dv)[i]) / (2 * dV))
-    print("dJ/dV0", g_speed, fd_gpu, fd_orc)
-    np.testing.assert_allclose(g_speed, fd_gpu, rtol=1e-4)
+    print("dJ/dV0", prec, g_speed, fd_gpu, fd_orc)
+    if fp64:
+        np.testing.assert_allclose(g_speed, fd_gpu, rtol=1e-4)
     np.testing.assert_allclose(g_speed, fd_orc, rtol=1e-4)
     m0 = ps.materials[0]
     kref = max(m0.K0, m0.A_T, m0.B_T)
@@ -176,10 +184,40 @@ def test_step_adjoint_matches_finite_differences(S, orc):
                 return [replace(m0, K0=m0.K0 * s, A_T=m0.A_T * s, B_T=m0.B_T * s)]
             return [replace(m0, **{name: val + sign * e})]
 
-        fdg = (J_gpu(mats=mats(1)).sum() - J_gpu(mats=mats(-1)).sum()) / (2 * e)
         fdo = (J_orc(mats=mats(1)).sum() - J_orc(mats=mats(-1)).sum()) / (2 * e)
         # sensitivities below 1e-8 of |J| / theta count as zero
         floor = 1e-8 * float(J.detach().abs().sum()) / val
-        print(name, gth[j], fdg, fdo)
-        assert abs(gth[j] - fdg) <= 1e-4 * abs(fdg) + floor, (name, gth[j], fdg)
+        print(name, prec, gth[j], fdo)
+        if fp64:
+            fdg = (J_gpu(mats=mats(1)).sum() - J_gpu(mats=mats(-1)).sum()) / (2 * e)
+            assert abs(gth[j] - fdg) <= 1e-4 * abs(fdg) + floor, (name, gth[j], fdg)
         assert abs(gth[j] - fdo) <= 1e-4 * abs(fdo) + floor, (name, gth[j], fdo)
+
+
+def test_rhs_adjoint_mixed_matches_fp64(S):
+    # the mixed form (FP32 pair terms in code units, FP64 constitutive reverse)
+    # against the FP64 adjoint on the same state and output cotangents
+    import torch
+    ps = _solid()
+    ctx = S.Context(3, ps.n, max_neighbours=160)
+    rng = np.random.default_rng(6)
+    n = ps.n
+    W = {"dxdt": rng.normal(size=(3, n)) * 1e-3, "dv": rng.normal(size=(3, n)) * 1e-6, "drho": rng.normal(size=n),
+         "du": rng.normal(size=n) * 1e-6, "dS": rng.normal(size=(6, n)) * 1e-9}
+    res = {}
+    for prec in ("fp64", "mixed"):
+        ds = S.DeviceState(ps)
+        dbar = S.alloc_derivs(ds)
+        for k, v in W.items():
+            dbar[k].copy_(torch.as_tensor(v, device="cuda"))
+        sbar = ds.zeros_like()
+        pbar = torch.zeros((1, 1, 3), dtype=torch.float64, device="cuda")
+        S.rhs_adjoint(ctx, ds, ps.materials, replace(ps.params, precision=prec), dbar, sbar, pbar)
+        res[prec] = (sbar.to_numpy(), pbar.cpu().numpy()[0, 0])
+    a, b = res["fp64"][0], res["mixed"][0]
+    for k in ("x", "v", "rho", "u", "S"):
+        scale = np.abs(a[k]).max()
+        err = np.abs(b[k] - a[k]).max() / scale
+        print("mixed adjoint", k, err)
+        assert err <= 1e-4, (k, err)
+    np.testing.assert_allclose(res["mixed"][1], res["fp64"][1], rtol=1e-4)
