@@ -307,40 +307,79 @@ __device__ void eos_scaled(const sph_material &M0, double s, double rho, double 
   eos_eval<double>(M, K, rho, u, p, cs, pr, pu);
 }
 
+// MIXED: the pass-A sums are recomputed in FP32 in the forward's code units
+// (as the mixed forward pass forms them) and converted to SI; the reverse of
+// the constitutive update below is FP64 in both forms.
+template <bool MIXED>
 __global__ void k_adj_update(AdjArgs A) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= A.n) return;
   const int dim = A.dim, ns = nsym(dim);
   const sph_params &P = A.prm;
   // ---- pass-A sums, recomputed ----
-  double xc[3] = {0, 0, 0}, vc[3] = {0, 0, 0};
-  for (int i = 0; i < dim; ++i) {
-    xc[i] = A.x[i][c];
-    vc[i] = A.v[i][c];
-  }
-  const double hc = A.h[c], rc = A.rho[c];
+  const double rc = A.rho[c];
   double srho = 0.0, L[3][3], G[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) L[i][j] = G[i][j] = 0.0;
   const int cnt = A.nb_cnt[c];
-  for (int k = 0; k < cnt; ++k) {
-    const int32_t e = A.nb_idx[(int64_t)k * A.ld + c];
-    double d[3] = {0, 0, 0}, w[3] = {0, 0, 0}, r2 = 0.0;
-    for (int i = 0; i < dim; ++i) {
-      d[i] = xc[i] - A.x[i][e];
-      w[i] = vc[i] - A.v[i][e];
-      r2 += d[i] * d[i];
+  if constexpr (MIXED) {
+    const float4 Pc = A.pk.px(c), Qc = A.pk.pxl(c), Vc = A.pk.pv(c), Wc = A.pk.pvl(c);
+    KahanT<float> s32;
+    float L32[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    float G32[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    for (int k = 0; k < cnt; ++k) {
+      const int32_t e = A.nb_idx[(int64_t)k * A.ld + c];
+      const float4 Pe = A.pk.px(e), Qe = A.pk.pxl(e), Ve = A.pk.pv(e), We = A.pk.pvl(e);
+      const float d[3] = {(Pc.x - Pe.x) + (Qc.x - Qe.x), (Pc.y - Pe.y) + (Qc.y - Qe.y),
+                          dim == 3 ? (Pc.z - Pe.z) + (Qc.z - Qe.z) : 0.f};
+      const float w[3] = {(Vc.x - Ve.x) + (Wc.x - We.x), (Vc.y - Ve.y) + (Wc.y - We.y),
+                          dim == 3 ? (Vc.z - Ve.z) + (Wc.z - We.z) : 0.f};
+      const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      const KPair<float> K = kernel_pair<float>(dim, sqrtf(r2), 0.5f * (Pc.w + Pe.w));
+      const float vol = We.w;  // m / rho
+      float wg = 0.f;
+      for (int i = 0; i < dim; ++i) wg += w[i] * K.phi * d[i];
+      s32.add(vol * wg);
+      for (int i = 0; i < dim; ++i)
+        for (int j = 0; j < dim; ++j) {
+          L32[i][j] -= vol * d[i] * K.phi * d[j];
+          G32[i][j] -= vol * w[i] * K.phi * d[j];
+        }
     }
-    const KernelPair K = kernel_pair(dim, sqrt(r2), 0.5 * (hc + A.h[e]));
-    const double vol = A.m[e] / A.rho[e];
-    double wg = 0.0;
-    for (int i = 0; i < dim; ++i) wg += w[i] * K.phi * d[i];
-    srho += vol * wg;
+    // the continuity sum and G are rates (code unit 1/T), L is a number
+    const double it = A.U->invT;
+    srho = s32.value() * it;
     for (int i = 0; i < dim; ++i)
       for (int j = 0; j < dim; ++j) {
-        L[i][j] -= vol * d[i] * K.phi * d[j];
-        G[i][j] -= vol * w[i] * K.phi * d[j];
+        L[i][j] = L32[i][j];
+        G[i][j] = (double)G32[i][j] * it;
       }
+  } else {
+    double xc[3] = {0, 0, 0}, vc[3] = {0, 0, 0};
+    for (int i = 0; i < dim; ++i) {
+      xc[i] = A.x[i][c];
+      vc[i] = A.v[i][c];
+    }
+    const double hc = A.h[c];
+    for (int k = 0; k < cnt; ++k) {
+      const int32_t e = A.nb_idx[(int64_t)k * A.ld + c];
+      double d[3] = {0, 0, 0}, w[3] = {0, 0, 0}, r2 = 0.0;
+      for (int i = 0; i < dim; ++i) {
+        d[i] = xc[i] - A.x[i][e];
+        w[i] = vc[i] - A.v[i][e];
+        r2 += d[i] * d[i];
+      }
+      const KernelPair K = kernel_pair(dim, sqrt(r2), 0.5 * (hc + A.h[e]));
+      const double vol = A.m[e] / A.rho[e];
+      double wg = 0.0;
+      for (int i = 0; i < dim; ++i) wg += w[i] * K.phi * d[i];
+      srho += vol * wg;
+      for (int i = 0; i < dim; ++i)
+        for (int j = 0; j < dim; ++j) {
+          L[i][j] -= vol * d[i] * K.phi * d[j];
+          G[i][j] -= vol * w[i] * K.phi * d[j];
+        }
+    }
   }
   double C[3][3];
   const bool corr = P.consistency && cnt >= dim + 1 && invert_L(dim, L, C);
@@ -933,13 +972,13 @@ void rhs_adjoint(sph_ctx *c, const sph_state *s, const MatTable &mt, const sph_p
     { k_adj_unpack32<<<nblk(n, 256), 256, 0, st>>>(A, T64, cs64); ++sph::g_launches; }
     if (s->dim == 3) { k_adj_passB32<3><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
     else { k_adj_passB32<2><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
-    { k_adj_update<<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    { k_adj_update<true><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
     { k_adj_pack_acot32<<<nblk(n, 256), 256, 0, st>>>(A); ++sph::g_launches; }
     if (s->dim == 3) { k_adj_passA32<3><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
     else { k_adj_passA32<2><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
   } else {
     { k_adj_passB<<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
-    { k_adj_update<<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    { k_adj_update<false><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
     { k_adj_passA<<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
   }
   const int ninst = s->ninst > 0 ? s->ninst : 1;
