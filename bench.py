@@ -143,7 +143,18 @@ def algorithmic_bytes(phase, K, n_flaw_mean, dim=3):
 # flaw distribution of the measured configuration (Sect. 3.2) and the
 # friends-of-friends fragments of a 1M-particle fragmented body (Sect. 4).
 # ----------------------------------------------------------------------------
-def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3, cloud_n=2_000_000):
+def oracle_time(fn):
+    """Seconds of one oracle call on all host cores (the oracle as it stands)."""
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    oracle.set_threads(cores)
+    t0 = time.perf_counter()
+    fn(oracle)
+    return time.perf_counter() - t0, cores
+
+
+def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3, cloud_n=2_000_000, with_oracle=False):
     import numpy as np
     import torch
     from dataclasses import replace
@@ -173,6 +184,10 @@ def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3, cloud_n=2_000_000):
              "ms": ms_f, "flaws": nfl, "value": nfl / (ms_f * 1e-3), "unit": "flaws/s", "phases_ms": ph_f,
              # output bytes: thresholds (4 B each) and offsets (8 B per particle)
              "hbm_frac_output_bytes": (4 * nfl + 8 * ps.n) / (ms_f * 1e-3) / 1e9 / hbm_peak}
+    if with_oracle:
+        sec, cores = oracle_time(lambda o: o.flaws(ps, seed=12345))
+        flaws["cpu_baseline"] = {"value": nfl / sec, "unit": "flaws/s", "cores": cores, "kind": "oracle",
+                                 "sample": "the same call on the host (%.1f s)" % sec}
     del ds, off, eps
     fb = wl.fragmented_body(seed=21)
     dsf = sph.DeviceState(fb)
@@ -181,6 +196,10 @@ def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3, cloud_n=2_000_000):
                         % fb.n,
             "ms": ms_g, "fragments": int(cnt.numel()), "value": fb.n / (ms_g * 1e-3), "unit": "particles/s",
             "phases_ms": ph_g}
+    if with_oracle:
+        sec, cores = oracle_time(lambda o: o.fof(fb.x, fb.h, fb.m, 3, b=1.01, d_remove=1.0, min_size=3, dmg=fb.dmg))
+        frag["cpu_baseline"] = {"value": fb.n / sec, "unit": "particles/s", "cores": cores, "kind": "oracle",
+                                "sample": "the same call on the host (%.1f s)" % sec}
     del dsf, lab, cnt, mass
 
     # gravity/hydro decoupling (Sect. 5): the 2M-particle collapsing cloud,
@@ -536,7 +555,8 @@ def main():
     e2e = {"value": replica_value(world, n, e2e_steps, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
 
-    aux = aux_rows(sph, wl, ctx, ps, stream, hbm_peak, cloud_n=args.cloud_n) if not args.no_aux else None
+    aux = (aux_rows(sph, wl, ctx, ps, stream, hbm_peak, cloud_n=args.cloud_n,
+                    with_oracle=rank == 0 and not args.no_cpu) if not args.no_aux else None)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
