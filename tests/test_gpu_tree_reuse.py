@@ -2,8 +2,10 @@
 gravity/hydro decoupling of Sect. 5) against the oracle stepping with the
 same reuse: a self-gravitating cloud (pseudo-particles of the build, leaves
 at current positions), a pair of self-gravitating basalt bodies with
-strength and damage, and an impact without gravity (partners stay exact, so
-the steps equal plain steps); with the tolerances of the plain step tests.
+strength and damage, an impact without gravity (partners stay exact, so
+the steps equal plain steps), three batched impacts and a cloud with variable
+smoothing length (which builds every step); with the tolerances of the plain
+step tests.
 The reuse is also checked to take effect (the cloud's steps differ from
 the steps that build a tree per evaluation)."""
 from dataclasses import replace
@@ -44,7 +46,23 @@ def _impact():
     return wl.measurement_1m(seed=11, n_side=14)
 
 
-CASES = {"cloud": _cloud, "pair": _pair, "impact": _impact}
+def _batch():
+    # three impacts in one state: the walks take the tree's per-instance groups
+    ps = wl.batched_impacts(seed=5, ninst=3, nmin=400, nmax=1500)
+    ps.params = replace(ps.params, max_depth=19)
+    return ps
+
+
+def _cloud_vh():
+    # variable smoothing length: h changes every step, so every step builds
+    ps = _cloud()
+    rng = np.random.default_rng(13)
+    ps.h = ps.h * rng.uniform(0.8, 1.25, ps.n)
+    ps.params = replace(ps.params, n_des=50.0, h_tol=2, h_iter=4)
+    return ps
+
+
+CASES = {"cloud": _cloud, "pair": _pair, "impact": _impact, "batch": _batch, "cloud_vh": _cloud_vh}
 
 
 def _gpu_steps(S, ps, prm, nsteps):
@@ -57,7 +75,8 @@ def _gpu_steps(S, ps, prm, nsteps):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("case,reuse,nsteps", [("cloud", 3, 5), ("pair", 2, 3), ("impact", 4, 4)])
+@pytest.mark.parametrize("case,reuse,nsteps", [("cloud", 3, 5), ("pair", 2, 3), ("impact", 4, 4), ("batch", 3, 4),
+                                               ("cloud_vh", 3, 2)])
 def test_reuse_steps_match_oracle(orc, S, case, reuse, nsteps, prec):
     ps = CASES[case]()
     prm = replace(ps.params, tree_reuse=reuse)
@@ -65,8 +84,8 @@ def test_reuse_steps_match_oracle(orc, S, case, reuse, nsteps, prec):
     dt, g = _gpu_steps(S, ps, replace(prm, precision=prec), nsteps)
     np.testing.assert_allclose(dt, olog[-1], rtol=1e-9 if prec == "fp64" else 1e-4)
     tol = 1e-9 if prec == "fp64" else 2e-5
-    for f in ("x", "v", "rho", "u", "S", "dmg"):
-        if ost.get(f) is None:
+    for f in ("x", "v", "rho", "u", "S", "dmg", "h"):
+        if ost.get(f) is None or (f == "h" and not prm.n_des > 0):
             continue
         init = getattr(ps, f)
         change = np.abs(ost[f] - init).max()
