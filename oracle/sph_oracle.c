@@ -1583,7 +1583,12 @@ int32_t orc_step_rk3(orc_state *s, const orc_material *mats, int32_t nmat, const
   double *err = (double *)malloc((size_t)ninst * sizeof(double));
   int32_t *acc = (int32_t *)malloc((size_t)ninst * sizeof(int32_t));
   int rc = 0;
+  int32_t *hcnt = P->n_des > 0.0 ? (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t)) : NULL;
   for (int32_t st = 0; st < nsteps && rc == 0; ++st) {
+    /* variable smoothing length at the start of each attempt, from the current */
+    /* h (Sect. 4.2); a rejected attempt keeps the adapted h                     */
+    if (hcnt)
+      orc_adapt_h(dim, n, s->x, s->y, s->z, s->h, s->inst_off, ninst, P->n_des, P->h_tol, P->h_iter, hcnt);
     rc = orc_rhs(s, mats, nmat, P, &d[0].d);
     if (rc) break;
     orc_timestep(s, mats, nmat, P, &d[0].d, lim); /* first step size where none is given */
@@ -1648,6 +1653,7 @@ int32_t orc_step_rk3(orc_state *s, const orc_material *mats, int32_t nmat, const
   free(lim);
   free(err);
   free(acc);
+  free(hcnt);
   return rc;
 }
 

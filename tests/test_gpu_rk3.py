@@ -30,7 +30,7 @@ def _by_id(d):
 
 def _advance(ps, st):
     q = ps.copy()
-    for f in ("x", "v", "rho", "u", "S", "dmg"):
+    for f in ("x", "v", "rho", "u", "S", "dmg", "h"):  # h: adapted at each attempt when n_des > 0
         if st.get(f) is not None:
             setattr(q, f, st[f])
     return q
@@ -38,7 +38,7 @@ def _advance(ps, st):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("case,eps", [("solid3d", 1e-3), ("impact", 3e-3), ("impact_fast", 1e-3), ("batch", 1e-3),
-                                      ("cloud", 1e-3)])
+                                      ("cloud", 1e-3), ("cloud_vh", 1e-3)])
 def test_rk3_attempts_match_oracle(orc, S, case, eps, prec):
     """Attempt by attempt from the same step size (the oracle's): the error
     estimate is a difference of three right-hand sides, so it is compared with
@@ -78,8 +78,8 @@ def test_rk3_attempts_match_oracle(orc, S, case, eps, prec):
         np.testing.assert_allclose(gdt[above], odt[above], rtol=rt_err)
         seen.update(int(v) for v in oacc[0])
         g = _by_id(ds.to_numpy())
-        for f in ("x", "v", "rho", "u", "S", "dmg"):
-            if ost.get(f) is None:
+        for f in ("x", "v", "rho", "u", "S", "dmg", "h"):
+            if ost.get(f) is None or (f == "h" and not prm.n_des > 0):
                 continue
             init = getattr(ps, f)
             change = np.abs(ost[f] - init).max()
