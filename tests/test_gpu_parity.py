@@ -245,6 +245,29 @@ def test_gravity_matches_oracle(orc, S, prec, theta, L, dim):
         assert (np.abs(g - d) / sc).max() <= TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_gravity_respects_instances(orc, S, prec):
+    # two bodies in the same region of space as separate instances: each one's
+    # field is its own (per-instance trees and roots, the tree's groups)
+    rng = np.random.default_rng(43)
+    a = rng.normal(size=(3, 1800))
+    b = rng.normal(size=(3, 1300)) * 0.7 + 0.2
+    x = np.concatenate([a, b], 1)
+    n = x.shape[1]
+    m = rng.uniform(0.5, 1.5, n)
+    h = rng.uniform(0.02, 0.1, n)
+    ps = _bare_set(x, m, h)
+    ps.inst_off = np.array([0, 1800, n], np.int64)
+    prm = wl.Params(dim=3, G=1.3, theta=0.5, eps_grav=0.5, leaf_size=8, max_depth=19, precision=prec)
+    ctx = S.Context(3, n, max_instances=2, leaf_size=8)
+    g = S.gravity(ctx, S.DeviceState(ps), prm).cpu().numpy()
+    for lo, hi in ((0, 1800), (1800, n)):
+        o = orc.gravity_bh(x[:, lo:hi], m[lo:hi], h[lo:hi], 3, 1.3, 0.5, 0.5, 8, 19)
+        sc = _grav_scale(x[:, lo:hi], m[lo:hi], h[lo:hi], 1.3, 0.5)
+        err = (np.abs(g[:, lo:hi] - o) / sc).max()
+        assert err <= TOL[prec], err
+
+
 # ---------------------------------------------------------------------------
 # Predictor-corrector steps
 # ---------------------------------------------------------------------------
