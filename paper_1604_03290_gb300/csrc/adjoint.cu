@@ -507,21 +507,35 @@ __global__ void k_adj_update(AdjArgs A) {
   double Kbar = 0.0;
   {
     const double er = 1e-6 * rc, eu = 1e-6 * (fabs(uc) + 1e-3 * fabs(M.E0) + 1e-30), es = 1e-6;
-    double p1, c1, p2, c2;
-    if (csbar != 0.0) {
-      eos_scaled(M, 1.0, rc + er, uc, p1, c1, nullptr, nullptr);
-      eos_scaled(M, 1.0, rc - er, uc, p2, c2, nullptr, nullptr);
-      rhobar += csbar * (c1 - c2) / (2.0 * er);
-      eos_scaled(M, 1.0, rc, uc + eu, p1, c1, nullptr, nullptr);
-      eos_scaled(M, 1.0, rc, uc - eu, p2, c2, nullptr, nullptr);
-      ubar += csbar * (c1 - c2) / (2.0 * eu);
-    }
     const double Kref = fmax(fmax(M.K0, M.A_T), M.B_T);
-    if (Kref > 0.0) {
-      eos_scaled(M, 1.0 + es, rc, uc, p1, c1, nullptr, nullptr);
-      eos_scaled(M, 1.0 - es, rc, uc, p2, c2, nullptr, nullptr);
-      Kbar = (pbar * (p1 - p2) + csbar * (c1 - c2)) / (2.0 * es * Kref);
+    // the six evaluations of the central differences (rho +-, u +-, scale +-)
+    // in one loop, so that the equation of state is emitted once here: six
+    // inlined copies overflowed the instruction cache.  c+ + (-c-) from zero is
+    // the same value as c+ - c-.
+    double dcr = 0.0, dcu = 0.0, dps = 0.0, dcs = 0.0;
+#pragma unroll 1
+    for (int k = 0; k < 6; ++k) {
+      if (k < 4 ? csbar == 0.0 : !(Kref > 0.0)) continue;
+      const double sg = (k & 1) ? -1.0 : 1.0;
+      const double r1 = k == 0 ? rc + er : (k == 1 ? rc - er : rc);
+      const double u1 = k == 2 ? uc + eu : (k == 3 ? uc - eu : uc);
+      const double s1 = k == 4 ? 1.0 + es : (k == 5 ? 1.0 - es : 1.0);
+      double p1, c1;
+      eos_scaled(M, s1, r1, u1, p1, c1, nullptr, nullptr);
+      if (k < 2) {
+        dcr += sg * c1;
+      } else if (k < 4) {
+        dcu += sg * c1;
+      } else {
+        dps += sg * p1;
+        dcs += sg * c1;
+      }
     }
+    if (csbar != 0.0) {
+      rhobar += csbar * dcr / (2.0 * er);
+      ubar += csbar * dcu / (2.0 * eu);
+    }
+    if (Kref > 0.0) Kbar = (pbar * dps + csbar * dcs) / (2.0 * es * Kref);
   }
   // ---- reverse: grad v = G C, C = L^-1 ----
   double Gbar[3][3], Lbar[3][3];
