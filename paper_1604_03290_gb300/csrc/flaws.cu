@@ -9,7 +9,8 @@
 // that hits the member, and the flaws are exactly draws 1..J.  So:
 //   1. sort the particles by (group, id): the members of group g are the
 //      sorted positions goff[g] .. goff[g+1];
-//   2. V_g = sum m / rho0 over the members (one block per group);
+//   2. V_g = sum m / rho0 over the members (chunks of members, one block
+//      each, then each group's chunks in order: the same sum every run);
 //   3. coverage rounds: make a batch of draws of every group that is not
 //      yet covered and record, per member, the smallest j that hit it
 //      (atomicMin); repeat for the groups with members still unhit;
