@@ -2,7 +2,8 @@
 of the method rather than by its formulas: third-order convergence on a smooth
 problem (the predictor-corrector is second order), the error estimate shrinking
 as dt^3, exact motion of free particles with a zero error estimate (dt grows to
-dt_max), and a rejected step that leaves the state untouched and shrinks dt."""
+dt_max), a rejected step that leaves the state untouched and shrinks dt, and
+variable h as the iteration of Sect. 4.2 followed by the attempt."""
 from dataclasses import replace
 
 import numpy as np
@@ -93,3 +94,24 @@ def test_rejected_step_keeps_the_state(orc):
     np.testing.assert_array_equal(st["x"], ps.x)
     np.testing.assert_array_equal(st["v"], ps.v)
     assert 0.0 < dtv[0] < 0.9 * 0.3
+
+
+def test_variable_h_adapts_at_each_attempt(orc):
+    # one attempt with n_des > 0 is the iteration of Sect. 4.2 followed by the
+    # attempt with the adapted h (accepted or rejected alike: h stays adapted)
+    ps = _smooth_block()
+    rng = np.random.default_rng(4)
+    ps.h = ps.h * rng.uniform(0.85, 1.2, ps.n)
+    prm = replace(ps.params, dt_max=1.0, n_des=18.0, h_tol=1, h_iter=3)
+    for eps, dt in ((np.inf, 0.05), (1e-30, 0.05)):
+        st, dtv, tv, err, acc = orc.step_rk3(ps, ps.materials, prm, eps_des=eps, nsteps=1, dt=[dt])
+        hh, _, _ = orc.adapt_h(ps.x, ps.h, ps.dim, 18.0, tol=1, max_iter=3)
+        q = ps.copy()
+        q.h = hh
+        st2, dtv2, tv2, err2, acc2 = orc.step_rk3(q, q.materials, replace(prm, n_des=0.0), eps_des=eps, nsteps=1,
+                                                  dt=[dt])
+        np.testing.assert_array_equal(st["h"], hh)
+        for f in ("x", "v", "rho", "u"):
+            np.testing.assert_array_equal(st[f], st2[f])
+        np.testing.assert_array_equal(err, err2)
+        assert acc.tolist() == acc2.tolist()
