@@ -115,7 +115,7 @@ class ClockSampler:
 # particle count at this density.  Set to None when a kernel changes and the
 # capture has not been repeated.
 NCU_PER_PARTICLE = {
-    "partners": {"inst": 703.47, "dram": 297.87, "fp32_pipe": 0.265, "issue": 0.650},
+    "partners": None,  # changed (records the partner shells): capture pending
     "passA": {"inst": 365.57, "dram": 506.52, "fp32_pipe": 0.378, "issue": 0.597},
     "passB": {"inst": 395.24, "dram": 348.77, "fp32_pipe": 0.440, "issue": 0.628},
 }
@@ -134,7 +134,16 @@ def algorithmic_bytes(phase, K, n_flaw_mean, dim=3):
     if phase == "passB":
         return 64 + 32 + 4 + 4 * K + 8 * dim + 8  # packs, T pack, list; dv, du
     if phase == "partners":
-        return 32 + 4 + 4 + 4 * K + 4  # positions, perm, slot; list and count
+        # positions, perm, slot; list and count; the shell list of the step's
+        # later evaluations (partners within (1 + 1/64) h_ab but not h_ab: about
+        # ((1 + 1/64)^D - 1) K of them) and its count
+        shell = ((1.0 + 1.0 / 64.0) ** dim - 1.0) * K
+        return 32 + 4 + 4 + 4 * K + 4 + 4 * shell + 4
+    if phase == "refine":
+        # per particle: counts and h; the old list, the shell and the new list
+        # (partner positions reused from cache)
+        shell = ((1.0 + 1.0 / 64.0) ** dim - 1.0) * K
+        return 4 + 4 + 8 + 32 + 4 * (K + shell) + 4 * K + 4
     raise KeyError(phase)
 
 
@@ -159,7 +168,7 @@ def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3, cloud_n=2_000_000, with
     import torch
     from dataclasses import replace
 
-    def timed(fn):
+    def timed(fn, ctx=ctx):
         fn()  # warm-up
         ctx.sync_status()
         ctx.profile(True)
@@ -191,7 +200,10 @@ def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3, cloud_n=2_000_000, with
     del ds, off, eps
     fb = wl.fragmented_body(seed=21)
     dsf = sph.DeviceState(fb)
-    ms_g, ph_g, (lab, cnt, mass) = timed(lambda: sph.fragments(ctx, dsf, link=1.01, d_remove=1.0, min_size=3))
+    # the bench's context when it holds the body (a smaller --n-side: one of its own)
+    ctxf = ctx if fb.n <= ctx.max_particles else sph.Context(3, fb.n, max_neighbours=ctx.max_neighbours)
+    ms_g, ph_g, (lab, cnt, mass) = timed(lambda: sph.fragments(ctxf, dsf, link=1.01, d_remove=1.0, min_size=3),
+                                         ctxf)
     frag = {"workload": "friends-of-friends of the fragmented body (%d particles, 10 damaged slabs, link 1.01 h)"
                         % fb.n,
             "ms": ms_g, "fragments": int(cnt.numel()), "value": fb.n / (ms_g * 1e-3), "unit": "particles/s",
@@ -200,7 +212,7 @@ def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3, cloud_n=2_000_000, with
         sec, cores = oracle_time(lambda o: o.fof(fb.x, fb.h, fb.m, 3, b=1.01, d_remove=1.0, min_size=3, dmg=fb.dmg))
         frag["cpu_baseline"] = {"value": fb.n / sec, "unit": "particles/s", "cores": cores, "kind": "oracle",
                                 "sample": "the same call on the host (%.1f s)" % sec}
-    del dsf, lab, cnt, mass
+    del dsf, lab, cnt, mass, ctxf
 
     # gravity/hydro decoupling (Sect. 5): the 2M-particle collapsing cloud,
     # steps that build a tree per evaluation against steps that reuse one
@@ -467,12 +479,13 @@ def main():
     value = replica_value(world, n, args.steps, ms)
 
     # ---- rooflines ----
-    # The partner walk is bound by instruction issue (latency and ALU work of
-    # an irregular tree walk): its roofline is warp instructions issued per
-    # second against SMs x 4 issue slots x the SM clock seen under load.  The
-    # neighbour passes are reported against HBM with their algorithmic bytes
-    # (each array once), and against issue the same way.  Launch times are the
-    # library's CUDA events on the launching stream over the timed region.
+    # The partner walk and the neighbour passes are bound by instruction issue
+    # (latency and ALU work of irregular gathers and an irregular tree walk):
+    # their roofline is warp instructions issued per second against SMs x 4
+    # issue slots x the SM clock seen under load.  Each is also reported
+    # against HBM with its algorithmic bytes (each array once).  Launch times
+    # are the library's CUDA events on the launching stream over the timed
+    # region.
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
     issue_peak = nsm * ISSUE_SLOTS_PER_SM * sm_mhz * 1e6 / 1e9  # G warp-instructions / s
@@ -496,11 +509,11 @@ def main():
             r["fp32_pipe_frac_ncu"] = c["fp32_pipe"]
         return r
 
-    kr = {p: kernel_roof(p) for p in ("partners", "passA", "passB")}
+    kr = {p: kernel_roof(p) for p in ("partners", "refine", "passA", "passB")}
     timed = {p: phases[p][0] for p in kr if kr[p] is not None}
     dom = max(timed, key=timed.get) if timed else "partners"
     d = kr[dom]
-    if dom == "partners" and "issue" in d:
+    if "issue" in d:
         roof = {"bound": "alu", "kernel": dom, "achieved": d["issue"]["achieved"], "peak": issue_peak,
                 "unit": "G warp-instructions/s", "frac": d["issue"]["frac"],
                 "traffic": d.get("dram_bytes_ncu"),

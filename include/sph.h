@@ -141,12 +141,17 @@ typedef struct sph_ctx sph_ctx;
  * value.  walk_leaf: the partner walk stops descending at nodes of at most
  * this many particles and tests their whole particle range (8..1024).
  * walk_blocks_per_sm: resident blocks per SM of the persistent walk grids
- * (1..32).  pass_threads: threads per block of the neighbour passes (64 or 128). */
+ * (1..32).  pass_threads: threads per block of the neighbour passes (64 or 128).
+ * walk_every_eval: 0 (default) lets the later evaluations of one sph_step or
+ * sph_step_rk3 step without gravity take their partners from the step's first
+ * walk, which also records each particle's candidates within (1 + 1/64) h_ab,
+ * whenever no particle moved by 1/64 h / (4 sqrt D) or more per axis (else
+ * they walk); 1 walks the tree at every evaluation (Sect. 3.5.2 as printed). */
 typedef struct {
   int32_t walk_leaf;
   int32_t walk_blocks_per_sm;
   int32_t pass_threads;
-  int32_t reserved;
+  int32_t walk_every_eval;
 } sph_tuning;
 
 /* Creates a context for up to max_particles particles in up to
@@ -372,16 +377,18 @@ sph_status sph_pc_update_adjoint(sph_ctx *ctx, const sph_state *base, const sph_
                                  double frac, const sph_state *out_bar, sph_state *base_bar, sph_derivs *d_bar,
                                  double *param_bar, void *stream);
 
-/* Reads / replaces the tuning of a context (defaults: 64, 16, 128). */
+/* Reads / replaces the tuning of a context (defaults: 64, 16, 128, 0). */
 sph_status sph_get_tuning(const sph_ctx *ctx, sph_tuning *out);
 sph_status sph_set_tuning(sph_ctx *ctx, const sph_tuning *t);
 
 /* Optional per-phase timing.  When enabled, every phase of sph_rhs and
  * sph_step is bracketed by CUDA events recorded on the call's stream (at most
  * 8192 phases between reads; later ones go untimed).  Phases, in order:
- * 0 tree build, 1 state reorder, 2 partner search, 3 density sum,
+ * 0 tree build, 1 state reorder, 2 partner search (tree walk), 3 density sum,
  * 4 neighbour pass A with the constitutive update, 5 momentum/energy pass B,
- * 6 gravity, 7 integrator (time step and updates). */
+ * 6 gravity, 7 integrator (time step and updates), 8 flaw draws and 9 flaw
+ * thresholds (sph_flaws), 10 friends-of-friends links (sph_fragments),
+ * 11 partners refined from the step's first walk (see walk_every_eval). */
 sph_status sph_profile_enable(sph_ctx *ctx, int32_t on);
 /* Milliseconds and call counts per phase since the last read (nphase
  * entries of each); synchronises on the recorded events, then resets. */

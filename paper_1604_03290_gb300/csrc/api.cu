@@ -3,6 +3,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <utility>
 
 #include "sph_internal.cuh"
 
@@ -79,6 +80,7 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   c->tune.walk_leaf = 64;
   c->tune.walk_blocks_per_sm = 16;
   c->tune.pass_threads = 128;
+  c->tune.walk_every_eval = 0;
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   if (c->num_sms < 1) c->num_sms = 1;
   const int64_t N = max_particles;
@@ -137,6 +139,11 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   c->pk.pvl_ = ctx_alloc<float4>(c, N, ok);
   c->nb_idx = ctx_alloc<int32_t>(c, (int64_t)max_neighbours * N, ok);
   c->nb_cnt = ctx_alloc<int32_t>(c, N, ok);
+  c->nb_alt = ctx_alloc<int32_t>(c, (int64_t)max_neighbours * N, ok);
+  c->nb_cnt_alt = ctx_alloc<int32_t>(c, N, ok);
+  c->sh_idx = ctx_alloc<int32_t>(c, (int64_t)kMaxShell * N, ok);
+  c->sh_cnt = ctx_alloc<int32_t>(c, N, ok);
+  c->need_walk = ctx_alloc<int32_t>(c, 1, ok);
   c->csr_total = ctx_alloc<int64_t>(c, 1, ok);
   c->hflags = ctx_alloc<int32_t>(c, kMaxHIter + 3, ok);
   c->T = ctx_alloc<double>(c, 8 * N, ok);
@@ -329,19 +336,36 @@ static void timed_tree(sph_ctx *c, const sph_state *s, const sph_params &p, cuda
 }
 
 // grow: displacement bound since the tree build (NULL: built at s);
-// greuse: gravity from the pseudo-particles of an earlier build
+// greuse: gravity from the pseudo-particles of an earlier build;
+// shell: the walk also records the partner shells (for a later refine);
+// move: refine the partners from the lists and shells of the last walk, which
+// every particle has left by at most *move per axis (NULL: walk)
 static void partners_gravity_passes(sph_ctx *c, sph_state *s, const MatTable &mt, const sph_params &p,
                                     const sph_derivs &out, cudaStream_t st,
-                                    const unsigned long long *grow = nullptr, bool greuse = false) {
-  int pr = prof_begin(c, st, PH_PARTNERS);
-  find_partners(c, s, st, grow);
-  prof_end(c, st, pr);
+                                    const unsigned long long *grow = nullptr, bool greuse = false,
+                                    bool shell = false, const unsigned long long *move = nullptr) {
+  int pr;
+  if (move) {
+    pr = prof_begin(c, st, PH_REFINE);
+    refine_partners(c, s, move, grow, st);
+    prof_end(c, st, pr);
+    std::swap(c->nb_idx, c->nb_alt);  // the passes read the refined lists
+    std::swap(c->nb_cnt, c->nb_cnt_alt);
+  } else {
+    pr = prof_begin(c, st, PH_PARTNERS);
+    find_partners(c, s, st, grow, shell);
+    prof_end(c, st, pr);
+  }
   if (p.gravity) {
     pr = prof_begin(c, st, PH_GRAVITY);
     gravity_walk(c, s, p, c->ag, c->ag + c->cap_n, c->ag + 2 * c->cap_n, st, greuse);
     prof_end(c, st, pr);
   }
   rhs_passes(c, s, mt, p, out, st);
+  if (move) {  // the walk's lists, counts and shells stay for the next refine
+    std::swap(c->nb_idx, c->nb_alt);
+    std::swap(c->nb_cnt, c->nb_cnt_alt);
+  }
 }
 
 static void rhs_all(sph_ctx *c, sph_state *s, const MatTable &mt, const sph_params &p, const sph_derivs &out,
@@ -538,6 +562,9 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
   // partner search, boxes widened by the summed displacement bounds).
   const int R = p->tree_reuse > 0 ? p->tree_reuse : 0;
   const bool reuse_pred = !p->gravity || R > 0;
+  // The predictor's partners: refined from the lists and shells of the step's
+  // first walk (a walk follows only where the particles moved too far)
+  const bool refine = reuse_pred && c->tune.walk_every_eval == 0;
   int age = 0;
   for (int it = 0; it < nsteps; ++it) {
     const bool vh = p->n_des > 0.0;
@@ -556,12 +583,12 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
       tree_reorder_state(c, s, st);
       prof_end(c, st, pr);
       if (R > 0) cudaMemsetAsync(B.dbuild, 0, sizeof(unsigned long long), st);
-      partners_gravity_passes(c, s, mt, *p, d[0], st);
+      partners_gravity_passes(c, s, mt, *p, d[0], st, nullptr, false, refine);
     } else {
       pr = prof_begin(c, st, PH_TREE);
       pack_f32(c, s, st);
       prof_end(c, st, pr);
-      partners_gravity_passes(c, s, mt, *p, d[0], st, B.dbuild, p->gravity);
+      partners_gravity_passes(c, s, mt, *p, d[0], st, B.dbuild, p->gravity, refine);
     }
     pr = prof_begin(c, st, PH_INTEGRATE);
     timestep_reduce(c, s, *p, d[0], st);
@@ -573,7 +600,8 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
       pr = prof_begin(c, st, PH_TREE);
       pack_f32(c, &q, st);
       prof_end(c, st, pr);
-      partners_gravity_passes(c, &q, mt, *p, d[1], st, build ? B.dmove : B.dgrow, p->gravity);
+      partners_gravity_passes(c, &q, mt, *p, d[1], st, build ? B.dmove : B.dgrow, p->gravity, false,
+                              refine ? B.dmove : nullptr);
     } else {
       rhs_all(c, &q, mt, *p, d[1], st);
     }
@@ -631,6 +659,7 @@ sph_status sph_step_rk3(sph_ctx *c, sph_state *s, const sph_material *mats, int3
   const sph_derivs *k1[1] = {&d[0]}, *k12[2] = {&d[0], &d[1]}, *k123[3] = {&d[0], &d[1], &d[2]};
   const double c2[1] = {0.5}, c3[2] = {-1.0, 2.0}, cf[3] = {1.0 / 6.0, 4.0 / 6.0, 1.0 / 6.0};
   const bool reuse = !p->gravity;  // stage states keep the slots of s and use its tree (as in sph_step)
+  const bool refine = reuse && c->tune.walk_every_eval == 0;  // stage partners refined from k1's walk
   auto stage = [&](const sph_derivs *const *k, const double *coef, int nd, sph_derivs &out) {
     int pr = prof_begin(c, st, PH_INTEGRATE);
     if (reuse) cudaMemsetAsync(B.dmove, 0, sizeof(unsigned long long), st);
@@ -640,7 +669,7 @@ sph_status sph_step_rk3(sph_ctx *c, sph_state *s, const sph_material *mats, int3
       pr = prof_begin(c, st, PH_TREE);
       pack_f32(c, &q, st);
       prof_end(c, st, pr);
-      partners_gravity_passes(c, &q, mt, *p, out, st, B.dmove);
+      partners_gravity_passes(c, &q, mt, *p, out, st, B.dmove, false, false, refine ? B.dmove : nullptr);
     } else {
       rhs_all(c, &q, mt, *p, out, st);
     }
@@ -656,7 +685,7 @@ sph_status sph_step_rk3(sph_ctx *c, sph_state *s, const sph_material *mats, int3
     int pr = prof_begin(c, st, PH_REORDER);
     tree_reorder_state(c, s, st);
     prof_end(c, st, pr);
-    partners_gravity_passes(c, s, mt, *p, d[0], st);  // k1
+    partners_gravity_passes(c, s, mt, *p, d[0], st, nullptr, false, refine);  // k1
     pr = prof_begin(c, st, PH_INTEGRATE);
     timestep_reduce(c, s, *p, d[0], st);  // the limit, for a first step size
     rk_set_dt(c, s, dt, st);
@@ -749,7 +778,7 @@ sph_status sph_set_tuning(sph_ctx *c, const sph_tuning *t) {
   if (!c || !t) return SPH_ERR_INVALID;
   const int pt = t->pass_threads;
   if (t->walk_leaf < 8 || t->walk_leaf > 1024 || t->walk_blocks_per_sm < 1 || t->walk_blocks_per_sm > 32 ||
-      !(pt == 64 || pt == 128))
+      !(pt == 64 || pt == 128) || (t->walk_every_eval != 0 && t->walk_every_eval != 1))
     return fail(c, SPH_ERR_INVALID, "tuning out of range");
   c->tune = *t;
   return SPH_OK;

@@ -65,22 +65,35 @@ __device__ __forceinline__ bool exact_within_own_h(const double *__restrict__ x,
   return r2 < __dmul_rn(h[a], h[a]);
 }
 
-// OWN_H = false: interaction partners (h_ab), lists and counts.  OWN_H = true:
-// only the number of particles within each particle's own h (the current h
-// of the state, not the packed one), plus the count of particles whose number
+// Shells (SHELL = true): the walk also records, in ascending order, every b
+// with h_ab <= r_ab < (1 + kSkin) h_ab (FP32 test with the band's margin, so
+// possibly a few more), for k_partners_refine.
+constexpr float kSkinF = (float)kSkin;
+constexpr float kShell2 = (1.0f + kSkinF) * (1.0f + kSkinF) * (1.0f + kBand);
+
+// OWN_H = false: interaction partners (h_ab), lists and counts, skipped when
+// the flag `done` is given and is 0 (it is then a run-if flag).  OWN_H = true:
+// only the number of particles within each particle's own h (the current h of
+// the state, not the packed one), plus the count of particles whose number
 // lies farther than tol from n_des (*unconverged); the walk is skipped once
 // *done is set.
-template <bool OWN_H>
+template <bool OWN_H, bool SHELL>
 __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *__restrict__ x,
                                            const double *__restrict__ y, const double *__restrict__ z,
                                            const double *__restrict__ h, int dim, int kmax,
                                            int32_t *__restrict__ nb_idx, int32_t *__restrict__ nb_cnt, int64_t ld,
                                            int32_t *err, const unsigned long long *__restrict__ grow,
                                            const Units *__restrict__ U, const int32_t *__restrict__ done,
-                                           int32_t *__restrict__ unconverged, double n_des, int tol) {
+                                           int32_t *__restrict__ unconverged, double n_des, int tol,
+                                           int32_t *__restrict__ sh_idx, int32_t *__restrict__ sh_cnt) {
+  static_assert(!(OWN_H && SHELL), "shells are partner candidates");
   if constexpr (OWN_H) {
     if (*done) return;
+  } else {
+    if (done && *done == 0) return;  // done is run_if here
   }
+  // the shell widens every test by the factor (1 + kSkin) of its radius
+  const float wide = SHELL ? 1.0f + kSkinF : 1.0f;
   __shared__ float4 sc[kNbWarps][kMaxLeaf];
   __shared__ int32_t sb[kNbWarps][kMaxLeaf];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -138,7 +151,7 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
     const unsigned lt_mask = (1u << lane) - 1u;
     const int32_t root = T.inst_root[inst];
     const int32_t stop = root >= 0 ? T.skip[root] : root;
-    int cnt = 0;
+    int cnt = 0, scnt = 0;
     int iter = 0;
     // Stackless pre-order walk over the node box words: (lo, +-hmax) and
     // (hi, skip), the sign of hmax marking the nodes where the walk stops.
@@ -149,7 +162,7 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
       float gy = fmaxf(0.f, fmaxf(bl.y - gh[1], gl[1] - bh.y));
       float gz = fmaxf(0.f, fmaxf(bl.z - gh[2], gl[2] - bh.z));
       float d2 = gx * gx + gy * gy + gz * gz;
-      float thr = (OWN_H ? hg : 0.5f * (hg + hw)) * (1.0f + 1e-5f);
+      float thr = (OWN_H ? hg : 0.5f * (hg + hw)) * (1.0f + 1e-5f) * wide;
       bool enter = false;
       if (d2 <= thr * thr) {
         if (__float_as_uint(bl.w) >> 31) {  // the walk stops here: cull its particles
@@ -168,7 +181,7 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
               float qx = fmaxf(0.f, fmaxf(rl[0] - cand.x, cand.x - rh[0]));
               float qy = fmaxf(0.f, fmaxf(rl[1] - cand.y, cand.y - rh[1]));
               float qz = fmaxf(0.f, fmaxf(rl[2] - cand.z, cand.z - rh[2]));
-              float reach = (OWN_H ? hg : 0.5f * hg + cand.w) * (1.0f + 1e-5f) + rslack;
+              float reach = (OWN_H ? hg : 0.5f * hg + cand.w) * (1.0f + 1e-5f) * wide + rslack;
               keep = qx * qx + qy * qy + qz * qz <= reach * reach;
             }
             const unsigned km = __ballot_sync(0xffffffffu, keep);
@@ -195,6 +208,11 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
                   if constexpr (!OWN_H)
                     if (cnt < kmax) nb_idx[(int64_t)cnt * ld + a] = b;
                   ++cnt;
+                } else if constexpr (SHELL) {
+                  if (b != a && r2 <= h2 * kShell2) {
+                    if (scnt < kMaxShell) sh_idx[(int64_t)scnt * ld + a] = b;
+                    ++scnt;
+                  }
                 }
               }
             }
@@ -215,16 +233,104 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
     } else if (act) {
       nb_cnt[a] = min(cnt, kmax);
       if (cnt > kmax) raise_err(err, ERR_NB_OVERFLOW);
+      if constexpr (SHELL) sh_cnt[a] = scnt <= kMaxShell ? scnt : -1;
     }
   }
 }
 
-void find_partners(sph_ctx *c, const sph_state *s, cudaStream_t st, const unsigned long long *grow) {
+// Partners at moved positions from the lists and shells of an earlier walk
+// (the Verlet-list idea applied within one step).  When every particle moved
+// by at most `move` per axis since that walk, a pair's distance changed by at
+// most 2 sqrt(D) move; with 4 sqrt(D) move <= kSkin h_a that is at most
+// kSkin h_ab (h_ab >= h_a / 2), so every partner of a at the new positions was
+// a partner or a shell candidate of a.  The old list and the shell are both
+// ascending and disjoint: merged, they are visited in ascending order, each
+// candidate is decided by the walk's predicate (FP32 outside the band, the
+// FP64 definition inside it), and the new list equals that of a walk at the
+// new positions bit for bit.  A particle whose bound does not hold, or whose
+// shell overflowed, sets *need_walk instead, and a walk follows.
+__global__ void __launch_bounds__(128)
+    k_partners_refine(PackedF32 pk, const double *__restrict__ x, const double *__restrict__ y,
+                      const double *__restrict__ z, const double *__restrict__ h, int dim, int64_t n, int64_t ld,
+                      int kmax, const int32_t *__restrict__ old_idx, const int32_t *__restrict__ old_cnt,
+                      const int32_t *__restrict__ sh_idx, const int32_t *__restrict__ sh_cnt,
+                      int32_t *__restrict__ new_idx, int32_t *__restrict__ new_cnt,
+                      const unsigned long long *__restrict__ move, int32_t *__restrict__ need_walk, int32_t *err) {
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  const int ns = sh_cnt[a];
+  const double sqd = dim == 3 ? 1.7320508075688772 : 1.4142135623730951;  // sqrt(D)
+  const double bound = __dmul_ru(__dmul_ru(4.0 * sqd, bitsd(*move)), 1.0 + 1e-6);
+  if (ns < 0 || !(bound <= __dmul_rd(kSkin, h[a]))) {
+    *need_walk = 1;
+    return;
+  }
+  const float4 P = pk.px(a), Q = pk.pxl(a);
+  const float hha = 0.5f * P.w;
+  const int nl = old_cnt[a];
+  const int ntot = nl + ns;
+  int i = 0, j = 0, cnt = 0;
+  int32_t bl = nl > 0 ? old_idx[a] : INT_MAX;
+  int32_t bs = ns > 0 ? sh_idx[a] : INT_MAX;
+  for (int k = 0; k < ntot; ++k) {
+    int32_t b;
+    if (bl < bs) {
+      b = bl;
+      ++i;
+      bl = i < nl ? old_idx[(int64_t)i * ld + a] : INT_MAX;
+    } else {
+      b = bs;
+      ++j;
+      bs = j < ns ? sh_idx[(int64_t)j * ld + a] : INT_MAX;
+    }
+    const float4 Pb = pk.px(b), Qb = pk.pxl(b);
+    const float dx = (P.x - Pb.x) + (Q.x - Qb.x), dy = (P.y - Pb.y) + (Q.y - Qb.y),
+                dz = (P.z - Pb.z) + (Q.z - Qb.z);
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float hab = hha + 0.5f * Pb.w;
+    const float h2 = hab * hab;
+    bool in;
+    if (r2 < h2 * (1.0f - kBand)) in = true;
+    else if (r2 > h2 * (1.0f + kBand)) in = false;
+    else in = exact_partner(x, y, z, h, dim, a, b);
+    if (in) {
+      if (cnt < kmax) new_idx[(int64_t)cnt * ld + a] = b;
+      ++cnt;
+    }
+  }
+  new_cnt[a] = min(cnt, kmax);
+  if (cnt > kmax) raise_err(err, ERR_NB_OVERFLOW);
+}
+
+static void walk(sph_ctx *c, const sph_state *s, cudaStream_t st, const unsigned long long *grow, int32_t *idx,
+                 int32_t *cnt, bool shell, const int32_t *run_if) {
+  const int blocks = c->num_sms * c->tune.walk_blocks_per_sm * (4 / kNbWarps);
+  if (shell)
+    k_partners<false, true><<<blocks, kNbWarps * 32, 0, st>>>(
+        c->tree, c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim, c->kmax, idx, cnt, c->cap_n, c->d_err, grow,
+        c->units, run_if, nullptr, 0.0, 0, c->sh_idx, c->sh_cnt);
+  else
+    k_partners<false, false><<<blocks, kNbWarps * 32, 0, st>>>(
+        c->tree, c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim, c->kmax, idx, cnt, c->cap_n, c->d_err, grow,
+        c->units, run_if, nullptr, 0.0, 0, nullptr, nullptr);
+  ++sph::g_launches;
+}
+
+void find_partners(sph_ctx *c, const sph_state *s, cudaStream_t st, const unsigned long long *grow, bool shell) {
   if (s->n == 0) return;
-  int blocks = c->num_sms * c->tune.walk_blocks_per_sm * (4 / kNbWarps);
-  { k_partners<false><<<blocks, kNbWarps * 32, 0, st>>>(c->tree, c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim,
-                                                     c->kmax, c->nb_idx, c->nb_cnt, c->cap_n, c->d_err, grow,
-                                                     c->units, nullptr, nullptr, 0.0, 0); ++sph::g_launches; }
+  walk(c, s, st, grow, c->nb_idx, c->nb_cnt, shell && c->sh_idx != nullptr, nullptr);
+}
+
+void refine_partners(sph_ctx *c, const sph_state *s, const unsigned long long *move, const unsigned long long *grow,
+                     cudaStream_t st) {
+  const int64_t n = s->n;
+  if (n == 0) return;
+  cudaMemsetAsync(c->need_walk, 0, sizeof(int32_t), st);
+  { k_partners_refine<<<nblk(n, 128), 128, 0, st>>>(c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim, n, c->cap_n,
+                                                   c->kmax, c->nb_idx, c->nb_cnt, c->sh_idx, c->sh_cnt, c->nb_alt,
+                                                   c->nb_cnt_alt, move, c->need_walk, c->d_err); ++sph::g_launches; }
+  // returns at once unless a particle set the flag
+  walk(c, s, st, grow, c->nb_alt, c->nb_cnt_alt, false, c->need_walk);
 }
 
 // ---------------------------------------------------------------------------
@@ -260,9 +366,10 @@ void adapt_h(sph_ctx *c, sph_state *s, double n_des, int tol, int max_iter, int3
   if (n == 0) return;
   const int blocks = c->num_sms * c->tune.walk_blocks_per_sm * (4 / kNbWarps);
   for (int i = 0; i <= max_iter; ++i) {
-    { k_partners<true><<<blocks, kNbWarps * 32, 0, st>>>(c->tree, c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim,
-                                                        c->kmax, c->nb_idx, c->nb_cnt, c->cap_n, c->d_err, nullptr,
-                                                        c->units, flags, flags + 2 + i, n_des, tol); ++sph::g_launches; }
+    { k_partners<true, false><<<blocks, kNbWarps * 32, 0, st>>>(c->tree, c->pk, s->x[0], s->x[1], s->x[2], s->h,
+                                                               s->dim, c->kmax, c->nb_idx, c->nb_cnt, c->cap_n,
+                                                               c->d_err, nullptr, c->units, flags, flags + 2 + i,
+                                                               n_des, tol, nullptr, nullptr); ++sph::g_launches; }
     if (i == max_iter) break;
     { k_h_update<<<nblk(n, 256), 256, 0, st>>>(s->h, c->nb_cnt, n, s->dim, n_des, flags + 2 + i, flags,
                                              flags + 1); ++sph::g_launches; }

@@ -18,7 +18,7 @@ extern std::atomic<int64_t> g_launches;
 
 // Phases timed by the optional profiler (CUDA events on the launch stream).
 enum { PH_TREE = 0, PH_REORDER, PH_PARTNERS, PH_DENSITY, PH_PASSA, PH_PASSB, PH_GRAVITY, PH_INTEGRATE,
-       PH_FLAW_DRAWS, PH_FLAW_FILL, PH_FOF_LINKS, PH_COUNT };
+       PH_FLAW_DRAWS, PH_FLAW_FILL, PH_FOF_LINKS, PH_REFINE, PH_COUNT };
 constexpr int kMaxProfEvents = 8192;
 
 // ---------------------------------------------------------------------------
@@ -35,6 +35,12 @@ enum : int32_t {
 constexpr int kWarp = 32;
 constexpr int kMaxLeaf = 32;
 constexpr int kMaxHIter = 64;  // most updates of one variable smoothing length iteration
+// Partner shells: a walk may also record, per particle, the candidates with
+// h_ab <= r_ab < (1 + kSkin) h_ab (at most kMaxShell of them), from which the
+// partners at positions moved by less than kSkin h / (4 sqrt D) follow
+// without a walk (neighbours.cu).
+constexpr double kSkin = 1.0 / 64.0;
+constexpr int kMaxShell = 24;
 
 // Per-particle FP32 views used by the walks and the mixed-precision passes.
 // Positions are split X = x - corner into hi = float(X), lo = float(X - hi)
@@ -170,6 +176,11 @@ struct sph_ctx {
   // partners, column-major: nb_idx[k * cap_n + a]
   int32_t *nb_idx;
   int32_t *nb_cnt;
+  int32_t *nb_alt;      // second lists and counts (partners refined from nb_idx)
+  int32_t *nb_cnt_alt;
+  int32_t *sh_idx;      // shell candidates, column-major, kMaxShell per particle
+  int32_t *sh_cnt;      // their number, -1 when more than kMaxShell
+  int32_t *need_walk;   // device flag: some particle could not refine its list
   int64_t *csr_total;   // device scalar for sph_neighbours
   int32_t *hflags;      // variable-h iteration: done, updates, off-target count per pass
   // pass A -> pass B per-particle data
@@ -307,7 +318,17 @@ void pack_f32(sph_ctx *c, const sph_state *s, cudaStream_t st);
 // neighbours.cu
 // grow (device, may be NULL): bits of a displacement bound by which every
 // particle may have left the node boxes of the current tree, per axis
-void find_partners(sph_ctx *c, const sph_state *s, cudaStream_t st, const unsigned long long *grow = nullptr);
+// shell: also record the shell candidates of every particle (sh_idx, sh_cnt)
+void find_partners(sph_ctx *c, const sph_state *s, cudaStream_t st, const unsigned long long *grow = nullptr,
+                   bool shell = false);
+// Partners of s into c->nb_alt / nb_cnt_alt from the lists and shells of the
+// last walk (nb_idx, nb_cnt, sh_idx, sh_cnt; left unchanged), whose positions
+// every particle of s left by at most `move` per axis (device bits); a walk
+// with boxes grown by `grow` recomputes every list when some particle cannot
+// refine its own.  The caller swaps the two list buffers (and the two count
+// arrays) for the passes that read the result.
+void refine_partners(sph_ctx *c, const sph_state *s, const unsigned long long *move, const unsigned long long *grow,
+                     cudaStream_t st);
 // variable smoothing length iteration; flags: device int32[max_iter + 3]
 void adapt_h(sph_ctx *c, sph_state *s, double n_des, int tol, int max_iter, int32_t *flags, cudaStream_t st);
 void partners_to_csr(sph_ctx *c, const sph_state *s, int64_t *off, int32_t *idx, int64_t cap, cudaStream_t st);

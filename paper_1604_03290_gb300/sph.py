@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "CAPACITY", 3: "NONFINITE", 4: "TIMEOU
 EOS = {"linear": 0, "murnaghan": 1, "tillotson": 2, "isothermal": 3}
 PRECISION = {"fp64": 0, "mixed": 1}
 PHASES = ("tree", "reorder", "partners", "density", "passA", "passB", "gravity", "integrate", "flaw_draws",
-          "flaw_fill", "fof_links")
+          "flaw_fill", "fof_links", "refine")
 
 
 class SphError(RuntimeError):
@@ -69,7 +69,7 @@ class State(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("walk_leaf", C.c_int32), ("walk_blocks_per_sm", C.c_int32), ("pass_threads", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("walk_every_eval", C.c_int32)]
 
 
 class Derivs(C.Structure):
@@ -225,12 +225,13 @@ class Context:
     def get_tuning(self) -> dict:
         t = Tuning()
         self.check(self._lib.sph_get_tuning(self.h, C.byref(t)), "sph_get_tuning")
-        return {"walk_leaf": t.walk_leaf, "walk_blocks_per_sm": t.walk_blocks_per_sm, "pass_threads": t.pass_threads}
+        return {"walk_leaf": t.walk_leaf, "walk_blocks_per_sm": t.walk_blocks_per_sm, "pass_threads": t.pass_threads,
+                "walk_every_eval": t.walk_every_eval}
 
     def set_tuning(self, **kw):
         cur = self.get_tuning()
         cur.update(kw)
-        t = Tuning(cur["walk_leaf"], cur["walk_blocks_per_sm"], cur["pass_threads"], 0)
+        t = Tuning(cur["walk_leaf"], cur["walk_blocks_per_sm"], cur["pass_threads"], int(cur["walk_every_eval"]))
         self.check(self._lib.sph_set_tuning(self.h, C.byref(t)), "sph_set_tuning")
 
     def profile(self, on=True):

@@ -1,0 +1,123 @@
+"""Partners of the later evaluations of a step refined from the step's first
+walk (its lists plus the candidates within (1 + 1/64) h_ab) against a tree
+walk at every evaluation: the states and time steps must be bit-identical,
+because the refined lists are the same sets in the same ascending order.
+Covered: an impact whose predictor moves particles by ~1e-4 h (the lists are
+refined), the same impact with a fixed step that moves the projectile by half
+its support radius (the bound fails and the walk runs), batched instances,
+2D rings with XSPH and artificial stress, a self-gravitating pair stepping
+with a reused tree, and the embedded Runge-Kutta step; FP64 and mixed."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+from paper_1604_03290_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1604_03290_gb300 import sph
+    return sph
+
+
+def _impact():
+    return wl.measurement_1m(seed=31, n_side=18)
+
+
+def _impact_fast():
+    ps = wl.measurement_1m(seed=33, n_side=14)
+    hp = ps.h[ps.v[2] < -1000.0].min()
+    ps.params = replace(ps.params, dt_fixed=2 * 0.5 * hp / 7000.0)
+    return ps
+
+
+def _batch():
+    ps = wl.batched_impacts(seed=5, ninst=4, nmin=400, nmax=1500)
+    ps.params = replace(ps.params, max_depth=19)
+    return ps
+
+
+def _rings():
+    ps = wl.rings_2d(artificial_stress=True)
+    ps.params = replace(ps.params, dt_fixed=0.02)
+    return ps
+
+
+def _pair_reuse():
+    ps = wl.ceres_pair(seed=4, n_each=2500)
+    ps.params = replace(ps.params, dt_fixed=2.0, tree_reuse=2)
+    return ps
+
+
+CASES = {"impact": _impact, "impact_fast": _impact_fast, "batch": _batch, "rings": _rings,
+         "pair_reuse": _pair_reuse}
+
+
+def _run(S, ps, prm, walk_every_eval, nsteps, rk3=False):
+    ctx = S.Context(ps.dim, ps.n, max_instances=max(ps.ninst, 1), max_neighbours=160, leaf_size=prm.leaf_size)
+    ctx.set_tuning(walk_every_eval=walk_every_eval)
+    ds = S.DeviceState(ps)
+    ctx.profile(True)
+    if rk3:
+        dt, t, err, acc = S.step_rk3(ctx, ds, ps.materials, prm, 1e-4, nsteps)
+        extra = [dt.cpu().numpy(), t.cpu().numpy(), err.cpu().numpy(), acc.cpu().numpy()]
+    else:
+        extra = [S.step(ctx, ds, ps.materials, prm, nsteps).cpu().numpy()]
+    phases = ctx.profile_read()
+    ctx.profile(False)
+    return ds.to_numpy(), extra, phases
+
+
+def _identical(a, b):
+    for k in ("x", "v", "rho", "u", "S", "dmg", "h", "id"):
+        if a.get(k) is None:
+            continue
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", list(CASES))
+def test_refined_steps_equal_walked_steps(S, case, prec):
+    ps = CASES[case]()
+    prm = replace(ps.params, precision=prec)
+    nsteps = 3
+    a, ea, pa = _run(S, ps, prm, 0, nsteps)
+    b, eb, pb = _run(S, ps, prm, 1, nsteps)
+    _identical(a, b)
+    for x, y in zip(ea, eb):
+        np.testing.assert_array_equal(x, y)
+    # one walk per step with refinement, two without
+    assert pa["refine"][1] == nsteps and pa["partners"][1] == nsteps
+    assert pb["refine"][1] == 0 and pb["partners"][1] == 2 * nsteps
+
+
+def test_refine_bound_holds_and_fails_where_intended(S):
+    # the predictor half-step moves every particle by at most dt/2 max|v| per
+    # axis (no XSPH): the refined lists are usable where 4 sqrt(3) of that is
+    # below h / 64, as in the impact with the limiter's step, and not in the
+    # impact with the long fixed step
+    for case, usable in (("impact", True), ("impact_fast", False)):
+        ps = CASES[case]()
+        _, (dt,), _ = _run(S, ps, replace(ps.params, precision="fp64"), 0, 1)
+        move = 0.5 * float(dt[0]) * np.abs(ps.v).max()
+        ratio = 4 * np.sqrt(3) * move / (ps.h.min() / 64)
+        assert (ratio < 0.5) if usable else (ratio > 2), (case, ratio)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_refined_rk3_equals_walked_rk3(S, prec):
+    ps = _impact()
+    prm = replace(ps.params, precision=prec)
+    a, ea, pa = _run(S, ps, prm, 0, 2, rk3=True)
+    b, eb, pb = _run(S, ps, prm, 1, 2, rk3=True)
+    _identical(a, b)
+    for x, y in zip(ea, eb):
+        np.testing.assert_array_equal(x, y)
+    assert pa["refine"][1] == 4 and pa["partners"][1] == 2
+    assert pb["refine"][1] == 0 and pb["partners"][1] == 6
