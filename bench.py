@@ -109,15 +109,17 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # Per particle and launch, from one ncu capture of the kernels as built (the
 # first right-hand side of the warm-up step, after the state is put in tree
-# order, of the 514,109-particle case of this workload, n_side 80; profiles/
-# holds the summary): warp instructions issued (smsp__inst_executed.sum) and DRAM bytes
+# order, and the refine of its predictor evaluation, of the 514,109-particle
+# case of this workload, n_side 80; profiles/ holds the summary): warp
+# instructions issued (smsp__inst_executed.sum) and DRAM bytes
 # (dram__bytes_read.sum + dram__bytes_write.sum).  Both scale with the
 # particle count at this density.  Set to None when a kernel changes and the
 # capture has not been repeated.
 NCU_PER_PARTICLE = {
-    "partners": None,  # changed (records the partner shells): capture pending
-    "passA": {"inst": 365.57, "dram": 506.52, "fp32_pipe": 0.378, "issue": 0.597},
-    "passB": {"inst": 395.24, "dram": 348.77, "fp32_pipe": 0.440, "issue": 0.628},
+    "partners": {"inst": 790.70, "dram": 349.98, "fp32_pipe": 0.269, "issue": 0.662},
+    "refine": {"inst": 137.11, "dram": 458.28, "fp32_pipe": 0.192, "issue": 0.436},
+    "passA": {"inst": 365.57, "dram": 507.89, "fp32_pipe": 0.380, "issue": 0.594},
+    "passB": {"inst": 395.25, "dram": 347.20, "fp32_pipe": 0.440, "issue": 0.627},
 }
 ISSUE_SLOTS_PER_SM = 4  # one warp instruction per clock per SM sub-partition
 
