@@ -4,7 +4,8 @@ walk at every evaluation: the states and time steps must be bit-identical,
 because the refined lists are the same sets in the same ascending order.
 Covered: an impact whose predictor moves particles by ~1e-4 h (the lists are
 refined), the same impact with a fixed step that moves the projectile by half
-its support radius (the bound fails and the walk runs), batched instances,
+its support radius (the bound fails and the walk runs), a lattice whose
+shells hold more candidates than their slots (the walk runs), batched instances,
 2D rings with XSPH and artificial stress, a self-gravitating pair stepping
 with a reused tree, and the embedded Runge-Kutta step; FP64 and mixed."""
 from dataclasses import replace
@@ -49,6 +50,16 @@ def _rings():
     return ps
 
 
+def _lattice_crowded_shell():
+    # a cubic lattice with h just below 3 dx: the 30 lattice points at 3 dx fall
+    # in every interior particle's shell, more than its 24 slots, so those
+    # particles cannot refine and the walk runs
+    ps = wl.lattice_block(seed=6, nx=12, ny=12, nz=12, jitter=0.0, h_factor=3.0 * (1.0 - 1e-4))
+    ps.v = np.random.default_rng(6).normal(0.0, 0.01, ps.v.shape)
+    ps.params = replace(ps.params, dt_fixed=0.01)
+    return ps
+
+
 def _pair_reuse():
     ps = wl.ceres_pair(seed=4, n_each=2500)
     ps.params = replace(ps.params, dt_fixed=2.0, tree_reuse=2)
@@ -56,7 +67,7 @@ def _pair_reuse():
 
 
 CASES = {"impact": _impact, "impact_fast": _impact_fast, "batch": _batch, "rings": _rings,
-         "pair_reuse": _pair_reuse}
+         "pair_reuse": _pair_reuse, "lattice_crowded_shell": _lattice_crowded_shell}
 
 
 def _run(S, ps, prm, walk_every_eval, nsteps, rk3=False):
@@ -108,6 +119,15 @@ def test_refine_bound_holds_and_fails_where_intended(S):
         move = 0.5 * float(dt[0]) * np.abs(ps.v).max()
         ratio = 4 * np.sqrt(3) * move / (ps.h.min() / 64)
         assert (ratio < 0.5) if usable else (ratio > 2), (case, ratio)
+
+
+def test_crowded_shell_exceeds_its_slots(orc):
+    # the lattice case above does overflow the shell (checked by brute force)
+    ps = _lattice_crowded_shell()
+    off, idx = orc.neighbours(ps.x, ps.h, 3, method="brute")
+    offw, idxw = orc.neighbours(ps.x, ps.h * (1.0 + 1.0 / 64.0), 3, method="brute")
+    shell = np.diff(offw) - np.diff(off)
+    assert shell.max() == 30 and (shell > 24).sum() > 100
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
