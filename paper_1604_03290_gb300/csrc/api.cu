@@ -47,10 +47,14 @@ static sph_status cuda_check(sph_ctx *c, const char *where) {
 
 template <class T>
 static T *ctx_alloc(sph_ctx *c, int64_t count, bool &ok) {
-  if (!ok) return nullptr;
+  constexpr int kMaxAllocs = (int)(sizeof(c->allocs) / sizeof(c->allocs[0]));
+  if (!ok || c->nallocs >= kMaxAllocs) {
+    ok = false;
+    return nullptr;
+  }
   void *p = nullptr;
   size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
-  if (cudaMalloc(&p, bytes) != cudaSuccess || c->nallocs >= 256) {
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
     ok = false;
     return nullptr;
   }
