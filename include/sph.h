@@ -143,10 +143,13 @@ typedef struct sph_ctx sph_ctx;
  * walk_blocks_per_sm: resident blocks per SM of the persistent walk grids
  * (1..32).  pass_threads: threads per block of the neighbour passes (64 or 128).
  * walk_every_eval: 0 (default) lets the later evaluations of one sph_step or
- * sph_step_rk3 step without gravity take their partners from the step's first
- * walk, which also records each particle's candidates within (1 + 1/64) h_ab,
- * whenever no particle moved by 1/64 h / (4 sqrt D) or more per axis (else
- * they walk); 1 walks the tree at every evaluation (Sect. 3.5.2 as printed). */
+ * sph_step_rk3 step that reuse its tree take their partners from the step's
+ * first walk, which also records each particle's candidates within
+ * (1 + 1/64) h_ab, as long as the largest per-axis displacement of any
+ * particle since that walk is at most h_a / (256 sqrt D) for every particle a
+ * and no particle has more than 24 such candidates (else they walk); the
+ * lists are the same either way.  1 walks the tree at every evaluation
+ * (Sect. 3.5.2 as printed). */
 typedef struct {
   int32_t walk_leaf;
   int32_t walk_blocks_per_sm;
