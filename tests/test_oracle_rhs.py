@@ -270,3 +270,42 @@ def test_rings_bounce_with_artificial_stress(orc):
     assert dE < 0.05
     assert nbmin >= 3          # no particle broke loose
     assert res[False][1] < 0.0  # without artificial stress they are still entangled
+
+
+def test_xsph_two_particle_closed_form(orc):
+    # Sect. 3.1.5: dx_a/dt = v_a + eps sum_b 2 m_b / (rho_a + rho_b) (v_b - v_a) W_ab;
+    # for two particles the sum has one term (the kernel itself is pinned above)
+    mat = wl.Material(eos="linear", rho0=1.0, cs=1.0)
+    for dim in (2, 3):
+        x = np.zeros((dim, 2))
+        x[0, 1] = 0.37
+        v = np.zeros((dim, 2))
+        v[:, 0] = 0.3
+        v[-1, 1] = -0.2
+        rho, m, h = np.array([1.0, 1.4]), np.array([0.7, 1.9]), np.array([1.0, 0.8])
+        eps = 0.5
+        ps = wl.ParticleSet(dim=dim, x=x, v=v, rho=rho, u=np.zeros(2), m=m, h=h, mat=np.zeros(2, np.int32),
+                            id=np.arange(2, dtype=np.int32), materials=[mat],
+                            params=wl.Params(dim=dim, consistency=False, xsph=eps))
+        out = orc.rhs(ps, [mat], ps.params)
+        w = float(orc.W(0.37, 0.9, dim))
+        for a, b in ((0, 1), (1, 0)):
+            want = v[:, a] + eps * 2 * m[b] / (rho[a] + rho[b]) * (v[:, b] - v[:, a]) * w
+            np.testing.assert_allclose(out["dxdt"][:, a], want, rtol=1e-14, atol=1e-16)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_xsph_vanishes_for_uniform_flow_and_conserves_momentum(orc, dim):
+    ps = _random_state(9, dim, n_side=9 if dim == 3 else 20, strength=False)
+    ps.params = replace(ps.params, xsph=0.5)
+    ps.v = np.repeat(np.array([0.3, -0.2, 0.1])[:dim, None], ps.n, 1)
+    out = orc.rhs(ps, ps.materials, ps.params)
+    np.testing.assert_array_equal(out["dxdt"], ps.v)  # every difference v_b - v_a is exactly 0
+    ps = _random_state(10, dim, n_side=9 if dim == 3 else 20, strength=False)
+    ps.params = replace(ps.params, xsph=0.5)
+    out = orc.rhs(ps, ps.materials, ps.params)
+    corr = out["dxdt"] - ps.v
+    # the pair terms are antisymmetric (h_ab, W_ab and the mean density are symmetric)
+    tot = (ps.m * corr).sum(1)
+    scale = (ps.m * np.abs(corr)).sum(1).max()
+    assert scale > 0 and np.abs(tot).max() <= 1e-13 * scale
