@@ -309,3 +309,51 @@ def test_xsph_vanishes_for_uniform_flow_and_conserves_momentum(orc, dim):
     tot = (ps.m * corr).sum(1)
     scale = (ps.m * np.abs(corr)).sum(1).max()
     assert scale > 0 and np.abs(tot).max() <= 1e-13 * scale
+
+
+def _rot3(rng):
+    q, r = np.linalg.qr(rng.normal(size=(3, 3)))
+    return q * np.sign(np.diag(r))
+
+
+def test_artificial_stress_two_particle_closed_form(orc):
+    # Sect. 3.1.4: each particle's tensile principal stresses sigma_i > 0 give
+    # zeta_i = -eps_s sigma_i / rho^2 in the principal frame, and the pair adds
+    # m_b (zeta_a + zeta_b) f^n grad_a W to dv_a/dt with f = W(r) / W(dmpd);
+    # the energy equation does not see it.  Stresses from numpy's eigh, not
+    # the oracle's Jacobi rotations.
+    rng = np.random.default_rng(12)
+    # two materials at their reference densities (zero pressure, so sigma = S)
+    mats = [wl.Material(eos="linear", rho0=1.3, cs=1.0, K0=1.0, mu=0.5, strength=True),
+            wl.Material(eos="linear", rho0=0.8, cs=1.0, K0=1.0, mu=0.5, strength=True)]
+    rho, m, h = np.array([1.3, 0.8]), np.array([0.8, 1.3]), np.array([1.0, 1.2])
+    x = np.array([[0.0, 0.45], [0.0, 0.1], [0.0, -0.05]])
+    v = np.array([[-0.01, 0.02], [0.0, 0.01], [0.0, 0.0]])  # receding: no artificial viscosity
+    S = []
+    for a in range(2):
+        R = _rot3(rng)
+        S.append(R @ np.diag([0.3, -0.05, -0.25] if a == 0 else [0.2, 0.1, -0.3]) @ R.T)
+    comp = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    Svec = np.array([[S[a][i, j] for a in range(2)] for i, j in comp])
+    eps_s, n_as, dmpd = 0.3, 4.0, 0.5
+    base = dict(dim=3, x=x, v=v, rho=rho, u=np.zeros(2), m=m, h=h, S=Svec, mat=np.array([0, 1], np.int32),
+                id=np.arange(2, dtype=np.int32), materials=mats)
+    p0 = wl.Params(dim=3, consistency=False, n_as=n_as, dmpd=dmpd)
+    off = orc.rhs(wl.ParticleSet(params=p0, **base), mats, p0)
+    p1 = replace(p0, eps_s=eps_s)
+    on = orc.rhs(wl.ParticleSet(params=p1, **base), mats, p1)
+    assert (v[:, 0] - v[:, 1]) @ (x[:, 0] - x[:, 1]) > 0
+    zeta = []
+    for a in range(2):
+        lam, Q = np.linalg.eigh(S[a])
+        zeta.append(Q @ np.diag(np.where(lam > 0, -eps_s * lam / rho[a] ** 2, 0.0)) @ Q.T)
+    d = x[:, 0] - x[:, 1]
+    r = np.linalg.norm(d)
+    hab = 0.5 * (h[0] + h[1])
+    fn = (float(orc.W(r, hab, 3)) / float(orc.W(dmpd, hab, 3))) ** n_as
+    g = float(orc.dWdr(r, hab, 3)) * d / r
+    for a, b, sgn in ((0, 1, 1.0), (1, 0, -1.0)):
+        want = m[b] * (zeta[a] + zeta[b]) @ (sgn * g) * fn
+        np.testing.assert_allclose(on["dv"][:, a] - off["dv"][:, a], want, rtol=1e-12, atol=1e-15)
+    np.testing.assert_array_equal(on["du"], off["du"])
+    assert np.abs(on["dv"] - off["dv"]).max() > 1e-6  # the term is not negligible here
