@@ -357,3 +357,31 @@ def test_artificial_stress_two_particle_closed_form(orc):
         np.testing.assert_allclose(on["dv"][:, a] - off["dv"][:, a], want, rtol=1e-12, atol=1e-15)
     np.testing.assert_array_equal(on["du"], off["du"])
     assert np.abs(on["dv"] - off["dv"]).max() > 1e-6  # the term is not negligible here
+
+
+def test_artificial_viscosity_two_particle_closed_form(orc):
+    # Sect. 3.1.3: for an approaching pair nu = h_ab v_ab.x_ab / (r^2 + eps_v h_ab^2),
+    # Pi = (-alpha cbar nu + beta nu^2) / rhobar with the mean sound speed and
+    # density; with zero stress dv_a/dt = -m_b Pi grad_a W and
+    # du_a/dt = 1/2 m_b Pi v_ab.grad_a W
+    mats = [wl.Material(eos="linear", rho0=1.3, cs=0.9), wl.Material(eos="linear", rho0=0.8, cs=1.7)]
+    rho, m, h = np.array([1.3, 0.8]), np.array([0.8, 1.3]), np.array([1.0, 1.2])
+    x = np.array([[0.0, 0.45], [0.0, 0.1], [0.0, -0.05]])
+    v = np.array([[0.2, -0.1], [0.05, 0.0], [0.0, 0.03]])
+    alpha, beta, eps_v = 1.1, 2.3, 0.01
+    prm = wl.Params(dim=3, consistency=False, alpha=alpha, beta=beta, eps_v=eps_v)
+    ps = wl.ParticleSet(dim=3, x=x, v=v, rho=rho, u=np.zeros(2), m=m, h=h, mat=np.array([0, 1], np.int32),
+                        id=np.arange(2, dtype=np.int32), materials=mats, params=prm)
+    out = orc.rhs(ps, mats, prm)
+    d, w = x[:, 0] - x[:, 1], v[:, 0] - v[:, 1]
+    assert w @ d < 0  # approaching
+    r2 = d @ d
+    hab = 0.5 * (h[0] + h[1])
+    nu = hab * (w @ d) / (r2 + eps_v * hab ** 2)
+    Pi = (-alpha * 0.5 * (0.9 + 1.7) * nu + beta * nu ** 2) / (0.5 * (rho[0] + rho[1]))
+    g = float(orc.dWdr(np.sqrt(r2), hab, 3)) * d / np.sqrt(r2)
+    for a, b, sgn in ((0, 1, 1.0), (1, 0, -1.0)):
+        ga = sgn * g
+        wab = sgn * w
+        np.testing.assert_allclose(out["dv"][:, a], -m[b] * Pi * ga, rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(out["du"][a], 0.5 * m[b] * Pi * (wab @ ga), rtol=1e-12)
