@@ -69,6 +69,31 @@ def test_rigid_rotation_co_rotates_the_stress(orc, dim):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
+def test_hooke_and_jaumann_for_a_linear_flow(orc, dim):
+    # Sect. 2.4: for v = G x + c the corrected gradient is exact, so
+    # dS/dt = 2 mu (eps - tr(eps)/D I) + R S - S R with eps = (G + G^T)/2 and
+    # R = (G - G^T)/2, for a uniform S (no yield limit, no damage)
+    ps = _random_state(21, dim, n_side=9 if dim == 3 else 16)
+    n = ps.n
+    rng = np.random.default_rng(22)
+    G = rng.normal(size=(dim, dim)) * 1e-2
+    ps.v = G @ ps.x + rng.normal(size=(dim, 1))
+    S0 = rng.normal(size=(dim, dim)) * 1e-3
+    S0 = S0 + S0.T
+    S0 -= np.trace(S0) / dim * np.eye(dim)
+    comps = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)] if dim == 3 else [(0, 0), (1, 1), (0, 1)]
+    ps.S = np.array([np.full(n, S0[i, j]) for i, j in comps])
+    mu = ps.materials[0].mu
+    eps = 0.5 * (G + G.T)
+    R = 0.5 * (G - G.T)
+    expect = 2 * mu * (eps - np.trace(eps) / dim * np.eye(dim)) + R @ S0 - S0 @ R
+    out = orc.rhs(ps, ps.materials, ps.params)
+    scale = np.abs(expect).max()
+    for k, (i, j) in enumerate(comps):
+        assert np.abs(out["dS"][k] - expect[i, j]).max() < 1e-10 * scale, (i, j)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
 def test_deviatoric_rate_is_trace_free(orc, dim):
     ps = _random_state(3, dim, n_side=8 if dim == 3 else 14)
     out = orc.rhs(ps, ps.materials, ps.params)
