@@ -53,3 +53,58 @@ def test_argument_errors_need_no_device(libsph):
         getattr(libsph, f).restype = C.c_int
     assert libsph.sph_rhs(None, None, None, 0, None, None, None) == SPH_ERR_INVALID
     assert libsph.sph_neighbours(None, None, 16, 21, None, None, C.c_int64(0), None) == SPH_ERR_INVALID
+
+
+STRUCTS = {"sph_material": "Material", "sph_params": "Params", "sph_state": "State", "sph_derivs": "Derivs",
+           "sph_tuning": "Tuning"}
+
+
+def _c_fields(struct):
+    """Field names of a typedef'd struct in the header, in order."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    body = dict((n, b) for b, n in re.findall(r"typedef struct \{([^{}]*)\}\s*(\w+);", text))[struct]
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        for part in decl.split(","):
+            m = re.search(r"\**\s*([A-Za-z_][A-Za-z0-9_]*)\s*(\[[^\]]*\])?\s*$", part.strip())
+            names.append(m.group(1))
+    return names
+
+
+def test_header_is_plain_c_and_the_binding_matches_its_layout(tmp_path):
+    # the header compiles as C99 on its own, and every ctypes mirror in the
+    # binding has the C struct's size and field offsets
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_1604_03290_gb300 import sph
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "sph.h"', "int main(void) {"]
+    for cs in STRUCTS:
+        lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (cs, cs))
+        for f in _c_fields(cs):
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cs, f, cs, f))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            a, b, c = line.split()
+            got[(a, b)] = int(c)
+    for cs, py in STRUCTS.items():
+        cls = getattr(sph, py)
+        assert C.sizeof(cls) == got[(cs, "size")], cs
+        cfields = _c_fields(cs)
+        assert [f[0] for f in cls._fields_] == cfields, cs
+        for f in cfields:
+            assert getattr(cls, f).offset == got[(cs, f)], (cs, f)
