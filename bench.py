@@ -137,9 +137,9 @@ def algorithmic_bytes(phase, K, n_flaw_mean, dim=3):
         return 64 + 32 + 4 + 4 * K + 8 * dim + 8  # packs, T pack, list; dv, du
     if phase == "partners":
         # positions, perm, slot; list and count; the shell list of the step's
-        # later evaluations (partners within (1 + 1/64) h_ab but not h_ab: at
-        # most ((1 + 1/64)^D - 1) K of them for uniformly spread neighbours;
-        # the bench lattice has fewer) and its count
+        # later evaluations (partners within (1 + 1/64) h_ab but not h_ab: about
+        # ((1 + 1/64)^D - 1) K of them for uniformly spread neighbours; fewer
+        # on the bench lattice) and its count
         shell = ((1.0 + 1.0 / 64.0) ** dim - 1.0) * K
         return 32 + 4 + 4 + 4 * K + 4 + 4 * shell + 4
     if phase == "refine":
