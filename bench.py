@@ -217,7 +217,7 @@ def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3, cloud_n=2_000_000, with
                                 "sample": "the same call on the host (%.1f s)" % sec}
     del dsf, lab, cnt, mass, ctxf
 
-    # gravity/hydro decoupling (Sect. 5): the 2M-particle collapsing cloud,
+    # gravity/hydro decoupling (Sect. 6.3): the 2M-particle collapsing cloud,
     # steps that build a tree per evaluation against steps that reuse one
     # tree (and its pseudo-particles) over 4 steps
     cl = wl.cloud_collapse(seed=3, n=cloud_n)

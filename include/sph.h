@@ -93,7 +93,7 @@ typedef struct {
   int32_t tree_reuse;     /* sph_step: > 0 lets the tree built at a step start
                              serve every evaluation of this many consecutive
                              steps (gravity from its pseudo-particles: the
-                             gravity/hydro decoupling of Sect. 5; partners stay
+                             gravity/hydro decoupling of Sect. 6.3; partners stay
                              exact); 0: with gravity, a tree per evaluation.
                              Variable h builds every step; each call starts
                              with a build.                                  */
@@ -224,8 +224,9 @@ sph_status sph_neighbours(sph_ctx *ctx, const sph_state *state, int32_t leaf_siz
  * no cudaMalloc, cudaFree or other allocating routine.
  *
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current) and keeps it; make that
- * first call before any stream capture.  All calls on a device share the
+ * (cudaGetSymbolAddress, with that device current) and keeps it for the life
+ * of the process; make that first call before any stream capture.  After
+ * cudaDeviceReset the array may move: calls after a reset are not supported.  All calls on a device share the
  * array and it keeps the last call's contents (each call clears its own error
  * word): calls whose work overlaps on the GPU, from two streams or two host
  * threads, race and corrupt each other's results, so serialise them.  Blocks

@@ -50,7 +50,7 @@ typedef struct {
   double n_des;                   /* > 0: variable h (Sect. 4.2) at the start of each step */
   int32_t h_tol, h_iter;          /* its count tolerance and most updates   */
   int32_t tree_reuse;             /* > 0: with gravity, one tree (and its pseudo-particles) serves the
-                                     evaluations of this many consecutive steps (Sect. 5); 0: a tree per
+                                     evaluations of this many consecutive steps (Sect. 6.3); 0: a tree per
                                      evaluation */
   int32_t pad2;
 } orc_params;

@@ -1686,7 +1686,7 @@ int32_t orc_step(orc_state *s, const orc_material *mats, int32_t nmat, const orc
   dstore_alloc(&d1, dim, n);
   int rc = 0;
   int32_t *hcnt = P->n_des > 0.0 ? (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t)) : NULL;
-  /* Decoupled self-gravity (tree_reuse = R > 0, Sect. 5): the tree built at */
+  /* Decoupled self-gravity (tree_reuse = R > 0, Sect. 6.3): the tree built at */
   /* the start of a step serves every evaluation of R consecutive steps; its */
   /* pseudo-particles are reused (positions of the build kept in xb).  With  */
   /* variable h every step builds.  A call starts with a build.             */

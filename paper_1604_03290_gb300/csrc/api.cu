@@ -561,7 +561,7 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
   // and reuses its tree, the walk widening its boxes by the displacement
   // since the build.  Gravity's multipole sums depend on the tree: each
   // evaluation builds one, unless tree_reuse = R > 0 (the gravity/hydro
-  // decoupling of Sect. 5), when the tree of a step start serves every
+  // decoupling of Sect. 6.3), when the tree of a step start serves every
   // evaluation of R consecutive steps with its pseudo-particles (and, for the
   // partner search, boxes widened by the summed displacement bounds).
   const int R = p->tree_reuse > 0 ? p->tree_reuse : 0;

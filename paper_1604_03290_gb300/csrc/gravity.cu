@@ -13,7 +13,7 @@
 // (the paper's Eq. gravitational_force read as attractive, with Plummer
 // softening).
 //
-// Reused tree (gravity/hydro decoupling, Sect. 5): the pseudo-particles,
+// Reused tree (gravity/hydro decoupling, Sect. 6.3): the pseudo-particles,
 // node cubes and leaf membership are those of the build, the particle's cell
 // is recomputed from its current position in the build's root cube, and
 // leaves are summed at the members' current positions (the packed views are

@@ -1,5 +1,5 @@
 """Steps that reuse one tree over several steps (tree_reuse; the
-gravity/hydro decoupling of Sect. 5) against the oracle stepping with the
+gravity/hydro decoupling of Sect. 6.3) against the oracle stepping with the
 same reuse: a self-gravitating cloud (pseudo-particles of the build, leaves
 at current positions), a pair of self-gravitating basalt bodies with
 strength and damage, an impact without gravity (partners stay exact, so

@@ -1,5 +1,5 @@
 """Pins of the oracle's Barnes-Hut evaluation with reused pseudo-particles
-(the gravity/hydro decoupling of Sect. 5): the tree, node masses and centres
+(the gravity/hydro decoupling of Sect. 6.3): the tree, node masses and centres
 of mass come from the build positions, containment from the particle's
 current cell, leaves are summed at current positions.  Pinned by: theta = 0
 (no pseudo-particle is used) equals the direct sum at the current positions
