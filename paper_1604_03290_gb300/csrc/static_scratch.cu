@@ -140,8 +140,10 @@ extern "C" sph_status sph_neighbours_static(const sph_state *s, int32_t leaf_siz
   }
   if (leaf_size < 1 || leaf_size > kMaxLeaf)
     return report(&c, msg, msg_len, SPH_ERR_INVALID, "leaf_size must be in 1..32");
+  // bits of the instance id in a key; 64-bit shifts, so any int32 ninst ends
+  // the loop (at most 31 bits)
   int ibits = 0;
-  while ((1 << ibits) < ninst) ++ibits;
+  while (((int64_t)1 << ibits) < (int64_t)ninst) ++ibits;
   if (max_depth < 1 || max_depth > 21 || s->dim * max_depth + ibits > 64)
     return report(&c, msg, msg_len, SPH_ERR_INVALID,
                   "max_depth must be in 1..21 with dim * max_depth + log2(ninst) <= 64");

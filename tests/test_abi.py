@@ -108,3 +108,25 @@ def test_header_is_plain_c_and_the_binding_matches_its_layout(tmp_path):
         assert [f[0] for f in cls._fields_] == cfields, cs
         for f in cfields:
             assert getattr(cls, f).offset == got[(cs, f)], (cs, f)
+
+
+def test_static_entry_rejects_huge_instance_counts_on_the_host(libsph):
+    # ninst = INT32_MAX needs 31 instance bits, more than a 3D key at depth 21
+    # leaves: SPH_ERR_INVALID from argument checks, before any device call
+    from paper_1604_03290_gb300 import sph
+    SPH_ERR_INVALID = 1
+    st = sph.State()
+    st.dim, st.ninst, st.n = 3, 2 ** 31 - 1, 10
+    dummy = C.c_double(0.0)
+    for ax in range(3):
+        st.x[ax] = st.v[ax] = C.cast(C.byref(dummy), C.c_void_p)
+    st.rho = st.u = st.m = st.h = st.inst_off = C.cast(C.byref(dummy), C.c_void_p)
+    f = libsph.sph_neighbours_static
+    f.restype = C.c_int
+    f.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64, C.c_char_p,
+                  C.c_int32, C.c_void_p]
+    msg = C.create_string_buffer(256)
+    out = C.c_int64(0)
+    r = f(C.byref(st), 16, 21, 64, C.byref(out), C.byref(out), 0, msg, 256, None)
+    assert r == SPH_ERR_INVALID
+    assert b"max_depth" in msg.value

@@ -68,3 +68,36 @@ def test_static_partner_overflow_is_reported_then_cleared(S):
     off, idx = S.neighbours_static(ds, leaf, depth, kmax)  # the error word of the last call is not carried over
     np.testing.assert_array_equal(off.cpu().numpy(), ro)
     np.testing.assert_array_equal(idx.cpu().numpy(), ri)
+
+
+def test_static_calls_leave_device_free_memory_unchanged(S):
+    """The promise itself: with the state and the outputs allocated up front
+    (the caller's buffers), calls in a row change neither the device's free
+    memory (cudaMemGetInfo) nor what torch's caching allocator holds.  The
+    first call of the process may load the library's device code, array
+    included, so one call runs before the readings start."""
+    import ctypes as C
+
+    import torch
+    name, ps, leaf, depth, kmax = _cases()[0]
+    ds = S.DeviceState(ps)
+    S.neighbours_static(ds, leaf, depth, kmax)  # loads the module on this device
+    cap = ps.n * kmax
+    off = torch.zeros(ps.n + 1, dtype=torch.int64, device="cuda")
+    idx = torch.zeros(cap, dtype=torch.int32, device="cuda")
+    st = ds.struct()
+    msg = C.create_string_buffer(512)
+    lib = S.lib()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    reserved0 = torch.cuda.memory_reserved()
+    for _ in range(3):
+        r = lib.sph_neighbours_static(C.byref(st), leaf, depth, kmax, C.c_void_p(off.data_ptr()),
+                                      C.c_void_p(idx.data_ptr()), cap, msg, len(msg), None)
+        assert r == S.SPH_OK, msg.value
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert torch.cuda.memory_reserved() == reserved0
+    ro, ri = _with_context(S, ps, leaf, depth, kmax)
+    np.testing.assert_array_equal(off.cpu().numpy(), ro)
+    np.testing.assert_array_equal(idx[: ri.size].cpu().numpy(), ri)
