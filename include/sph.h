@@ -149,12 +149,18 @@ typedef struct sph_ctx sph_ctx;
  * particle since that walk is at most h_a / (256 sqrt D) for every particle a
  * and no particle has more than 24 such candidates (else they walk); the
  * lists are the same either way.  1 walks the tree at every evaluation
- * (Sect. 3.5.2 as printed). */
+ * (Sect. 3.5.2 as printed).  iter_cap: 0 (default) bounds each tree walk
+ * (partner search and gravity) by the number of tree nodes and each find of
+ * the friends-of-friends union by 2^24 pointer steps; a positive value lowers
+ * both bounds to iter_cap.  A walk or find that reaches its bound stops and
+ * the call returns SPH_ERR_TIMEOUT; a positive value exists to make that
+ * happen on purpose (tests of the timeout report). */
 typedef struct {
   int32_t walk_leaf;
   int32_t walk_blocks_per_sm;
   int32_t pass_threads;
   int32_t walk_every_eval;
+  int32_t iter_cap;
 } sph_tuning;
 
 /* Creates a context for up to max_particles particles in up to

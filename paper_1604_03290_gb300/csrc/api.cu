@@ -85,6 +85,7 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   c->tune.walk_blocks_per_sm = 16;
   c->tune.pass_threads = 128;
   c->tune.walk_every_eval = 0;
+  c->tune.iter_cap = 0;
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   if (c->num_sms < 1) c->num_sms = 1;
   const int64_t N = max_particles;
@@ -782,9 +783,10 @@ sph_status sph_set_tuning(sph_ctx *c, const sph_tuning *t) {
   if (!c || !t) return SPH_ERR_INVALID;
   const int pt = t->pass_threads;
   if (t->walk_leaf < 8 || t->walk_leaf > 1024 || t->walk_blocks_per_sm < 1 || t->walk_blocks_per_sm > 32 ||
-      !(pt == 64 || pt == 128) || (t->walk_every_eval != 0 && t->walk_every_eval != 1))
+      !(pt == 64 || pt == 128) || (t->walk_every_eval != 0 && t->walk_every_eval != 1) || t->iter_cap < 0)
     return fail(c, SPH_ERR_INVALID, "tuning out of range");
   c->tune = *t;
+  c->tree.iter_cap = t->iter_cap;
   return SPH_OK;
 }
 

@@ -31,13 +31,13 @@ __global__ void k_fof_init(const double *__restrict__ h0, const double *__restri
 
 // Representative of x, halving the path on the way (every pointer only ever
 // moves to an ancestor, and roots are only changed by the hook below).
-__device__ __forceinline__ int32_t fof_rep(int32_t *parent, int32_t x, int &steps) {
+__device__ __forceinline__ int32_t fof_rep(int32_t *parent, int32_t x, int &steps, int limit) {
   int32_t cur = __ldcg(parent + x);
   if (cur == x) return x;
   int32_t prev = x;
   for (;;) {
     const int32_t next = __ldcg(parent + cur);
-    if (next == cur || ++steps > kFindLimit) break;
+    if (next == cur || ++steps > limit) break;
     parent[prev] = next;
     prev = cur;
     cur = next;
@@ -46,7 +46,7 @@ __device__ __forceinline__ int32_t fof_rep(int32_t *parent, int32_t x, int &step
 }
 
 __global__ void k_fof_union(int32_t *parent, const int32_t *__restrict__ nb_idx, const int32_t *__restrict__ nb_cnt,
-                            int64_t ld, int64_t n, int32_t *err) {
+                            int64_t ld, int64_t n, int limit, int32_t *err) {
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= n || __ldcg(parent + a) < 0) return;
   const int k = nb_cnt[a];
@@ -54,12 +54,12 @@ __global__ void k_fof_union(int32_t *parent, const int32_t *__restrict__ nb_idx,
   // a's representative is kept across its pairs.  It may go stale (hooked
   // by another thread); a hook on it then fails and it is found again, and
   // hooking a root under it is still a union with a's set.
-  int32_t ra = fof_rep(parent, (int32_t)a, steps);
+  int32_t ra = fof_rep(parent, (int32_t)a, steps, limit);
   for (int i = 0; i < k; ++i) {
     const int32_t b = nb_idx[(int64_t)i * ld + a];
     if (b <= a || __ldcg(parent + b) < 0) continue;  // each pair once, survivors only
-    int32_t rb = fof_rep(parent, b, steps);
-    while (ra != rb && steps <= kFindLimit) {
+    int32_t rb = fof_rep(parent, b, steps, limit);
+    while (ra != rb && steps <= limit) {
       const int32_t hi = ra > rb ? ra : rb, lo = ra > rb ? rb : ra;
       const int32_t old = atomicCAS(parent + hi, hi, lo);
       if (old == hi) {  // hooked: lo now represents both sets
@@ -68,10 +68,10 @@ __global__ void k_fof_union(int32_t *parent, const int32_t *__restrict__ nb_idx,
       }
       // hi was hooked elsewhere meanwhile: continue from its new representative
       ++steps;
-      if (hi == ra) ra = fof_rep(parent, old, steps);
-      else rb = fof_rep(parent, old, steps);
+      if (hi == ra) ra = fof_rep(parent, old, steps, limit);
+      else rb = fof_rep(parent, old, steps, limit);
     }
-    if (steps > kFindLimit) {
+    if (steps > limit) {
       raise_err(err, ERR_TIMEOUT);
       return;
     }
@@ -81,12 +81,12 @@ __global__ void k_fof_union(int32_t *parent, const int32_t *__restrict__ nb_idx,
 // parent[i] <- root, and the component's count and mass (no hooks run now,
 // so the reads only ever see ancestors; each thread writes its own entry)
 __global__ void k_fof_roots(int32_t *parent, const double *__restrict__ m, int64_t n, int32_t *cnt, double *mass,
-                            int32_t *err) {
+                            int limit, int32_t *err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int32_t r = __ldcg(parent + i);
   if (r < 0) return;
-  for (int s = 0; s < kFindLimit; ++s) {
+  for (int s = 0; s < limit; ++s) {
     const int32_t p = __ldcg(parent + r);
     if (p == r) break;
     r = p;
@@ -157,6 +157,7 @@ void fragments_fof(sph_ctx *c, const sph_state *s, const double *h0, double b, d
   { k_fof_init<<<nblk(n, 256), 256, 0, st>>>(h0 ? h0 : s->h, s->dmg, n, b, d_remove, hq, parent); ++g_launches; }
   sph_state q = *s;
   q.h = hq;
+  const int limit = c->tune.iter_cap > 0 ? c->tune.iter_cap : kFindLimit;
   int pr = prof_begin(c, st, PH_TREE);
   tree_build(c, &q, leaf_size, max_depth, st);
   prof_end(c, st, pr);
@@ -164,10 +165,10 @@ void fragments_fof(sph_ctx *c, const sph_state *s, const double *h0, double b, d
   find_partners(c, &q, st);
   prof_end(c, st, pr);
   pr = prof_begin(c, st, PH_FOF_LINKS);
-  { k_fof_union<<<nblk(n, 128), 128, 0, st>>>(parent, c->nb_idx, c->nb_cnt, c->cap_n, n, c->d_err); ++g_launches; }
+  { k_fof_union<<<nblk(n, 128), 128, 0, st>>>(parent, c->nb_idx, c->nb_cnt, c->cap_n, n, limit, c->d_err); ++g_launches; }
   cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), st);
   cudaMemsetAsync(mass, 0, sizeof(double) * n, st);
-  { k_fof_roots<<<nblk(n, 256), 256, 0, st>>>(parent, s->m, n, cnt, mass, c->d_err); ++g_launches; }
+  { k_fof_roots<<<nblk(n, 256), 256, 0, st>>>(parent, s->m, n, cnt, mass, limit, c->d_err); ++g_launches; }
   { k_fof_flag<<<nblk(n + 1, 256), 256, 0, st>>>(parent, cnt, n, min_size, pos); ++g_launches; }
   scan_counts(c, pos, pos, n + 1, st);
   int32_t nf = 0;

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kGrWarps * 32, SPH_GRAV_MIN_BLOCKS) k_gravity(
   const int ngroups = chunks ? (int)((T.n + 31) >> 5) : *T.ngroups;
   constexpr int dim = DIM;
   const int L = T.leaf_size, B = T.max_depth;
-  const int nnodes = *T.nnodes;
+  const int nnodes = T.iter_cap > 0 ? min(*T.nnodes, T.iter_cap) : *T.nnodes;
   const int64_t cap = T.cap_nodes;
   const double Gs = MIXED ? A.G * A.U->M * A.U->T * A.U->T * A.U->invL * A.U->invL * A.U->invL : A.G;
   const R G = (R)Gs;

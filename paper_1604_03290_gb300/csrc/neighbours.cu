@@ -101,7 +101,7 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
   // The walk stops at nodes flagged in their box word (at most
   // max(leaf_size, walk_leaf) particles, or depth B; set by the tree build)
   // and culls their whole particle range: any stopping rule gives the same set.
-  const int nnodes = *T.nnodes;
+  const int nnodes = T.iter_cap > 0 ? min(*T.nnodes, T.iter_cap) : *T.nnodes;
   // Node boxes are those of the tree the walk runs on; when the particles have
   // moved since it was built (by at most `grow` per axis), widening the
   // group's box by that much keeps every node that may hold a partner.

@@ -100,6 +100,7 @@ struct Tree {
   int leaf_size, max_depth, dim, ninst;
   int64_t n;
   int perm_identity;   // host flag: the state is in tree order (perm[i] = i)
+  int iter_cap;        // > 0: node visits of one walk are bounded by this instead of the node count
 };
 
 struct MatTable {
