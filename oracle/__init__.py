@@ -78,7 +78,8 @@ class Derivs(C.Structure):
                 ("drho", _dp), ("du", _dp), ("dS", _dp), ("ddmg", _dp), ("p", _dp), ("cs", _dp),
                 ("n_act", _ip), ("nnb", _ip), ("mag_drho", _dp), ("mag_dv", _dp), ("mag_du", _dp),
                 ("mag_gradv", _dp), ("mag1_drho", _dp), ("mag1_dv", _dp), ("mag1_du", _dp), ("mag1_gradv", _dp),
-                ("mag_rho", _dp), ("mag1_rho", _dp), ("gradv", _dp), ("agx", _dp), ("agy", _dp), ("agz", _dp)]
+                ("mag_rho", _dp), ("mag1_rho", _dp), ("gradv", _dp), ("agx", _dp), ("agy", _dp), ("agz", _dp),
+                ("eps_t", _dp)]
 
 
 def lib():
@@ -201,7 +202,7 @@ def _derivs(dim, n, ns):
         "mag_dv": np.zeros(n), "mag_du": np.zeros(n), "mag_gradv": np.zeros(n),
         "gradv": np.zeros((dim * dim, n)), "ag": np.zeros((dim, n)), "mag1_drho": np.zeros(n),
         "mag1_dv": np.zeros(n), "mag1_du": np.zeros(n), "mag1_gradv": np.zeros(n), "mag_rho": np.zeros(n),
-        "mag1_rho": np.zeros(n),
+        "mag1_rho": np.zeros(n), "eps_t": np.zeros(n),
     }
     d = Derivs()
     d.dxdt, d.dydt = _p(out["dxdt"][0]), _p(out["dxdt"][1])
@@ -217,6 +218,7 @@ def _derivs(dim, n, ns):
     d.mag1_gradv, d.mag_rho, d.mag1_rho = _p(out["mag1_gradv"]), _p(out["mag_rho"]), _p(out["mag1_rho"])
     d.agx, d.agy = _p(out["ag"][0]), _p(out["ag"][1])
     d.agz = _p(out["ag"][2]) if dim == 3 else _p(None)
+    d.eps_t = _p(out["eps_t"])
     return d, out
 
 

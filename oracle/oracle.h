@@ -91,6 +91,7 @@ typedef struct {
   double *mag1_drho, *mag1_dv, *mag1_du, *mag1_gradv, *mag_rho, *mag1_rho;
   double *gradv;           /* corrected velocity gradient, D*D per particle,  component-major */
   double *agx, *agy, *agz; /* gravitational acceleration alone               */
+  double *eps_t;           /* local strain of the damage model, sigma_max / ((1 - d) E); 0 without damage */
 } orc_derivs;
 
 /* Kernel (Sect. 3.1.1) */

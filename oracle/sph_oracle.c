@@ -1041,7 +1041,7 @@ static int rhs_instance(orc_state *s, const orc_material *mats, int nmat, const 
     }
 
     /* Damage, Sects. 2.7 and 3.2: sigma_d = -p_hat I + (1 - d) S */
-    double dmgd = 0.0, dd = 0.0;
+    double dmgd = 0.0, dd = 0.0, eps_t = 0.0;
     int nact = 0;
     int damage = s->dmg != NULL && M->damage;
     if (damage) {
@@ -1067,6 +1067,7 @@ static int rhs_instance(orc_state *s, const orc_material *mats, int nmat, const 
       double smax = lam[dim - 1];
       double den = (1.0 - dmgd) * E;
       double eps = den > 0.0 ? smax / den : 0.0;
+      eps_t = eps;
       int64_t id = s->id ? s->id[a] : a;
       int64_t f0 = s->flaw_off ? s->flaw_off[id] : 0, f1 = s->flaw_off ? s->flaw_off[id + 1] : 0;
       int64_t ntot = f1 - f0;
@@ -1112,6 +1113,7 @@ static int rhs_instance(orc_state *s, const orc_material *mats, int nmat, const 
     if (d->dS && any_strength) sym_store(dim, dS, d->dS, n, a);
     if (d->ddmg) d->ddmg[a] = dd;
     if (d->n_act) d->n_act[a] = nact;
+    if (d->eps_t) d->eps_t[a] = eps_t;
     if (d->p) d->p[a] = p;
     if (d->cs) d->cs[a] = cs;
     if (d->nnb) d->nnb[a] = nnb;
@@ -1264,6 +1266,7 @@ static orc_derivs derivs_view(const orc_derivs *d, int64_t lo) {
   v.agx = SHIFT(d->agx, lo);
   v.agy = SHIFT(d->agy, lo);
   v.agz = SHIFT(d->agz, lo);
+  v.eps_t = SHIFT(d->eps_t, lo);
   v.dS = NULL;
   v.gradv = NULL;
   return v;

@@ -63,3 +63,53 @@ def compare_rhs(ps, o, g, tol, fields=("drho", "dv", "du", "dS", "dxdt", "p", "c
     bad = {k: v for k, v in errs.items() if not v <= tol}
     assert not bad, "fields over tolerance %g: %s (all: %s)" % (tol, bad, errs)
     return errs
+
+
+def check_damage(ps, o, g, prec, tol, report=None):
+    """Activated flaws and damage growth (Sects. 2.7, 3.2) against the oracle.
+
+    FP64: n_act equal everywhere.  Mixed: the constitutive update runs in
+    FP32, so the local strain eps = sigma_max / ((1 - d) E) carries an error of
+    its own; a count may differ only where every threshold counted by one side
+    and not the other lies within that error of the oracle's eps:
+        |eps_j - eps| <= (|p_gpu - p| + 2^-18 ((1 - d) |S|_F + |p|)) / ((1 - d) E) + 2^-20 |eps|,
+    i.e. the particle's own pressure difference (bounded by the pressure test)
+    plus 64 FP32 roundings of the stress magnitude for the eigen-solve and 16
+    of eps itself.  Where the counts agree, d(d^1/3)/dt matches to the field
+    tolerance; where they differ it must be the growth of the GPU's count,
+    n_act c_g / h (R16, R17) while d < n_act / n_tot, else 0."""
+    if ps.dmg is None:
+        return
+    n_g, n_o = np.asarray(g["n_act"]), np.asarray(o["n_act"])
+    same = n_g == n_o
+    scale = np.abs(o["ddmg"]).max() + 1e-300
+    if prec == "fp64":
+        assert same.all(), "n_act differs on %d particles" % (~same).sum()
+    bad = np.flatnonzero(~same)
+    u32 = 2.0 ** -24
+    mats = ps.materials
+    off, thr = np.asarray(ps.flaw_off), np.asarray(ps.flaw_eps, np.float64)
+    ids = np.asarray(ps.id)
+    expect = np.array(g["ddmg"], np.float64, copy=True)
+    for a in bad:
+        M = mats[int(ps.mat[a])]
+        dd = float(ps.dmg[a]) ** 3
+        E = 9 * M.K0 * M.mu / (3 * M.K0 + M.mu)
+        den = (1 - dd) * E
+        Sf = float(np.sqrt((ps.S[:, a] ** 2).sum() + (ps.S[ps.dim:, a] ** 2).sum())) if ps.S is not None else 0.0
+        delta = (abs(g["p"][a] - o["p"][a]) + 64 * u32 * ((1 - dd) * Sf + abs(o["p"][a]))) / den + \
+            16 * u32 * abs(o["eps_t"][a])
+        t = thr[off[ids[a]]:off[ids[a] + 1]]
+        lo, hi = min(n_g[a], n_o[a]), max(n_g[a], n_o[a])
+        e = max(o["eps_t"][a], 0.0)
+        assert np.all(np.abs(t[lo:hi] - e) <= delta), \
+            "particle %d: n_act %d vs %d, eps %.9g, thresholds %s, bound %.3g" % (a, n_g[a], n_o[a], e, t[lo:hi], delta)
+        ntot = len(t)
+        rate = 0.4 * np.sqrt((M.K0 + 4.0 / 3.0 * (1 - dd) * M.mu) / ps.rho[a]) / ps.h[a]
+        expect[a] = n_g[a] * rate if (n_g[a] > 0 and dd < n_g[a] / ntot) else 0.0
+    err_same = float(np.abs(g["ddmg"] - o["ddmg"])[same].max() / scale) if same.any() else 0.0
+    err_flip = float(np.abs(g["ddmg"] - expect)[bad].max() / scale) if bad.size else 0.0
+    if report is not None:
+        report.update({"n_act_flips": int(bad.size), "ddmg_same": err_same, "ddmg_flipped": err_flip})
+    assert err_same <= 10 * tol, err_same
+    assert err_flip <= 10 * tol, err_flip
