@@ -1,0 +1,162 @@
+"""Long runs: the mixed-precision step against the FP64 step over hundreds of
+steps, where FP32 pair sums could drift apart, and a reduced copy of the
+impact against the FP64 oracle.
+
+* Aluminium sphere into the aluminium cube (Sect. 4.3 geometry, 64^3 cube +
+  sphere, 263k particles), 500 predictor-corrector steps in each precision on
+  one time grid (the FP64 run's device-computed steps, replayed as fixed
+  steps by the mixed run).  Crater depth, read as the projectile's
+  mass-weighted mean depth below the target's top face (a smooth measure of
+  how far the crater floor has been pushed down), must agree to 1e-3 of its
+  change over the run.
+* The same impact at 16^3 + sphere, 40 steps, GPU in both precisions against
+  the oracle on the oracle's own time grid.
+* The rotating isothermal cloud with self-gravity (Sect. 4.2 set-up, 50k
+  particles), 1,000 steps in each precision on one time grid: total energy
+  (kinetic + internal + softened potential), linear and angular momentum.
+  Their drifts are reported for both precisions; the mixed run's drift must
+  stay within a few times the FP64 run's own.
+"""
+import math
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+from paper_1604_03290_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1604_03290_gb300 import sph
+    return sph
+
+
+def _ctx(S, ps, kmax=128):
+    return S.Context(ps.dim, ps.n, max_instances=max(ps.ninst, 1), max_neighbours=kmax,
+                     leaf_size=ps.params.leaf_size)
+
+
+def _by_id(d):
+    order = np.argsort(d["id"])
+    return {k: (None if v is None else v[..., order]) for k, v in d.items()}
+
+
+def _run(S, ps, prec, nsteps, dts=None, kmax=128):
+    """nsteps single steps; dts=None: device-computed steps (returned), else
+    the given steps as fixed ones.  Returns (state by id, dt list)."""
+    ctx = _ctx(S, ps, kmax)
+    ds = S.DeviceState(ps)
+    P = replace(ps.params, precision=prec)
+    out = []
+    for i in range(nsteps):
+        Pi = P if dts is None else replace(P, dt_fixed=float(dts[i]))
+        dt = S.step(ctx, ds, ps.materials, Pi, 1)
+        out.append(float(dt[0].item()) if dts is None else float(dts[i]))
+    return _by_id(ds.to_numpy()), out
+
+
+def _crater_depth(x, m, proj, z_top=0.0):
+    mp = m * proj
+    return z_top - float((mp * x[2]).sum() / mp.sum())
+
+
+def _field_errors(a, b, init):
+    errs = {}
+    for f in ("x", "v", "rho", "u", "S", "dmg"):
+        if b.get(f) is None:
+            continue
+        change = np.abs(b[f] - init[f]).max() + 1e-300
+        errs[f] = float(np.abs(a[f] - b[f]).max() / change)
+    return errs
+
+
+def test_impact_crater_depth_500_steps_mixed_vs_fp64(S):
+    ps = wl.al_impact()
+    nc = 64 ** 3
+    proj = (np.arange(ps.n) >= nc).astype(np.float64)
+    init = {"x": ps.x, "v": ps.v, "rho": ps.rho, "u": ps.u, "S": ps.S, "dmg": None}
+    g64, dts = _run(S, ps, "fp64", 500)
+    gmx, _ = _run(S, ps, "mixed", 500, dts=dts)
+    d0 = _crater_depth(ps.x, ps.m, proj)
+    d64 = _crater_depth(g64["x"], g64["m"], proj)
+    dmx = _crater_depth(gmx["x"], gmx["m"], proj)
+    rel = abs(dmx - d64) / abs(d64 - d0)
+    errs = _field_errors(gmx, g64, init)
+    print("crater depth: t = %.4g s, start %.6g m, fp64 %.9g m, mixed %.9g m, rel. to change %.3g; fields %s"
+          % (sum(dts), d0, d64, dmx, rel, errs))
+    assert d64 > d0  # the projectile has moved into the target
+    assert rel <= 1e-3
+
+
+def test_impact_reduced_40_steps_against_oracle(S, orc):
+    ps = wl.al_impact(n_side=16)
+    nc = 16 ** 3
+    proj = (np.arange(ps.n) >= nc).astype(np.float64)
+    init = {"x": ps.x, "v": ps.v, "rho": ps.rho, "u": ps.u, "S": ps.S, "dmg": None}
+    ost, olog = orc.step(ps, ps.materials, ps.params, 40)
+    dts = olog[:, 0]
+    d0 = _crater_depth(ps.x, ps.m, proj)
+    do = _crater_depth(ost["x"], ps.m, proj)
+    for prec, tol_depth, tol_field in (("fp64", 1e-9, 1e-8), ("mixed", 1e-3, 1e-3)):
+        g, _ = _run(S, ps, prec, 40, dts=dts)
+        dg = _crater_depth(g["x"], g["m"], proj)
+        rel = abs(dg - do) / abs(do - d0)
+        errs = _field_errors(g, ost, init)
+        print("reduced impact %s: depth oracle %.9g gpu %.9g rel %.3g; fields %s" % (prec, do, dg, rel, errs))
+        assert rel <= tol_depth
+        assert max(errs.values()) <= tol_field, errs
+
+
+def _energy_momenta(st, G, eps_grav):
+    """(E, P, L): E = sum m (v^2/2 + u) + W with the pair potential
+    -G m_a m_b / sqrt(r^2 + (eps_a^2 + eps_b^2)/2), eps = eps_grav h (direct
+    sum in FP64 on the device, a diagnostic only); P and L about the origin."""
+    import torch
+    x = torch.as_tensor(st["x"], device="cuda")
+    v = torch.as_tensor(st["v"], device="cuda")
+    m = torch.as_tensor(st["m"], device="cuda")
+    e2 = (eps_grav * torch.as_tensor(st["h"], device="cuda")) ** 2
+    ekin = float((0.5 * m * (v ** 2).sum(0)).sum())
+    eint = float((m * torch.as_tensor(st["u"], device="cuda")).sum())
+    n = m.numel()
+    W = 0.0
+    for s in range(0, n, 2048):
+        xs = x[:, s:s + 2048]
+        r2 = ((xs[:, :, None] - x[:, None, :]) ** 2).sum(0)
+        q = r2 + 0.5 * (e2[s:s + 2048, None] + e2[None, :])
+        inv = torch.rsqrt(q)
+        idx = torch.arange(s, min(s + 2048, n), device="cuda")
+        inv[idx - s, idx] = 0.0
+        W += float(-0.5 * G * (m[s:s + 2048, None] * m[None, :] * inv).sum())
+    P = (m * v).sum(1).cpu().numpy()
+    L = torch.linalg.cross(x.T, v.T).mul(m[:, None]).sum(0).cpu().numpy()
+    return ekin + eint + W, P, L, (ekin, eint, W)
+
+
+def test_cloud_1000_steps_drift_mixed_vs_fp64(S):
+    ps = wl.cloud_collapse(seed=3, n=50_000)
+    G, eg = ps.params.G, ps.params.eps_grav
+    st0 = {"x": ps.x, "v": ps.v, "m": ps.m, "h": ps.h, "u": ps.u}
+    E0, P0, L0, parts0 = _energy_momenta(st0, G, eg)
+    g64, dts = _run(S, ps, "fp64", 1000, kmax=160)
+    gmx, _ = _run(S, ps, "mixed", 1000, dts=dts, kmax=160)
+    res = {}
+    for name, g in (("fp64", g64), ("mixed", gmx)):
+        E, P, L, parts = _energy_momenta(g, G, eg)
+        Pscale = float((ps.m * np.sqrt((ps.v ** 2).sum(0))).sum())
+        res[name] = {"dE_rel": (E - E0) / abs(parts0[2]), "dP_rel": float(np.abs(P - P0).max() / Pscale),
+                     "dLz_rel": float((L[2] - L0[2]) / abs(L0[2]))}
+    t_ff = math.sqrt(3 * math.pi / (32 * G * (3 * ps.m.sum() / (4 * math.pi * 3.2e14 ** 3))))
+    print("cloud 50k, 1000 steps to t = %.4g s (%.3g t_ff): %s" % (sum(dts), sum(dts) / t_ff, res))
+    # linear momentum: pair forces are antisymmetric, gravity only to the
+    # Barnes-Hut error; angular momentum and energy drift with the walk's
+    # truncation and the time step.  The mixed run may not drift by more than
+    # a few times the FP64 run plus a floor of FP32 resolution.
+    for k in ("dE_rel", "dLz_rel", "dP_rel"):
+        assert abs(res["mixed"][k]) <= 4 * abs(res["fp64"][k]) + 1e-5, (k, res)
