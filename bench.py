@@ -113,14 +113,32 @@ class ClockSampler:
 # case of this workload, n_side 80; profiles/ holds the summary): warp
 # instructions issued (smsp__inst_executed.sum) and DRAM bytes
 # (dram__bytes_read.sum + dram__bytes_write.sum).  Both scale with the
-# particle count at this density.  Set to None when a kernel changes and the
-# capture has not been repeated.
+# particle count at this density.  "src" is the first 16 hex digits of the
+# SHA-256 of the kernel's source file at capture time: when the file differs
+# now, the figures are stale and are not used (the kernel is then reported
+# against HBM alone, with traffic null).
 NCU_PER_PARTICLE = {
-    "partners": {"inst": 790.70, "dram": 349.98, "fp32_pipe": 0.269, "issue": 0.662},
-    "refine": {"inst": 137.11, "dram": 458.28, "fp32_pipe": 0.192, "issue": 0.436},
-    "passA": {"inst": 365.57, "dram": 507.89, "fp32_pipe": 0.380, "issue": 0.594},
-    "passB": {"inst": 395.25, "dram": 347.20, "fp32_pipe": 0.440, "issue": 0.627},
+    "partners": {"inst": 790.70, "dram": 349.98, "fp32_pipe": 0.269, "issue": 0.662,
+                 "src": ("neighbours.cu", "d6c10fd598ed2997")},
+    "refine": {"inst": 137.11, "dram": 458.28, "fp32_pipe": 0.192, "issue": 0.436,
+               "src": ("neighbours.cu", "d6c10fd598ed2997")},
+    "passA": {"inst": 365.57, "dram": 507.89, "fp32_pipe": 0.380, "issue": 0.594,
+              "src": ("rhs.cu", "61cd28223971269a")},
+    "passB": {"inst": 395.25, "dram": 347.20, "fp32_pipe": 0.440, "issue": 0.627,
+              "src": ("rhs.cu", "61cd28223971269a")},
 }
+
+
+def ncu_figures(phase):
+    """The captured per-particle figures of `phase` if its source is unchanged."""
+    import hashlib
+    c = NCU_PER_PARTICLE.get(phase)
+    if not c:
+        return None
+    fn, sha = c["src"]
+    with open(os.path.join(ROOT, "paper_1604_03290_gb300", "csrc", fn), "rb") as f:
+        now = hashlib.sha256(f.read()).hexdigest()[:16]
+    return c if now == sha else None
 ISSUE_SLOTS_PER_SM = 4  # one warp instruction per clock per SM sub-partition
 
 
@@ -354,6 +372,45 @@ def host_steps(sph, ctx, ds, host, materials, prm, nsteps, stream):
     stream.wait_stream(down)
 
 
+def field_errors(sph, ctx, ps, prm):
+    """Mixed against FP64 on the GPU, per field, on the measured state: one
+    right-hand side each (max |mixed - fp64| over max |fp64| of the field, and
+    the particles whose activated-flaw count differs), then one
+    predictor-corrector step each on the same time step (the FP64 step's),
+    compared by particle id relative to each field's change over the step."""
+    import numpy as np
+    from dataclasses import replace
+    outs = {}
+    for prec in ("mixed", "fp64"):
+        ds = sph.DeviceState(ps)
+        o = sph.rhs(ctx, ds, ps.materials, replace(prm, precision=prec))
+        outs[prec] = {k: v.cpu().numpy() for k, v in o.items()}
+        del ds, o
+    rhs = {}
+    for f in ("drho", "dv", "du", "dS", "dxdt", "p", "cs", "ddmg"):
+        a, b = outs["mixed"][f].astype(np.float64), outs["fp64"][f].astype(np.float64)
+        rhs[f] = float(np.abs(a - b).max() / (np.abs(b).max() + 1e-300))
+    rhs["n_act_differs"] = int((outs["mixed"]["n_act"] != outs["fp64"]["n_act"]).sum())
+    states = {}
+    dt = None
+    for prec in ("fp64", "mixed"):
+        ds = sph.DeviceState(ps)
+        p = replace(prm, precision=prec) if dt is None else replace(prm, precision=prec, dt_fixed=dt)
+        d = sph.step(ctx, ds, ps.materials, p, 1)
+        dt = float(d[0].item()) if dt is None else dt
+        g = ds.to_numpy()
+        order = np.argsort(g["id"])
+        states[prec] = {k: g[k][..., order] for k in ("x", "v", "rho", "u", "S", "dmg")}
+        del ds
+    init = {"x": ps.x, "v": ps.v, "rho": ps.rho, "u": ps.u, "S": ps.S, "dmg": ps.dmg}
+    step = {}
+    for f in init:
+        change = np.abs(states["fp64"][f] - init[f]).max() + 1e-300
+        step[f] = float(np.abs(states["mixed"][f] - states["fp64"][f]).max() / change)
+    return {"rhs_max_over_field_max": rhs, "step_max_over_field_change": step, "dt": dt,
+            "what": "mixed vs FP64 GPU on the measured state: one right-hand side, and one step on the same dt"}
+
+
 def reduce_max_ms(ms, dist, device):
     """The slowest rank's time: every rank runs its own replica, and the job
     takes as long as the slowest (max over ranks; NCCL on GPUs, gloo on CPU)."""
@@ -371,25 +428,32 @@ def replica_value(world, units_per_rank, steps, ms):
     return world * units_per_rank * steps / (ms * 1e-3)
 
 
-def cpu_baseline(n_side, steps=1):
+def cpu_baseline(n_side, steps=1, repeats=3):
+    """The oracle's predictor-corrector step on the host cores: one untimed
+    warm-up call, then the median of `repeats` timed calls of `steps` steps."""
     import oracle
     from paper_1604_03290_gb300 import workloads as wl
     oracle.build()
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
     oracle.set_threads(cores)
     ps = wl.measurement_1m(seed=11, n_side=n_side)
-    t0 = time.perf_counter()
-    oracle.step(ps, ps.materials, ps.params, steps)
-    dt = time.perf_counter() - t0
+    oracle.step(ps, ps.materials, ps.params, 1)
+    ts = []
+    for _ in range(max(repeats, 1)):
+        t0 = time.perf_counter()
+        oracle.step(ps, ps.materials, ps.params, steps)
+        ts.append(time.perf_counter() - t0)
+    dt = statistics.median(ts)
     return {"value": ps.n * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "same physics at %d^3 cube particles (%d particles), %d predictor-corrector step(s), "
-                      "%.1f s on %d host threads" % (n_side, ps.n, steps, dt, cores), "seconds": dt}
+            "sample": "same physics at %d^3 cube particles (%d particles), %d predictor-corrector step(s) per call, "
+                      "median of %d calls after a warm-up call: %.2f s on %d host threads"
+                      % (n_side, ps.n, steps, len(ts), dt, cores), "seconds": dt}
 
 
 def run_reference(args, rank):
     if rank != 0:
         return
-    base = cpu_baseline(args.cpu_side, steps=max(args.steps, 1))
+    base = cpu_baseline(args.cpu_side, steps=max(args.steps, 1), repeats=1)
     line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * base["seconds"] / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -503,7 +567,8 @@ def main():
              "hbm": {"achieved": ab / (launch_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                      "frac": ab / (launch_ms * 1e-3) / 1e9 / hbm_peak,
                      "bytes_per_particle": algorithmic_bytes(phase, K, n_flaw)}}
-        c = NCU_PER_PARTICLE.get(phase)
+        c = ncu_figures(phase)
+        r["ncu_current"] = c is not None
         if c:
             ginst = c["inst"] * n / (launch_ms * 1e-3) / 1e9
             r["issue"] = {"achieved": ginst, "peak": issue_peak, "unit": "G warp-instructions/s",
@@ -571,6 +636,8 @@ def main():
     e2e = {"value": replica_value(world, n, e2e_steps, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
 
+    ferr = field_errors(sph, ctx, ps, prm) if rank == 0 else None
+
     aux = (aux_rows(sph, wl, ctx, ps, stream, hbm_peak, cloud_n=args.cloud_n,
                     with_oracle=rank == 0 and not args.no_cpu) if not args.no_aux else None)
 
@@ -590,6 +657,7 @@ def main():
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "fp64": fp64,
                 "speedup_mixed_over_fp64": (value / world / fp64["value"]) if fp64 else None,
+                "field_errors": ferr,
                 "phases": phase_report, "next_rows": aux}
         print(json.dumps(line), flush=True)
     if dist is not None:
