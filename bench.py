@@ -1,10 +1,13 @@
 #!/usr/bin/env python
 """Throughput of the SPH predictor-corrector step on GB300.
 
-One step = tree build, state reorder, partner search, both neighbour passes
-with the constitutive update, the device-side time step and the predictor
-update, then tree, partners and passes again at the predicted state and the
-corrector update (sph_step).  Workload: aluminium sphere into aluminium cube,
+One step = partner search, both neighbour passes with the constitutive
+update, the device-side time step and the predictor update, then partners and
+passes again at the predicted state and the corrector update (sph_step).  A
+tree (and the state's order along it) serves --tree-reuse consecutive steps
+(default 4): the step that builds it walks it for the partners, and every
+later evaluation of the window refines those lists, exactly, while the
+particles' displacement allows (else it walks).  Workload: aluminium sphere into aluminium cube,
 Tillotson EOS, strength, von Mises yield and Grady-Kipp damage, 100^3 cube
 particles plus a 1 cm projectile (1,004,189 particles), with a perturbed state
 so every branch runs.  Metric: particle-updates per second.
@@ -41,12 +44,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n-side", type=int, default=100)
-    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=8)
     ap.add_argument("--cpu-side", type=int, default=100, help="cube side of the CPU-baseline sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-aux", action="store_true", help="skip timing the flaw and fragment steps")
     ap.add_argument("--only-aux", action="store_true", help="time only the flaw, fragment and decoupling legs")
     ap.add_argument("--cloud-n", type=int, default=2_000_000, help="particles of the decoupling leg's cloud")
+    ap.add_argument("--tree-reuse", type=int, default=4,
+                    help="steps one tree serves (partners refined from the build step's walk); 0: a tree per step")
     return ap.parse_args()
 
 
@@ -350,6 +355,7 @@ def host_steps(sph, ctx, ds, host, materials, prm, nsteps, stream):
     synchronising."""
     import torch
     outs = [k for k in ("x", "v", "rho", "u", "m", "h", "S", "dmg", "mat", "id") if host.get(k) is not None]
+    cont = prm.tree_reuse > 0
     up, down = torch.cuda.Stream(), torch.cuda.Stream()
     got = {k: torch.cuda.Event() for k in outs}
     ready, done = torch.cuda.Event(), torch.cuda.Event()
@@ -362,7 +368,9 @@ def host_steps(sph, ctx, ds, host, materials, prm, nsteps, stream):
                 getattr(ds, k).copy_(host[k], non_blocking=True)
             ready.record(up)
         stream.wait_event(ready)
-        sph.step(ctx, ds, materials, prm, 1, check=False)
+        # each call continues the tree window of the last (the state it
+        # uploads is the one the last call returned, which the call checks)
+        sph.step(ctx, ds, materials, prm, 1, check=False, cont=cont and it > 0)
         done.record(stream)
         down.wait_event(done)
         with torch.cuda.stream(down):
@@ -494,7 +502,7 @@ def main():
 
     ps = wl.measurement_1m(seed=11, n_side=args.n_side)
     n = ps.n
-    prm = replace(ps.params, precision="mixed")
+    prm = replace(ps.params, precision="mixed", tree_reuse=args.tree_reuse)
     ctx = sph.Context(3, n, max_neighbours=128, leaf_size=prm.leaf_size)
     stream = torch.cuda.current_stream()
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -518,8 +526,7 @@ def main():
 
     # ---- device-resident throughput (mixed) ----
     ds = sph.DeviceState(ps)
-    for _ in range(args.warmup):
-        sph.step(ctx, ds, ps.materials, prm, 1, check=False)
+    sph.step(ctx, ds, ps.materials, prm, args.warmup, check=False)
     ctx.sync_status()
     clocks = ClockSampler(local)
     barrier()
@@ -531,8 +538,8 @@ def main():
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     e0.record(stream)
-    for _ in range(args.steps):
-        sph.step(ctx, ds, ps.materials, prm, 1, check=False)
+    # the K steps in one call (a tree serves tree_reuse consecutive steps)
+    sph.step(ctx, ds, ps.materials, prm, args.steps, check=False)
     e1.record(stream)
     e1.synchronize()
     launches = sph.launch_count() - l0
@@ -651,6 +658,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32 pair/f64 state (mixed)", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n_particles": n, "mean_partners": K,
+                           "tree_reuse": args.tree_reuse,
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "inputs larger than L2 (state %.0f MB, partner lists %.0f MB)" %
                                  (144 * n / 1e6, 4 * K * n / 1e6)},

@@ -94,10 +94,24 @@ typedef struct {
                              serve every evaluation of this many consecutive
                              steps (gravity from its pseudo-particles: the
                              gravity/hydro decoupling of Sect. 6.3; partners stay
-                             exact); 0: with gravity, a tree per evaluation.
-                             Variable h builds every step; each call starts
-                             with a build.                                  */
-  int32_t pad2;
+                             exact, refined from the build step's walk
+                             while the displacement bound allows, see
+                             sph_tuning); the state is reordered only at a
+                             build.  0: with gravity, a tree per evaluation;
+                             without, a tree per step.  Variable h builds
+                             every step; each call starts with a build,
+                             unless tree_continue.                          */
+  int32_t tree_continue;  /* sph_step with tree_reuse > 0: 1 continues the
+                             window of R steps that the previous call on the
+                             context left (its age, tree, partner lists and
+                             displacement bound), so a window may span calls.
+                             The state must hold the positions and h that
+                             call returned, in the same slots (as after
+                             copying the state out and back); the call checks
+                             them bit for bit (blocking on the stream) and
+                             returns SPH_ERR_INVALID if they differ or if
+                             another call used the context in between.
+                             Ignored when tree_reuse = 0 or n_des > 0.      */
 } sph_params;
 
 /* Particle state (device pointers).  S and dmg may be NULL.  Flaw thresholds
@@ -142,13 +156,15 @@ typedef struct sph_ctx sph_ctx;
  * this many particles and tests their whole particle range (8..1024).
  * walk_blocks_per_sm: resident blocks per SM of the persistent walk grids
  * (1..32).  pass_threads: threads per block of the neighbour passes (64 or 128).
- * walk_every_eval: 0 (default) lets the later evaluations of one sph_step or
- * sph_step_rk3 step that reuse its tree take their partners from the step's
- * first walk, which also records each particle's candidates within
- * (1 + 1/64) h_ab, as long as the largest per-axis displacement of any
- * particle since that walk is at most h_a / (256 sqrt D) for every particle a
- * and no particle has more than 24 such candidates (else they walk); the
- * lists are the same either way.  1 walks the tree at every evaluation
+ * walk_every_eval: 0 (default) lets the evaluations that reuse a tree take
+ * their partners from the last walk on it (within one sph_step or
+ * sph_step_rk3 step, the step's first walk; across the steps that share a
+ * tree under tree_reuse, the walk of the step that built it), which also
+ * records each particle's candidates within (1 + 1/64) h_ab, as long as the
+ * summed bound on the largest per-axis displacement of any particle since
+ * that walk is at most h_a / (256 sqrt D) for every particle a and no
+ * particle has more than 24 such candidates (else they walk); the lists are
+ * the same either way.  1 walks the tree at every evaluation
  * (Sect. 3.5.2 as printed).  iter_cap: 0 (default) bounds each tree walk
  * (partner search and gravity) by the number of tree nodes and each find of
  * the friends-of-friends union by 2^24 pointer steps; a positive value lowers

@@ -190,6 +190,8 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   S.dt = ctx_alloc<double>(c, ci, ok);
   S.gather = ctx_alloc<double>(c, N, ok);
   S.gather_i = ctx_alloc<int32_t>(c, N, ok);
+  for (int k = 0; k < 4; ++k) S.snap[k] = ctx_alloc<double>(c, N, ok);
+  S.differ = ctx_alloc<int32_t>(c, 1, ok);
   FlawBufs &F = c->fl;
   F.cap_groups = (int64_t)ci * SPH_MAX_MATERIALS;
   F.cap_plan = (int)F.cap_groups;
@@ -256,6 +258,10 @@ sph_status sph_sync_status(sph_ctx *c, void *stream) {
 
 static sph_status check_state(sph_ctx *c, const sph_state *s) {
   if (!c || !s) return SPH_ERR_INVALID;
+  // any call may rebuild the tree or rewrite the partner lists: the window a
+  // previous sph_step left is only kept for an sph_step that continues it
+  c->win_was = c->win_valid;
+  c->win_valid = false;
   if (s->dim != c->dim) return fail(c, SPH_ERR_INVALID, "state dim differs from the context's");
   if (s->n < 0 || s->n > c->cap_n) return fail(c, SPH_ERR_INVALID, "n exceeds the context capacity");
   int ninst = s->ninst > 0 ? s->ninst : 1;
@@ -448,6 +454,7 @@ sph_status sph_flaws(sph_ctx *c, const sph_state *s, const sph_material *mats, i
                      const double *weibull_m, uint64_t seed, int64_t *flaw_off, float *flaw_eps,
                      int64_t eps_capacity, int64_t *nflaws, void *stream) {
   if (!c || !s) return SPH_ERR_INVALID;
+  c->win_valid = false;  // its sort runs on the tree's scratch
   if (s->n < 0 || s->n > c->cap_n) return fail(c, SPH_ERR_INVALID, "n exceeds the context capacity");
   const int ninst = s->ninst > 0 ? s->ninst : 1;
   if (ninst > c->cap_inst) return fail(c, SPH_ERR_INVALID, "ninst exceeds the context capacity");
@@ -522,6 +529,59 @@ sph_status sph_gravity(sph_ctx *c, const sph_state *s, const sph_params *p, doub
   return finish(c, p, st, "sph_gravity");
 }
 
+// *differ = 1 when a position or h of the state differs (bit for bit) from
+// the copy the last sph_step call kept (s0..s3: x, y, z or unused, h)
+__global__ void k_differs(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+                          const double *__restrict__ h, const double *__restrict__ s0, const double *__restrict__ s1,
+                          const double *__restrict__ s2, const double *__restrict__ s3, int dim, int64_t n,
+                          int32_t *differ) {
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  bool d = __double_as_longlong(x[a]) != __double_as_longlong(s0[a]) ||
+           __double_as_longlong(y[a]) != __double_as_longlong(s1[a]) ||
+           __double_as_longlong(h[a]) != __double_as_longlong(s3[a]);
+  if (dim == 3) d = d || __double_as_longlong(z[a]) != __double_as_longlong(s2[a]);
+  if (d) *differ = 1;
+}
+
+// Checks the promise of params.tree_continue: the previous call on c was an
+// sph_step that left a tree window with the same settings, and the state's
+// positions and h are those it returned.  Blocks on the stream.
+static sph_status check_continue(sph_ctx *c, const sph_state *s, const sph_params *p, cudaStream_t st) {
+  const int ninst = s->ninst > 0 ? s->ninst : 1;
+  if (!c->win_was || c->win_R != p->tree_reuse || c->win_n != s->n || c->win_ninst != ninst ||
+      c->win_leaf != p->leaf_size || c->win_depth != p->max_depth || c->win_gravity != (p->gravity != 0))
+    return fail(c, SPH_ERR_INVALID,
+                "tree_continue: the previous call on this context was not an sph_step with the same tree_reuse, "
+                "n, instances, leaf_size, max_depth and gravity setting");
+  if (s->n == 0) return SPH_OK;
+  StepBufs &B = c->st;
+  cudaMemsetAsync(B.differ, 0, sizeof(int32_t), st);
+  { k_differs<<<nblk(s->n, 256), 256, 0, st>>>(s->x[0], s->x[1], s->dim == 3 ? s->x[2] : s->x[0], s->h, B.snap[0],
+                                              B.snap[1], B.snap[2], B.snap[3], s->dim, s->n, B.differ); ++g_launches; }
+  int32_t d = 0;
+  cudaMemcpyAsync(&d, B.differ, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check(c, "sph_step");
+  if (d) return fail(c, SPH_ERR_INVALID, "tree_continue: positions or h differ from those the previous sph_step returned");
+  return SPH_OK;
+}
+
+// Keeps what a later call needs to continue the tree window of this one.
+static void keep_window(sph_ctx *c, const sph_state *s, const sph_params *p, int age, cudaStream_t st) {
+  StepBufs &B = c->st;
+  const int64_t n = s->n;
+  for (int k = 0; k < s->dim; ++k) cudaMemcpyAsync(B.snap[k], s->x[k], sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(B.snap[3], s->h, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  c->win_valid = true;
+  c->win_age = age;
+  c->win_R = p->tree_reuse;
+  c->win_n = n;
+  c->win_ninst = s->ninst > 0 ? s->ninst : 1;
+  c->win_leaf = p->leaf_size;
+  c->win_depth = p->max_depth;
+  c->win_gravity = p->gravity != 0;
+}
+
 sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t nmat, const sph_params *p, double *dt,
                     int32_t nsteps, void *stream) {
   sph_status r = check_state(c, s);
@@ -567,10 +627,17 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
   // partner search, boxes widened by the summed displacement bounds).
   const int R = p->tree_reuse > 0 ? p->tree_reuse : 0;
   const bool reuse_pred = !p->gravity || R > 0;
-  // The predictor's partners: refined from the lists and shells of the step's
-  // first walk (a walk follows only where the particles moved too far)
+  // Later evaluations' partners: refined from the lists and shells of the
+  // last walk, the step's first one or, on a reused tree, the build step's
+  // (a walk follows only where the particles moved too far since it)
   const bool refine = reuse_pred && c->tune.walk_every_eval == 0;
+  // a window of R steps on one tree may span calls (params.tree_continue)
+  const bool window = R > 0 && !(p->n_des > 0.0);
   int age = 0;
+  if (window && p->tree_continue) {
+    if ((r = check_continue(c, s, p, st)) != SPH_OK) return r;
+    age = c->win_age;
+  }
   for (int it = 0; it < nsteps; ++it) {
     const bool vh = p->n_des > 0.0;
     if (vh) {  // variable smoothing length from the last step's h (Sect. 4.2)
@@ -593,7 +660,10 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
       pr = prof_begin(c, st, PH_TREE);
       pack_f32(c, s, st);
       prof_end(c, st, pr);
-      partners_gravity_passes(c, s, mt, *p, d[0], st, B.dbuild, p->gravity, refine);
+      // the lists and shells of the build step's walk stay in place: while
+      // the displacement since that walk is within the shell's bound, the
+      // partners are refined from them (else a walk over the widened boxes)
+      partners_gravity_passes(c, s, mt, *p, d[0], st, B.dbuild, p->gravity, false, refine ? B.dbuild : nullptr);
     }
     pr = prof_begin(c, st, PH_INTEGRATE);
     timestep_reduce(c, s, *p, d[0], st);
@@ -605,8 +675,10 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
       pr = prof_begin(c, st, PH_TREE);
       pack_f32(c, &q, st);
       prof_end(c, st, pr);
-      partners_gravity_passes(c, &q, mt, *p, d[1], st, build ? B.dmove : B.dgrow, p->gravity, false,
-                              refine ? B.dmove : nullptr);
+      // displacement since the walk whose lists are refined: this step's walk
+      // at a build, the build step's walk otherwise
+      const unsigned long long *since = build ? B.dmove : B.dgrow;
+      partners_gravity_passes(c, &q, mt, *p, d[1], st, since, p->gravity, false, refine ? since : nullptr);
     } else {
       rhs_all(c, &q, mt, *p, d[1], st);
     }
@@ -622,6 +694,7 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
     prof_end(c, st, pr);
   }
   if (dt && nsteps > 0) cudaMemcpyAsync(dt, B.dt, sizeof(double) * ninst, cudaMemcpyDeviceToDevice, st);
+  if (window) keep_window(c, s, p, age, st);
   return finish(c, p, st, "sph_step");
 }
 

@@ -140,6 +140,8 @@ struct StepBufs {
   double *dt;                  // per instance
   double *gather;              // reorder scratch (n doubles)
   int32_t *gather_i;
+  double *snap[4];             // positions and h an sph_step call returned (tree_continue check)
+  int32_t *differ;             // device flag of that check
 };
 
 // Per-group scratch of the flaw generator (group = instance x material).
@@ -204,6 +206,11 @@ struct sph_ctx {
   int32_t *prof_phase;        // kMaxProfEvents
   sph::StepBufs st;
   sph::FlawBufs fl;
+  // tree window of sph_step (tree_reuse) that a later call may continue:
+  // valid only while no other call has touched the tree or the lists
+  bool win_valid, win_was;
+  int win_age, win_R, win_ninst, win_leaf, win_depth, win_gravity;
+  int64_t win_n;
   // allocation list
   void *allocs[256];
   int nallocs;

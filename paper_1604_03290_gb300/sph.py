@@ -55,7 +55,8 @@ class Params(C.Structure):
                 ("c_courant", C.c_double), ("c_accel", C.c_double), ("c_quantity", C.c_double),
                 ("u_floor", C.c_double), ("S_floor", C.c_double), ("dmg_floor", C.c_double),
                 ("dt_max", C.c_double), ("dt_fixed", C.c_double), ("n_des", C.c_double),
-                ("h_tol", C.c_int32), ("h_iter", C.c_int32), ("tree_reuse", C.c_int32), ("pad2", C.c_int32)]
+                ("h_tol", C.c_int32), ("h_iter", C.c_int32), ("tree_reuse", C.c_int32),
+                ("tree_continue", C.c_int32)]
 
 
 _vp = C.c_void_p
@@ -159,7 +160,7 @@ def material_struct(m: wl.Material) -> Material:
     return s
 
 
-def params_struct(p: wl.Params, check: bool = True) -> Params:
+def params_struct(p: wl.Params, check: bool = True, cont: bool = False) -> Params:
     s = Params()
     ints = ("dim", "density_sum", "consistency", "gravity", "leaf_size", "max_depth", "h_tol", "h_iter",
             "tree_reuse")
@@ -168,8 +169,8 @@ def params_struct(p: wl.Params, check: bool = True) -> Params:
             s.precision = PRECISION[p.precision]
         elif k == "check":
             s.check = int(check)
-        elif k == "pad2":
-            continue
+        elif k == "tree_continue":
+            s.tree_continue = int(cont)
         else:
             v = getattr(p, k)
             setattr(s, k, int(v) if k in ints else float(v))
@@ -465,9 +466,12 @@ def gravity(ctx: Context, ds: DeviceState, params: wl.Params, check=True, stream
 
 
 def step(ctx: Context, ds: DeviceState, materials, params: wl.Params, nsteps: int, check=True, stream=None,
-         dt_out=None):
+         dt_out=None, cont=False):
+    """nsteps predictor-corrector steps (Sect. 3.4.1) in place.  cont: continue
+    the tree window the previous step call on ctx left (params.tree_reuse > 0;
+    the state must be the one that call returned)."""
     st = ds.struct()
-    P = params_struct(params, check)
+    P = params_struct(params, check, cont)
     M = materials_array(materials)
     dt = dt_out if dt_out is not None else torch.zeros(max(ds.ninst, 1), dtype=torch.float64, device=ds.x.device)
     ctx.check(ctx._lib.sph_step(ctx.h, C.byref(st), M, len(materials), C.byref(P), _ptr(dt), int(nsteps),

@@ -2,7 +2,9 @@
 host_steps: every step uploads all fields and downloads its result, with the
 uploads of the next step overlapping the downloads) gives the same state,
 bit for bit, as the same steps on a device-resident state; the device copy
-is scrambled first, so only the uploads can make it right."""
+is scrambled first, so only the uploads can make it right.  As in the bench,
+one tree serves 4 steps and each one-step call continues the window of the
+last, across the host round trip."""
 import os
 import sys
 from dataclasses import replace
@@ -30,12 +32,11 @@ def test_host_steps_equal_device_steps(S):
     sys.path.insert(0, ROOT)
     import bench
     ps = wl.measurement_1m(seed=11, n_side=30)
-    prm = replace(ps.params, precision="mixed")
+    prm = replace(ps.params, precision="mixed", tree_reuse=4)
     ctx = S.Context(3, ps.n, max_neighbours=128, leaf_size=prm.leaf_size)
     stream = torch.cuda.current_stream()
     ref = S.DeviceState(ps)
-    for _ in range(3):
-        S.step(ctx, ref, ps.materials, prm, 1, check=False)
+    S.step(ctx, ref, ps.materials, prm, 6, check=False)
     R = ref.to_numpy()
     ds = S.DeviceState(ps)
     host = {k: (None if v is None else v.detach().cpu().pin_memory()) for k, v in
@@ -43,7 +44,7 @@ def test_host_steps_equal_device_steps(S):
              "mat": ds.mat, "id": ds.id}.items()}
     for k in ("x", "v", "rho", "u", "m", "h", "S", "dmg"):
         getattr(ds, k).fill_(1.2345)
-    bench.host_steps(S, ctx, ds, host, ps.materials, prm, 3, stream)
+    bench.host_steps(S, ctx, ds, host, ps.materials, prm, 6, stream)
     torch.cuda.synchronize()
     ctx.sync_status()
     for k in ("x", "v", "rho", "u", "m", "h", "S", "dmg", "mat", "id"):

@@ -103,6 +103,14 @@ def test_step_measured_1m(S, orc, m1):
     _check_step(S, orc, m1)
 
 
+def test_steps_measured_1m_reused_tree(S, orc, m1):
+    # the bench's configuration: one tree serves 3 steps, and the evaluations
+    # after the build refine their partners from the build step's walk
+    ps = wl.measurement_1m(seed=11, n_side=100)
+    ps.params = replace(ps.params, tree_reuse=3)
+    _check_step(S, orc, ps, nsteps=3)
+
+
 def test_step_256_batched_impacts(S, orc):
     ps = wl.batched_impacts(seed=5)
     assert ps.ninst == 256

@@ -7,7 +7,10 @@ refined), the same impact with a fixed step that moves the projectile by half
 its support radius (the bound fails and the walk runs), a lattice whose
 shells hold more candidates than their slots (the walk runs), batched instances,
 2D rings with XSPH and artificial stress, a self-gravitating pair stepping
-with a reused tree, and the embedded Runge-Kutta step; FP64 and mixed."""
+with a reused tree, the impact on a tree reused for 3 steps (every evaluation
+after a build refines from the build step's walk) and for 6 steps with a
+longer step (the bound fails within the window), and the embedded
+Runge-Kutta step; FP64 and mixed."""
 from dataclasses import replace
 
 import numpy as np
@@ -66,8 +69,26 @@ def _pair_reuse():
     return ps
 
 
+def _impact_reuse():
+    # the measured configuration's physics on a tree reused for 3 steps: the
+    # steps after a build refine both evaluations from the build step's walk
+    ps = wl.measurement_1m(seed=35, n_side=18)
+    ps.params = replace(ps.params, tree_reuse=3)
+    return ps
+
+
+def _impact_reuse_long():
+    # reused for 6 steps with a fixed step 8x the limiter's: the bound fails
+    # within the window, and those evaluations walk the widened boxes
+    ps = wl.measurement_1m(seed=37, n_side=14)
+    hp = ps.h.min()
+    ps.params = replace(ps.params, tree_reuse=6, dt_fixed=0.8 * hp / 64 / (4 * np.sqrt(3)) / 7000.0)
+    return ps
+
+
 CASES = {"impact": _impact, "impact_fast": _impact_fast, "batch": _batch, "rings": _rings,
-         "pair_reuse": _pair_reuse, "lattice_crowded_shell": _lattice_crowded_shell}
+         "pair_reuse": _pair_reuse, "lattice_crowded_shell": _lattice_crowded_shell,
+         "impact_reuse": _impact_reuse, "impact_reuse_long": _impact_reuse_long}
 
 
 def _run(S, ps, prm, walk_every_eval, nsteps, rk3=False):
@@ -97,14 +118,18 @@ def _identical(a, b):
 def test_refined_steps_equal_walked_steps(S, case, prec):
     ps = CASES[case]()
     prm = replace(ps.params, precision=prec)
-    nsteps = 3
+    R = prm.tree_reuse
+    nsteps = 4 if R > 0 else 3
     a, ea, pa = _run(S, ps, prm, 0, nsteps)
     b, eb, pb = _run(S, ps, prm, 1, nsteps)
     _identical(a, b)
     for x, y in zip(ea, eb):
         np.testing.assert_array_equal(x, y)
-    # one walk per step with refinement, two without
-    assert pa["refine"][1] == nsteps and pa["partners"][1] == nsteps
+    # with refinement: a walk at every tree build (each step, or every R-th
+    # with a reused tree) and a refine at every other evaluation; without:
+    # two walks per step
+    builds = nsteps if R == 0 else -(-nsteps // R)
+    assert pa["partners"][1] == builds and pa["refine"][1] == 2 * nsteps - builds
     assert pb["refine"][1] == 0 and pb["partners"][1] == 2 * nsteps
 
 
