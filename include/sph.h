@@ -160,7 +160,8 @@ typedef struct sph_ctx sph_ctx;
  * their partners from the last walk on it (within one sph_step or
  * sph_step_rk3 step, the step's first walk; across the steps that share a
  * tree under tree_reuse, the walk of the step that built it), which also
- * records each particle's candidates within (1 + 1/64) h_ab, as long as the
+ * records each particle's candidates with (1 - 1/64) h_ab <= r_ab <
+ * (1 + 1/64) h_ab (only those are tested again), as long as the
  * summed bound on the largest per-axis displacement of any particle since
  * that walk is at most h_a / (256 sqrt D) for every particle a and no
  * particle has more than 24 such candidates (else they walk); the lists are

@@ -66,10 +66,12 @@ __device__ __forceinline__ bool exact_within_own_h(const double *__restrict__ x,
 }
 
 // Shells (SHELL = true): the walk also records, in ascending order, every b
-// with h_ab <= r_ab < (1 + kSkin) h_ab (FP32 test with the band's margin, so
-// possibly a few more), for k_partners_refine.
+// with (1 - kSkin) h_ab <= r_ab < (1 + kSkin) h_ab (FP32 tests with the band's
+// margin on both sides, so possibly a few more): the partners near the
+// support radius and the non-partners just beyond it, for k_partners_refine.
 constexpr float kSkinF = (float)kSkin;
 constexpr float kShell2 = (1.0f + kSkinF) * (1.0f + kSkinF) * (1.0f + kBand);
+constexpr float kInner2 = (1.0f - kSkinF) * (1.0f - kSkinF) * (1.0f - kBand);
 
 // OWN_H = false: interaction partners (h_ab), lists and counts, skipped when
 // the flag `done` is given and is 0 (it is then a run-if flag).  OWN_H = true:
@@ -208,6 +210,12 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
                   if constexpr (!OWN_H)
                     if (cnt < kmax) nb_idx[(int64_t)cnt * ld + a] = b;
                   ++cnt;
+                  if constexpr (SHELL) {
+                    if (r2 >= h2 * kInner2) {  // a partner near the support radius
+                      if (scnt < kMaxShell) sh_idx[(int64_t)scnt * ld + a] = b;
+                      ++scnt;
+                    }
+                  }
                 } else if constexpr (SHELL) {
                   if (b != a && r2 <= h2 * kShell2) {
                     if (scnt < kMaxShell) sh_idx[(int64_t)scnt * ld + a] = b;
@@ -239,23 +247,29 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
 }
 
 // Partners at moved positions from the lists and shells of an earlier walk
-// (the Verlet-list idea applied within one step).  When every particle moved
-// by at most `move` per axis since that walk, a pair's distance changed by at
-// most 2 sqrt(D) move; with 4 sqrt(D) move <= kSkin h_a that is at most
-// kSkin h_ab (h_ab >= h_a / 2), so every partner of a at the new positions was
-// a partner or a shell candidate of a.  The old list and the shell are both
-// ascending and disjoint: merged, they are visited in ascending order, each
-// candidate is decided by the walk's predicate (FP32 outside the band, the
-// FP64 definition inside it), and the new list equals that of a walk at the
-// new positions bit for bit.  A particle whose bound does not hold, or whose
-// shell overflowed, sets *need_walk instead, and a walk follows.
-__global__ void __launch_bounds__(128)
+// (the Verlet-list idea).  When every particle moved by at most `move` per
+// axis since that walk, a pair's distance changed by at most 2 sqrt(D) move;
+// with 4 sqrt(D) move <= kSkin h_a that is at most kSkin h_ab (h_ab >= h_a / 2).
+// So a partner of the walk closer than (1 - kSkin) h_ab is still one, a
+// non-partner farther than (1 + kSkin) h_ab is still none, and only the shell
+// between the two can change.  The old list and the shell are both ascending,
+// and the shell's partners are also in the list: merged, the candidates are
+// visited in ascending order, the list's members outside the shell are kept
+// as they are (no gather), and each shell member is decided by the walk's
+// predicate (FP32 outside the band, the FP64 definition inside it), so the new
+// list equals that of a walk at the new positions bit for bit.  A particle
+// whose bound does not hold, or whose shell overflowed, sets *need_walk
+// instead, and a walk follows.
+constexpr int kRefineThreads = 128;
+__global__ void __launch_bounds__(kRefineThreads)
     k_partners_refine(PackedF32 pk, const double *__restrict__ x, const double *__restrict__ y,
                       const double *__restrict__ z, const double *__restrict__ h, int dim, int64_t n, int64_t ld,
                       int kmax, const int32_t *__restrict__ old_idx, const int32_t *__restrict__ old_cnt,
                       const int32_t *__restrict__ sh_idx, const int32_t *__restrict__ sh_cnt,
                       int32_t *__restrict__ new_idx, int32_t *__restrict__ new_cnt,
                       const unsigned long long *__restrict__ move, int32_t *__restrict__ need_walk, int32_t *err) {
+  // the shell of each thread's particle, staged for the merge
+  __shared__ int32_t shs[kMaxShell][kRefineThreads];
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= n) return;
   const int ns = sh_cnt[a];
@@ -265,39 +279,63 @@ __global__ void __launch_bounds__(128)
     *need_walk = 1;
     return;
   }
-  const float4 P = pk.px(a), Q = pk.pxl(a);
-  const float hha = 0.5f * P.w;
-  const int nl = old_cnt[a];
-  const int ntot = nl + ns;
-  int i = 0, j = 0, cnt = 0;
-  int32_t bl = nl > 0 ? old_idx[a] : INT_MAX;
-  int32_t bs = ns > 0 ? sh_idx[a] : INT_MAX;
-  for (int k = 0; k < ntot; ++k) {
-    int32_t b;
-    if (bl < bs) {
-      b = bl;
-      ++i;
-      bl = i < nl ? old_idx[(int64_t)i * ld + a] : INT_MAX;
-    } else {
-      b = bs;
-      ++j;
-      bs = j < ns ? sh_idx[(int64_t)j * ld + a] : INT_MAX;
-    }
-    const float4 Pb = pk.px(b), Qb = pk.pxl(b);
-    const float dx = (P.x - Pb.x) + (Q.x - Qb.x), dy = (P.y - Pb.y) + (Q.y - Qb.y),
-                dz = (P.z - Pb.z) + (Q.z - Qb.z);
-    const float r2 = dx * dx + dy * dy + dz * dz;
-    const float hab = hha + 0.5f * Pb.w;
-    const float h2 = hab * hab;
-    bool in;
-    if (r2 < h2 * (1.0f - kBand)) in = true;
-    else if (r2 > h2 * (1.0f + kBand)) in = false;
-    else in = exact_partner(x, y, z, h, dim, a, b);
-    if (in) {
-      if (cnt < kmax) new_idx[(int64_t)cnt * ld + a] = b;
-      ++cnt;
+  const int t = threadIdx.x;
+  // 1. decide every shell member at the new positions (bit j of `in`)
+  uint32_t in = 0;
+  {
+    const float4 P = pk.px(a), Q = pk.pxl(a);
+    const float hha = 0.5f * P.w;
+    for (int j = 0; j < ns; ++j) {
+      const int32_t b = sh_idx[(int64_t)j * ld + a];
+      shs[j][t] = b;
+      const float4 Pb = pk.px(b), Qb = pk.pxl(b);
+      const float dx = (P.x - Pb.x) + (Q.x - Qb.x), dy = (P.y - Pb.y) + (Q.y - Qb.y),
+                  dz = (P.z - Pb.z) + (Q.z - Qb.z);
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      const float hab = hha + 0.5f * Pb.w;
+      const float h2 = hab * hab;
+      bool ok;
+      if (r2 < h2 * (1.0f - kBand)) ok = true;
+      else if (r2 > h2 * (1.0f + kBand)) ok = false;
+      else ok = exact_partner(x, y, z, h, dim, a, b);
+      in |= (uint32_t)ok << j;
     }
   }
+  // 2. merge: list members outside the shell are kept, shell members that are
+  // in are emitted once (in the list or inserted), the others dropped; the
+  // list is read 8 entries at a time so that its loads overlap
+  const int nl = old_cnt[a];
+  int j = 0, cnt = 0;
+  int32_t bs = ns > 0 ? shs[0][t] : INT_MAX;
+  auto emit = [&](int32_t b) {
+    if (cnt < kmax) new_idx[(int64_t)cnt * ld + a] = b;
+    ++cnt;
+  };
+  for (int base = 0; base < nl; base += 8) {
+    int32_t buf[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) buf[u] = base + u < nl ? old_idx[(int64_t)(base + u) * ld + a] : INT_MAX;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int32_t b = buf[u];
+      if (b != INT_MAX) {
+        while (bs < b) {  // shell members below b that are not in the list
+          if ((in >> j) & 1u) emit(bs);
+          ++j;
+          bs = j < ns ? shs[j][t] : INT_MAX;
+        }
+        if (bs == b) {  // a list member in the shell: kept if still in
+          if ((in >> j) & 1u) emit(b);
+          ++j;
+          bs = j < ns ? shs[j][t] : INT_MAX;
+        } else {
+          emit(b);
+        }
+      }
+    }
+  }
+  for (; j < ns; ++j)
+    if ((in >> j) & 1u) emit(shs[j][t]);
   new_cnt[a] = min(cnt, kmax);
   if (cnt > kmax) raise_err(err, ERR_NB_OVERFLOW);
 }
@@ -326,7 +364,7 @@ void refine_partners(sph_ctx *c, const sph_state *s, const unsigned long long *m
   const int64_t n = s->n;
   if (n == 0) return;
   cudaMemsetAsync(c->need_walk, 0, sizeof(int32_t), st);
-  { k_partners_refine<<<nblk(n, 128), 128, 0, st>>>(c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim, n, c->cap_n,
+  { k_partners_refine<<<nblk(n, kRefineThreads), kRefineThreads, 0, st>>>(c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim, n, c->cap_n,
                                                    c->kmax, c->nb_idx, c->nb_cnt, c->sh_idx, c->sh_cnt, c->nb_alt,
                                                    c->nb_cnt_alt, move, c->need_walk, c->d_err); ++sph::g_launches; }
   // returns at once unless a particle set the flag

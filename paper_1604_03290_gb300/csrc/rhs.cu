@@ -96,6 +96,44 @@ __device__ __forceinline__ double rcp_rn<double>(double x) {
   return __drcp_rn(x);
 }
 
+// Reciprocal and quotient inside the pair loops.  Mixed: the hardware's
+// approximations (relative error below 2^-22, a few FP32 roundings of a pair
+// term, well inside the mixed tolerance; operands are in code units, far from
+// the subnormal range).  FP64: correctly rounded, as everywhere else.
+#ifndef SPH_FAST_PAIR_MATH
+#define SPH_FAST_PAIR_MATH 1
+#endif
+template <class R>
+__device__ __forceinline__ R pair_rcp(R x);
+template <>
+__device__ __forceinline__ float pair_rcp<float>(float x) {
+#if SPH_FAST_PAIR_MATH
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+#else
+  return __frcp_rn(x);
+#endif
+}
+template <>
+__device__ __forceinline__ double pair_rcp<double>(double x) {
+  return __drcp_rn(x);
+}
+template <class R>
+__device__ __forceinline__ R pair_div(R a, R b);
+template <>
+__device__ __forceinline__ float pair_div<float>(float a, float b) {
+#if SPH_FAST_PAIR_MATH
+  return __fdividef(a, b);
+#else
+  return a / b;
+#endif
+}
+template <>
+__device__ __forceinline__ double pair_div<double>(double a, double b) {
+  return a / b;
+}
+
 // ---------------------------------------------------------------------------
 // Pair geometry: a - b differences of position and velocity, b's scalars.
 // ---------------------------------------------------------------------------
@@ -258,7 +296,7 @@ __global__ void __launch_bounds__(128) k_density_sum(RhsArgs A) {
     o.pair(A, b, d, w, hb, rhob, mb, vol);
     R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     R r = r2 * rsqrt_or_zero(r2);
-    R hinv = rcp_rn(R(0.5) * ((R)o.h + hb));
+    R hinv = pair_rcp(R(0.5) * ((R)o.h + hb));
     sum.add(mb * kern_W(r * hinv, sig * hpow(hinv, dim)));
   }
   A.rho_out[a] = sum.value() * (MIXED ? A.U->rho : 1.0);
@@ -387,7 +425,7 @@ __global__ void SPH_PASSA_BOUNDS k_passA(RhsArgs A) {
     const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     const R rinv = rsqrt_or_zero(r2);
     const R r = r2 * rinv;
-    const R hinv = rcp_rn(R(0.5) * (ha + hb));
+    const R hinv = pair_rcp(R(0.5) * (ha + hb));
     const R q = r * hinv;
     const R hD = hpow(hinv, dim);
     const R fr = kern_dW(q, R(6) * sig * hD * hinv) * rinv;
@@ -403,7 +441,7 @@ __global__ void SPH_PASSA_BOUNDS k_passA(RhsArgs A) {
       }
     }
     if (xsph) {
-      const R c = R(2) * mb / (rhoa + rhob) * kern_W(q, sig * hD);
+      const R c = pair_div(R(2) * mb, rhoa + rhob) * kern_W(q, sig * hD);
       for (int i = 0; i < 3; ++i) xs[i] -= c * w[i];
     }
   }
@@ -705,7 +743,7 @@ __global__ void SPH_PASSB_BOUNDS k_passB(RhsArgs A) {
     const R rinv = rsqrt_or_zero(r2);
     const R r = r2 * rinv;
     const R hab = R(0.5) * (ha + hb);
-    const R hinv = rcp_rn(hab);
+    const R hinv = pair_rcp(hab);
     const R q = r * hinv;
     const R hD = hpow(hinv, dim);
     const R fr = kern_dW(q, R(6) * sig * hD * hinv) * rinv;
@@ -714,8 +752,8 @@ __global__ void SPH_PASSB_BOUNDS k_passB(RhsArgs A) {
     const R vx = w[0] * d[0] + w[1] * d[1] + w[2] * d[2];
     R Pi = R(0);
     if (vx < R(0)) {
-      const R nu = hab * vx / (r2 + epsv * hab * hab);
-      Pi = (-alpha * R(0.5) * (csa + csb) * nu + beta * nu * nu) / (R(0.5) * (rhoa + rhob));
+      const R nu = pair_div(hab * vx, r2 + epsv * hab * hab);
+      Pi = pair_div(-alpha * R(0.5) * (csa + csb) * nu + beta * nu * nu, R(0.5) * (rhoa + rhob));
     }
     R tsum[6];
     for (int c = 0; c < 6; ++c) tsum[c] = Ta[c] + Tb[c];

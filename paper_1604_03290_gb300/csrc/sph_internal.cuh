@@ -36,9 +36,11 @@ constexpr int kWarp = 32;
 constexpr int kMaxLeaf = 32;
 constexpr int kMaxHIter = 64;  // most updates of one variable smoothing length iteration
 // Partner shells: a walk may also record, per particle, the candidates with
-// h_ab <= r_ab < (1 + kSkin) h_ab (at most kMaxShell of them), from which the
-// partners at positions moved by less than kSkin h / (4 sqrt D) follow
-// without a walk (neighbours.cu).
+// (1 - kSkin) h_ab <= r_ab < (1 + kSkin) h_ab (at most kMaxShell of them),
+// partners and non-partners alike, from which the partners at positions
+// moved by less than kSkin h / (4 sqrt D) follow without a walk: a partner
+// outside the shell stays one, a non-partner outside it stays none, and only
+// the shell is tested again (neighbours.cu).
 constexpr double kSkin = 1.0 / 64.0;
 constexpr int kMaxShell = 24;
 

@@ -8,6 +8,8 @@
 //   component and d^1/3 (the paper's sqrt(q^2 / dq^2) with a floor so that a
 //   quantity starting at zero does not force dt = 0), capped at dt_max.
 // The acceleration limit takes the square root that makes it a time.
+#include <cmath>
+
 #include "fpbits.cuh"
 #include "sph_internal.cuh"
 
@@ -324,6 +326,7 @@ struct PcArgs {
   double *ox[3], *ov[3], *orho, *ou, *oS, *odmg;
   DSet d[3];
   double coef[3];
+  int pow2;  // one derivative set whose coefficient is a power of two
   int nd;
   const int32_t *mask;  // per instance: update only where set (NULL: all)
   const int32_t *nact, *mat, *id;  // nact: of the last set
@@ -347,18 +350,28 @@ __device__ __forceinline__ double comb(const PcArgs &A, const double *p0, const 
   return v;
 }
 
+// b + dt (c_0 d_0[i] + ...).  With one set and c_0 a power of two,
+// (c_0 dt) d_0[i] is the same exact product as dt (c_0 d_0[i]), so the update
+// is one fused multiply-add with the same rounding.
+__device__ __forceinline__ double upd(const PcArgs &A, double b, double dt, double dtc, const double *p0,
+                                      const double *p1, const double *p2, int64_t i) {
+  if (A.pow2) return b + dtc * p0[i];
+  return b + dt * comb(A, p0, p1, p2, i);
+}
+
 // Update of particle a; returns the bits of max_axis |out.x - base.x| when
 // A.dmove is set (else 0).
 __device__ __forceinline__ unsigned long long pc_particle(const PcArgs &A, int64_t a) {
   const int inst = inst_of(A.inst_off, A.ninst, a);
   if (A.mask && !A.mask[inst]) return 0ULL;
   const double dt = A.dt[inst];
+  const double dtc = dt * A.coef[0];
   unsigned long long mv = 0ULL;  // bits of max |ox - bx| (non-negative doubles order as integers)
   bool bad = false;
   for (int ax = 0; ax < A.dim; ++ax) {
     const double bx = A.bx[ax][a];
-    const double ox = bx + dt * comb(A, A.d[0].dx[ax], A.d[1].dx[ax], A.d[2].dx[ax], a);
-    const double ov = A.bv[ax][a] + dt * comb(A, A.d[0].dv[ax], A.d[1].dv[ax], A.d[2].dv[ax], a);
+    const double ox = upd(A, bx, dt, dtc, A.d[0].dx[ax], A.d[1].dx[ax], A.d[2].dx[ax], a);
+    const double ov = upd(A, A.bv[ax][a], dt, dtc, A.d[0].dv[ax], A.d[1].dv[ax], A.d[2].dv[ax], a);
     A.ox[ax][a] = ox;
     A.ov[ax][a] = ov;
     if (A.dmove) {
@@ -367,12 +380,12 @@ __device__ __forceinline__ unsigned long long pc_particle(const PcArgs &A, int64
       bad |= !finite_bits(ox) || !finite_bits(ov);
     }
   }
-  A.orho[a] = A.density_sum ? A.brho[a] : A.brho[a] + dt * comb(A, A.d[0].drho, A.d[1].drho, A.d[2].drho, a);
+  A.orho[a] = A.density_sum ? A.brho[a] : upd(A, A.brho[a], dt, dtc, A.d[0].drho, A.d[1].drho, A.d[2].drho, a);
   if (A.dmove) {
     bad |= !positive_finite_bits(A.orho[a]);
     if (bad) raise_err(A.err, ERR_NONFINITE);
   }
-  A.ou[a] = A.bu[a] + dt * comb(A, A.d[0].du, A.d[1].du, A.d[2].du, a);
+  A.ou[a] = upd(A, A.bu[a], dt, dtc, A.d[0].du, A.d[1].du, A.d[2].du, a);
   const int mi = A.mat ? A.mat[a] : 0;
   const sph_material &M = A.mt.m[(mi >= 0 && mi < A.mt.nmat) ? mi : 0];
   if (A.bS) {
@@ -381,7 +394,7 @@ __device__ __forceinline__ unsigned long long pc_particle(const PcArgs &A, int64
     double J2 = 0.0;
     for (int k = 0; k < ns; ++k) {
       int64_t i = (int64_t)k * A.n + a;
-      S[k] = A.bS[i] + dt * comb(A, A.d[0].dS, A.d[1].dS, A.d[2].dS, i);
+      S[k] = upd(A, A.bS[i], dt, dtc, A.d[0].dS, A.d[1].dS, A.d[2].dS, i);
       J2 += (k < A.dim ? 1.0 : 2.0) * S[k] * S[k];  // off-diagonal terms appear twice in S:S
     }
     J2 *= 0.5;
@@ -397,7 +410,7 @@ __device__ __forceinline__ unsigned long long pc_particle(const PcArgs &A, int64
   }
   if (A.bdmg) {
     const double dd = comb(A, A.d[0].ddmg, A.d[1].ddmg, A.d[2].ddmg, a);
-    double nd = A.bdmg[a] + dt * dd;
+    double nd = A.pow2 ? A.bdmg[a] + dtc * A.d[0].ddmg[a] : A.bdmg[a] + dt * dd;
     if (dd > 0.0) {
       const int64_t idp = A.id ? A.id[a] : a;
       const int64_t ntot = A.flaw_off[idp + 1] - A.flaw_off[idp];
@@ -466,6 +479,8 @@ void combine_update(sph_ctx *c, const sph_state *base, sph_state *out, const sph
     A.d[j] = dset_of(*d[j]);
     A.coef[j] = coef[j];
   }
+  int e2 = 0;
+  A.pow2 = nd == 1 && std::frexp(coef[0], &e2) == 0.5;
   A.nact = d[nd - 1]->n_act;
   A.mask = mask;
   A.mat = base->mat;
