@@ -359,8 +359,32 @@ __device__ __forceinline__ double upd(const PcArgs &A, double b, double dt, doub
   return b + dt * comb(A, p0, p1, p2, i);
 }
 
-// Update of particle a; returns the bits of max_axis |out.x - base.x| when
-// A.dmove is set (else 0).
+// The exact difference, for the rare operands outside FP32's range (kept out
+// of line, as the FP64 fallbacks of fpbits.cuh)
+static __device__ __noinline__ uint64_t move_bits_slow(double ox, double bx) {
+  return dbits(ox - bx) & 0x7fffffffffffffffULL;
+}
+
+// Bits of an upper bound of |ox - bx| for ox = fl(bx + dtc d) (one rounding):
+// |dtc d| + ulp(ox) / 2 <= fl_up(fl_up(|dtc|) fl_up(|d|)) + ulp(ox), taken in
+// FP32 with upward rounding from the bit patterns, so that no FP64
+// instruction is spent on the displacement bound.
+__device__ __forceinline__ uint64_t move_bound_bits(double dtc, double d, double ox, double bx) {
+  const uint64_t mag = 0x7fffffffffffffffULL;
+  float fa, fb;
+  const int e = (int)((dbits(ox) >> 52) & 0x7ff);
+  const int ef = e - 1075 + 127;  // float exponent field of ulp(ox) = 2^(e - 1075)
+  if (ef <= 254 && f32_dir_scaled(bitsd(dbits(dtc) & mag), 0, true, fa) &&
+      f32_dir_scaled(bitsd(dbits(d) & mag), 0, true, fb)) {
+    const float ulp = bitsf((uint32_t)(ef >= 1 ? ef : 1) << 23);  // 2^-126 bounds the smaller ulps
+    double out;
+    if (f64_scaled(__fadd_ru(__fmul_ru(fa, fb), ulp), 0, out)) return dbits(out);
+  }
+  return move_bits_slow(ox, bx);
+}
+
+// Update of particle a; returns the bits of an upper bound of
+// max_axis |out.x - base.x| when A.dmove is set (else 0).
 __device__ __forceinline__ unsigned long long pc_particle(const PcArgs &A, int64_t a) {
   const int inst = inst_of(A.inst_off, A.ninst, a);
   if (A.mask && !A.mask[inst]) return 0ULL;
@@ -375,7 +399,8 @@ __device__ __forceinline__ unsigned long long pc_particle(const PcArgs &A, int64
     A.ox[ax][a] = ox;
     A.ov[ax][a] = ov;
     if (A.dmove) {
-      const unsigned long long m = dbits(ox - bx) & 0x7fffffffffffffffULL;
+      const unsigned long long m =
+          A.pow2 ? move_bound_bits(dtc, A.d[0].dx[ax][a], ox, bx) : (dbits(ox - bx) & 0x7fffffffffffffffULL);
       mv = m > mv ? m : mv;
       bad |= !finite_bits(ox) || !finite_bits(ov);
     }
@@ -391,27 +416,49 @@ __device__ __forceinline__ unsigned long long pc_particle(const PcArgs &A, int64
   if (A.bS) {
     const int ns = nsym(A.dim);
     double S[6];
-    double J2 = 0.0;
     for (int k = 0; k < ns; ++k) {
       int64_t i = (int64_t)k * A.n + a;
       S[k] = upd(A, A.bS[i], dt, dtc, A.d[0].dS, A.d[1].dS, A.d[2].dS, i);
-      J2 += (k < A.dim ? 1.0 : 2.0) * S[k] * S[k];  // off-diagonal terms appear twice in S:S
     }
-    J2 *= 0.5;
     // f_Y = min(Y0^2 / (3 J2), 1) differs from 1 only if Y0^2 < 3 J2 (both
     // rounded as in the quotient), so the division runs for yielding
-    // particles only; the result is the same bit for bit
-    const double y2 = M.Y0 * M.Y0, j3 = 3.0 * J2;
-    if (M.strength && M.Y0 > 0.0 && J2 > 0.0 && y2 < j3) {
-      const double fY = fmin(y2 / j3, 1.0);
-      for (int k = 0; k < ns; ++k) S[k] *= fY;
+    // particles only; the result is the same bit for bit.  An FP32 screen
+    // from the bit patterns (relative error below 2^-20) first excludes the
+    // particles clearly inside the yield surface, 3 J2 < Y0^2 (1 - 2^-12),
+    // without FP64 instructions.
+    if (M.strength && M.Y0 > 0.0) {
+      bool inside = false;
+      {
+        float s2 = 0.f, y0f;
+        bool ok = f32_rn_scaled(M.Y0, 0, y0f);
+        for (int k = 0; k < ns; ++k) {
+          float f;
+          ok = ok && f32_rn_scaled(S[k], 0, f);
+          s2 += (k < A.dim ? 1.f : 2.f) * f * f;
+        }
+        inside = ok && 1.5f * s2 < y0f * y0f * (1.f - 1.f / 4096.f);
+      }
+      if (!inside) {
+        double J2 = 0.0;
+        for (int k = 0; k < ns; ++k) J2 += (k < A.dim ? 1.0 : 2.0) * S[k] * S[k];  // off-diagonals twice in S:S
+        J2 *= 0.5;
+        const double y2 = M.Y0 * M.Y0, j3 = 3.0 * J2;
+        if (J2 > 0.0 && y2 < j3) {
+          const double fY = fmin(y2 / j3, 1.0);
+          for (int k = 0; k < ns; ++k) S[k] *= fY;
+        }
+      }
     }
     for (int k = 0; k < ns; ++k) A.oS[(int64_t)k * A.n + a] = S[k];
   }
   if (A.bdmg) {
-    const double dd = comb(A, A.d[0].ddmg, A.d[1].ddmg, A.d[2].ddmg, a);
-    double nd = A.pow2 ? A.bdmg[a] + dtc * A.d[0].ddmg[a] : A.bdmg[a] + dt * dd;
-    if (dd > 0.0) {
+    // with one set of coefficient c_0 > 0, dd > 0 iff its derivative is
+    // positive (a test of the bits)
+    const double d0 = A.d[0].ddmg[a];
+    const double dd = A.pow2 ? d0 : comb(A, A.d[0].ddmg, A.d[1].ddmg, A.d[2].ddmg, a);
+    double nd = A.pow2 ? A.bdmg[a] + dtc * d0 : A.bdmg[a] + dt * dd;
+    const bool grows = A.pow2 ? (int64_t)dbits(d0) > 0 : dd > 0.0;
+    if (grows) {
       const int64_t idp = A.id ? A.id[a] : a;
       const int64_t ntot = A.flaw_off[idp + 1] - A.flaw_off[idp];
       // the cap (n_act / n_tot)^(1/3) binds only if nd^3 n_tot >= n_act; an
@@ -421,7 +468,7 @@ __device__ __forceinline__ unsigned long long pc_particle(const PcArgs &A, int64
                          ndf * ndf * ndf * (float)ntot < (float)A.nact[a] * (1.f - 1.f / 4096.f);
       if (!below) nd = fmin(nd, cbrt((double)A.nact[a] / (double)ntot));
     }
-    A.odmg[a] = fmin(nd, 1.0);
+    A.odmg[a] = (ord_of(nd) <= ord_of(1.0) && finite_bits(nd)) ? nd : 1.0;  // min(nd, 1) on the integer pipe
   }
   return mv;
 }
