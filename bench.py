@@ -123,14 +123,14 @@ class ClockSampler:
 # now, the figures are stale and are not used (the kernel is then reported
 # against HBM alone, with traffic null).
 NCU_PER_PARTICLE = {
-    "partners": {"inst": 790.70, "dram": 349.98, "fp32_pipe": 0.269, "issue": 0.662,
-                 "src": ("neighbours.cu", "d6c10fd598ed2997")},
-    "refine": {"inst": 137.11, "dram": 458.28, "fp32_pipe": 0.192, "issue": 0.436,
-               "src": ("neighbours.cu", "d6c10fd598ed2997")},
-    "passA": {"inst": 365.57, "dram": 507.89, "fp32_pipe": 0.380, "issue": 0.594,
-              "src": ("rhs.cu", "61cd28223971269a")},
-    "passB": {"inst": 395.25, "dram": 347.20, "fp32_pipe": 0.440, "issue": 0.627,
-              "src": ("rhs.cu", "61cd28223971269a")},
+    "partners": {"inst": 856.36, "dram": 349.83, "fp32_pipe": 0.284, "issue": 0.682, "l1": 0.331,
+                 "src": ("neighbours.cu", "0b68670dee48e6ce")},
+    "refine": {"inst": 95.27, "dram": 442.94, "fp32_pipe": 0.183, "issue": 0.609, "l1": 0.344,
+               "src": ("neighbours.cu", "0b68670dee48e6ce")},
+    "passA": {"inst": 346.48, "dram": 504.89, "fp32_pipe": 0.385, "issue": 0.585, "l1": 0.619,
+              "src": ("rhs.cu", "eb113c70734f51a8")},
+    "passB": {"inst": 360.47, "dram": 347.45, "fp32_pipe": 0.451, "issue": 0.623, "l1": 0.911,
+              "src": ("rhs.cu", "eb113c70734f51a8")},
 }
 
 
@@ -158,18 +158,17 @@ def algorithmic_bytes(phase, K, n_flaw_mean, dim=3):
         return reads + writes
     if phase == "passB":
         return 64 + 32 + 4 + 4 * K + 8 * dim + 8  # packs, T pack, list; dv, du
+    # the shell of the later evaluations: candidates with (1 - 1/64) h_ab <=
+    # r_ab < (1 + 1/64) h_ab, about ((1 + 1/64)^D - (1 - 1/64)^D) K of them for
+    # uniformly spread neighbours (fewer on the bench lattice)
+    shell = ((1.0 + 1.0 / 64.0) ** dim - (1.0 - 1.0 / 64.0) ** dim) * K
     if phase == "partners":
-        # positions, perm, slot; list and count; the shell list of the step's
-        # later evaluations (partners within (1 + 1/64) h_ab but not h_ab: about
-        # ((1 + 1/64)^D - 1) K of them for uniformly spread neighbours; fewer
-        # on the bench lattice) and its count
-        shell = ((1.0 + 1.0 / 64.0) ** dim - 1.0) * K
+        # positions, perm, slot; list and count; the shell list and its count
         return 32 + 4 + 4 + 4 * K + 4 + 4 * shell + 4
     if phase == "refine":
-        # per particle: counts and h; the old list, the shell and the new list
-        # (partner positions reused from cache)
-        shell = ((1.0 + 1.0 / 64.0) ** dim - 1.0) * K
-        return 4 + 4 + 8 + 32 + 4 * (K + shell) + 4 * K + 4
+        # per particle: counts and h, own positions; the old list, the shell
+        # and its members' positions (gathered: 32 B each), the new list
+        return 4 + 4 + 8 + 32 + 4 * K + 36 * shell + 4 * K + 4
     raise KeyError(phase)
 
 
@@ -582,6 +581,7 @@ def main():
                           "frac": ginst / issue_peak, "inst_per_particle_ncu": c["inst"]}
             r["dram_bytes_ncu"] = c["dram"] * n
             r["fp32_pipe_frac_ncu"] = c["fp32_pipe"]
+            r["l1_throughput_frac_ncu"] = c["l1"]
         return r
 
     kr = {p: kernel_roof(p) for p in ("partners", "refine", "passA", "passB")}
