@@ -264,6 +264,30 @@ def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3, cloud_n=2_000_000, with
                                     "phases_ms_per_step": {k: v[0] / 8 for k, v in ph.items() if v[1] > 0}}
         del dsc
     dec["speedup"] = dec["tree_reuse_0"]["ms_per_step"] / dec["tree_reuse_4"]["ms_per_step"]
+    # the Barnes-Hut walk alone (sph_gravity on the initial cloud): its
+    # interactions (device counters) and the FP32 rate they give, with 25 FP32
+    # operations per interaction (difference of hi/lo positions 9, r^2 5,
+    # softening 1, reciprocal square root 1, cube 2, mass 1, components 3,
+    # accumulation 3) against the measured FMA peak
+    prm = replace(cl.params, precision="mixed")
+    dsc = sph.DeviceState(cl)
+    sph.gravity(cctx, dsc, prm)
+    cctx.sync_status()
+    cctx.profile(True)
+    sph.gravity(cctx, dsc, prm, check=False)
+    ms_g = cctx.profile_read()["gravity"][0]  # the walk's own CUDA events (the call also builds a tree)
+    gc = cctx.profile_counters()
+    cctx.profile(False)
+    cctx.sync_status()
+    inter = gc["grav_nodes"] + gc["grav_terms"]
+    fp32_peak = sph.measure_fma_peak("mixed")
+    dec["gravity_walk"] = {
+        "ms": ms_g, "nodes_per_particle": gc["grav_nodes"] / cl.n, "terms_per_particle": gc["grav_terms"] / cl.n,
+        "interactions_per_s": inter / (ms_g * 1e-3), "flop_per_interaction": 25,
+        "fp32_tflops": 25 * inter / (ms_g * 1e-3) / 1e12, "fp32_peak_tflops_measured": fp32_peak / 1e12,
+        "fp32_frac": 25 * inter / (ms_g * 1e-3) / fp32_peak,
+        "lane_use": inter / (32.0 * gc["grav_visits"]) if gc["grav_visits"] else None}
+    del dsc
     del cctx
 
     # batched instances: the 256 impacts of uneven size in one concatenated
@@ -543,6 +567,7 @@ def main():
     e1.synchronize()
     launches = sph.launch_count() - l0
     phases = ctx.profile_read()
+    ctrs = ctx.profile_counters()
     ctx.profile(False)
     ms = e0.elapsed_time(e1)
     clk = clocks.stop() if rank == 0 else None
@@ -601,6 +626,11 @@ def main():
                 "frac": d["hbm"]["frac"], "traffic": d.get("dram_bytes_ncu"), "peak_source": peak_src,
                 "avg_launch_ms": d["avg_launch_ms"]}
     roof["mean_partners"] = K
+    walks = phases.get("reorder", (0.0, 0))[1]  # one walk over all particles per tree build
+    if walks:
+        roof["partner_walk_counters"] = {
+            "candidates_tested_per_particle": ctrs["walk_tests"] / (walks * n),
+            "partners_per_particle": ctrs["walk_partners"] / (walks * n), "walks": walks}
     roof["kernels"] = kr
     total_ms = sum(v[0] for v in phases.values())
     phase_report = {p: {"ms_per_step": v[0] / args.steps, "share": v[0] / total_ms if total_ms else None,

@@ -420,6 +420,15 @@ sph_status sph_profile_enable(sph_ctx *ctx, int32_t on);
 /* Milliseconds and call counts per phase since the last read (nphase
  * entries of each); synchronises on the recorded events, then resets. */
 sph_status sph_profile_read(sph_ctx *ctx, double *ms, int32_t *calls, int32_t nphase);
+/* Interaction counters summed on the device by the walks that ran while the
+ * profiler was enabled (since it was enabled or last read), for the
+ * instruction and FP32 rooflines of the walks: 0 nodes used as
+ * pseudo-particles by the Barnes-Hut walk (Sect. 3.3), 1 particle-particle
+ * terms it summed, 2 tree nodes its warps visited, 3 candidates the partner
+ * walk (Sect. 3.5.2) tested against the partner predicate, 4 partners it
+ * found.  Writes n entries of `out` (host int64; entries beyond 5 are 0),
+ * blocking on `stream`, then resets the counters. */
+sph_status sph_profile_counters(sph_ctx *ctx, int64_t *out, int32_t n, void *stream);
 /* Number of kernels this library has launched in this process. */
 int64_t sph_launch_count(void);
 

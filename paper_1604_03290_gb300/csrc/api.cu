@@ -157,6 +157,7 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   c->p = ctx_alloc<double>(c, N, ok);
   c->ag = ctx_alloc<double>(c, 3 * N, ok);
   c->units = ctx_alloc<Units>(c, 1, ok);
+  c->d_ctr = ctx_alloc<unsigned long long>(c, kNumCounters, ok);
   c->adj_inter = ctx_alloc<double>(c, 22 * N, ok);
   c->adj32 = ctx_alloc<float4>(c, 7 * N, ok);
   c->vscale = 1.0;
@@ -524,8 +525,12 @@ sph_status sph_gravity(sph_ctx *c, const sph_state *s, const sph_params *p, doub
   if (!ax || !ay || (s->dim == 3 && !az)) return fail(c, SPH_ERR_INVALID, "null output");
   cudaStream_t st = (cudaStream_t)stream;
   set_materials(c, nullptr);
+  int pr = prof_begin(c, st, PH_TREE);
   tree_build(c, s, p->leaf_size, p->max_depth, st);
+  prof_end(c, st, pr);
+  pr = prof_begin(c, st, PH_GRAVITY);
   gravity_walk(c, s, *p, ax, ay, az, st);
+  prof_end(c, st, pr);
   return finish(c, p, st, "sph_gravity");
 }
 
@@ -871,9 +876,21 @@ sph_status sph_profile_enable(sph_ctx *c, int32_t on) {
     for (int i = 0; i < 2 * kMaxProfEvents; ++i)
       if (cudaEventCreate(&c->prof_ev[i]) != cudaSuccess) return cuda_check(c, "sph_profile_enable");
   }
+  if (on && !c->prof) cudaMemset(c->d_ctr, 0, sizeof(unsigned long long) * kNumCounters);
   c->prof = on ? 1 : 0;
   c->prof_used = 0;
-  return SPH_OK;
+  return cuda_check(c, "sph_profile_enable");
+}
+
+sph_status sph_profile_counters(sph_ctx *c, int64_t *out, int32_t n, void *stream) {
+  if (!c || !out || n < 1) return SPH_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long h[kNumCounters];
+  cudaMemcpyAsync(h, c->d_ctr, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check(c, "sph_profile_counters");
+  for (int k = 0; k < n; ++k) out[k] = k < kNumCounters ? (int64_t)h[k] : 0;
+  cudaMemsetAsync(c->d_ctr, 0, sizeof(h), st);
+  return cuda_check(c, "sph_profile_counters");
 }
 
 sph_status sph_profile_read(sph_ctx *c, double *ms, int32_t *calls, int32_t nphase) {

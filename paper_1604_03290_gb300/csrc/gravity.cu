@@ -105,6 +105,7 @@ struct GravArgs {
   const Units *U;
   int32_t *err;
   int reuse;  // the tree was built at earlier positions: locate each particle anew
+  unsigned long long *ctr;  // NULL, or the interaction counters
 };
 
 template <int DIM>
@@ -164,6 +165,7 @@ __global__ void __launch_bounds__(kGrWarps * 32, SPH_GRAV_MIN_BLOCKS) k_gravity(
     const int32_t root = T.inst_root[inst];
     const int32_t stop = root >= 0 ? T.skip[root] : root;
     int iter = 0;
+    unsigned nacc = 0, nterm = 0;  // this lane's accepted nodes and particle terms (counters)
     for (int32_t nd = root; nd < stop && iter <= nnodes; ++iter) {
       const int4 rec = T.nrec[nd];  // (first, end, skip, level)
       const int32_t f = rec.x, e1 = rec.y, sk = rec.z;
@@ -208,6 +210,7 @@ __global__ void __launch_bounds__(kGrWarps * 32, SPH_GRAV_MIN_BLOCKS) k_gravity(
           const R gq = -G * mp * inv_q32(r2 + eps2);
           acc.add(gq * d[0], gq * d[1], dim == 3 ? gq * d[2] : R(0));
           skip_until = sk;
+          ++nacc;
         } else if (leaf) {
           direct = true;
           skip_until = sk;
@@ -247,6 +250,7 @@ __global__ void __launch_bounds__(kGrWarps * 32, SPH_GRAV_MIN_BLOCKS) k_gravity(
               if (!(q > R(0))) continue;
               const R gq = gm * inv_q32(q);
               acc.add(gq * d[0], gq * d[1], dim == 3 ? gq * d[2] : R(0));
+              ++nterm;
             }
           }
           __syncwarp();
@@ -255,6 +259,11 @@ __global__ void __launch_bounds__(kGrWarps * 32, SPH_GRAV_MIN_BLOCKS) k_gravity(
       nd = any_open ? nd + 1 : sk;
     }
     if (iter > nnodes) raise_err(A.err, ERR_TIMEOUT);
+    if (A.ctr) {
+      warp_count(A.ctr + CTR_GRAV_NODES, nacc);
+      warp_count(A.ctr + CTR_GRAV_TERMS, nterm);
+      if (lane == 0) atomicAdd(A.ctr + CTR_GRAV_VISITS, (unsigned long long)iter);
+    }
     if (act) {
       double gx, gy, gz;
       acc.value(gx, gy, gz);
@@ -286,6 +295,7 @@ void gravity_walk(sph_ctx *c, const sph_state *s, const sph_params &p, double *a
   A.U = c->units;
   A.err = c->d_err;
   A.reuse = reuse ? 1 : 0;
+  A.ctr = counters(c);
   int blocks = c->num_sms * SPH_GRAV_MIN_BLOCKS;  // persistent: the resident blocks, looping over groups
   const bool mixed = p.precision == SPH_MIXED;
   if (s->dim == 3) {

@@ -87,7 +87,8 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
                                            int32_t *err, const unsigned long long *__restrict__ grow,
                                            const Units *__restrict__ U, const int32_t *__restrict__ done,
                                            int32_t *__restrict__ unconverged, double n_des, int tol,
-                                           int32_t *__restrict__ sh_idx, int32_t *__restrict__ sh_cnt) {
+                                           int32_t *__restrict__ sh_idx, int32_t *__restrict__ sh_cnt,
+                                           unsigned long long *ctr) {
   static_assert(!(OWN_H && SHELL), "shells are partner candidates");
   if constexpr (OWN_H) {
     if (*done) return;
@@ -155,6 +156,7 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
     const int32_t stop = root >= 0 ? T.skip[root] : root;
     int cnt = 0, scnt = 0;
     int iter = 0;
+    unsigned ntest = 0;  // candidates this lane tested (counters)
     // Stackless pre-order walk over the node box words: (lo, +-hmax) and
     // (hi, skip), the sign of hmax marking the nodes where the walk stops.
     for (int32_t nd = root; nd < stop && iter <= nnodes; ++iter) {
@@ -195,6 +197,7 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
             }
             __syncwarp();
             if (act) {
+              ntest += c;
               for (int k = 0; k < c; ++k) {
                 const float4 cb = sc[w][k];
                 const int32_t b = sb[w][k];
@@ -233,6 +236,10 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
       nd = enter ? nd + 1 : __float_as_int(bh.w);
     }
     if (iter > nnodes) raise_err(err, ERR_TIMEOUT);
+    if (ctr) {
+      warp_count(ctr + CTR_WALK_TESTS, ntest);
+      warp_count(ctr + CTR_WALK_PARTNERS, act && !OWN_H ? (unsigned)cnt : 0u);
+    }
     if constexpr (OWN_H) {
       if (act) {
         nb_cnt[a] = cnt;
@@ -346,11 +353,11 @@ static void walk(sph_ctx *c, const sph_state *s, cudaStream_t st, const unsigned
   if (shell)
     k_partners<false, true><<<blocks, kNbWarps * 32, 0, st>>>(
         c->tree, c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim, c->kmax, idx, cnt, c->cap_n, c->d_err, grow,
-        c->units, run_if, nullptr, 0.0, 0, c->sh_idx, c->sh_cnt);
+        c->units, run_if, nullptr, 0.0, 0, c->sh_idx, c->sh_cnt, counters(c));
   else
     k_partners<false, false><<<blocks, kNbWarps * 32, 0, st>>>(
         c->tree, c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim, c->kmax, idx, cnt, c->cap_n, c->d_err, grow,
-        c->units, run_if, nullptr, 0.0, 0, nullptr, nullptr);
+        c->units, run_if, nullptr, 0.0, 0, nullptr, nullptr, counters(c));
   ++sph::g_launches;
 }
 
@@ -407,7 +414,7 @@ void adapt_h(sph_ctx *c, sph_state *s, double n_des, int tol, int max_iter, int3
     { k_partners<true, false><<<blocks, kNbWarps * 32, 0, st>>>(c->tree, c->pk, s->x[0], s->x[1], s->x[2], s->h,
                                                                s->dim, c->kmax, c->nb_idx, c->nb_cnt, c->cap_n,
                                                                c->d_err, nullptr, c->units, flags, flags + 2 + i,
-                                                               n_des, tol, nullptr, nullptr); ++sph::g_launches; }
+                                                               n_des, tol, nullptr, nullptr, nullptr); ++sph::g_launches; }
     if (i == max_iter) break;
     { k_h_update<<<nblk(n, 256), 256, 0, st>>>(s->h, c->nb_cnt, n, s->dim, n_des, flags + 2 + i, flags,
                                              flags + 1); ++sph::g_launches; }

@@ -202,6 +202,7 @@ struct sph_ctx {
   sph_tuning tune;      // launch shapes and walk granularity
   int num_sms;
   // profiler
+  unsigned long long *d_ctr;  // device interaction counters (kNumCounters), summed while profiling
   int prof;
   int prof_used;
   cudaEvent_t *prof_ev;       // 2 * kMaxProfEvents
@@ -318,6 +319,16 @@ enum { MF_RHO0, MF_CS, MF_K0, MF_NM, MF_AT, MF_BT, MF_E0, MF_EIV, MF_ECV, MF_AA,
        MF_RHOCUT, MF_MU, MF_Y0 };
 
 double velocity_scale(const MatTable &mt);
+// Interaction counters, accumulated while the profiler is enabled
+enum { CTR_GRAV_NODES, CTR_GRAV_TERMS, CTR_GRAV_VISITS, CTR_WALK_TESTS, CTR_WALK_PARTNERS, kNumCounters };
+inline unsigned long long *counters(const sph_ctx *c) { return c->prof ? c->d_ctr : nullptr; }
+
+// Sum of v over the warp, added to *ctr by lane 0 (every lane must arrive)
+__device__ __forceinline__ void warp_count(unsigned long long *ctr, unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(ctr, v);
+}
+
 // api.cu: profiler hooks (no-ops unless enabled)
 int prof_begin(sph_ctx *c, cudaStream_t st, int phase);
 void prof_end(sph_ctx *c, cudaStream_t st, int idx);

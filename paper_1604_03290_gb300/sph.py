@@ -29,6 +29,7 @@ EOS = {"linear": 0, "murnaghan": 1, "tillotson": 2, "isothermal": 3}
 PRECISION = {"fp64": 0, "mixed": 1}
 PHASES = ("tree", "reorder", "partners", "density", "passA", "passB", "gravity", "integrate", "flaw_draws",
           "flaw_fill", "fof_links", "refine")
+COUNTERS = ("grav_nodes", "grav_terms", "grav_visits", "walk_tests", "walk_partners")
 
 
 class SphError(RuntimeError):
@@ -115,6 +116,7 @@ def lib():
             L.sph_measure_fma_peak.argtypes = [C.c_int32, C.POINTER(C.c_double)]
             L.sph_profile_enable.argtypes = [_vp, C.c_int32]
             L.sph_profile_read.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_int32]
+            L.sph_profile_counters.argtypes = [_vp, C.POINTER(C.c_int64), C.c_int32, _vp]
             L.sph_rhs_adjoint.argtypes = [_vp, C.POINTER(State), C.POINTER(Material), C.c_int32, C.POINTER(Params),
                                           C.POINTER(Derivs), C.POINTER(State), _vp, _vp]
             L.sph_pc_update.argtypes = [_vp, C.POINTER(State), C.POINTER(Derivs), C.POINTER(Material), C.c_int32,
@@ -129,7 +131,7 @@ def lib():
             for f in ("sph_create", "sph_sync_status", "sph_build_tree", "sph_tree_nodes", "sph_neighbours",
                       "sph_neighbours_static", "sph_adapt_h", "sph_step_rk3", "sph_flaws", "sph_fragments",
                       "sph_rhs", "sph_gravity", "sph_step", "sph_measure_fma_peak", "sph_profile_enable",
-                      "sph_profile_read", "sph_get_tuning", "sph_set_tuning", "sph_rhs_adjoint", "sph_pc_update",
+                      "sph_profile_read", "sph_profile_counters", "sph_get_tuning", "sph_set_tuning", "sph_rhs_adjoint", "sph_pc_update",
                       "sph_pc_update_adjoint"):
                 getattr(L, f).restype = C.c_int
             _lib = L
@@ -238,6 +240,14 @@ class Context:
 
     def profile(self, on=True):
         self.check(self._lib.sph_profile_enable(self.h, int(on)), "sph_profile_enable")
+
+    def profile_counters(self, stream=None):
+        """Interaction counters of the walks since profiling began or the last
+        read (sph_profile_counters), then reset."""
+        out = (C.c_int64 * len(COUNTERS))()
+        self.check(self._lib.sph_profile_counters(self.h, out, len(COUNTERS), _stream(stream)),
+                   "sph_profile_counters")
+        return {k: int(out[i]) for i, k in enumerate(COUNTERS)}
 
     def profile_read(self):
         ms = (C.c_double * len(PHASES))()
