@@ -188,6 +188,53 @@ def oracle_time(fn):
     return time.perf_counter() - t0, cores
 
 
+def adjoint_rollout(sph, wl, stream, nsteps=50, every=10):
+    """Gradients of the penetration depth of 256 batched impacts after 50
+    fixed steps with respect to each impact speed and to mu, Y0 and K, by the
+    checkpointed adjoint (a checkpoint every 10 steps, damage off), mixed
+    precision: forward and backward time and the device memory they use."""
+    import numpy as np
+    import torch
+    from dataclasses import replace
+    from paper_1604_03290_gb300 import adjoint
+    bt = wl.batched_impacts(seed=5, with_flaws=False)
+    mat = replace(bt.materials[0], damage=False)
+    bt.materials, bt.dmg = [mat], None
+    cmax = float(np.sqrt(mat.A_T / mat.rho0))
+    dt = 0.25 * float(bt.h.min()) / (cmax + 6000.0)
+    prm = replace(bt.params, max_depth=18, alpha=1.0, beta=2.0, dt_fixed=dt, precision="mixed")
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
+    base = torch.cuda.memory_allocated()
+    ctx = sph.Context(3, bt.n, max_instances=bt.ninst, max_neighbours=128, leaf_size=prm.leaf_size)
+    runner = adjoint.Runner(ctx, bt, prm, dt, nsteps, every=every)
+    proj = torch.as_tensor((bt.v[2] < 0).astype(np.float64), device="cuda")
+    inst = torch.as_tensor(np.repeat(np.arange(bt.ninst), np.diff(bt.inst_off)), device="cuda")
+    x0 = torch.as_tensor(bt.x, device="cuda")
+    v0 = torch.as_tensor(bt.v, device="cuda").requires_grad_(True)
+    m = torch.as_tensor(bt.m, device="cuda")
+    theta = adjoint.theta_of(bt.materials).requires_grad_(True)
+    t0 = time.perf_counter()
+    xN, vN = adjoint.rollout(runner, bt.materials, x0, v0, theta)
+    J = adjoint.penetration_depth(xN, m, proj, 0.0, inst, bt.ninst)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    J.sum().backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    g_speed = -(v0.grad[2] * proj).cpu().numpy()
+    per_inst = np.bincount(inst.cpu().numpy(), weights=g_speed, minlength=bt.ninst)
+    out = {"workload": "%d batched basalt impacts (%d particles), %d fixed steps of %.3g s, checkpoint every %d, "
+                       "mixed precision, damage off" % (bt.ninst, bt.n, nsteps, dt, every),
+           "forward_s": t1 - t0, "backward_s": t2 - t1,
+           "particle_steps_per_s": bt.n * nsteps / (t2 - t0),
+           "peak_torch_bytes": torch.cuda.max_memory_allocated() - base, "context_bytes": ctx.bytes,
+           "dJ_dV0_range": [float(per_inst.min()), float(per_inst.max())],
+           "dJ_dtheta": [float(v) for v in theta.grad.numpy()[0]]}
+    del runner, ctx
+    return out
+
+
 def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3, cloud_n=2_000_000, with_oracle=False):
     import numpy as np
     import torch
@@ -312,7 +359,10 @@ def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3, cloud_n=2_000_000, with
     bctx.sync_status()
     del graph
     dsb = sph.DeviceState(bt)
+    # the same steps as the graph's timed replays: steps 6..17 of the run (the
+    # graph ran a warm-up step and one untimed replay of 4 before them)
     sph.step(bctx, dsb, bt.materials, bprm, 1, check=False)
+    sph.step(bctx, dsb, bt.materials, bprm, 4, check=False)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
     sph.step(bctx, dsb, bt.materials, bprm, 12, check=False)
@@ -361,6 +411,7 @@ def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3, cloud_n=2_000_000, with
     adjoint["adjoint_over_rhs_fp64"] = adjoint["ms_adjoint_fp64"] / adjoint["ms_rhs_fp64"]
     adjoint["adjoint_speedup_mixed_over_fp64"] = adjoint["ms_adjoint_fp64"] / adjoint["ms_adjoint_mixed"]
     del dsa, actx, out, dbar, sbar
+    adjoint["rollout_256"] = adjoint_rollout(sph, wl, stream)
     return {"flaws": flaws, "fragments": frag, "decoupled_gravity": dec, "batched": batched, "adjoint": adjoint}
 
 

@@ -6,8 +6,10 @@ checkpoint and runs the hand-written adjoint of the update
 (sph_pc_update_adjoint) and of the right-hand side (sph_rhs_adjoint) step by
 step in reverse.  Partner lists and damage are those of the forward
 evaluation (damage is held at its initial value: run with damage off), and
-the time step is fixed.  The particle order never changes (no reordering),
-so cotangents line up with the inputs.
+the time step is fixed.  The runner puts the particles in the tree order of
+the initial state once (so that the partner gathers stay coherent) and keeps
+that order for the whole trajectory; inputs, outputs and cotangents are in
+the caller's order, permuted at the boundary.
 
 ``Rollout`` wraps this as a ``torch.autograd.Function`` of the initial
 positions, velocities and the material parameters theta (nmat x 3: shear
@@ -16,6 +18,7 @@ modulus, yield stress, bulk modulus).
 from __future__ import annotations
 
 from dataclasses import replace
+from types import SimpleNamespace
 
 import numpy as np
 import torch
@@ -52,6 +55,9 @@ class Runner:
         self.nsteps = int(nsteps)
         self.every = max(1, int(every))
         self.template = sph.DeviceState(template)
+        # the tree order of the initial state: slot i holds particle order[i]
+        sph.build_tree(ctx, self.template, params.leaf_size, params.max_depth, reorder=True)
+        self.order = self.template.id.long()
         n = max(self.template.ninst, 1)
         self.dt = torch.as_tensor(np.broadcast_to(np.asarray(dt, np.float64), (n,)).copy(), device="cuda")
         self.d0 = sph.alloc_derivs(self.template)
@@ -61,9 +67,15 @@ class Runner:
 
     def _state(self, x0, v0):
         s = self.template.clone()
-        s.x.copy_(x0)
-        s.v.copy_(v0)
+        s.x.copy_(x0[:, self.order])
+        s.v.copy_(v0[:, self.order])
         return s
+
+    def to_caller(self, t):
+        """A (dim, n) tensor in the runner's order, back in the caller's."""
+        out = torch.empty_like(t)
+        out[:, self.order] = t
+        return out
 
     def _step(self, q, qp):
         """q <- one step; qp receives the predicted state; d0 / d1 the derivatives."""
@@ -74,6 +86,8 @@ class Runner:
         sph.pc_update(ctx, q, self.d1, M, P, self.dt, 1.0, q, check=False)
 
     def forward(self, x0, v0, theta):
+        """The end state's positions and velocities (attributes x, v), in the
+        caller's order, from x0, v0 in that order."""
         self.materials = materials_with(self.base_materials, theta)
         q = self._state(x0, v0)
         qp = q.clone()
@@ -83,22 +97,19 @@ class Runner:
             if (k + 1) % self.every == 0 and k + 1 < self.nsteps:
                 self.checkpoints[k + 1] = q.clone()
         self.ctx.sync_status()
-        return q
+        return SimpleNamespace(x=self.to_caller(q.x), v=self.to_caller(q.v))
 
-    def backward(self, xbar, vbar, rhobar=None, ubar=None, Sbar=None):
+    def backward(self, xbar, vbar):
+        """Cotangents of x0, v0 (attributes x, v, caller's order) and of the
+        material parameters (ninst, nmat, 3) from those of the end state's
+        positions and velocities (caller's order)."""
         ctx, P, M = self.ctx, self.params, self.materials
         nmat = len(M)
         ninst = max(self.template.ninst, 1)
         pbar = torch.zeros((ninst, nmat, 3), dtype=torch.float64, device="cuda")
         lam = self.template.zeros_like()
-        lam.x.copy_(xbar)
-        lam.v.copy_(vbar)
-        if rhobar is not None:
-            lam.rho.copy_(rhobar)
-        if ubar is not None:
-            lam.u.copy_(ubar)
-        if Sbar is not None and lam.S is not None:
-            lam.S.copy_(Sbar)
+        lam.x.copy_(xbar[:, self.order])
+        lam.v.copy_(vbar[:, self.order])
         lam_k = self.template.zeros_like()
         lam_p = self.template.zeros_like()
         qp = self.template.clone()
@@ -132,7 +143,7 @@ class Runner:
                 sph.rhs_adjoint(ctx, q, M, P, self.fbar, lam_k, pbar, check=False)
                 lam, lam_k = lam_k, lam
         ctx.sync_status()
-        return lam, pbar
+        return SimpleNamespace(x=self.to_caller(lam.x), v=self.to_caller(lam.v)), pbar
 
 
 class Rollout(torch.autograd.Function):
