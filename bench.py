@@ -342,6 +342,7 @@ def aux_rows(sph, wl, ctx, ps, stream, hbm_peak, reps=3, cloud_n=2_000_000, with
     # and launched directly
     bt = wl.batched_impacts(seed=5)
     bctx = sph.Context(3, bt.n, max_instances=bt.ninst, max_neighbours=128, leaf_size=bt.params.leaf_size)
+    sph.fill_flaws(bctx, bt)
     bprm = replace(bt.params, precision="mixed")
     dsb = sph.DeviceState(bt)
     graph = sph.StepGraph(bctx, dsb, bt.materials, bprm, nsteps=4)
@@ -578,6 +579,7 @@ def main():
     n = ps.n
     prm = replace(ps.params, precision="mixed", tree_reuse=args.tree_reuse)
     ctx = sph.Context(3, n, max_neighbours=128, leaf_size=prm.leaf_size)
+    sph.fill_flaws(ctx, ps)  # the Weibull flaws, drawn on the device (sph_flaws)
     stream = torch.cuda.current_stream()
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm_peak, peak_src = 6800.0, "fallback 6.8 TB/s"

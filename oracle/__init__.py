@@ -420,9 +420,18 @@ def sym_eig(A):
     return w, V
 
 
+def ensure_flaws(ps):
+    """Draws the particle set's Weibull flaws with orc_flaws (Sect. 3.2) from
+    its flaw_seed when they are still missing, in place; returns ps."""
+    if ps.flaw_off is None and getattr(ps, "flaw_seed", None) is not None:
+        ps.flaw_off, ps.flaw_eps = flaws(ps, seed=ps.flaw_seed)
+    return ps
+
+
 def rhs(ps, materials, params):
     """One right-hand side.  Returns a dict of derivatives and diagnostics;
     ``rho`` holds the (possibly recomputed) density."""
+    ensure_flaws(ps)
     st = _StateArrays(ps)
     ns = 6 if ps.dim == 3 else 3
     d, out = _derivs(ps.dim, ps.n, ns)
@@ -436,6 +445,7 @@ def rhs(ps, materials, params):
 
 
 def timestep(ps, materials, params, derivs):
+    ensure_flaws(ps)
     st = _StateArrays(ps)
     d = Derivs()
     dim = ps.dim
@@ -455,6 +465,7 @@ def step_rk3(ps, materials, params, eps_des, nsteps, dt=None, t=None):
     """nsteps embedded Runge-Kutta attempts (Sect. 3.4.2) on a copy.  dt, t: per
     instance (None: dt from the predictor-corrector limit, t = 0).  Returns
     (state dict, dt, t, error log [nsteps, ninst], accepted log [nsteps, ninst])."""
+    ensure_flaws(ps)
     st = _StateArrays(ps)
     ninst = max(ps.ninst, 1)
     dtv = np.zeros(ninst) if dt is None else np.array(dt, dtype=np.float64, copy=True)
@@ -471,6 +482,7 @@ def step_rk3(ps, materials, params, eps_des, nsteps, dt=None, t=None):
 
 def step(ps, materials, params, nsteps):
     """Run nsteps predictor-corrector steps on a copy; returns (state dict, dt log [nsteps, ninst])."""
+    ensure_flaws(ps)
     st = _StateArrays(ps)
     ninst = max(ps.ninst, 1)
     dt = np.zeros(ninst)

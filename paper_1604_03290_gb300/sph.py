@@ -261,6 +261,9 @@ class DeviceState:
 
     def __init__(self, ps: wl.ParticleSet, device="cuda"):
         _require_cuda()
+        if ps.flaw_off is None and getattr(ps, "flaw_seed", None) is not None:
+            raise ValueError("the particle set's Weibull flaws are not drawn yet: fill_flaws(ctx, ps) draws them "
+                             "on the device from ps.flaw_seed")
         f64 = lambda a: None if a is None else torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64,
                                                                 device=device).contiguous()
         self.dim = ps.dim
@@ -418,6 +421,20 @@ def flaws(ctx: Context, ds: DeviceState, materials, weibull_k=None, weibull_m=No
         r = ctx._lib.sph_flaws(*args, _ptr(off), _ptr(eps), int(tot.value), C.byref(tot), _stream(stream))
     ctx.check(r, "sph_flaws")
     return off, eps[: tot.value]
+
+
+def fill_flaws(ctx: Context, ps: wl.ParticleSet, stream=None) -> wl.ParticleSet:
+    """Draws the Weibull flaws of ps (Sect. 3.2) on the device from
+    ps.flaw_seed with the materials' k and m (sph_flaws), into ps.flaw_off and
+    ps.flaw_eps (host arrays, indexed by id); returns ps.  No-op when ps has
+    its flaws or needs none."""
+    from dataclasses import replace
+    if ps.flaw_off is not None or getattr(ps, "flaw_seed", None) is None:
+        return ps
+    ds = DeviceState(replace(ps, flaw_seed=None))
+    off, eps = flaws(ctx, ds, ps.materials, seed=ps.flaw_seed, stream=stream)
+    ps.flaw_off, ps.flaw_eps = off.cpu().numpy(), eps.cpu().numpy()
+    return ps
 
 
 def fragments(ctx: Context, ds: DeviceState, h0=None, link=1.01, d_remove=1.0, min_size=3, leaf_size=16,

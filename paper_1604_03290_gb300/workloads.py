@@ -1,10 +1,13 @@
 """Seeded synthetic particle sets shaped like the paper's test problems.
 
 This module only *creates inputs*: lattices, jitter, masses, velocities,
-material and run parameters, and the Weibull flaw thresholds that the damage
-model consumes as data.  It holds none of the right-hand-side arithmetic.
-Both the CUDA path and the CPU oracle are fed from it, so neither one's input
-depends on the other.
+material and run parameters.  It holds none of the method's arithmetic.  The
+Weibull flaws the damage model needs (Sect. 3.2) are not drawn here: a damage
+workload carries the seed of its flaws (``flaw_seed``), and the flaw
+generator of the library (sph_flaws) or of the oracle (orc_flaws), pinned
+against each other, draws them from it.  Both the CUDA path and the CPU
+oracle are fed from this module, so neither one's input depends on the
+other.
 
 Units are SI except for the 2D ring problem, which uses the paper's code units
 (length cm, density rho0, velocity c_s; Sect. 4.1).
@@ -112,6 +115,7 @@ class ParticleSet:
     dmg: Optional[np.ndarray] = None    # d^(1/3)
     flaw_off: Optional[np.ndarray] = None   # int64 (n+1), indexed by id
     flaw_eps: Optional[np.ndarray] = None   # float32, ascending per particle
+    flaw_seed: Optional[int] = None         # seed of the flaws still to draw (flaw_off is None until then)
     inst_off: Optional[np.ndarray] = None   # int64 (ninst+1)
     materials: List[Material] = field(default_factory=list)
     params: Params = field(default_factory=Params)
@@ -195,31 +199,6 @@ def _lattice_ball(radius, dx, center=(0.0, 0.0, 0.0)):
     return pts[:, keep] + np.asarray(center, dtype=np.float64)[:, None]
 
 
-def weibull_flaws(rng, n, volume, k, m):
-    """Activation thresholds of Sect. 3.2 (after Benz & Asphaug): flaw j = 1,
-    2, ... goes to a uniformly drawn particle with threshold (j / (k V))^(1/m),
-    until every particle holds at least one.  Returns CSR (offsets int64[n+1],
-    thresholds float32, ascending within a particle)."""
-    if n == 0:
-        return np.zeros(1, np.int64), np.zeros(0, np.float32)
-    draws = []
-    covered = np.zeros(n, bool)
-    while not covered.all():
-        c = rng.integers(0, n, size=max(n, 4096), dtype=np.int64)
-        draws.append(c)
-        covered[c] = True
-    d = np.concatenate(draws)
-    _, first = np.unique(d, return_index=True)
-    d = d[: int(first.max()) + 1]
-    j = np.arange(1, len(d) + 1, dtype=np.float64)
-    eps = (j / (k * volume)) ** (1.0 / m)
-    order = np.argsort(d, kind="stable")
-    counts = np.bincount(d, minlength=n)
-    off = np.zeros(n + 1, np.int64)
-    np.cumsum(counts, out=off[1:])
-    return off, eps[order].astype(np.float32)
-
-
 def _finish(dim, x, v, m, h, rho, u, mat, materials, params, with_S=True, with_dmg=False, name="",
             inst_off=None):
     n = x.shape[1]
@@ -300,7 +279,8 @@ def measurement_1m(seed=11, n_side=100, damage=True, weibull_k=5e34, weibull_m=8
     cm for 100^3) plus the projectile, with a state perturbed so that every
     branch runs: rho = rho0 (1 + N(0, 0.01)), u ~ U[0, 1.5e7] J/kg (all three
     Tillotson regimes), v ~ N(0, 10 m/s), S_ij ~ N(0, 0.3 Y0) (some yield),
-    d^(1/3) ~ U[0, 0.5] and Weibull flaws (k, m as for the basalt bodies)."""
+    d^(1/3) ~ U[0, 0.5] and Weibull flaws (k, m as for the basalt bodies;
+    drawn from flaw_seed = seed + 2000)."""
     ps = al_impact(seed=seed, n_side=n_side)
     rng = np.random.default_rng(seed + 1000)
     n = ps.n
@@ -313,8 +293,7 @@ def measurement_1m(seed=11, n_side=100, damage=True, weibull_k=5e34, weibull_m=8
         mat = replace(mat, damage=True, weibull_k=weibull_k, weibull_m=weibull_m)
         ps.materials = [mat]
         ps.dmg = rng.uniform(0.0, 0.5, n)
-        vol = float(np.sum(ps.m / mat.rho0))
-        ps.flaw_off, ps.flaw_eps = weibull_flaws(rng, n, vol, weibull_k, weibull_m)
+        ps.flaw_seed = seed + 2000
     ps.name = "measurement_%d" % n
     return ps
 
@@ -355,7 +334,8 @@ def ceres_pair(seed=4, n_each=1_000_000, R=470e3, speed=1000.0, angle_deg=45.0, 
     """Two basalt bodies (Sect. 5 scenario, sizes as given for this workload):
     radius R each, cubic lattices with +/-0.1 spacing jitter, relative speed
     `speed` with impact parameter 2R sin(angle), one spacing apart at
-    contact; Weibull flaws k = 5e34, m = 8.5; Barnes-Hut opening angle 0.6."""
+    contact; Weibull flaws k = 5e34, m = 8.5 (flaw_seed = seed + 2000);
+    Barnes-Hut opening angle 0.6."""
     rng = np.random.default_rng(seed)
     dx = R * (4.0 * math.pi / 3.0 / n_each) ** (1.0 / 3.0)
     body = _lattice_ball(R, dx)
@@ -374,8 +354,7 @@ def ceres_pair(seed=4, n_each=1_000_000, R=470e3, speed=1000.0, angle_deg=45.0, 
                     u_floor=1e3, S_floor=1e5)
     ps = _finish(3, x, v, np.full(n, mat.rho0 * dx ** 3), np.full(n, 2.4 * dx), np.full(n, mat.rho0), np.zeros(n),
                  np.zeros(n, np.int32), [mat], params, with_dmg=True, name="ceres_pair_%d" % n)
-    vol = float(np.sum(ps.m / mat.rho0))
-    ps.flaw_off, ps.flaw_eps = weibull_flaws(rng, n, vol, mat.weibull_k, mat.weibull_m)
+    ps.flaw_seed = seed + 2000
     return ps
 
 
@@ -422,8 +401,7 @@ def batched_impacts(seed=5, ninst=256, nmin=2000, nmax=50000, dx=1e-3, vmin=3000
                  np.zeros(n, np.int32), [mat], params, with_dmg=True, name="batched_%d" % ninst,
                  inst_off=np.asarray(off, np.int64))
     if with_flaws:
-        vol = float(np.sum(ps.m / mat.rho0))
-        ps.flaw_off, ps.flaw_eps = weibull_flaws(rng, n, vol, mat.weibull_k, mat.weibull_m)
+        ps.flaw_seed = seed + 2000
     return ps
 
 

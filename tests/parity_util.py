@@ -113,3 +113,11 @@ def check_damage(ps, o, g, prec, tol, report=None):
         report.update({"n_act_flips": int(bad.size), "ddmg_same": err_same, "ddmg_flipped": err_flip})
     assert err_same <= 10 * tol, err_same
     assert err_flip <= 10 * tol, err_flip
+
+
+def flawed(ps):
+    """The particle set with its Weibull flaws drawn by the oracle (orc_flaws,
+    Sect. 3.2) from its flaw_seed, so that both sides of a comparison read the
+    same pinned flaws; returns ps."""
+    import oracle
+    return oracle.ensure_flaws(ps)

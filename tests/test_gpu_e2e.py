@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 from paper_1604_03290_gb300 import workloads as wl
+from parity_util import flawed
 
 pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -31,7 +32,7 @@ def test_host_steps_equal_device_steps(S):
     import torch
     sys.path.insert(0, ROOT)
     import bench
-    ps = wl.measurement_1m(seed=11, n_side=30)
+    ps = flawed(wl.measurement_1m(seed=11, n_side=30))
     prm = replace(ps.params, precision="mixed", tree_reuse=4)
     ctx = S.Context(3, ps.n, max_neighbours=128, leaf_size=prm.leaf_size)
     stream = torch.cuda.current_stream()

@@ -13,6 +13,7 @@ import pytest
 
 from paper_1604_03290_gb300 import workloads as wl
 from parity_util import check_damage, compare_rhs
+from parity_util import flawed
 
 pytestmark = pytest.mark.gpu
 
@@ -63,7 +64,7 @@ def _check_rhs(S, orc, ps, precs=("fp64", "mixed")):
 
 @pytest.fixture(scope="module")
 def m1():
-    return wl.measurement_1m(seed=11, n_side=100)
+    return flawed(wl.measurement_1m(seed=11, n_side=100))
 
 
 def test_rhs_measured_1m_every_particle(S, orc, m1):
@@ -106,13 +107,13 @@ def test_step_measured_1m(S, orc, m1):
 def test_steps_measured_1m_reused_tree(S, orc, m1):
     # the bench's configuration: one tree serves 3 steps, and the evaluations
     # after the build refine their partners from the build step's walk
-    ps = wl.measurement_1m(seed=11, n_side=100)
+    ps = flawed(wl.measurement_1m(seed=11, n_side=100))
     ps.params = replace(ps.params, tree_reuse=3)
     _check_step(S, orc, ps, nsteps=3)
 
 
 def test_step_256_batched_impacts(S, orc):
-    ps = wl.batched_impacts(seed=5)
+    ps = flawed(wl.batched_impacts(seed=5))
     assert ps.ninst == 256
     _check_step(S, orc, ps)
 
@@ -154,7 +155,7 @@ def test_cloud_2m_rhs_and_sampled_gravity(S, orc):
 
 
 def test_ceres_pair_rhs_and_sampled_gravity(S, orc):
-    ps = wl.ceres_pair(seed=4)
+    ps = flawed(wl.ceres_pair(seed=4))
     assert ps.n > 1_900_000
     _check_gravity(S, orc, ps)
     ps.params = replace(ps.params, gravity=False)

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from paper_1604_03290_gb300 import workloads as wl
-from parity_util import check_damage, compare_rhs
+from parity_util import check_damage, compare_rhs, flawed
 
 pytestmark = pytest.mark.gpu
 
@@ -125,14 +125,15 @@ def _random_solid(seed=0, dim=3, n_side=10, damage=True):
     ps.S = rng.normal(0, 0.02, (ps.nsym, n))
     ps.materials = [replace(ps.materials[0], Y0=0.05, damage=damage, K0=1.0, mu=0.5)]
     if damage:
+        import oracle
         ps.dmg = rng.uniform(0, 0.6, n)
-        ps.flaw_off, ps.flaw_eps = wl.weibull_flaws(rng, n, float(n), 1e10, 6.0)
+        ps.flaw_off, ps.flaw_eps = oracle.flaws(ps, weibull_k=[1e10], weibull_m=[6.0], seed=seed + 7)
     ps.params = replace(ps.params, eps_s=0.2, n_as=4.0, xsph=0.5)
     return ps
 
 
 def _small_impact(seed=31):
-    ps = wl.measurement_1m(seed=seed, n_side=18)
+    ps = flawed(wl.measurement_1m(seed=seed, n_side=18))
     return ps
 
 
@@ -140,7 +141,7 @@ def _fast_impact(seed=33):
     # a fixed step long enough that the predictor half-step moves the projectile
     # by about half its support radius: the predictor evaluation's partner
     # search must still find every partner
-    ps = wl.measurement_1m(seed=seed, n_side=14)
+    ps = flawed(wl.measurement_1m(seed=seed, n_side=14))
     hp = ps.h[ps.v[2] < -1000.0].min()
     ps.params = replace(ps.params, dt_fixed=2 * 0.5 * hp / 7000.0)
     return ps
@@ -162,7 +163,7 @@ def _cloud_variable_h():
 
 
 def _small_batch():
-    ps = wl.batched_impacts(seed=5, ninst=3, nmin=400, nmax=1500)
+    ps = flawed(wl.batched_impacts(seed=5, ninst=3, nmin=400, nmax=1500))
     rng = np.random.default_rng(9)
     ps.u = rng.uniform(0, 1e7, ps.n)
     ps.S = rng.normal(0, 1e8, (6, ps.n))

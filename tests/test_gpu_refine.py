@@ -17,6 +17,7 @@ import numpy as np
 import pytest
 
 from paper_1604_03290_gb300 import workloads as wl
+from parity_util import flawed
 
 pytestmark = pytest.mark.gpu
 
@@ -31,18 +32,18 @@ def S():
 
 
 def _impact():
-    return wl.measurement_1m(seed=31, n_side=18)
+    return flawed(wl.measurement_1m(seed=31, n_side=18))
 
 
 def _impact_fast():
-    ps = wl.measurement_1m(seed=33, n_side=14)
+    ps = flawed(wl.measurement_1m(seed=33, n_side=14))
     hp = ps.h[ps.v[2] < -1000.0].min()
     ps.params = replace(ps.params, dt_fixed=2 * 0.5 * hp / 7000.0)
     return ps
 
 
 def _batch():
-    ps = wl.batched_impacts(seed=5, ninst=4, nmin=400, nmax=1500)
+    ps = flawed(wl.batched_impacts(seed=5, ninst=4, nmin=400, nmax=1500))
     ps.params = replace(ps.params, max_depth=19)
     return ps
 
@@ -64,7 +65,7 @@ def _lattice_crowded_shell():
 
 
 def _pair_reuse():
-    ps = wl.ceres_pair(seed=4, n_each=2500)
+    ps = flawed(wl.ceres_pair(seed=4, n_each=2500))
     ps.params = replace(ps.params, dt_fixed=2.0, tree_reuse=2)
     return ps
 
@@ -72,7 +73,7 @@ def _pair_reuse():
 def _impact_reuse():
     # the measured configuration's physics on a tree reused for 3 steps: the
     # steps after a build refine both evaluations from the build step's walk
-    ps = wl.measurement_1m(seed=35, n_side=18)
+    ps = flawed(wl.measurement_1m(seed=35, n_side=18))
     ps.params = replace(ps.params, tree_reuse=3)
     return ps
 
@@ -80,7 +81,7 @@ def _impact_reuse():
 def _impact_reuse_long():
     # reused for 6 steps with a fixed step 8x the limiter's: the bound fails
     # within the window, and those evaluations walk the widened boxes
-    ps = wl.measurement_1m(seed=37, n_side=14)
+    ps = flawed(wl.measurement_1m(seed=37, n_side=14))
     hp = ps.h.min()
     ps.params = replace(ps.params, tree_reuse=6, dt_fixed=0.8 * hp / 64 / (4 * np.sqrt(3)) / 7000.0)
     return ps

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 from paper_1604_03290_gb300 import workloads as wl
+from parity_util import flawed
 
 pytestmark = pytest.mark.gpu
 
@@ -26,7 +27,7 @@ def S():
 
 
 def _case():
-    ps = wl.measurement_1m(seed=41, n_side=20)
+    ps = flawed(wl.measurement_1m(seed=41, n_side=20))
     ps.params = replace(ps.params, tree_reuse=4)
     return ps
 

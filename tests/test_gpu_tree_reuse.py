@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 
 from paper_1604_03290_gb300 import workloads as wl
+from parity_util import flawed
 
 pytestmark = pytest.mark.gpu
 
@@ -37,18 +38,18 @@ def _cloud():
 
 
 def _pair():
-    ps = wl.ceres_pair(seed=4, n_each=2500)
+    ps = flawed(wl.ceres_pair(seed=4, n_each=2500))
     ps.params = replace(ps.params, dt_fixed=2.0)
     return ps
 
 
 def _impact():
-    return wl.measurement_1m(seed=11, n_side=14)
+    return flawed(wl.measurement_1m(seed=11, n_side=14))
 
 
 def _batch():
     # three impacts in one state: the walks take the tree's per-instance groups
-    ps = wl.batched_impacts(seed=5, ninst=3, nmin=400, nmax=1500)
+    ps = flawed(wl.batched_impacts(seed=5, ninst=3, nmin=400, nmax=1500))
     ps.params = replace(ps.params, max_depth=19)
     return ps
 

@@ -21,9 +21,10 @@ def _random_state(seed=0, dim=3, n_side=9, jitter=0.25, strength=True, damage=Fa
     ns = 6 if dim == 3 else 3
     ps.S = rng.normal(0, 0.01, (ns, n)) if strength else None
     if damage:
+        import oracle
         ps.dmg = rng.uniform(0, 0.5, n)
-        ps.flaw_off, ps.flaw_eps = wl.weibull_flaws(rng, n, float(n), 1e8, 6.0)
         ps.materials = [replace(ps.materials[0], damage=True)]
+        ps.flaw_off, ps.flaw_eps = oracle.flaws(ps, weibull_k=[1e8], weibull_m=[6.0], seed=seed + 7)
     return ps
 
 

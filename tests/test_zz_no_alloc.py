@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 from paper_1604_03290_gb300 import workloads as wl
+from parity_util import flawed
 
 pytestmark = pytest.mark.gpu
 
@@ -20,8 +21,8 @@ def S():
 
 
 def _cases():
-    solid = wl.measurement_1m(seed=4, n_side=20)                       # 3D, one body
-    batch = wl.batched_impacts(seed=5, ninst=3, nmin=400, nmax=1500)   # 3D, three instances
+    solid = flawed(wl.measurement_1m(seed=4, n_side=20))                       # 3D, one body
+    batch = flawed(wl.batched_impacts(seed=5, ninst=3, nmin=400, nmax=1500))   # 3D, three instances
     rings = wl.rings_2d(seed=3)                                        # 2D
     return [("solid", solid, 16, 21, 160), ("batch", batch, 16, 19, 256), ("rings", rings, 8, 21, 128)]
 
@@ -45,7 +46,7 @@ def test_static_lists_equal_context_lists_on_calls_in_a_row(S):
 
 
 def test_static_rejects_sizes_beyond_the_scratch(S):
-    big = wl.measurement_1m(seed=4, n_side=40)  # 64k particles: ~69 MB at 128 partners
+    big = flawed(wl.measurement_1m(seed=4, n_side=40))  # 64k particles: ~69 MB at 128 partners
     with pytest.raises(S.SphError) as e:
         S.neighbours_static(S.DeviceState(big), 16, 21, 128)
     assert e.value.status == S.SPH_ERR_CAPACITY
