@@ -148,6 +148,7 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   c->nb_cnt_alt = ctx_alloc<int32_t>(c, N, ok);
   c->sh_idx = ctx_alloc<int32_t>(c, (int64_t)kMaxShell * N, ok);
   c->sh_cnt = ctx_alloc<int32_t>(c, N, ok);
+  c->sh_in = ctx_alloc<int32_t>(c, N, ok);
   c->need_walk = ctx_alloc<int32_t>(c, 1, ok);
   c->csr_total = ctx_alloc<int64_t>(c, 1, ok);
   c->hflags = ctx_alloc<int32_t>(c, kMaxHIter + 3, ok);

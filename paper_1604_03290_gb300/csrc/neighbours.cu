@@ -88,7 +88,7 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
                                            const Units *__restrict__ U, const int32_t *__restrict__ done,
                                            int32_t *__restrict__ unconverged, double n_des, int tol,
                                            int32_t *__restrict__ sh_idx, int32_t *__restrict__ sh_cnt,
-                                           unsigned long long *ctr) {
+                                           int32_t *__restrict__ sh_in, unsigned long long *ctr) {
   static_assert(!(OWN_H && SHELL), "shells are partner candidates");
   if constexpr (OWN_H) {
     if (*done) return;
@@ -155,6 +155,7 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
     const int32_t root = T.inst_root[inst];
     const int32_t stop = root >= 0 ? T.skip[root] : root;
     int cnt = 0, scnt = 0;
+    uint32_t sin = 0;  // shell entries that are partners (bit per entry)
     int iter = 0;
     unsigned ntest = 0;  // candidates this lane tested (counters)
     // Stackless pre-order walk over the node box words: (lo, +-hmax) and
@@ -215,7 +216,10 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
                   ++cnt;
                   if constexpr (SHELL) {
                     if (r2 >= h2 * kInner2) {  // a partner near the support radius
-                      if (scnt < kMaxShell) sh_idx[(int64_t)scnt * ld + a] = b;
+                      if (scnt < kMaxShell) {
+                        sh_idx[(int64_t)scnt * ld + a] = b;
+                        sin |= 1u << scnt;
+                      }
                       ++scnt;
                     }
                   }
@@ -248,7 +252,10 @@ __global__ void SPH_WALK_BOUNDS k_partners(Tree T, PackedF32 pk, const double *_
     } else if (act) {
       nb_cnt[a] = min(cnt, kmax);
       if (cnt > kmax) raise_err(err, ERR_NB_OVERFLOW);
-      if constexpr (SHELL) sh_cnt[a] = scnt <= kMaxShell ? scnt : -1;
+      if constexpr (SHELL) {
+        sh_cnt[a] = scnt <= kMaxShell ? scnt : -1;
+        sh_in[a] = (int32_t)sin;
+      }
     }
   }
 }
@@ -273,7 +280,8 @@ __global__ void __launch_bounds__(kRefineThreads)
                       const double *__restrict__ z, const double *__restrict__ h, int dim, int64_t n, int64_t ld,
                       int kmax, const int32_t *__restrict__ old_idx, const int32_t *__restrict__ old_cnt,
                       const int32_t *__restrict__ sh_idx, const int32_t *__restrict__ sh_cnt,
-                      int32_t *__restrict__ new_idx, int32_t *__restrict__ new_cnt,
+                      const int32_t *__restrict__ sh_in, int32_t *__restrict__ new_idx,
+                      int32_t *__restrict__ new_cnt,
                       const unsigned long long *__restrict__ move, int32_t *__restrict__ need_walk, int32_t *err) {
   // the shell of each thread's particle, staged for the merge
   __shared__ int32_t shs[kMaxShell][kRefineThreads];
@@ -308,7 +316,13 @@ __global__ void __launch_bounds__(kRefineThreads)
       in |= (uint32_t)ok << j;
     }
   }
-  // 2. merge: list members outside the shell are kept, shell members that are
+  // 2a. no shell member changed sides: the list is the walk's, and a count of
+  // -1 tells the passes to read that list (nothing is copied)
+  if (in == (uint32_t)sh_in[a]) {
+    new_cnt[a] = -1;
+    return;
+  }
+  // 2b. merge: list members outside the shell are kept, shell members that are
   // in are emitted once (in the list or inserted), the others dropped; the
   // list is read 8 entries at a time so that its loads overlap
   const int nl = old_cnt[a];
@@ -353,11 +367,11 @@ static void walk(sph_ctx *c, const sph_state *s, cudaStream_t st, const unsigned
   if (shell)
     k_partners<false, true><<<blocks, kNbWarps * 32, 0, st>>>(
         c->tree, c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim, c->kmax, idx, cnt, c->cap_n, c->d_err, grow,
-        c->units, run_if, nullptr, 0.0, 0, c->sh_idx, c->sh_cnt, counters(c));
+        c->units, run_if, nullptr, 0.0, 0, c->sh_idx, c->sh_cnt, c->sh_in, counters(c));
   else
     k_partners<false, false><<<blocks, kNbWarps * 32, 0, st>>>(
         c->tree, c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim, c->kmax, idx, cnt, c->cap_n, c->d_err, grow,
-        c->units, run_if, nullptr, 0.0, 0, nullptr, nullptr, counters(c));
+        c->units, run_if, nullptr, 0.0, 0, nullptr, nullptr, nullptr, counters(c));
   ++sph::g_launches;
 }
 
@@ -372,7 +386,7 @@ void refine_partners(sph_ctx *c, const sph_state *s, const unsigned long long *m
   if (n == 0) return;
   cudaMemsetAsync(c->need_walk, 0, sizeof(int32_t), st);
   { k_partners_refine<<<nblk(n, kRefineThreads), kRefineThreads, 0, st>>>(c->pk, s->x[0], s->x[1], s->x[2], s->h, s->dim, n, c->cap_n,
-                                                   c->kmax, c->nb_idx, c->nb_cnt, c->sh_idx, c->sh_cnt, c->nb_alt,
+                                                   c->kmax, c->nb_idx, c->nb_cnt, c->sh_idx, c->sh_cnt, c->sh_in, c->nb_alt,
                                                    c->nb_cnt_alt, move, c->need_walk, c->d_err); ++sph::g_launches; }
   // returns at once unless a particle set the flag
   walk(c, s, st, grow, c->nb_alt, c->nb_cnt_alt, false, c->need_walk);
@@ -414,7 +428,7 @@ void adapt_h(sph_ctx *c, sph_state *s, double n_des, int tol, int max_iter, int3
     { k_partners<true, false><<<blocks, kNbWarps * 32, 0, st>>>(c->tree, c->pk, s->x[0], s->x[1], s->x[2], s->h,
                                                                s->dim, c->kmax, c->nb_idx, c->nb_cnt, c->cap_n,
                                                                c->d_err, nullptr, c->units, flags, flags + 2 + i,
-                                                               n_des, tol, nullptr, nullptr, nullptr); ++sph::g_launches; }
+                                                               n_des, tol, nullptr, nullptr, nullptr, nullptr); ++sph::g_launches; }
     if (i == max_iter) break;
     { k_h_update<<<nblk(n, 256), 256, 0, st>>>(s->h, c->nb_cnt, n, s->dim, n_des, flags + 2 + i, flags,
                                              flags + 1); ++sph::g_launches; }

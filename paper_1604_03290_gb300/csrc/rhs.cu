@@ -46,6 +46,9 @@ struct RhsArgs {
   const int64_t *flaw_off;
   const float *flaw_eps;
   const int32_t *nb_idx, *nb_cnt;
+  // a count of -1 (a refined list left as it was) means: the list and count
+  // of the walk it was refined from, here
+  const int32_t *nb_idx2, *nb_cnt2;
   PackedF32 pk;
   double *dx[3], *dv[3], *drho, *du, *dS, *ddmg, *p_out, *cs_out;
   int32_t *nact, *nnb;
@@ -226,6 +229,17 @@ struct Own<true> {
 #define SPH_PASS_PREFETCH 1
 #endif
 
+// Particle a's partner column and count (see RhsArgs::nb_idx2)
+__device__ __forceinline__ int partner_list(const RhsArgs &A, int64_t a, const int32_t *&col) {
+  int cnt = A.nb_cnt[a];
+  col = A.nb_idx + a;
+  if (cnt < 0) {
+    cnt = A.nb_cnt2[a];
+    col = A.nb_idx2 + a;
+  }
+  return cnt;
+}
+
 template <bool MIXED, bool WITH_T = false>
 struct PartnerCursor {
   using Raw = typename Own<MIXED>::Raw;
@@ -236,8 +250,8 @@ struct PartnerCursor {
   int32_t b1, b2;
   Raw r1;
   float4 t0, t1;
-  __device__ __forceinline__ void start(const RhsArgs &A, const Own<MIXED> &o, int64_t a, int n) {
-    col = A.nb_idx + a;
+  __device__ __forceinline__ void start(const RhsArgs &A, const Own<MIXED> &o, const int32_t *list, int n) {
+    col = list;
     ld = A.ld;
     cnt = n;
     b1 = n > 0 ? col[0] : 0;
@@ -289,9 +303,10 @@ __global__ void __launch_bounds__(128) k_density_sum(RhsArgs A) {
     R hinv = rcp_rn((R)o.h);
     sum.add((R)o.m * sig * hpow(hinv, dim));
   }
-  const int cnt = A.nb_cnt[a];
+  const int32_t *list;
+  const int cnt = partner_list(A, a, list);
   for (int k = 0; k < cnt; ++k) {
-    const int32_t b = A.nb_idx[(int64_t)k * A.ld + a];
+    const int32_t b = list[(int64_t)k * A.ld];
     R d[3], w[3], hb, rhob, mb, vol;
     o.pair(A, b, d, w, hb, rhob, mb, vol);
     R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -406,10 +421,11 @@ __global__ void SPH_PASSA_BOUNDS k_passA(RhsArgs A) {
   R L[3][3], G[3][3], xs[3] = {R(0), R(0), R(0)};
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) L[i][j] = G[i][j] = R(0);
-  const int cnt = A.nb_cnt[a];
+  const int32_t *list;
+  const int cnt = partner_list(A, a, list);
 #if SPH_PASS_PREFETCH
   PartnerCursor<MIXED> cur;
-  cur.start(A, o, a, cnt);
+  cur.start(A, o, list, cnt);
 #endif
   for (int k = 0; k < cnt; ++k) {
     R d[3], w[3], hb, rhob, mb, vol;
@@ -419,7 +435,7 @@ __global__ void SPH_PASSA_BOUNDS k_passA(RhsArgs A) {
     cur.next(A, o, k, raw, t0, t1);
     o.from(A, raw, d, w, hb, rhob, mb, vol);
 #else
-    const int32_t b = A.nb_idx[(int64_t)k * A.ld + a];
+    const int32_t b = list[(int64_t)k * A.ld];
     o.pair(A, b, d, w, hb, rhob, mb, vol);
 #endif
     const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -710,10 +726,11 @@ __global__ void SPH_PASSB_BOUNDS k_passB(RhsArgs A) {
   const R alpha = (R)P.alpha, beta = (R)P.beta, epsv = (R)P.eps_v, nas = (R)P.n_as;
   const R dmpd = (R)(P.dmpd * (MIXED ? A.U->invL : 1.0));
   KahanT<R> acc[3], du;
-  const int cnt = A.nb_cnt[a];
+  const int32_t *list;
+  const int cnt = partner_list(A, a, list);
 #if SPH_PASS_PREFETCH
   PartnerCursor<MIXED, true> cur;
-  cur.start(A, o, a, cnt);
+  cur.start(A, o, list, cnt);
 #endif
   for (int k = 0; k < cnt; ++k) {
     R d[3], w[3], hb, rhob, mb, vol;
@@ -735,7 +752,7 @@ __global__ void SPH_PASSB_BOUNDS k_passB(RhsArgs A) {
       load_T<MIXED>(A, b, ns, Tb, csb);
     }
 #else
-    const int32_t b = A.nb_idx[(int64_t)k * A.ld + a];
+    const int32_t b = list[(int64_t)k * A.ld];
     o.pair(A, b, d, w, hb, rhob, mb, vol);
     load_T<MIXED>(A, b, ns, Tb, csb);
 #endif
@@ -837,6 +854,8 @@ void rhs_passes(sph_ctx *c, sph_state *s, const MatTable &mt, const sph_params &
   A.flaw_eps = s->flaw_eps;
   A.nb_idx = c->nb_idx;
   A.nb_cnt = c->nb_cnt;
+  A.nb_idx2 = c->nb_alt;
+  A.nb_cnt2 = c->nb_cnt_alt;
   A.pk = c->pk;
   A.drho = out.drho;
   A.du = out.du;

@@ -185,6 +185,7 @@ struct sph_ctx {
   int32_t *nb_cnt_alt;
   int32_t *sh_idx;      // shell candidates, column-major, kMaxShell per particle
   int32_t *sh_cnt;      // their number, -1 when more than kMaxShell
+  int32_t *sh_in;       // bit j set when shell entry j was a partner at the walk
   int32_t *need_walk;   // device flag: some particle could not refine its list
   int64_t *csr_total;   // device scalar for sph_neighbours
   int32_t *hflags;      // variable-h iteration: done, updates, off-target count per pass
