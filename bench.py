@@ -123,14 +123,14 @@ class ClockSampler:
 # now, the figures are stale and are not used (the kernel is then reported
 # against HBM alone, with traffic null).
 NCU_PER_PARTICLE = {
-    "partners": {"inst": 856.36, "dram": 349.83, "fp32_pipe": 0.284, "issue": 0.682, "l1": 0.331,
-                 "src": ("neighbours.cu", "0b68670dee48e6ce")},
-    "refine": {"inst": 95.27, "dram": 442.94, "fp32_pipe": 0.183, "issue": 0.609, "l1": 0.344,
-               "src": ("neighbours.cu", "0b68670dee48e6ce")},
-    "passA": {"inst": 346.48, "dram": 504.89, "fp32_pipe": 0.385, "issue": 0.585, "l1": 0.619,
-              "src": ("rhs.cu", "eb113c70734f51a8")},
-    "passB": {"inst": 360.47, "dram": 347.45, "fp32_pipe": 0.451, "issue": 0.623, "l1": 0.911,
-              "src": ("rhs.cu", "eb113c70734f51a8")},
+    "partners": {"inst": 862.46, "dram": 356.52, "fp32_pipe": 0.274, "issue": 0.683, "l1": 0.328,
+                 "src": ("neighbours.cu", "9347fbb88607e52e")},
+    "refine": {"inst": 10.60, "dram": 67.06, "fp32_pipe": 0.095, "issue": 0.228, "l1": 0.290,
+               "src": ("neighbours.cu", "9347fbb88607e52e")},
+    "passA": {"inst": 346.76, "dram": 506.29, "fp32_pipe": 0.384, "issue": 0.575, "l1": 0.615,
+              "src": ("rhs.cu", "7b5c9ebb04e49f62")},
+    "passB": {"inst": 360.78, "dram": 347.96, "fp32_pipe": 0.409, "issue": 0.569, "l1": 0.831,
+              "src": ("rhs.cu", "7b5c9ebb04e49f62")},
 }
 
 
@@ -166,9 +166,11 @@ def algorithmic_bytes(phase, K, n_flaw_mean, dim=3):
         # positions, perm, slot; list and count; the shell list and its count
         return 32 + 4 + 4 + 4 * K + 4 + 4 * shell + 4
     if phase == "refine":
-        # per particle: counts and h, own positions; the old list, the shell
-        # and its members' positions (gathered: 32 B each), the new list
-        return 4 + 4 + 8 + 32 + 4 * K + 36 * shell + 4 * K + 4
+        # per particle: counts, shell bits and h, own positions, the shell and
+        # its members' positions (gathered: 32 B each), the new count; the old
+        # list is read and a new one written only where a shell member changed
+        # sides (none on the bench workload's lattice)
+        return 4 + 4 + 4 + 8 + 32 + 36 * shell + 4
     raise KeyError(phase)
 
 
