@@ -16,6 +16,9 @@ impact against the FP64 oracle.
   (kinetic + internal + softened potential), linear and angular momentum.
   Their drifts are reported for both precisions; the mixed run's drift must
   stay within a few times the FP64 run's own.
+* Two self-gravitating basalt bodies with damage (Sect. 5 set-up, 2 x 20k
+  particles), 2,000 steps on one tree per 4 steps, both precisions on one
+  time grid: finite states, damage in [0, 1] and growing, and matching drifts.
 """
 import math
 from dataclasses import replace
@@ -24,6 +27,7 @@ import numpy as np
 import pytest
 
 from paper_1604_03290_gb300 import workloads as wl
+from parity_util import flawed
 
 pytestmark = pytest.mark.gpu
 
@@ -56,7 +60,8 @@ def _run(S, ps, prec, nsteps, dts=None, kmax=128):
     out = []
     for i in range(nsteps):
         Pi = P if dts is None else replace(P, dt_fixed=float(dts[i]))
-        dt = S.step(ctx, ds, ps.materials, Pi, 1)
+        # with a reused tree each call continues the window of the last
+        dt = S.step(ctx, ds, ps.materials, Pi, 1, cont=i > 0 and P.tree_reuse > 0)
         out.append(float(dt[0].item()) if dts is None else float(dts[i]))
     return _by_id(ds.to_numpy()), out
 
@@ -159,4 +164,32 @@ def test_cloud_1000_steps_drift_mixed_vs_fp64(S):
     # truncation and the time step.  The mixed run may not drift by more than
     # a few times the FP64 run plus a floor of FP32 resolution.
     for k in ("dE_rel", "dLz_rel", "dP_rel"):
+        assert abs(res["mixed"][k]) <= 4 * abs(res["fp64"][k]) + 1e-5, (k, res)
+
+
+def test_ceres_pair_2000_steps_mixed_vs_fp64(S):
+    """Two self-gravitating basalt bodies with damage (Sect. 5 set-up, 2 x 20k
+    particles), 2,000 steps on one tree per 4 steps (the gravity/hydro
+    decoupling), FP64 and mixed on one time grid: both runs finish with
+    finite states and damage in [0, 1] that never decreased, and their
+    energy, linear- and angular-momentum drifts agree."""
+    ps = flawed(wl.ceres_pair(seed=4, n_each=20_000))
+    ps.params = replace(ps.params, tree_reuse=4)
+    G, eg = ps.params.G, ps.params.eps_grav
+    st0 = {"x": ps.x, "v": ps.v, "m": ps.m, "h": ps.h, "u": ps.u}
+    E0, P0, L0, parts0 = _energy_momenta(st0, G, eg)
+    g64, dts = _run(S, ps, "fp64", 2000, kmax=160)
+    gmx, _ = _run(S, ps, "mixed", 2000, dts=dts, kmax=160)
+    Pscale = float((ps.m * np.sqrt((ps.v ** 2).sum(0))).sum())
+    Lscale = float(np.abs(np.cross(ps.x.T, (ps.m * ps.v).T)).sum())
+    res = {}
+    for name, g in (("fp64", g64), ("mixed", gmx)):
+        assert all(np.isfinite(g[k]).all() for k in ("x", "v", "rho", "u", "S", "dmg"))
+        assert g["dmg"].min() >= 0.0 and g["dmg"].max() <= 1.0
+        assert np.all(g["dmg"] >= ps.dmg)  # damage only grows
+        E, P, L, parts = _energy_momenta(g, G, eg)
+        res[name] = {"dE_rel": (E - E0) / abs(parts0[2]), "dP_rel": float(np.abs(P - P0).max() / Pscale),
+                     "dL_rel": float(np.abs(L - L0).max() / Lscale), "max_dmg": float(g["dmg"].max())}
+    print("ceres pair 2 x 20k, 2000 steps to t = %.4g s: %s" % (sum(dts), res))
+    for k in ("dE_rel", "dP_rel", "dL_rel"):
         assert abs(res["mixed"][k]) <= 4 * abs(res["fp64"][k]) + 1e-5, (k, res)
