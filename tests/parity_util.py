@@ -46,6 +46,23 @@ def field_scales(ps, o, prec="fp64", tol=1.0):
     return sc
 
 
+def edge_share(ps, o, g, tol, prec, fields=("drho", "dv", "du", "dS")):
+    """How much the edge-conditioning term of the tolerance is used: per field,
+    the fraction of particles whose error exceeds tol times the bound without
+    that term (they pass only because of it), and the largest ratio of error
+    to that bound."""
+    sc0 = field_scales(ps, {**o, **{k: np.zeros_like(v) for k, v in o.items() if k.startswith("mag1_")}}, prec, tol)
+    out = {}
+    for f in fields:
+        if f == "dS" and ps.S is None:
+            continue
+        a, b = np.asarray(g[f], np.float64), np.asarray(o[f], np.float64)
+        r = np.abs(a - b) / (tol * sc0[f])
+        r = r.max(0) if r.ndim == 2 else r
+        out[f] = (float((r > 1.0).mean()), float(r.max()))
+    return out
+
+
 def compare_rhs(ps, o, g, tol, fields=("drho", "dv", "du", "dS", "dxdt", "p", "cs"), report=None, prec="fp64"):
     sc = field_scales(ps, o, prec, tol)
     errs = {}
