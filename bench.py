@@ -209,13 +209,22 @@ def adjoint_rollout(sph, wl, stream, nsteps=50, every=10):
     torch.cuda.reset_peak_memory_stats()
     base = torch.cuda.memory_allocated()
     ctx = sph.Context(3, bt.n, max_instances=bt.ninst, max_neighbours=128, leaf_size=prm.leaf_size)
-    runner = adjoint.Runner(ctx, bt, prm, dt, nsteps, every=every)
     proj = torch.as_tensor((bt.v[2] < 0).astype(np.float64), device="cuda")
     inst = torch.as_tensor(np.repeat(np.arange(bt.ninst), np.diff(bt.inst_off)), device="cuda")
     x0 = torch.as_tensor(bt.x, device="cuda")
-    v0 = torch.as_tensor(bt.v, device="cuda").requires_grad_(True)
     m = torch.as_tensor(bt.m, device="cuda")
+    # warm-up: one checkpoint segment forward and back (loads the kernels and
+    # fills the allocator's pool with the segment's states), not timed
+    warm = adjoint.Runner(ctx, bt, prm, dt, every, every=every)
+    vw = torch.as_tensor(bt.v, device="cuda").requires_grad_(True)
+    tw = adjoint.theta_of(bt.materials).requires_grad_(True)
+    xw, _ = adjoint.rollout(warm, bt.materials, x0, vw, tw)
+    adjoint.penetration_depth(xw, m, proj, 0.0, inst, bt.ninst).sum().backward()
+    del warm, xw, vw, tw
+    runner = adjoint.Runner(ctx, bt, prm, dt, nsteps, every=every)
+    v0 = torch.as_tensor(bt.v, device="cuda").requires_grad_(True)
     theta = adjoint.theta_of(bt.materials).requires_grad_(True)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     xN, vN = adjoint.rollout(runner, bt.materials, x0, v0, theta)
     J = adjoint.penetration_depth(xN, m, proj, 0.0, inst, bt.ninst)
