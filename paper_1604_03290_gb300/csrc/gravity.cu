@@ -160,6 +160,11 @@ __global__ void __launch_bounds__(kGrWarps * 32, SPH_GRAV_MIN_BLOCKS) k_gravity(
     const double s0r = T.inst_s0[inst];
     const double th = A.theta;
     const float th2f = (float)(th * th);
+    // A node whose cube holds the particle also holds its centre of mass, so
+    // r <= sqrt(D) s there; with D theta^2 < 1 (by a margin far above the
+    // rounding of either test) the opening criterion already rejects it and
+    // the containment test can be skipped: the accepted set is the same.
+    const bool test_inside = (double)dim * th * th >= 0.99;
     typename std::conditional<MIXED, GravSumF, GravSumD>::type acc;
     int32_t skip_until = -1;
     const int32_t root = T.inst_root[inst];
@@ -173,7 +178,7 @@ __global__ void __launch_bounds__(kGrWarps * 32, SPH_GRAV_MIN_BLOCKS) k_gravity(
       const bool leaf = (e1 - f <= L) || lev == B;
       bool open = false, direct = false;
       if (act && nd >= skip_until) {
-        const bool inside = (ka >> (dim * (B - lev))) == T.cell[nd];
+        const bool inside = test_inside && (ka >> (dim * (B - lev))) == T.cell[nd];
         bool accept = false;
         float mpf = 0.f;
         R d[3] = {R(0), R(0), R(0)}, r2 = R(0);
