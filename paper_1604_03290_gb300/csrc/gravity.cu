@@ -43,6 +43,13 @@ constexpr int kGrWarps = SPH_GRAV_WARPS;  // warps (particle groups) per block
 #endif
 constexpr float kMacBand = 1e-4f;
 constexpr int kFlushTerms = 16;
+// A leaf summed directly by few lanes: rather than each of them looping over
+// the members while the others wait, the warp takes the lanes one at a time,
+// every member lane evaluates its term for that lane, and a butterfly sum
+// over the warp gives the leaf's contribution (mixed precision).  Chosen when
+// (lanes summing the leaf) x kTransposedCost < (members) x kSerialCost, the
+// instruction counts of the two forms per lane and per member.
+constexpr int kTransposedCost = 66, kSerialCost = 29;
 
 // Sum of the FP32 terms of one particle: a plain partial sum, added into a
 // compensated (Kahan) sum every kFlushTerms terms, so that the error stays
@@ -224,18 +231,62 @@ __global__ void __launch_bounds__(kGrWarps * 32, SPH_GRAV_MIN_BLOCKS) k_gravity(
         }
       }
       const bool any_open = __any_sync(0xffffffffu, open);
-      if (__any_sync(0xffffffffu, direct)) {
+      const unsigned dmask = __ballot_sync(0xffffffffu, direct);
+      if (dmask) {
         for (int32_t base = f; base < e1; base += kMaxLeaf) {
           const int c = min(e1 - base, kMaxLeaf);
+          int32_t bm = -1;
+          float4 pb = make_float4(0.f, 0.f, 0.f, 0.f), qb = pb;
           if (lane < c) {
-            const int32_t b = T.perm[base + lane];
-            const float4 pb = A.pk.px(b), qb = A.pk.pxl(b);
+            bm = T.perm[base + lane];
+            pb = A.pk.px(bm);
+            qb = A.pk.pxl(bm);
             sh_hi[w][lane] = make_float4(pb.x, pb.y, pb.z, -(float)G * qb.w);  // qb.w = m as float
             sh_lo[w][lane] = make_float4(qb.x, qb.y, qb.z, qb.w);
-            sh_b[w][lane] = b;
+            sh_b[w][lane] = bm;
           }
           __syncwarp();
-          if (direct) {
+          bool transposed = false;
+          if constexpr (MIXED) transposed = __popc(dmask) * kTransposedCost < c * kSerialCost;
+          if (transposed) {
+            const float gmk = -(float)G * qb.w;
+            unsigned mm = dmask;
+            while (mm) {
+              const int i = __ffs(mm) - 1;
+              mm &= mm - 1;
+              // lane i's particle, against member `lane`
+              const float ax = __shfl_sync(0xffffffffu, Pa.x, i), ay = __shfl_sync(0xffffffffu, Pa.y, i),
+                          az = __shfl_sync(0xffffffffu, Pa.z, i);
+              const float lx = __shfl_sync(0xffffffffu, Qa.x, i), ly = __shfl_sync(0xffffffffu, Qa.y, i),
+                          lz = __shfl_sync(0xffffffffu, Qa.z, i);
+              const float e2i = __shfl_sync(0xffffffffu, (float)eps2, i);
+              const int32_t ai = __shfl_sync(0xffffffffu, a, i);
+              float fx = 0.f, fy = 0.f, fz = 0.f;
+              bool ok = false;
+              if (lane < c && bm != ai) {
+                const float dx = (ax - pb.x) + (lx - qb.x), dy = (ay - pb.y) + (ly - qb.y),
+                            dz = (az - pb.z) + (lz - qb.z);
+                const float q = dx * dx + dy * dy + dz * dz + e2i;
+                if (q > 0.f) {
+                  const float gq = gmk * inv_q32(q);
+                  fx = gq * dx;
+                  fy = gq * dy;
+                  fz = gq * dz;
+                  ok = true;
+                }
+              }
+              for (int o = 16; o > 0; o >>= 1) {
+                fx += __shfl_xor_sync(0xffffffffu, fx, o);
+                fy += __shfl_xor_sync(0xffffffffu, fy, o);
+                fz += __shfl_xor_sync(0xffffffffu, fz, o);
+              }
+              const unsigned okm = __ballot_sync(0xffffffffu, ok);
+              if (lane == i) {
+                acc.add((R)fx, (R)fy, dim == 3 ? (R)fz : R(0));
+                nterm += __popc(okm);
+              }
+            }
+          } else if (direct) {
             for (int k = 0; k < c; ++k) {
               const int32_t b = sh_b[w][k];
               if (b == a) continue;
