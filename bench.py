@@ -5,7 +5,7 @@ One step = partner search, both neighbour passes with the constitutive
 update, the device-side time step and the predictor update, then partners and
 passes again at the predicted state and the corrector update (sph_step).  A
 tree (and the state's order along it) serves --tree-reuse consecutive steps
-(default 4): the step that builds it walks it for the partners, and every
+(default 5): the step that builds it walks it for the partners, and every
 later evaluation of the window refines those lists, exactly, while the
 particles' displacement allows (else it walks).  Workload: aluminium sphere into aluminium cube,
 Tillotson EOS, strength, von Mises yield and Grady-Kipp damage, 100^3 cube
@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-aux", action="store_true", help="skip timing the flaw and fragment steps")
     ap.add_argument("--only-aux", action="store_true", help="time only the flaw, fragment and decoupling legs")
     ap.add_argument("--cloud-n", type=int, default=2_000_000, help="particles of the decoupling leg's cloud")
-    ap.add_argument("--tree-reuse", type=int, default=4,
+    ap.add_argument("--tree-reuse", type=int, default=5,
                     help="steps one tree serves (partners refined from the build step's walk); 0: a tree per step")
     return ap.parse_args()
 
