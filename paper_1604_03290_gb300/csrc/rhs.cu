@@ -447,12 +447,13 @@ __global__ void SPH_PASSA_BOUNDS k_passA(RhsArgs A) {
     const R fr = kern_dW(q, R(6) * sig * hD * hinv) * rinv;
     R g[3] = {fr * d[0], fr * d[1], fr * d[2]};
     drho.add(vol * (w[0] * g[0] + w[1] * g[1] + w[2] * g[2]));
+    // L is symmetric (grad W is parallel to d): its lower triangle only
     for (int i = 0; i < 3; ++i) {
       if (i >= dim) break;
       const R vd = vol * d[i], vw = vol * w[i];
       for (int j = 0; j < 3; ++j) {
         if (j >= dim) break;
-        L[i][j] -= vd * g[j];
+        if (j <= i) L[i][j] -= vd * g[j];
         G[i][j] -= vw * g[j];
       }
     }
@@ -473,6 +474,8 @@ __global__ void SPH_PASSA_BOUNDS k_passA(RhsArgs A) {
   const R Y0_r = MIXED ? (R)mf[MF_Y0] : (R)M.Y0;
   const R K0_r = MIXED ? (R)mf[MF_K0] : (R)M.K0;
   const double rho_d = A.rho[a];
+  for (int i = 0; i < 3; ++i)
+    for (int j = i + 1; j < 3; ++j) L[i][j] = L[j][i];
   R C[3][3];
   correction_tensor<R>(dim, L, P.consistency && cnt >= dim + 1, C);
   R gv[3][3];
