@@ -15,12 +15,15 @@ impact against the FP64 oracle.
   particles), 1,000 steps in each precision on one time grid: total energy
   (kinetic + internal + softened potential), linear and angular momentum.
   Their drifts are reported for both precisions; the mixed run's drift must
-  stay within a few times the FP64 run's own.
+  stay within a few times the FP64 run's own.  The same at the set-up's full
+  2M particles runs only with SPH_FULL_ACCURACY=1 (about 20 minutes of one
+  GB300, most of it the FP64 Barnes-Hut walks).
 * Two self-gravitating basalt bodies with damage (Sect. 5 set-up, 2 x 20k
   particles), 2,000 steps on one tree per 4 steps, both precisions on one
   time grid: finite states, damage in [0, 1] and growing, and matching drifts.
 """
 import math
+import os
 from dataclasses import replace
 
 import numpy as np
@@ -131,26 +134,28 @@ def _energy_momenta(st, G, eps_grav):
     eint = float((m * torch.as_tensor(st["u"], device="cuda")).sum())
     n = m.numel()
     W = 0.0
-    for s in range(0, n, 2048):
-        xs = x[:, s:s + 2048]
-        r2 = ((xs[:, :, None] - x[:, None, :]) ** 2).sum(0)
-        q = r2 + 0.5 * (e2[s:s + 2048, None] + e2[None, :])
-        inv = torch.rsqrt(q)
-        idx = torch.arange(s, min(s + 2048, n), device="cuda")
+    cs = max(64, min(2048, (1 << 28) // n))  # rows per block: at most 2 GB per temporary
+    for s in range(0, n, cs):
+        e = min(s + cs, n)
+        r2 = torch.zeros((e - s, n), dtype=torch.float64, device="cuda")
+        for ax in range(x.shape[0]):
+            r2.add_((x[ax, s:e, None] - x[ax, None, :]) ** 2)
+        inv = torch.rsqrt(r2.add_(0.5 * (e2[s:e, None] + e2[None, :])))
+        idx = torch.arange(s, e, device="cuda")
         inv[idx - s, idx] = 0.0
-        W += float(-0.5 * G * (m[s:s + 2048, None] * m[None, :] * inv).sum())
+        W += float(-0.5 * G * (m[s:e] * (inv @ m)).sum())
     P = (m * v).sum(1).cpu().numpy()
     L = torch.linalg.cross(x.T, v.T).mul(m[:, None]).sum(0).cpu().numpy()
     return ekin + eint + W, P, L, (ekin, eint, W)
 
 
-def test_cloud_1000_steps_drift_mixed_vs_fp64(S):
-    ps = wl.cloud_collapse(seed=3, n=50_000)
+def _cloud_drift(S, n, nsteps=1000):
+    ps = wl.cloud_collapse(seed=3, n=n)
     G, eg = ps.params.G, ps.params.eps_grav
     st0 = {"x": ps.x, "v": ps.v, "m": ps.m, "h": ps.h, "u": ps.u}
     E0, P0, L0, parts0 = _energy_momenta(st0, G, eg)
-    g64, dts = _run(S, ps, "fp64", 1000, kmax=160)
-    gmx, _ = _run(S, ps, "mixed", 1000, dts=dts, kmax=160)
+    g64, dts = _run(S, ps, "fp64", nsteps, kmax=160)
+    gmx, _ = _run(S, ps, "mixed", nsteps, dts=dts, kmax=160)
     res = {}
     for name, g in (("fp64", g64), ("mixed", gmx)):
         E, P, L, parts = _energy_momenta(g, G, eg)
@@ -158,13 +163,23 @@ def test_cloud_1000_steps_drift_mixed_vs_fp64(S):
         res[name] = {"dE_rel": (E - E0) / abs(parts0[2]), "dP_rel": float(np.abs(P - P0).max() / Pscale),
                      "dLz_rel": float((L[2] - L0[2]) / abs(L0[2]))}
     t_ff = math.sqrt(3 * math.pi / (32 * G * (3 * ps.m.sum() / (4 * math.pi * 3.2e14 ** 3))))
-    print("cloud 50k, 1000 steps to t = %.4g s (%.3g t_ff): %s" % (sum(dts), sum(dts) / t_ff, res))
+    print("cloud %d, %d steps to t = %.4g s (%.3g t_ff): %s" % (ps.n, nsteps, sum(dts), sum(dts) / t_ff, res))
     # linear momentum: pair forces are antisymmetric, gravity only to the
     # Barnes-Hut error; angular momentum and energy drift with the walk's
     # truncation and the time step.  The mixed run may not drift by more than
     # a few times the FP64 run plus a floor of FP32 resolution.
     for k in ("dE_rel", "dLz_rel", "dP_rel"):
         assert abs(res["mixed"][k]) <= 4 * abs(res["fp64"][k]) + 1e-5, (k, res)
+
+
+def test_cloud_1000_steps_drift_mixed_vs_fp64(S):
+    _cloud_drift(S, 50_000)
+
+
+@pytest.mark.skipif(os.environ.get("SPH_FULL_ACCURACY") != "1",
+                    reason="the 2M-particle drift run takes about 20 minutes; SPH_FULL_ACCURACY=1 runs it")
+def test_cloud_2m_1000_steps_drift_mixed_vs_fp64(S):
+    _cloud_drift(S, 2_000_000)
 
 
 def test_ceres_pair_2000_steps_mixed_vs_fp64(S):
