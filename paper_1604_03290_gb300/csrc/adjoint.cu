@@ -198,10 +198,14 @@ __device__ __forceinline__ void load_T64(const AdjArgs &A, int64_t a, double t[6
   for (int k = 0; k < 6; ++k) t[k] = k < ns ? A.T[(int64_t)k * A.ld + a] : 0.0;
 }
 
+// The kernels are instantiated per dimension, so that every small-matrix loop
+// has a compile-time bound and the matrices stay in registers.
+template <int DIM>
 __global__ void k_adj_passB(AdjArgs A) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= A.n) return;
-  const int dim = A.dim, ns = nsym(dim);
+  constexpr int dim = DIM;
+  const int ns = nsym(dim);
   double xc[3] = {0, 0, 0}, vc[3] = {0, 0, 0}, vbc[3] = {0, 0, 0};
   for (int i = 0; i < dim; ++i) {
     xc[i] = A.x[i][c];
@@ -265,7 +269,7 @@ __global__ void k_adj_passB(AdjArgs A) {
 // ---------------------------------------------------------------------------
 // Constitutive update, recomputed and reversed
 // ---------------------------------------------------------------------------
-__device__ bool invert_L(int dim, const double L[3][3], double C[3][3]) {
+__device__ __forceinline__ bool invert_L(int dim, const double L[3][3], double C[3][3]) {
   double det;
   if (dim == 2) det = L[0][0] * L[1][1] - L[0][1] * L[1][0];
   else
@@ -310,11 +314,12 @@ __device__ void eos_scaled(const sph_material &M0, double s, double rho, double 
 // MIXED: the pass-A sums are recomputed in FP32 in the forward's code units
 // (as the mixed forward pass forms them) and converted to SI; the reverse of
 // the constitutive update below is FP64 in both forms.
-template <bool MIXED>
+template <bool MIXED, int DIM>
 __global__ void k_adj_update(AdjArgs A) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= A.n) return;
-  const int dim = A.dim, ns = nsym(dim);
+  constexpr int dim = DIM;
+  const int ns = nsym(dim);
   const sph_params &P = A.prm;
   // ---- pass-A sums, recomputed ----
   const double rc = A.rho[c];
@@ -340,12 +345,16 @@ __global__ void k_adj_update(AdjArgs A) {
       float wg = 0.f;
       for (int i = 0; i < dim; ++i) wg += w[i] * K.phi * d[i];
       s32.add(vol * wg);
-      for (int i = 0; i < dim; ++i)
+      for (int i = 0; i < dim; ++i) {
+        const float vd = vol * d[i] * K.phi, vw = vol * w[i] * K.phi;
         for (int j = 0; j < dim; ++j) {
-          L32[i][j] -= vol * d[i] * K.phi * d[j];
-          G32[i][j] -= vol * w[i] * K.phi * d[j];
+          if (j <= i) L32[i][j] -= vd * d[j];  // L is symmetric: its lower triangle
+          G32[i][j] -= vw * d[j];
         }
+      }
     }
+    for (int i = 0; i < dim; ++i)
+      for (int j = i + 1; j < dim; ++j) L32[i][j] = L32[j][i];
     // the continuity sum and G are rates (code unit 1/T), L is a number
     const double it = A.U->invT;
     srho = s32.value() * it;
@@ -668,10 +677,11 @@ __device__ void pairA_adj(int dim, const R d[3], const R w[3], R r, const KPair<
   rho_b_bar += -volbar * vol / rho_b;
 }
 
+template <int DIM>
 __global__ void k_adj_passA(AdjArgs A) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= A.n) return;
-  const int dim = A.dim;
+  constexpr int dim = DIM;
   double xc[3] = {0, 0, 0}, vc[3] = {0, 0, 0};
   for (int i = 0; i < dim; ++i) {
     xc[i] = A.x[i][c];
@@ -717,17 +727,27 @@ __global__ void k_adj_passA(AdjArgs A) {
   A.grho[c] += grho;
 }
 
-// Per-instance, per-material sums of the particle parameter cotangents, in a
-// fixed order (one block per instance): param_bar[(inst * nmat + mat) * 3 + k].
-__global__ void k_adj_params(const double *__restrict__ pbar, int64_t ld, const int32_t *__restrict__ mat,
-                             const int64_t *__restrict__ inst_off, int ninst, int64_t n, int nmat, double *out) {
-  const int inst = blockIdx.x;
-  const int64_t lo = (ninst > 1 && inst_off) ? inst_off[inst] : 0;
-  const int64_t hi = (ninst > 1 && inst_off) ? inst_off[inst + 1] : n;
-  __shared__ double sh[256][3];
+// Per-instance, per-material sums of the particle parameter cotangents,
+// param_bar[(inst * nmat + mat) * 3 + k], in a fixed order.  Block (inst, j)
+// sums the j-th of gy equal chunks of its instance (a strided loop, then a
+// tree in shared memory); with part set it stores that partial sum, and
+// k_adj_params_final adds the gy partials of each entry in chunk order.  With
+// part NULL (gy = 1) the block adds its instance's sum to out itself.
+constexpr int kParamThreads = 256;
+constexpr int64_t kParamChunk = 4096;  // particles per block, about
+__global__ void __launch_bounds__(kParamThreads) k_adj_params(const double *__restrict__ pbar, int64_t ld,
+                                                              const int32_t *__restrict__ mat,
+                                                              const int64_t *__restrict__ inst_off, int ninst,
+                                                              int64_t n, int nmat, int gy, double *part, double *out) {
+  const int inst = blockIdx.x, j = blockIdx.y;
+  const int64_t lo0 = (ninst > 1 && inst_off) ? inst_off[inst] : 0;
+  const int64_t hi0 = (ninst > 1 && inst_off) ? inst_off[inst + 1] : n;
+  const int64_t len = hi0 - lo0, ch = (len + gy - 1) / gy;
+  const int64_t lo = lo0 + min(len, (int64_t)j * ch), hi = lo0 + min(len, (int64_t)(j + 1) * ch);
+  __shared__ double sh[kParamThreads][3];
   for (int mm = 0; mm < nmat; ++mm) {
     double acc[3] = {0, 0, 0};
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kParamThreads) {
       const int mi0 = mat ? mat[i] : 0;
       const int mi = (mi0 >= 0 && mi0 < nmat) ? mi0 : 0;
       if (mi != mm) continue;
@@ -735,14 +755,46 @@ __global__ void k_adj_params(const double *__restrict__ pbar, int64_t ld, const 
     }
     for (int k = 0; k < 3; ++k) sh[threadIdx.x][k] = acc[k];
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    for (int s = kParamThreads / 2; s > 0; s >>= 1) {
       if (threadIdx.x < s)
         for (int k = 0; k < 3; ++k) sh[threadIdx.x][k] += sh[threadIdx.x + s][k];
       __syncthreads();
     }
-    if (threadIdx.x == 0)
-      for (int k = 0; k < 3; ++k) out[((int64_t)inst * nmat + mm) * 3 + k] += sh[0][k];
+    if (threadIdx.x == 0) {
+      const int64_t q = (int64_t)inst * nmat + mm;
+      for (int k = 0; k < 3; ++k) {
+        if (part) part[(q * gy + j) * 3 + k] = sh[0][k];
+        else out[q * 3 + k] += sh[0][k];
+      }
+    }
     __syncthreads();
+  }
+}
+
+__global__ void k_adj_params_final(const double *__restrict__ part, int64_t m, int gy, double *out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // entry (inst * nmat + mat) * 3 + k
+  if (t >= m) return;
+  const int64_t q = t / 3;
+  const int k = (int)(t - 3 * q);
+  double s = 0.0;
+  for (int j = 0; j < gy; ++j) s += part[(q * gy + j) * 3 + k];
+  out[t] += s;
+}
+
+// The parameter cotangents of all particles (c->ag, 3 x cap_n) summed into
+// param_bar; the adjoint's intermediate buffer holds the partial sums (it is
+// free once pass A's reverse has read it).
+static void adj_params_sum(sph_ctx *c, const int32_t *mat, const int64_t *inst_off, int ninst, int64_t n, int nmat,
+                           double *param_bar, cudaStream_t st) {
+  int64_t g = (n / ninst + kParamChunk - 1) / kParamChunk;
+  int gy = (int)std::max<int64_t>(1, std::min<int64_t>(1024, g));
+  if ((int64_t)ninst * nmat * gy * 3 > (int64_t)22 * c->cap_n) gy = 1;
+  double *part = gy > 1 ? c->adj_inter : nullptr;
+  { k_adj_params<<<dim3(ninst, gy), kParamThreads, 0, st>>>(c->ag, c->cap_n, mat, inst_off, ninst, n, nmat, gy, part,
+                                                          param_bar); ++sph::g_launches; }
+  if (part) {
+    const int64_t m = (int64_t)ninst * nmat * 3;
+    { k_adj_params_final<<<nblk(m, 256), 256, 0, st>>>(part, m, gy, param_bar); ++sph::g_launches; }
   }
 }
 
@@ -984,20 +1036,27 @@ void rhs_adjoint(sph_ctx *c, const sph_state *s, const MatTable &mt, const sph_p
     A.T = T64;
     A.cs = cs64;
     { k_adj_unpack32<<<nblk(n, 256), 256, 0, st>>>(A, T64, cs64); ++sph::g_launches; }
-    if (s->dim == 3) { k_adj_passB32<3><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
-    else { k_adj_passB32<2><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
-    { k_adj_update<true><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    if (s->dim == 3) {
+      { k_adj_passB32<3><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+      { k_adj_update<true, 3><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    } else {
+      { k_adj_passB32<2><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+      { k_adj_update<true, 2><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    }
     { k_adj_pack_acot32<<<nblk(n, 256), 256, 0, st>>>(A); ++sph::g_launches; }
     if (s->dim == 3) { k_adj_passA32<3><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
     else { k_adj_passA32<2><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+  } else if (s->dim == 3) {
+    { k_adj_passB<3><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    { k_adj_update<false, 3><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    { k_adj_passA<3><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
   } else {
-    { k_adj_passB<<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
-    { k_adj_update<false><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
-    { k_adj_passA<<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    { k_adj_passB<2><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    { k_adj_update<false, 2><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
+    { k_adj_passA<2><<<nblk(n, T), T, 0, st>>>(A); ++sph::g_launches; }
   }
   const int ninst = s->ninst > 0 ? s->ninst : 1;
-  if (param_bar)
-    { k_adj_params<<<ninst, 256, 0, st>>>(c->ag, c->cap_n, s->mat, s->inst_off, ninst, n, mt.nmat, param_bar); ++sph::g_launches; }
+  if (param_bar) adj_params_sum(c, s->mat, s->inst_off, ninst, n, mt.nmat, param_bar, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -1103,8 +1162,7 @@ void pc_update_adjoint(sph_ctx *c, const sph_state *base, const sph_derivs &d, c
   A.density_sum = p.density_sum;
   { k_pc_adj<<<nblk(n, 256), 256, 0, st>>>(A); ++sph::g_launches; }
   const int ninst = base->ninst > 0 ? base->ninst : 1;
-  if (param_bar)
-    { k_adj_params<<<ninst, 256, 0, st>>>(c->ag, c->cap_n, base->mat, base->inst_off, ninst, n, mt.nmat, param_bar); ++sph::g_launches; }
+  if (param_bar) adj_params_sum(c, base->mat, base->inst_off, ninst, n, mt.nmat, param_bar, st);
 }
 
 }  // namespace sph
