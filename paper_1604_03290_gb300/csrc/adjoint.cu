@@ -408,7 +408,27 @@ __global__ void k_adj_update(AdjArgs A) {
   const sph_material &M = A.mt.m[mi];
   const double uc = A.u[c];
   double p, cs, pr, pu;
-  eos_scaled(M, 1.0, rc, uc, p, cs, &pr, &pu);
+  // MIXED: one evaluation in FP32 dual numbers, in the forward's code units,
+  // gives p, c_s, dp/drho, dp/du and the exact derivatives of c_s in rho and u
+  // and of p and c_s in the bulk-modulus scale; FP64: the analytic derivatives
+  // of p here, those of c_s and the scale by central differences below.
+  double dcr = 0.0, dcu = 0.0, dps = 0.0, dcs = 0.0;
+  if constexpr (MIXED) {
+    const Units *U = A.U;
+    const EosC<ad::Dual3> K = eos_consts<ad::Dual3>(M, U->matf[mi], U);
+    ad::Dual3 p3, c3, pr3, pu3;
+    eos_eval<ad::Dual3>(M, K, rc, uc, p3, c3, &pr3, &pu3);
+    p = (double)p3.v * U->sig;
+    cs = (double)c3.v * U->V;
+    pr = (double)pr3.v * U->sig * U->invrho;
+    pu = (double)pu3.v * U->sig * U->invE;
+    dcr = (double)c3.d[0] * U->V * U->invrho;
+    dcu = (double)c3.d[1] * U->V * U->invE;
+    dps = (double)p3.d[2] * U->sig;
+    dcs = (double)c3.d[2] * U->V;
+  } else {
+    eos_scaled(M, 1.0, rc, uc, p, cs, &pr, &pu);
+  }
   const bool strength = A.S != nullptr && M.strength;
   double S[3][3], St[3][3];
   for (int i = 0; i < 3; ++i)
@@ -514,14 +534,18 @@ __global__ void k_adj_update(AdjArgs A) {
   double ubar = pbar * pu;
   rhobar += pbar * pr;
   double Kbar = 0.0;
-  {
+  if constexpr (MIXED) {
+    const double Kref = fmax(fmax(M.K0, M.A_T), M.B_T);
+    rhobar += csbar * dcr;
+    ubar += csbar * dcu;
+    if (Kref > 0.0) Kbar = (pbar * dps + csbar * dcs) / Kref;
+  } else {
     const double er = 1e-6 * rc, eu = 1e-6 * (fabs(uc) + 1e-3 * fabs(M.E0) + 1e-30), es = 1e-6;
     const double Kref = fmax(fmax(M.K0, M.A_T), M.B_T);
     // the six evaluations of the central differences (rho +-, u +-, scale +-)
     // in one loop, so that the equation of state is emitted once here: six
     // inlined copies overflowed the instruction cache.  c+ + (-c-) from zero is
     // the same value as c+ - c-.
-    double dcr = 0.0, dcu = 0.0, dps = 0.0, dcs = 0.0;
 #pragma unroll 1
     for (int k = 0; k < 6; ++k) {
       if (k < 4 ? csbar == 0.0 : !(Kref > 0.0)) continue;
