@@ -457,9 +457,10 @@ __global__ void k_adj_update(AdjArgs A) {
       if (i < dim && j < dim) TbT += Tb[i][j] * Tc[sidx(dim, i, j)];
     }
   double rhobar = -2.0 * TbT / rc;
+  const double irc2 = 1.0 / (rc * rc);  // one division for the nine components below
   double sigbar[3][3];
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) sigbar[i][j] = Tb[i][j] / (rc * rc);
+    for (int j = 0; j < 3; ++j) sigbar[i][j] = Tb[i][j] * irc2;
   for (int i = 0; i < dim; ++i) trSig += sigbar[i][i];
   // sigma = -p_hat I + (1 - d) S_tilde
   const double phatbar = -trSig;
@@ -483,12 +484,13 @@ __global__ void k_adj_update(AdjArgs A) {
   for (int i = 0; i < dim; ++i) tr += ed[i][i];
   double mubar = 0.0, trSdb = 0.0;
   for (int i = 0; i < dim; ++i) trSdb += Sdb[i][i];
+  const double tr_d = tr / dim, trSdb_d = trSdb / dim;
   for (int i = 0; i < dim; ++i)
-    for (int j = 0; j < dim; ++j) mubar += 2.0 * (ed[i][j] - (i == j ? tr / dim : 0.0)) * Sdb[i][j];
+    for (int j = 0; j < dim; ++j) mubar += 2.0 * (ed[i][j] - (i == j ? tr_d : 0.0)) * Sdb[i][j];
   double edbar[3][3], Rbar[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      edbar[i][j] = (i < dim && j < dim) ? 2.0 * M.mu * (Sdb[i][j] - (i == j ? trSdb / dim : 0.0)) : 0.0;
+      edbar[i][j] = (i < dim && j < dim) ? 2.0 * M.mu * (Sdb[i][j] - (i == j ? trSdb_d : 0.0)) : 0.0;
       double a1 = 0.0, a2 = 0.0, b1 = 0.0, b2 = 0.0;
       for (int k = 0; k < dim; ++k) {
         a1 += Sdb[i][k] * St[k][j];  // Z S_t
@@ -519,11 +521,12 @@ __global__ void k_adj_update(AdjArgs A) {
     double proj = 0.0;
     for (int k = 0; k < ns; ++k) proj += Stb_st[k] * S_st[k];
     const bool yielding = M.Y0 > 0.0 && J2 > 0.0 && M.Y0 * M.Y0 / (3.0 * J2) < 1.0;
+    const double fjp = yielding ? fY / J2 * proj : 0.0;
     for (int k = 0; k < ns; ++k) {
       double sb = Stb_st[k];
       if (yielding) {
         const double wk = k < dim ? 1.0 : 2.0;
-        sb = fY * Stb_st[k] - fY / J2 * proj * wk * S_st[k];
+        sb = fY * Stb_st[k] - fjp * wk * S_st[k];
       }
       A.gS[(int64_t)k * A.n + c] += sb;
     }
