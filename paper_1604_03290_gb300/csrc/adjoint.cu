@@ -46,6 +46,7 @@ struct AdjArgs {
   float4 *Bpk;                        // output cotangents of dv and du in code units (ld)
   float4 *Apk;                        // cotangents of the pass-A sums in code units (6 * ld)
   const Units *U;
+  const float *sums;  // mixed: the forward pass A's pair sums (16 rows of stride ld)
 };
 
 __device__ __forceinline__ int sidx(int dim, int i, int j) { return symk(dim, i, j); }
@@ -311,9 +312,11 @@ __device__ void eos_scaled(const sph_material &M0, double s, double rho, double 
   eos_eval<double>(M, K, rho, u, p, cs, pr, pu);
 }
 
-// MIXED: the pass-A sums are recomputed in FP32 in the forward's code units
-// (as the mixed forward pass forms them) and converted to SI; the reverse of
-// the constitutive update below is FP64 in both forms.
+// MIXED: the pass-A sums are the forward pass A's own (FP32, code units, kept
+// by it for this kernel) converted to SI, and the equation of state is
+// differentiated in FP32 dual numbers; the rest of the reverse of the
+// constitutive update is FP64 in both forms.  FP64: the sums are recomputed
+// here.
 template <bool MIXED, int DIM>
 __global__ void k_adj_update(AdjArgs A) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -328,41 +331,16 @@ __global__ void k_adj_update(AdjArgs A) {
     for (int j = 0; j < 3; ++j) L[i][j] = G[i][j] = 0.0;
   const int cnt = A.nb_cnt[c];
   if constexpr (MIXED) {
-    const float4 Pc = A.pk.px(c), Qc = A.pk.pxl(c), Vc = A.pk.pv(c), Wc = A.pk.pvl(c);
-    KahanT<float> s32;
-    float L32[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-    float G32[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-    for (int k = 0; k < cnt; ++k) {
-      const int32_t e = A.nb_idx[(int64_t)k * A.ld + c];
-      const float4 Pe = A.pk.px(e), Qe = A.pk.pxl(e), Ve = A.pk.pv(e), We = A.pk.pvl(e);
-      const float d[3] = {(Pc.x - Pe.x) + (Qc.x - Qe.x), (Pc.y - Pe.y) + (Qc.y - Qe.y),
-                          dim == 3 ? (Pc.z - Pe.z) + (Qc.z - Qe.z) : 0.f};
-      const float w[3] = {(Vc.x - Ve.x) + (Wc.x - We.x), (Vc.y - Ve.y) + (Wc.y - We.y),
-                          dim == 3 ? (Vc.z - Ve.z) + (Wc.z - We.z) : 0.f};
-      const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-      const KPair<float> K = kernel_pair<float>(dim, sqrtf(r2), 0.5f * (Pc.w + Pe.w));
-      const float vol = We.w;  // m / rho
-      float wg = 0.f;
-      for (int i = 0; i < dim; ++i) wg += w[i] * K.phi * d[i];
-      s32.add(vol * wg);
-      for (int i = 0; i < dim; ++i) {
-        const float vd = vol * d[i] * K.phi, vw = vol * w[i] * K.phi;
-        for (int j = 0; j < dim; ++j) {
-          if (j <= i) L32[i][j] -= vd * d[j];  // L is symmetric: its lower triangle
-          G32[i][j] -= vw * d[j];
-        }
-      }
-    }
-    for (int i = 0; i < dim; ++i)
-      for (int j = i + 1; j < dim; ++j) L32[i][j] = L32[j][i];
-    // the continuity sum and G are rates (code unit 1/T), L is a number
+    // the forward pass A's own FP32 sums (k_passA's KEEP_SUMS layout); the
+    // continuity sum and G are rates (code unit 1/T), L is a number
+    const float *sm = A.sums;
+    const int64_t ld = A.ld;
     const double it = A.U->invT;
-    srho = s32.value() * it;
+    srho = (double)sm[c] * it;
     for (int i = 0; i < dim; ++i)
-      for (int j = 0; j < dim; ++j) {
-        L[i][j] = L32[i][j];
-        G[i][j] = (double)G32[i][j] * it;
-      }
+      for (int j = 0; j <= i; ++j) L[i][j] = L[j][i] = sm[(int64_t)(1 + i * (i + 1) / 2 + j) * ld + c];
+    for (int i = 0; i < dim; ++i)
+      for (int j = 0; j < dim; ++j) G[i][j] = (double)sm[(int64_t)(7 + 3 * i + j) * ld + c] * it;
   } else {
     double xc[3] = {0, 0, 0}, vc[3] = {0, 0, 0};
     for (int i = 0; i < dim; ++i) {
@@ -1057,6 +1035,7 @@ void rhs_adjoint(sph_ctx *c, const sph_state *s, const MatTable &mt, const sph_p
     A.Bpk = c->adj32;
     A.Apk = c->adj32 + c->cap_n;
     A.U = c->units;
+    A.sums = c->adj_sums;
     // FP64 SI copies of T and c_s for the constitutive reverse (the third
     // derivative set of the step buffers is free here)
     double *T64 = c->st.d_S[2], *cs64 = c->st.d_cs[2];

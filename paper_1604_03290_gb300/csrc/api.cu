@@ -161,6 +161,7 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   c->d_ctr = ctx_alloc<unsigned long long>(c, kNumCounters, ok);
   c->adj_inter = ctx_alloc<double>(c, 22 * N, ok);
   c->adj32 = ctx_alloc<float4>(c, 7 * N, ok);
+  c->adj_sums = ctx_alloc<float>(c, 16 * N, ok);
   c->vscale = 1.0;
   StepBufs &S = c->st;
   for (int k = 0; k < 3; ++k) {
@@ -818,7 +819,7 @@ sph_status sph_rhs_adjoint(sph_ctx *c, sph_state *s, const sph_material *mats, i
   fwd.n_act = B.d_nact[0];
   tree_build(c, s, q.leaf_size, q.max_depth, st);
   find_partners(c, s, st);
-  rhs_passes(c, s, mt, q, fwd, st);
+  rhs_passes(c, s, mt, q, fwd, st, q.precision == SPH_MIXED ? c->adj_sums : nullptr);
   rhs_adjoint(c, s, mt, q, *dbar, sbar, param_bar, st);
   return finish(c, p, st, "sph_rhs_adjoint");
 }

@@ -57,6 +57,7 @@ struct RhsArgs {
   const double *ag;         // gravity (3 * ld) or NULL
   double *rho_out;          // density-sum output
   const Units *U;           // code units of the FP32 views (mixed mode)
+  float *sums;              // mixed, KEEP_SUMS: pass A's pair sums (16 rows of stride ld)
   MatTable mt;
   sph_params prm;
   int32_t *err;
@@ -405,7 +406,11 @@ __device__ __forceinline__ void sym_eigen(int dim, R A[3][3], R w[3], R V[3][3])
 // ---------------------------------------------------------------------------
 // Pass A + per-particle update
 // ---------------------------------------------------------------------------
-template <bool MIXED, int DIM>
+// KEEP_SUMS (mixed, for the adjoint): also store the pair sums in A.sums,
+// rows of stride ld: 0 the continuity sum sum_b V_b (v_a - v_b).grad W (code
+// units 1/T), 1..6 the lower triangle of L (00, 10, 11, 20, 21, 22), 7..15 G
+// row by row (1/T).
+template <bool MIXED, int DIM, bool KEEP_SUMS = false>
 __global__ void SPH_PASSA_BOUNDS k_passA(RhsArgs A) {
   using R = typename std::conditional<MIXED, float, double>::type;
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -649,6 +654,15 @@ __global__ void SPH_PASSA_BOUNDS k_passA(RhsArgs A) {
   }
   if (A.nact) A.nact[a] = nact;
   if (A.nnb) A.nnb[a] = cnt;
+  if constexpr (MIXED && KEEP_SUMS) {
+    float *o = A.sums;
+    const int64_t ld = A.ld;
+    o[a] = drho.value();
+    for (int i = 0; i < dim; ++i)
+      for (int j = 0; j <= i; ++j) o[(int64_t)(1 + i * (i + 1) / 2 + j) * ld + a] = L[i][j];
+    for (int i = 0; i < dim; ++i)
+      for (int j = 0; j < dim; ++j) o[(int64_t)(7 + 3 * i + j) * ld + a] = G[i][j];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -831,7 +845,7 @@ __global__ void k_repack_rho(const double *__restrict__ rho, const double *__res
 }
 
 void rhs_passes(sph_ctx *c, sph_state *s, const MatTable &mt, const sph_params &p, const sph_derivs &out,
-                cudaStream_t st) {
+                cudaStream_t st, float *sums) {
   const int64_t n = s->n;
   if (n == 0) return;
   RhsArgs A;
@@ -880,6 +894,7 @@ void rhs_passes(sph_ctx *c, sph_state *s, const MatTable &mt, const sph_params &
   A.prm = p;
   A.err = c->d_err;
   const bool mixed = p.precision == SPH_MIXED;
+  A.sums = mixed ? sums : nullptr;
   const int T = c->tune.pass_threads;
   int pr = -1;
   const bool d3 = s->dim == 3;
@@ -897,8 +912,15 @@ void rhs_passes(sph_ctx *c, sph_state *s, const MatTable &mt, const sph_params &
     prof_end(c, st, pr);
   }
   pr = prof_begin(c, st, PH_PASSA);
-  if (mixed) SPH_LAUNCH(k_passA, true);
-  else SPH_LAUNCH(k_passA, false);
+  if (mixed && A.sums) {
+    if (d3) k_passA<true, 3, true><<<nblk(n, T), T, 0, st>>>(A);
+    else k_passA<true, 2, true><<<nblk(n, T), T, 0, st>>>(A);
+    ++sph::g_launches;
+  } else if (mixed) {
+    SPH_LAUNCH(k_passA, true);
+  } else {
+    SPH_LAUNCH(k_passA, false);
+  }
   prof_end(c, st, pr);
   const bool as = p.eps_s > 0.0;
   pr = prof_begin(c, st, PH_PASSB);

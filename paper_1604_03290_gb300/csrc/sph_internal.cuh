@@ -197,6 +197,7 @@ struct sph_ctx {
   double *ag;           // gravity acceleration, 3 * cap_n
   double *adj_inter;    // adjoint scratch, 22 * cap_n
   float4 *adj32;        // mixed adjoint scratch, 7 * cap_n float4
+  float *adj_sums;      // mixed adjoint: the forward pass A's pair sums, 16 * cap_n
   sph::Units *units;    // device
   double vscale;        // host: velocity scale for the time unit
   sph::MatTable mt;     // host copy of the materials of the current call
@@ -355,8 +356,10 @@ void refine_partners(sph_ctx *c, const sph_state *s, const unsigned long long *m
 void adapt_h(sph_ctx *c, sph_state *s, double n_des, int tol, int max_iter, int32_t *flags, cudaStream_t st);
 void partners_to_csr(sph_ctx *c, const sph_state *s, int64_t *off, int32_t *idx, int64_t cap, cudaStream_t st);
 // rhs.cu
+// sums: NULL, or (mixed) where pass A also stores its pair sums for the
+// adjoint (16 * cap_n floats, the layout of k_passA's KEEP_SUMS form)
 void rhs_passes(sph_ctx *c, sph_state *s, const MatTable &mt, const sph_params &p, const sph_derivs &out,
-                cudaStream_t st);
+                cudaStream_t st, float *sums = nullptr);
 // gravity.cu
 // reuse: the tree was built at earlier positions (pseudo-particles reused)
 void gravity_walk(sph_ctx *c, const sph_state *s, const sph_params &p, double *ax, double *ay, double *az,
