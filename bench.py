@@ -127,10 +127,10 @@ NCU_PER_PARTICLE = {
                  "src": ("neighbours.cu", "9347fbb88607e52e")},
     "refine": {"inst": 10.60, "dram": 67.06, "fp32_pipe": 0.095, "issue": 0.228, "l1": 0.290,
                "src": ("neighbours.cu", "9347fbb88607e52e")},
-    "passA": {"inst": 337.12, "dram": 502.26, "fp32_pipe": 0.378, "issue": 0.577, "l1": 0.598,
-              "src": ("rhs.cu", "8827649bc4c00d27")},
-    "passB": {"inst": 360.78, "dram": 348.28, "fp32_pipe": 0.413, "issue": 0.577, "l1": 0.839,
-              "src": ("rhs.cu", "8827649bc4c00d27")},
+    "passA": {"inst": 337.12, "dram": 501.14, "fp32_pipe": 0.379, "issue": 0.576, "l1": 0.601,
+              "src": ("rhs.cu", "61aa0561564061da")},
+    "passB": {"inst": 360.75, "dram": 348.58, "fp32_pipe": 0.409, "issue": 0.574, "l1": 0.833,
+              "src": ("rhs.cu", "61aa0561564061da")},
 }
 
 
