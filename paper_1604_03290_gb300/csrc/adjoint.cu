@@ -270,18 +270,19 @@ __global__ void k_adj_passB(AdjArgs A) {
 // ---------------------------------------------------------------------------
 // Constitutive update, recomputed and reversed
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool invert_L(int dim, const double L[3][3], double C[3][3]) {
-  double det;
+template <class R>
+__device__ __forceinline__ bool invert_L(int dim, const R L[3][3], R C[3][3]) {
+  R det;
   if (dim == 2) det = L[0][0] * L[1][1] - L[0][1] * L[1][0];
   else
     det = L[0][0] * (L[1][1] * L[2][2] - L[1][2] * L[2][1]) - L[0][1] * (L[1][0] * L[2][2] - L[1][2] * L[2][0]) +
           L[0][2] * (L[1][0] * L[2][1] - L[1][1] * L[2][0]);
-  double diag = 1.0;
+  R diag = R(1);
   for (int i = 0; i < dim; ++i) diag *= fabs(L[i][i]);
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) C[i][j] = i == j ? 1.0 : 0.0;
-  if (!(fabs(det) > 1e-8 * diag) || !(diag > 0.0)) return false;
-  const double inv = 1.0 / det;
+    for (int j = 0; j < 3; ++j) C[i][j] = i == j ? R(1) : R(0);
+  if (!(fabs(det) > R(1e-8) * diag) || !(diag > R(0))) return false;
+  const R inv = R(1) / det;
   if (dim == 2) {
     C[0][0] = L[1][1] * inv;
     C[0][1] = -L[0][1] * inv;
@@ -313,34 +314,39 @@ __device__ void eos_scaled(const sph_material &M0, double s, double rho, double 
 }
 
 // MIXED: the pass-A sums are the forward pass A's own (FP32, code units, kept
-// by it for this kernel) converted to SI, and the equation of state is
-// differentiated in FP32 dual numbers; the rest of the reverse of the
-// constitutive update is FP64 in both forms.  FP64: the sums are recomputed
-// here.
+// by it for this kernel), the equation of state is differentiated in FP32
+// dual numbers, and the rest of the reverse runs in FP32 in SI units.  The
+// reverse is linear in the cotangents it is given (of T, c_s and dS/dt), so
+// each particle's are scaled by a power of two to order one first and its
+// results scaled back exactly: FP32's exponent range then limits only the
+// state, whose SI values it holds.  FP64: the sums are recomputed here, and
+// the reverse is FP64 throughout (F = double, no scaling).
 template <bool MIXED, int DIM>
 __global__ void k_adj_update(AdjArgs A) {
+  using F = typename std::conditional<MIXED, float, double>::type;
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= A.n) return;
   constexpr int dim = DIM;
   const int ns = nsym(dim);
   const sph_params &P = A.prm;
-  // ---- pass-A sums, recomputed ----
+  const int64_t ld = A.ld;
+  // ---- pass-A sums ----
   const double rc = A.rho[c];
-  double srho = 0.0, L[3][3], G[3][3];
+  double srho = 0.0;
+  F L[3][3], G[3][3];
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) L[i][j] = G[i][j] = 0.0;
+    for (int j = 0; j < 3; ++j) L[i][j] = G[i][j] = F(0);
   const int cnt = A.nb_cnt[c];
   if constexpr (MIXED) {
-    // the forward pass A's own FP32 sums (k_passA's KEEP_SUMS layout); the
-    // continuity sum and G are rates (code unit 1/T), L is a number
+    // k_passA's KEEP_SUMS layout; the continuity sum and G are rates (code
+    // unit 1/T, a power of two: the conversion is exact), L is a number
     const float *sm = A.sums;
-    const int64_t ld = A.ld;
-    const double it = A.U->invT;
-    srho = (double)sm[c] * it;
+    const float it = (float)A.U->invT;
+    srho = (double)sm[c] * A.U->invT;
     for (int i = 0; i < dim; ++i)
       for (int j = 0; j <= i; ++j) L[i][j] = L[j][i] = sm[(int64_t)(1 + i * (i + 1) / 2 + j) * ld + c];
     for (int i = 0; i < dim; ++i)
-      for (int j = 0; j < dim; ++j) G[i][j] = (double)sm[(int64_t)(7 + 3 * i + j) * ld + c] * it;
+      for (int j = 0; j < dim; ++j) G[i][j] = sm[(int64_t)(7 + 3 * i + j) * ld + c] * it;
   } else {
     double xc[3] = {0, 0, 0}, vc[3] = {0, 0, 0};
     for (int i = 0; i < dim; ++i) {
@@ -368,158 +374,184 @@ __global__ void k_adj_update(AdjArgs A) {
         }
     }
   }
-  double C[3][3];
-  const bool corr = P.consistency && cnt >= dim + 1 && invert_L(dim, L, C);
+  F C[3][3];
+  const bool corr = P.consistency && cnt >= dim + 1 && invert_L<F>(dim, L, C);
   if (!corr)
     for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) C[i][j] = i == j ? 1.0 : 0.0;
-  double gv[3][3];
+      for (int j = 0; j < 3; ++j) C[i][j] = i == j ? F(1) : F(0);
+  F gv[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      double s = 0.0;
+      F s = F(0);
       for (int k = 0; k < dim; ++k) s += G[i][k] * C[k][j];
-      gv[i][j] = (i < dim && j < dim) ? s : 0.0;
+      gv[i][j] = (i < dim && j < dim) ? s : F(0);
     }
   // ---- constitutive state ----
   const int mi0 = A.mat ? A.mat[c] : 0;
   const int mi = (mi0 >= 0 && mi0 < A.mt.nmat) ? mi0 : 0;
   const sph_material &M = A.mt.m[mi];
   const double uc = A.u[c];
-  double p, cs, pr, pu;
+  const F mu = (F)M.mu, Y0 = (F)M.Y0;
+  F p, pr, pu;
   // MIXED: one evaluation in FP32 dual numbers, in the forward's code units,
-  // gives p, c_s, dp/drho, dp/du and the exact derivatives of c_s in rho and u
-  // and of p and c_s in the bulk-modulus scale; FP64: the analytic derivatives
-  // of p here, those of c_s and the scale by central differences below.
-  double dcr = 0.0, dcu = 0.0, dps = 0.0, dcs = 0.0;
+  // gives p, dp/drho, dp/du and the exact derivatives of c_s in rho and u and
+  // of p and c_s in the bulk-modulus scale (code units to SI by powers of
+  // two); FP64: the analytic derivatives of p here, those of c_s and the
+  // scale by central differences below.
+  F dcr = F(0), dcu = F(0), dps = F(0), dcs = F(0);
   if constexpr (MIXED) {
     const Units *U = A.U;
     const EosC<ad::Dual3> K = eos_consts<ad::Dual3>(M, U->matf[mi], U);
     ad::Dual3 p3, c3, pr3, pu3;
     eos_eval<ad::Dual3>(M, K, rc, uc, p3, c3, &pr3, &pu3);
-    p = (double)p3.v * U->sig;
-    cs = (double)c3.v * U->V;
-    pr = (double)pr3.v * U->sig * U->invrho;
-    pu = (double)pu3.v * U->sig * U->invE;
-    dcr = (double)c3.d[0] * U->V * U->invrho;
-    dcu = (double)c3.d[1] * U->V * U->invE;
-    dps = (double)p3.d[2] * U->sig;
-    dcs = (double)c3.d[2] * U->V;
+    p = p3.v * (float)U->sig;
+    pr = pr3.v * (float)(U->sig * U->invrho);
+    pu = pu3.v * (float)(U->sig * U->invE);
+    dcr = c3.d[0] * (float)(U->V * U->invrho);
+    dcu = c3.d[1] * (float)(U->V * U->invE);
+    dps = p3.d[2] * (float)U->sig;
+    dcs = c3.d[2] * (float)U->V;
   } else {
+    double cs;
     eos_scaled(M, 1.0, rc, uc, p, cs, &pr, &pu);
   }
   const bool strength = A.S != nullptr && M.strength;
-  double S[3][3], St[3][3];
+  F S[3][3], St[3][3];
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) S[i][j] = (strength && i < dim && j < dim) ? A.S[(int64_t)sidx(dim, i, j) * A.n + c] : 0.0;
-  double J2 = 0.0;
+    for (int j = 0; j < 3; ++j)
+      S[i][j] = (strength && i < dim && j < dim) ? (F)A.S[(int64_t)sidx(dim, i, j) * A.n + c] : F(0);
+  F J2 = F(0);
   for (int i = 0; i < dim; ++i)
     for (int j = 0; j < dim; ++j) J2 += S[i][j] * S[i][j];
-  J2 *= 0.5;
-  double fY = 1.0;
-  if (strength && M.Y0 > 0.0 && J2 > 0.0) fY = fmin(M.Y0 * M.Y0 / (3.0 * J2), 1.0);
+  J2 *= F(0.5);
+  F fY = F(1);
+  if (strength && M.Y0 > 0.0 && J2 > F(0)) {
+    const F q = Y0 * Y0 / (F(3) * J2);
+    fY = q < F(1) ? q : F(1);
+  }
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) St[i][j] = fY * S[i][j];
   const bool damage = A.dmg != nullptr && M.damage;
-  double dd = 0.0;
+  F dd = F(0);
   if (damage) {
-    const double del = A.dmg[c];
+    const F del = (F)A.dmg[c];
     dd = del * del * del;
   }
+  // ---- the cotangents (of T, c_s, dS/dt), scaled (MIXED) ----
+  double sc = 1.0, isc = 1.0;
+  if constexpr (MIXED) {
+    double mx = fabs(A.csbar[c]);
+    for (int k = 0; k < ns; ++k) mx = fmax(mx, fabs(A.Tbar[(int64_t)k * ld + c]));
+    if (A.bdS && strength)
+      for (int k = 0; k < ns; ++k) mx = fmax(mx, fabs(A.bdS[(int64_t)k * A.n + c]));
+    if (mx > 0.0 && mx < INFINITY) {
+      int e;
+      frexp(mx, &e);
+      sc = ldexp(1.0, -e);
+      isc = ldexp(1.0, e);
+    }
+  }
   // ---- reverse: T = sigma / rho^2 ----
-  double Tb[3][3], Tc[6];
-  load_T64(A, c, Tc);
-  double TbT = 0.0, trSig = 0.0;
+  F Tb[3][3], Tc[6];
+  {
+    double t64[6];
+    load_T64(A, c, t64);
+    for (int k = 0; k < 6; ++k) Tc[k] = (F)t64[k];
+  }
+  F TbT = F(0), trSig = F(0);
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      Tb[i][j] = (i < dim && j < dim) ? A.Tbar[(int64_t)sidx(dim, i, j) * A.ld + c] : 0.0;
+      Tb[i][j] = (i < dim && j < dim) ? (F)(A.Tbar[(int64_t)sidx(dim, i, j) * A.ld + c] * sc) : F(0);
       if (i < dim && j < dim) TbT += Tb[i][j] * Tc[sidx(dim, i, j)];
     }
-  double rhobar = -2.0 * TbT / rc;
-  const double irc2 = 1.0 / (rc * rc);  // one division for the nine components below
-  double sigbar[3][3];
+  const F rcf = (F)rc;
+  F rhobar = F(-2) * TbT / rcf;
+  const F irc2 = F(1) / (rcf * rcf);  // one division for the nine components below
+  F sigbar[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) sigbar[i][j] = Tb[i][j] * irc2;
   for (int i = 0; i < dim; ++i) trSig += sigbar[i][i];
   // sigma = -p_hat I + (1 - d) S_tilde
-  const double phatbar = -trSig;
-  const double pbar = p >= 0.0 ? phatbar : (1.0 - dd) * phatbar;
-  double Stbar[3][3];
+  const F phatbar = -trSig;
+  const F pbar = p >= F(0) ? phatbar : (F(1) - dd) * phatbar;
+  F Stbar[3][3];
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) Stbar[i][j] = (1.0 - dd) * sigbar[i][j];
+    for (int j = 0; j < 3; ++j) Stbar[i][j] = (F(1) - dd) * sigbar[i][j];
   // ---- reverse: dS = 2 mu (eps_dot - tr/D I) + R S_t - S_t R ----
-  double Sdb[3][3];  // full-matrix cotangent of dS (symmetric)
+  F Sdb[3][3];  // full-matrix cotangent of dS (symmetric)
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      double cst = (A.bdS && strength && i < dim && j < dim) ? A.bdS[(int64_t)sidx(dim, i, j) * A.n + c] : 0.0;
-      Sdb[i][j] = (i == j) ? cst : 0.5 * cst;
+      const F cst = (A.bdS && strength && i < dim && j < dim) ? (F)(A.bdS[(int64_t)sidx(dim, i, j) * A.n + c] * sc)
+                                                               : F(0);
+      Sdb[i][j] = (i == j) ? cst : F(0.5) * cst;
     }
-  double ed[3][3], Rr[3][3], tr = 0.0;
+  F ed[3][3], Rr[3][3], tr = F(0);
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      ed[i][j] = 0.5 * (gv[i][j] + gv[j][i]);
-      Rr[i][j] = 0.5 * (gv[i][j] - gv[j][i]);
+      ed[i][j] = F(0.5) * (gv[i][j] + gv[j][i]);
+      Rr[i][j] = F(0.5) * (gv[i][j] - gv[j][i]);
     }
   for (int i = 0; i < dim; ++i) tr += ed[i][i];
-  double mubar = 0.0, trSdb = 0.0;
+  F mubar = F(0), trSdb = F(0);
   for (int i = 0; i < dim; ++i) trSdb += Sdb[i][i];
-  const double tr_d = tr / dim, trSdb_d = trSdb / dim;
+  const F tr_d = tr / F(dim), trSdb_d = trSdb / F(dim);
   for (int i = 0; i < dim; ++i)
-    for (int j = 0; j < dim; ++j) mubar += 2.0 * (ed[i][j] - (i == j ? tr_d : 0.0)) * Sdb[i][j];
-  double edbar[3][3], Rbar[3][3];
+    for (int j = 0; j < dim; ++j) mubar += F(2) * (ed[i][j] - (i == j ? tr_d : F(0))) * Sdb[i][j];
+  F edbar[3][3], Rbar[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      edbar[i][j] = (i < dim && j < dim) ? 2.0 * M.mu * (Sdb[i][j] - (i == j ? trSdb_d : 0.0)) : 0.0;
-      double a1 = 0.0, a2 = 0.0, b1 = 0.0, b2 = 0.0;
+      edbar[i][j] = (i < dim && j < dim) ? F(2) * mu * (Sdb[i][j] - (i == j ? trSdb_d : F(0))) : F(0);
+      F a1 = F(0), a2 = F(0), b1 = F(0), b2 = F(0);
       for (int k = 0; k < dim; ++k) {
         a1 += Sdb[i][k] * St[k][j];  // Z S_t
         a2 += St[i][k] * Sdb[k][j];  // S_t Z
         b1 += Rr[i][k] * Sdb[k][j];  // R Z
         b2 += Sdb[i][k] * Rr[k][j];  // Z R
       }
-      Rbar[i][j] = (i < dim && j < dim) ? a1 - a2 : 0.0;
+      Rbar[i][j] = (i < dim && j < dim) ? a1 - a2 : F(0);
       if (i < dim && j < dim) Stbar[i][j] += -b1 + b2;
     }
   if (!strength)
     for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) edbar[i][j] = Rbar[i][j] = 0.0;
-  double gvbar[3][3];
+      for (int j = 0; j < 3; ++j) edbar[i][j] = Rbar[i][j] = F(0);
+  F gvbar[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j)
-      gvbar[i][j] = 0.5 * (edbar[i][j] + edbar[j][i]) + 0.5 * (Rbar[i][j] - Rbar[j][i]);
+      gvbar[i][j] = F(0.5) * (edbar[i][j] + edbar[j][i]) + F(0.5) * (Rbar[i][j] - Rbar[j][i]);
   // ---- reverse: S_t = f_Y S (stored components) ----
-  double Y0bar = 0.0;
+  F Y0bar = F(0);
   if (strength && A.gS) {
-    double Stb_st[6], S_st[6];
+    F Stb_st[6], S_st[6];
     for (int i = 0; i < dim; ++i)
       for (int j = i; j < dim; ++j) {
         const int k = sidx(dim, i, j);
         Stb_st[k] = (i == j) ? Stbar[i][i] : Stbar[i][j] + Stbar[j][i];
         S_st[k] = S[i][j];
       }
-    double proj = 0.0;
+    F proj = F(0);
     for (int k = 0; k < ns; ++k) proj += Stb_st[k] * S_st[k];
-    const bool yielding = M.Y0 > 0.0 && J2 > 0.0 && M.Y0 * M.Y0 / (3.0 * J2) < 1.0;
-    const double fjp = yielding ? fY / J2 * proj : 0.0;
+    const bool yielding = M.Y0 > 0.0 && J2 > F(0) && Y0 * Y0 / (F(3) * J2) < F(1);
+    const F fjp = yielding ? fY / J2 * proj : F(0);
     for (int k = 0; k < ns; ++k) {
-      double sb = Stb_st[k];
+      F sb = Stb_st[k];
       if (yielding) {
-        const double wk = k < dim ? 1.0 : 2.0;
+        const F wk = k < dim ? F(1) : F(2);
         sb = fY * Stb_st[k] - fjp * wk * S_st[k];
       }
-      A.gS[(int64_t)k * A.n + c] += sb;
+      A.gS[(int64_t)k * A.n + c] += (double)sb * isc;
     }
-    if (yielding) Y0bar = proj * 2.0 * fY / M.Y0;
+    if (yielding) Y0bar = proj * F(2) * fY / Y0;
   }
-  // ---- reverse: EOS (analytic dp/drho, dp/du; c_s and the bulk scale by central differences) ----
-  const double csbar = A.csbar[c];
-  double ubar = pbar * pu;
+  // ---- reverse: EOS ----
+  const F csbar = (F)(A.csbar[c] * sc);
+  F ubar = pbar * pu;
   rhobar += pbar * pr;
-  double Kbar = 0.0;
+  F Kbar = F(0);
   if constexpr (MIXED) {
-    const double Kref = fmax(fmax(M.K0, M.A_T), M.B_T);
+    const float Kref = (float)fmax(fmax(M.K0, M.A_T), M.B_T);
     rhobar += csbar * dcr;
     ubar += csbar * dcu;
-    if (Kref > 0.0) Kbar = (pbar * dps + csbar * dcs) / Kref;
+    if (Kref > 0.f) Kbar = (pbar * dps + csbar * dcs) / Kref;
   } else {
     const double er = 1e-6 * rc, eu = 1e-6 * (fabs(uc) + 1e-3 * fabs(M.E0) + 1e-30), es = 1e-6;
     const double Kref = fmax(fmax(M.K0, M.A_T), M.B_T);
@@ -552,54 +584,52 @@ __global__ void k_adj_update(AdjArgs A) {
     if (Kref > 0.0) Kbar = (pbar * dps + csbar * dcs) / (2.0 * es * Kref);
   }
   // ---- reverse: grad v = G C, C = L^-1 ----
-  double Gbar[3][3], Lbar[3][3];
+  F Gbar[3][3], Lbar[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      double s = 0.0;
+      F s = F(0);
       for (int k = 0; k < dim; ++k) s += gvbar[i][k] * C[j][k];  // gvbar C^T
-      Gbar[i][j] = (i < dim && j < dim) ? s : 0.0;
-      Lbar[i][j] = 0.0;
+      Gbar[i][j] = (i < dim && j < dim) ? s : F(0);
+      Lbar[i][j] = F(0);
     }
   if (corr) {
-    double Cbar[3][3], T1[3][3];
+    F Cbar[3][3], T1[3][3];
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) {
-        double s = 0.0;
+        F s = F(0);
         for (int k = 0; k < dim; ++k) s += G[k][i] * gvbar[k][j];  // G^T gvbar
         Cbar[i][j] = s;
       }
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) {
-        double s = 0.0;
+        F s = F(0);
         for (int k = 0; k < dim; ++k) s += Cbar[i][k] * C[j][k];  // Cbar C^T
         T1[i][j] = s;
       }
     for (int i = 0; i < dim; ++i)
       for (int j = 0; j < dim; ++j) {
-        double s = 0.0;
+        F s = F(0);
         for (int k = 0; k < dim; ++k) s += C[k][i] * T1[k][j];  // C^T (Cbar C^T)
         Lbar[i][j] = -s;
       }
   }
-  // ---- reverse: drho = rho * sum_rho ; dx = v + xsph * xs ----
+  // ---- reverse: drho = rho * sum_rho ; dx = v + xsph * xs (FP64, unscaled) ----
   const double bdr = A.bdrho ? A.bdrho[c] : 0.0;
-  rhobar += bdr * srho;
-  A.grho[c] += rhobar;
-  A.gu[c] += ubar;
+  A.grho[c] += (double)rhobar * isc + bdr * srho;
+  A.gu[c] += (double)ubar * isc;
   for (int i = 0; i < dim; ++i)
     if (A.bdx[i]) A.gv[i][c] += A.bdx[i][c];
   double *I = A.inter;
-  const int64_t ld = A.ld;
   I[c] = rc * bdr;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      I[(1 + 3 * i + j) * ld + c] = Lbar[i][j];
-      I[(10 + 3 * i + j) * ld + c] = Gbar[i][j];
+      I[(1 + 3 * i + j) * ld + c] = (double)Lbar[i][j] * isc;
+      I[(10 + 3 * i + j) * ld + c] = (double)Gbar[i][j] * isc;
     }
   for (int i = 0; i < 3; ++i) I[(19 + i) * ld + c] = (i < dim && A.bdx[i]) ? P.xsph * A.bdx[i][c] : 0.0;
-  A.pbar[c] = strength ? mubar : 0.0;
-  A.pbar[ld + c] = Y0bar;
-  A.pbar[2 * ld + c] = Kbar;
+  A.pbar[c] = strength ? (double)mubar * isc : 0.0;
+  A.pbar[ld + c] = (double)Y0bar * isc;
+  A.pbar[2 * ld + c] = (double)Kbar * isc;
 }
 
 // ---------------------------------------------------------------------------
