@@ -127,10 +127,10 @@ NCU_PER_PARTICLE = {
                  "src": ("neighbours.cu", "9347fbb88607e52e")},
     "refine": {"inst": 10.60, "dram": 67.06, "fp32_pipe": 0.095, "issue": 0.228, "l1": 0.290,
                "src": ("neighbours.cu", "9347fbb88607e52e")},
-    "passA": {"inst": 337.12, "dram": 501.14, "fp32_pipe": 0.379, "issue": 0.576, "l1": 0.601,
-              "src": ("rhs.cu", "61aa0561564061da")},
-    "passB": {"inst": 360.75, "dram": 348.58, "fp32_pipe": 0.409, "issue": 0.574, "l1": 0.833,
-              "src": ("rhs.cu", "61aa0561564061da")},
+    "passA": {"inst": 337.12, "dram": 501.59, "fp32_pipe": 0.378, "issue": 0.578, "l1": 0.597,
+              "src": ("rhs.cu", "694f09c579c6db1a")},
+    "passB": {"inst": 336.22, "dram": 347.68, "fp32_pipe": 0.420, "issue": 0.573, "l1": 0.897,
+              "src": ("rhs.cu", "694f09c579c6db1a")},
 }
 
 

@@ -241,48 +241,31 @@ __device__ __forceinline__ int partner_list(const RhsArgs &A, int64_t a, const i
   return cnt;
 }
 
-template <bool MIXED, bool WITH_T = false>
+// (The partner's stress pack in pass B is loaded in the loop body, not ahead:
+// prefetching it too took three more registers and made pass B 6 % slower.)
+template <bool MIXED>
 struct PartnerCursor {
   using Raw = typename Own<MIXED>::Raw;
-  static constexpr bool kT = MIXED && WITH_T;  // also the neighbour's T words (pass B, mixed)
   const int32_t *col;
   int64_t ld;
   int cnt;
   int32_t b1, b2;
   Raw r1;
-  float4 t0, t1;
   __device__ __forceinline__ void start(const RhsArgs &A, const Own<MIXED> &o, const int32_t *list, int n) {
     col = list;
     ld = A.ld;
     cnt = n;
     b1 = n > 0 ? col[0] : 0;
     b2 = n > 1 ? col[ld] : 0;
-    if (n > 0) {
-      r1 = o.fetch(A, b1);
-      if constexpr (kT) {
-        t0 = A.Tf[b1];
-        t1 = A.Tf[A.ld + b1];
-      }
-    }
+    if (n > 0) r1 = o.fetch(A, b1);
   }
-  // the pair k: its index, its raw data and (kT) its T words
-  __device__ __forceinline__ int32_t next(const RhsArgs &A, const Own<MIXED> &o, int k, Raw &cur, float4 &ct0,
-                                          float4 &ct1) {
+  // the pair k: its index and its raw data
+  __device__ __forceinline__ int32_t next(const RhsArgs &A, const Own<MIXED> &o, int k, Raw &cur) {
     const int32_t b = b1;
     cur = r1;
-    if constexpr (kT) {
-      ct0 = t0;
-      ct1 = t1;
-    }
     b1 = b2;
     if (k + 2 < cnt) b2 = col[(int64_t)(k + 2) * ld];
-    if (k + 1 < cnt) {
-      r1 = o.fetch(A, b1);
-      if constexpr (kT) {
-        t0 = A.Tf[b1];
-        t1 = A.Tf[A.ld + b1];
-      }
-    }
+    if (k + 1 < cnt) r1 = o.fetch(A, b1);
     return b;
   }
 };
@@ -436,8 +419,7 @@ __global__ void SPH_PASSA_BOUNDS k_passA(RhsArgs A) {
     R d[3], w[3], hb, rhob, mb, vol;
 #if SPH_PASS_PREFETCH
     typename Own<MIXED>::Raw raw;
-    float4 t0, t1;
-    cur.next(A, o, k, raw, t0, t1);
+    cur.next(A, o, k, raw);
     o.from(A, raw, d, w, hb, rhob, mb, vol);
 #else
     const int32_t b = list[(int64_t)k * A.ld];
@@ -746,7 +728,7 @@ __global__ void SPH_PASSB_BOUNDS k_passB(RhsArgs A) {
   const int32_t *list;
   const int cnt = partner_list(A, a, list);
 #if SPH_PASS_PREFETCH
-  PartnerCursor<MIXED, true> cur;
+  PartnerCursor<MIXED> cur;
   cur.start(A, o, list, cnt);
 #endif
   for (int k = 0; k < cnt; ++k) {
@@ -754,20 +736,9 @@ __global__ void SPH_PASSB_BOUNDS k_passB(RhsArgs A) {
     R Tb[6], csb;
 #if SPH_PASS_PREFETCH
     typename Own<MIXED>::Raw raw;
-    float4 t0, t1;
-    const int32_t b = cur.next(A, o, k, raw, t0, t1);
+    const int32_t b = cur.next(A, o, k, raw);
     o.from(A, raw, d, w, hb, rhob, mb, vol);
-    if constexpr (MIXED) {
-      Tb[0] = t0.x;
-      Tb[1] = t0.y;
-      Tb[2] = t0.z;
-      Tb[3] = t0.w;
-      Tb[4] = t1.x;
-      Tb[5] = t1.y;
-      csb = t1.z;
-    } else {
-      load_T<MIXED>(A, b, ns, Tb, csb);
-    }
+    load_T<MIXED>(A, b, ns, Tb, csb);
 #else
     const int32_t b = list[(int64_t)k * A.ld];
     o.pair(A, b, d, w, hb, rhob, mb, vol);
