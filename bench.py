@@ -127,10 +127,10 @@ NCU_PER_PARTICLE = {
                  "src": ("neighbours.cu", "9347fbb88607e52e")},
     "refine": {"inst": 10.60, "dram": 67.06, "fp32_pipe": 0.095, "issue": 0.228, "l1": 0.290,
                "src": ("neighbours.cu", "9347fbb88607e52e")},
-    "passA": {"inst": 337.12, "dram": 501.59, "fp32_pipe": 0.378, "issue": 0.578, "l1": 0.597,
-              "src": ("rhs.cu", "694f09c579c6db1a")},
-    "passB": {"inst": 336.22, "dram": 347.68, "fp32_pipe": 0.420, "issue": 0.573, "l1": 0.897,
-              "src": ("rhs.cu", "694f09c579c6db1a")},
+    "passA": {"inst": 315.03, "dram": 499.16, "fp32_pipe": 0.384, "issue": 0.582, "l1": 0.695,
+              "src": ("rhs.cu", "34f6a376fba94640")},
+    "passB": {"inst": 336.22, "dram": 347.92, "fp32_pipe": 0.416, "issue": 0.567, "l1": 0.889,
+              "src": ("rhs.cu", "34f6a376fba94640")},
 }
 
 

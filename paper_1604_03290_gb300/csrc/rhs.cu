@@ -76,10 +76,10 @@ __device__ __forceinline__ double rsqrt_or_zero<double>(double r2) {
 
 // Resident blocks per SM the neighbour passes are compiled for (register
 // budget).  Measured on GB300 with the partner prefetch below: pass A is
-// fastest at 6 (capped registers) in mixed precision, pass B with the
-// compiler's own choice.
+// fastest at 7 (capped registers, positions alone prefetched) in mixed
+// precision, pass B with the compiler's own choice.
 #ifndef SPH_PASSA_MIN_BLOCKS
-#define SPH_PASSA_MIN_BLOCKS 6
+#define SPH_PASSA_MIN_BLOCKS 7
 #endif
 #define SPH_PASSA_BOUNDS __launch_bounds__(128, MIXED ? SPH_PASSA_MIN_BLOCKS : 1)  // FP64: uncapped
 #ifdef SPH_PASSB_MIN_BLOCKS
@@ -172,7 +172,9 @@ struct Own<false> {
   struct Raw {
     int32_t b;
   };
+  using RawPos = Raw;
   __device__ __forceinline__ Raw fetch(const RhsArgs &, int32_t b) const { return Raw{b}; }
+  __device__ __forceinline__ Raw fetch_pos(const RhsArgs &, int32_t b) const { return Raw{b}; }
   __device__ __forceinline__ void from(const RhsArgs &A, const Raw &r, double d[3], double w[3], double &hb,
                                        double &rhob, double &mb, double &vol) const {
     pair(A, r.b, d, w, hb, rhob, mb, vol);
@@ -195,12 +197,24 @@ struct Own<true> {
   struct Raw {
     float4 P, Q, V, W;
   };
+  // the positions alone, the velocity views loaded when the pair is evaluated
+  struct RawPos {
+    float4 P, Q;
+    int32_t b;
+  };
   __device__ __forceinline__ Raw fetch(const RhsArgs &A, int32_t b) const {
     return Raw{A.pk.px(b), A.pk.pxl(b), A.pk.pv(b), A.pk.pvl(b)};
+  }
+  __device__ __forceinline__ RawPos fetch_pos(const RhsArgs &A, int32_t b) const {
+    return RawPos{A.pk.px(b), A.pk.pxl(b), b};
   }
   __device__ __forceinline__ void from(const RhsArgs &, const Raw &r, float d[3], float w[3], float &hb,
                                        float &rhob, float &mb, float &vol) const {
     unpack(r.P, r.Q, r.V, r.W, d, w, hb, rhob, mb, vol);
+  }
+  __device__ __forceinline__ void from(const RhsArgs &A, const RawPos &r, float d[3], float w[3], float &hb,
+                                       float &rhob, float &mb, float &vol) const {
+    unpack(r.P, r.Q, A.pk.pv(r.b), A.pk.pvl(r.b), d, w, hb, rhob, mb, vol);
   }
   __device__ __forceinline__ void pair(const RhsArgs &A, int32_t b, float d[3], float w[3], float &hb, float &rhob,
                                        float &mb, float &vol) const {
@@ -241,11 +255,17 @@ __device__ __forceinline__ int partner_list(const RhsArgs &A, int64_t a, const i
   return cnt;
 }
 
-// (The partner's stress pack in pass B is loaded in the loop body, not ahead:
-// prefetching it too took three more registers and made pass B 6 % slower.)
-template <bool MIXED>
+// POS: only the partner's position views are loaded ahead (pass A, whose
+// registers then allow 7 resident blocks per SM: 4 % faster on GB300); pass B
+// loads positions and velocities ahead (its stress pack in the loop body:
+// prefetching that too took three more registers and made it 6 % slower).
+template <bool MIXED, bool POS = false>
 struct PartnerCursor {
-  using Raw = typename Own<MIXED>::Raw;
+  using Raw = typename std::conditional<POS, typename Own<MIXED>::RawPos, typename Own<MIXED>::Raw>::type;
+  __device__ __forceinline__ static Raw get(const RhsArgs &A, const Own<MIXED> &o, int32_t b) {
+    if constexpr (POS) return o.fetch_pos(A, b);
+    else return o.fetch(A, b);
+  }
   const int32_t *col;
   int64_t ld;
   int cnt;
@@ -257,7 +277,7 @@ struct PartnerCursor {
     cnt = n;
     b1 = n > 0 ? col[0] : 0;
     b2 = n > 1 ? col[ld] : 0;
-    if (n > 0) r1 = o.fetch(A, b1);
+    if (n > 0) r1 = get(A, o, b1);
   }
   // the pair k: its index and its raw data
   __device__ __forceinline__ int32_t next(const RhsArgs &A, const Own<MIXED> &o, int k, Raw &cur) {
@@ -265,7 +285,7 @@ struct PartnerCursor {
     cur = r1;
     b1 = b2;
     if (k + 2 < cnt) b2 = col[(int64_t)(k + 2) * ld];
-    if (k + 1 < cnt) r1 = o.fetch(A, b1);
+    if (k + 1 < cnt) r1 = get(A, o, b1);
     return b;
   }
 };
@@ -412,13 +432,13 @@ __global__ void SPH_PASSA_BOUNDS k_passA(RhsArgs A) {
   const int32_t *list;
   const int cnt = partner_list(A, a, list);
 #if SPH_PASS_PREFETCH
-  PartnerCursor<MIXED> cur;
+  PartnerCursor<MIXED, true> cur;
   cur.start(A, o, list, cnt);
 #endif
   for (int k = 0; k < cnt; ++k) {
     R d[3], w[3], hb, rhob, mb, vol;
 #if SPH_PASS_PREFETCH
-    typename Own<MIXED>::Raw raw;
+    typename PartnerCursor<MIXED, true>::Raw raw;
     cur.next(A, o, k, raw);
     o.from(A, raw, d, w, hb, rhob, mb, vol);
 #else
