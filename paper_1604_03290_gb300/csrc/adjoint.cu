@@ -51,6 +51,40 @@ struct AdjArgs {
 
 __device__ __forceinline__ int sidx(int dim, int i, int j) { return symk(dim, i, j); }
 
+// Partner list of particle c in the mixed pair kernels: the index read two
+// pairs ahead and the partner's position views one pair ahead (as in the
+// forward pass A), so that their loads are in flight during the pair before.
+struct AdjCursor {
+  const int32_t *col;
+  int64_t ld;
+  int cnt;
+  int32_t e1, e2;
+  float4 P1, Q1;
+  __device__ __forceinline__ void start(const AdjArgs &A, int64_t c, int n) {
+    col = A.nb_idx + c;
+    ld = A.ld;
+    cnt = n;
+    e1 = n > 0 ? col[0] : 0;
+    e2 = n > 1 ? col[ld] : 0;
+    if (n > 0) {
+      P1 = A.pk.px(e1);
+      Q1 = A.pk.pxl(e1);
+    }
+  }
+  __device__ __forceinline__ int32_t next(const AdjArgs &A, int k, float4 &P, float4 &Q) {
+    const int32_t e = e1;
+    P = P1;
+    Q = Q1;
+    e1 = e2;
+    if (k + 2 < cnt) e2 = col[(int64_t)(k + 2) * ld];
+    if (k + 1 < cnt) {
+      P1 = A.pk.px(e1);
+      Q1 = A.pk.pxl(e1);
+    }
+    return e;
+  }
+};
+
 // Kernel radial factors for a pair: phi = dW/dr / r and phi'(r)/r, W, dW/dr.
 template <class R>
 struct KPair {
@@ -886,9 +920,12 @@ __global__ void k_adj_passB32(AdjArgs A) {
   const float vbc[3] = {bc.x, bc.y, bc.z};
   KahanT<float> gx[3], gv[3], Tb[6], csb, rhb;
   const int cnt = A.nb_cnt[c];
+  AdjCursor cur;
+  cur.start(A, c, cnt);
   for (int k = 0; k < cnt; ++k) {
-    const int32_t e = A.nb_idx[(int64_t)k * A.ld + c];
-    const float4 Pe = A.pk.px(e), Qe = A.pk.pxl(e), Ve = A.pk.pv(e), We = A.pk.pvl(e);
+    float4 Pe, Qe;
+    const int32_t e = cur.next(A, k, Pe, Qe);
+    const float4 Ve = A.pk.pv(e), We = A.pk.pvl(e);
     float d[3] = {(Pc.x - Pe.x) + (Qc.x - Qe.x), (Pc.y - Pe.y) + (Qc.y - Qe.y),
                   DIM == 3 ? (Pc.z - Pe.z) + (Qc.z - Qe.z) : 0.f};
     float w[3] = {(Vc.x - Ve.x) + (Wc.x - We.x), (Vc.y - Ve.y) + (Wc.y - We.y),
@@ -981,9 +1018,12 @@ __global__ void k_adj_passA32(AdjArgs A) {
   const ACot<float> Cc = load_acot32(A, c);
   KahanT<float> gx[3], gv[3], grho;
   const int cnt = A.nb_cnt[c];
+  AdjCursor cur;
+  cur.start(A, c, cnt);
   for (int k = 0; k < cnt; ++k) {
-    const int32_t e = A.nb_idx[(int64_t)k * A.ld + c];
-    const float4 Pe = A.pk.px(e), Qe = A.pk.pxl(e), Ve = A.pk.pv(e), We = A.pk.pvl(e);
+    float4 Pe, Qe;
+    const int32_t e = cur.next(A, k, Pe, Qe);
+    const float4 Ve = A.pk.pv(e), We = A.pk.pvl(e);
     float d[3] = {(Pc.x - Pe.x) + (Qc.x - Qe.x), (Pc.y - Pe.y) + (Qc.y - Qe.y),
                   DIM == 3 ? (Pc.z - Pe.z) + (Qc.z - Qe.z) : 0.f};
     float w[3] = {(Vc.x - Ve.x) + (Wc.x - We.x), (Vc.y - Ve.y) + (Wc.y - We.y),
