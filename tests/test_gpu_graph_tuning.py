@@ -51,6 +51,27 @@ def test_graph_replay_equals_direct_steps(S, prec, case):
     assert np.all(dt.cpu().numpy() > 0)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_graph_replay_with_tree_window_equals_direct_steps(S, prec):
+    # one tree per 4 steps inside each replay of a 4-step graph (params.tree_reuse):
+    # every replay starts its own window, as a 4-step call does
+    ps = flawed(wl.batched_impacts(seed=5, ninst=4, nmin=300, nmax=1200))
+    prm = replace(ps.params, max_depth=18, precision=prec, tree_reuse=4)
+    ctx1 = S.Context(3, ps.n, max_instances=ps.ninst, max_neighbours=160)
+    ctx2 = S.Context(3, ps.n, max_instances=ps.ninst, max_neighbours=160)
+    d1, d2 = S.DeviceState(ps), S.DeviceState(ps)
+    S.step(ctx1, d1, ps.materials, prm, 1)  # the graph helper's warm-up step
+    for _ in range(3):
+        S.step(ctx1, d1, ps.materials, prm, 4)
+    g = S.StepGraph(ctx2, d2, ps.materials, prm, nsteps=4)
+    for _ in range(3):
+        g.replay()
+    import torch
+    torch.cuda.synchronize()
+    ctx2.sync_status()
+    _state_equal(d1.to_numpy(), d2.to_numpy())
+
+
 def test_autotuner_keeps_results_identical(S, tmp_path):
     from paper_1604_03290_gb300 import autotune
     ps = flawed(wl.measurement_1m(seed=4, n_side=14))
