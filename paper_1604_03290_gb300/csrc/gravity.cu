@@ -127,8 +127,14 @@ __device__ __forceinline__ double r2_fp64(const double xa[3], double cx, double 
   return r2;
 }
 
-template <bool MIXED, int DIM>
+// PACKED (mixed, Tree::packed_walk): a node's skip, level and leaf flag come
+// from the w word of its second COM view, so that a visit loads two float4
+// (the node's member range only when some lane sums it directly), and the
+// node edge s0 / 2^level is the instance's FP32 edge shifted by the level:
+// the same value k_node_finish stores otherwise.
+template <bool MIXED, int DIM, bool PACKED>
 __global__ void __launch_bounds__(kGrWarps * 32, SPH_GRAV_MIN_BLOCKS) k_gravity(GravArgs A) {
+  static_assert(MIXED || !PACKED, "the packed word is read by the mixed walk");
   using R = typename std::conditional<MIXED, float, double>::type;
   __shared__ float4 sh_hi[kGrWarps][kMaxLeaf];  // (x_hi, y_hi, z_hi, G m_b) of leaf members
   __shared__ float4 sh_lo[kGrWarps][kMaxLeaf];
@@ -165,6 +171,8 @@ __global__ void __launch_bounds__(kGrWarps * 32, SPH_GRAV_MIN_BLOCKS) k_gravity(
     const double e = MIXED ? A.eps * (double)Pa.w : A.eps * A.h[a];
     const R eps2 = (R)(e * e);
     const double s0r = T.inst_s0[inst];
+    // the instance's root edge in FP32 code units (PACKED: shifted by the level per node)
+    const float s0f = PACKED ? to_f32_scaled(s0r, pow2_exp(A.U->invL), A.U->invL) : 0.f;
     const double th = A.theta;
     const float th2f = (float)(th * th);
     // A node whose cube holds the particle also holds its centre of mass, so
@@ -179,10 +187,25 @@ __global__ void __launch_bounds__(kGrWarps * 32, SPH_GRAV_MIN_BLOCKS) k_gravity(
     int iter = 0;
     unsigned nacc = 0, nterm = 0;  // this lane's accepted nodes and particle terms (counters)
     for (int32_t nd = root; nd < stop && iter <= nnodes; ++iter) {
-      const int4 rec = T.nrec[nd];  // (first, end, skip, level)
-      const int32_t f = rec.x, e1 = rec.y, sk = rec.z;
-      const int lev = rec.w;
-      const bool leaf = (e1 - f <= L) || lev == B;
+      int32_t f = 0, e1 = 0, sk;
+      int lev;
+      bool leaf;
+      float4 ch, cl;
+      if constexpr (PACKED) {
+        ch = T.fcom_hi[nd];
+        cl = T.fcom_lo[nd];
+        const uint32_t wd = __float_as_uint(cl.w);
+        sk = (int32_t)(wd & (uint32_t)kPackedSkip);
+        lev = (int)((wd >> 26) & 31u);
+        leaf = (wd >> 31) != 0u;
+      } else {
+        const int4 rec = T.nrec[nd];  // (first, end, skip, level)
+        f = rec.x;
+        e1 = rec.y;
+        sk = rec.z;
+        lev = rec.w;
+        leaf = (e1 - f <= L) || lev == B;
+      }
       bool open = false, direct = false;
       if (act && nd >= skip_until) {
         const bool inside = test_inside && (ka >> (dim * (B - lev))) == T.cell[nd];
@@ -191,13 +214,16 @@ __global__ void __launch_bounds__(kGrWarps * 32, SPH_GRAV_MIN_BLOCKS) k_gravity(
         R d[3] = {R(0), R(0), R(0)}, r2 = R(0);
         if (!inside) {
           if constexpr (MIXED) {
-            const float4 ch = T.fcom_hi[nd], cl = T.fcom_lo[nd];
+            if constexpr (!PACKED) {
+              ch = T.fcom_hi[nd];
+              cl = T.fcom_lo[nd];
+            }
             d[0] = (Pa.x - ch.x) + (Qa.x - cl.x);
             d[1] = (Pa.y - ch.y) + (Qa.y - cl.y);
             d[2] = (Pa.z - ch.z) + (Qa.z - cl.z);
             r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
             mpf = ch.w;
-            const float sf = cl.w;
+            const float sf = PACKED ? __int_as_float(__float_as_int(s0f) - (lev << 23)) : cl.w;
             const float lhs = sf * sf, rhs = th2f * r2;
             if (lhs < rhs * (1.0f - kMacBand)) accept = true;
             else if (lhs > rhs * (1.0f + kMacBand)) accept = false;
@@ -233,6 +259,11 @@ __global__ void __launch_bounds__(kGrWarps * 32, SPH_GRAV_MIN_BLOCKS) k_gravity(
       const bool any_open = __any_sync(0xffffffffu, open);
       const unsigned dmask = __ballot_sync(0xffffffffu, direct);
       if (dmask) {
+        if constexpr (PACKED) {
+          const int4 rec = T.nrec[nd];
+          f = rec.x;
+          e1 = rec.y;
+        }
         for (int32_t base = f; base < e1; base += kMaxLeaf) {
           const int c = min(e1 - base, kMaxLeaf);
           int32_t bm = -1;
@@ -354,12 +385,15 @@ void gravity_walk(sph_ctx *c, const sph_state *s, const sph_params &p, double *a
   A.ctr = counters(c);
   int blocks = c->num_sms * SPH_GRAV_MIN_BLOCKS;  // persistent: the resident blocks, looping over groups
   const bool mixed = p.precision == SPH_MIXED;
+  const bool packed = mixed && c->tree.packed_walk;
   if (s->dim == 3) {
-    if (mixed) { k_gravity<true, 3><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
-    else { k_gravity<false, 3><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
+    if (packed) { k_gravity<true, 3, true><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
+    else if (mixed) { k_gravity<true, 3, false><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
+    else { k_gravity<false, 3, false><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
   } else {
-    if (mixed) { k_gravity<true, 2><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
-    else { k_gravity<false, 2><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
+    if (packed) { k_gravity<true, 2, true><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
+    else if (mixed) { k_gravity<true, 2, false><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
+    else { k_gravity<false, 2, false><<<blocks, kGrWarps * 32, 0, st>>>(A); ++sph::g_launches; }
   }
 }
 

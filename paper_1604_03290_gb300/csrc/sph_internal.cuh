@@ -59,6 +59,9 @@ struct PackedF32 {
   __host__ __device__ float4 &pvl(int64_t i) const { return pvl_[i]; }  // (vx_lo, vy_lo, vz_lo, m/rho)
 };
 
+// Largest skip index of the packed node word of the gravity walk (26 bits).
+constexpr int64_t kPackedSkip = (1LL << 26) - 1;
+
 struct Tree {
   // sort
   unsigned long long *keys[2];
@@ -75,6 +78,7 @@ struct Tree {
   int32_t *scan_tmp;
   // nodes (pre-order)
   int64_t cap_nodes;
+  int packed_walk;     // fcom_lo.w holds the packed node word (cap_nodes <= kPackedSkip + 1)
   int32_t *nnodes;     // device scalar
   int32_t *first, *end, *skip, *parent, *nchild, *arrived, *level;
   int32_t *child;      // up to 8 child ids per node, in arrival order
@@ -87,7 +91,9 @@ struct Tree {
                        //  where the partner walk stops: at most max(leaf_size, walk_leaf) particles or depth B)
   float4 *fbox_hi;     // (hi xyz, rounded up; skip[] as int bits)
   float4 *fcom_hi;     // (com hi xyz relative to instance corner, mass)
-  float4 *fcom_lo;     // (com lo xyz, edge s0 / 2^level)
+  float4 *fcom_lo;     // (com lo xyz, w): w = the edge s0 / 2^level, or, where packed_walk, the word
+                       // skip | level << 26 | leaf << 31 as int bits (leaf: at most leaf_size
+                       // particles or level max_depth), the edge then being s0 / 2^level
   // per instance
   unsigned long long *inst_bb;  // 6 per instance: encoded min xyz, encoded max xyz
   double *inst_lo;     // 3 per instance

@@ -795,10 +795,16 @@ __global__ void k_node_finish(Tree T, int dim, int L, const int64_t *__restrict_
   // is built from its bits)
   const float ef = to_f32_scaled(T.inst_s0[inst], kL - lev, bitsd((uint64_t)(1023 + kL - lev) << 52));
   const bool stop = ne - nf <= Lw || lev == T.max_depth;
+  // the gravity walk's word: skip, level and whether the walk sums the node's
+  // members directly (its leaf test); the edge follows from the level
+  const bool gleaf = ne - nf <= L || lev == T.max_depth;
+  const float wf = T.packed_walk ? __uint_as_float((uint32_t)T.skip[node] | ((uint32_t)lev << 26) |
+                                                   (gleaf ? 0x80000000u : 0u))
+                                 : ef;
   T.fbox_lo[node] = make_float4(bl[0], bl[1], bl[2], stop ? -hf : hf);
   T.fbox_hi[node] = make_float4(bh[0], bh[1], bh[2], __int_as_float(T.skip[node]));
   T.fcom_hi[node] = make_float4(chi[0], chi[1], chi[2], mf);
-  T.fcom_lo[node] = make_float4(clo[0], clo[1], clo[2], ef);
+  T.fcom_lo[node] = make_float4(clo[0], clo[1], clo[2], wf);
 }
 
 // ---------------------------------------------------------------------------
@@ -818,6 +824,7 @@ void tree_build(sph_ctx *c, const sph_state *s, int leaf_size, int max_depth, cu
   const int dim = s->dim;
   T.leaf_size = leaf_size;
   T.max_depth = max_depth;
+  T.packed_walk = (T.cap_nodes <= kPackedSkip && max_depth <= 31) ? 1 : 0;
   T.perm_identity = 0;
   T.dim = dim;
   T.ninst = ninst;
