@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kGrWarps * 32, SPH_GRAV_MIN_BLOCKS) k_gravity(
     const int inst = chunks ? 0 : T.grp_inst[g];
     const int32_t slot = s0 + lane;
     const bool act = slot < s1;
-    const int32_t a = act ? T.perm[slot] : 0;
+    const int32_t a = act ? (T.perm_identity ? slot : T.perm[slot]) : 0;  // identity: state in tree order
     double xa[3] = {0, 0, 0};
     for (int ax = 0; ax < dim; ++ax) xa[ax] = A.x[ax][a];
     // the cell of the particle's current position (the key of the build
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(kGrWarps * 32, SPH_GRAV_MIN_BLOCKS) k_gravity(
           int32_t bm = -1;
           float4 pb = make_float4(0.f, 0.f, 0.f, 0.f), qb = pb;
           if (lane < c) {
-            bm = T.perm[base + lane];
+            bm = T.perm_identity ? base + lane : T.perm[base + lane];
             pb = A.pk.px(bm);
             qb = A.pk.pxl(bm);
             sh_hi[w][lane] = make_float4(pb.x, pb.y, pb.z, -(float)G * qb.w);  // qb.w = m as float
