@@ -645,6 +645,9 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
     if ((r = check_continue(c, s, p, st)) != SPH_OK) return r;
     age = c->win_age;
   }
+  // the FP32 views hold s already: the last corrector wrote them (the first
+  // step of a call packs, as the state may have been changed between calls)
+  bool packed = false;
   for (int it = 0; it < nsteps; ++it) {
     const bool vh = p->n_des > 0.0;
     if (vh) {  // variable smoothing length from the last step's h (Sect. 4.2)
@@ -664,9 +667,11 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
       if (R > 0) cudaMemsetAsync(B.dbuild, 0, sizeof(unsigned long long), st);
       partners_gravity_passes(c, s, mt, *p, d[0], st, nullptr, false, refine);
     } else {
-      pr = prof_begin(c, st, PH_TREE);
-      pack_f32(c, s, st);
-      prof_end(c, st, pr);
+      if (!packed) {
+        pr = prof_begin(c, st, PH_TREE);
+        pack_f32(c, s, st);
+        prof_end(c, st, pr);
+      }
       // the lists and shells of the build step's walk stay in place: while
       // the displacement since that walk is within the shell's bound, the
       // partners are refined from them (else a walk over the widened boxes)
@@ -675,13 +680,11 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
     pr = prof_begin(c, st, PH_INTEGRATE);
     timestep_reduce(c, s, *p, d[0], st);
     if (reuse_pred) cudaMemsetAsync(B.dmove, 0, sizeof(unsigned long long), st);
-    pc_update(c, s, &q, d[0], 0.5, mt, *p, st, reuse_pred ? B.dmove : nullptr);
+    // on a kept tree the update also writes the predicted state's FP32 views
+    pc_update(c, s, &q, d[0], 0.5, mt, *p, st, reuse_pred ? B.dmove : nullptr, reuse_pred);
     if (reuse_pred && !build) bound_add(B.dgrow, B.dbuild, B.dmove, st);
     prof_end(c, st, pr);
     if (reuse_pred) {
-      pr = prof_begin(c, st, PH_TREE);
-      pack_f32(c, &q, st);
-      prof_end(c, st, pr);
       // displacement since the walk whose lists are refined: this step's walk
       // at a build, the build step's walk otherwise
       const unsigned long long *since = build ? B.dmove : B.dgrow;
@@ -690,11 +693,15 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
       rhs_all(c, &q, mt, *p, d[1], st);
     }
     pr = prof_begin(c, st, PH_INTEGRATE);
+    packed = false;
     if (R > 0) {  // the corrector's displacement joins the bound of the reused tree
+      // views of the new state for the next step of this call, if it keeps the tree
+      const bool keep = it + 1 < nsteps && !vh && (age + 1) % R != 0;
       cudaMemsetAsync(B.dmove, 0, sizeof(unsigned long long), st);
-      pc_update(c, s, s, d[1], 1.0, mt, *p, st, B.dmove);
+      pc_update(c, s, s, d[1], 1.0, mt, *p, st, B.dmove, keep);
       bound_add(B.dbuild, B.dbuild, B.dmove, st);
       age = (age + 1) % R;
+      packed = keep;
     } else {
       pc_update(c, s, s, d[1], 1.0, mt, *p, st);
     }

@@ -388,13 +388,16 @@ void fragments_fof(sph_ctx *c, const sph_state *s, const double *h0, double b, d
 void timestep_reduce(sph_ctx *c, const sph_state *s, const sph_params &p, const sph_derivs &d, cudaStream_t st);
 // dmove (device, may be NULL): receives the bits of max over particles and
 // axes of |out.x - base.x|; non-finite output or rho <= 0 then raises the
-// non-finite error bit, as a tree build over `out` would
+// non-finite error bit, as a tree build over `out` would.  pack: also write
+// the FP32 views of out (c->pk, in the units and instance corners of the
+// current tree), as pack_f32 would.
 void pc_update(sph_ctx *c, const sph_state *base, sph_state *out, const sph_derivs &d, double frac,
-               const MatTable &mt, const sph_params &p, cudaStream_t st, unsigned long long *dmove = nullptr);
+               const MatTable &mt, const sph_params &p, cudaStream_t st, unsigned long long *dmove = nullptr,
+               bool pack = false);
 // out = base + dt (coef_0 d_0 + ...), nd <= 3 sets, where mask[inst] (NULL: all)
 void combine_update(sph_ctx *c, const sph_state *base, sph_state *out, const sph_derivs *const *d, const double *coef,
                     int nd, const int32_t *mask, const MatTable &mt, const sph_params &p, cudaStream_t st,
-                    unsigned long long *dmove = nullptr);
+                    unsigned long long *dmove = nullptr, bool pack = false);
 // embedded Runge-Kutta: step size of the attempt (c->st.dt), error and control
 void rk_set_dt(sph_ctx *c, const sph_state *s, double *dt_io, cudaStream_t st);
 // *out = a + b rounded up (bits of non-negative doubles)

@@ -11,6 +11,7 @@
 #include <cmath>
 
 #include "fpbits.cuh"
+#include "pack.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -338,6 +339,11 @@ struct PcArgs {
   int density_sum;
   unsigned long long *dmove;  // NULL, or max |out.x - base.x| (bits of a non-negative double)
   int32_t *err;
+  // pack: also write the FP32 views of out (those k_pack would write)
+  int pack;
+  PackedF32 pk;
+  const double *ilo, *h, *m;
+  const Units *U;
 };
 
 // The combined derivative c_0 d_0[i] + c_1 d_1[i] + c_2 d_2[i], in that
@@ -392,12 +398,17 @@ __device__ __forceinline__ unsigned long long pc_particle(const PcArgs &A, int64
   const double dtc = dt * A.coef[0];
   unsigned long long mv = 0ULL;  // bits of max |ox - bx| (non-negative doubles order as integers)
   bool bad = false;
-  for (int ax = 0; ax < A.dim; ++ax) {
+  double xo[3] = {0.0, 0.0, 0.0}, vo[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    if (ax >= A.dim) continue;  // a constant trip count keeps xo, vo in registers
     const double bx = A.bx[ax][a];
     const double ox = upd(A, bx, dt, dtc, A.d[0].dx[ax], A.d[1].dx[ax], A.d[2].dx[ax], a);
     const double ov = upd(A, A.bv[ax][a], dt, dtc, A.d[0].dv[ax], A.d[1].dv[ax], A.d[2].dv[ax], a);
     A.ox[ax][a] = ox;
     A.ov[ax][a] = ov;
+    xo[ax] = ox;
+    vo[ax] = ov;
     if (A.dmove) {
       const unsigned long long m =
           A.pow2 ? move_bound_bits(dtc, A.d[0].dx[ax][a], ox, bx) : (dbits(ox - bx) & 0x7fffffffffffffffULL);
@@ -405,11 +416,16 @@ __device__ __forceinline__ unsigned long long pc_particle(const PcArgs &A, int64
       bad |= !finite_bits(ox) || !finite_bits(ov);
     }
   }
-  A.orho[a] = A.density_sum ? A.brho[a] : upd(A, A.brho[a], dt, dtc, A.d[0].drho, A.d[1].drho, A.d[2].drho, a);
+  const double rho_o =
+      A.density_sum ? A.brho[a] : upd(A, A.brho[a], dt, dtc, A.d[0].drho, A.d[1].drho, A.d[2].drho, a);
+  A.orho[a] = rho_o;
   if (A.dmove) {
-    bad |= !positive_finite_bits(A.orho[a]);
+    bad |= !positive_finite_bits(rho_o);
     if (bad) raise_err(A.err, ERR_NONFINITE);
   }
+  if (A.pack)
+    pack_particle(A.pk, a, A.dim, xo[0], xo[1], xo[2], vo[0], vo[1], vo[2], A.h[a], A.m[a], rho_o, A.ilo + 3 * inst,
+                  A.U);
   A.ou[a] = upd(A, A.bu[a], dt, dtc, A.d[0].du, A.d[1].du, A.d[2].du, a);
   const int mi = A.mat ? A.mat[a] : 0;
   const sph_material &M = A.mt.m[(mi >= 0 && mi < A.mt.nmat) ? mi : 0];
@@ -501,7 +517,7 @@ static DSet dset_of(const sph_derivs &d) {
 
 void combine_update(sph_ctx *c, const sph_state *base, sph_state *out, const sph_derivs *const *d, const double *coef,
                     int nd, const int32_t *mask, const MatTable &mt, const sph_params &p, cudaStream_t st,
-                    unsigned long long *dmove) {
+                    unsigned long long *dmove, bool pack) {
   if (base->n == 0) return;
   PcArgs A;
   memset(&A, 0, sizeof(A));
@@ -540,13 +556,21 @@ void combine_update(sph_ctx *c, const sph_state *base, sph_state *out, const sph
   A.density_sum = p.density_sum;
   A.dmove = dmove;
   A.err = c->d_err;
+  A.pack = pack ? 1 : 0;
+  if (pack) {
+    A.pk = c->pk;
+    A.ilo = c->tree.inst_lo;
+    A.h = out->h;
+    A.m = out->m;
+    A.U = c->units;
+  }
   { k_pc<<<nblk(base->n, 256), 256, 0, st>>>(A); ++sph::g_launches; }
 }
 
 void pc_update(sph_ctx *c, const sph_state *base, sph_state *out, const sph_derivs &d, double frac,
-               const MatTable &mt, const sph_params &p, cudaStream_t st, unsigned long long *dmove) {
+               const MatTable &mt, const sph_params &p, cudaStream_t st, unsigned long long *dmove, bool pack) {
   const sph_derivs *dd[1] = {&d};
-  combine_update(c, base, out, dd, &frac, 1, nullptr, mt, p, st, dmove);
+  combine_update(c, base, out, dd, &frac, 1, nullptr, mt, p, st, dmove, pack);
 }
 
 // ---------------------------------------------------------------------------

@@ -19,6 +19,7 @@
 #include "sph_internal.cuh"
 #include "fpbits.cuh"
 #include "morton.cuh"
+#include "pack.cuh"
 
 namespace sph {
 
@@ -231,25 +232,8 @@ __global__ void k_pack(const double *__restrict__ x, const double *__restrict__ 
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int inst = inst_of(inst_off, ninst, i);
-  // the code units are powers of two: scaling is an exponent shift, and the
-  // conversions and hi/lo splits run on the integer pipe (fpbits.cuh); only
-  // the corner subtraction needs the FP64 unit
-  const int kL = pow2_exp(U->invL), kV = pow2_exp(U->invV), kM = pow2_exp(U->invM), kR = pow2_exp(U->invrho);
-  const double X[3] = {__dsub_rn(x[i], ilo[3 * inst]), __dsub_rn(y[i], ilo[3 * inst + 1]),
-                       dim == 3 ? __dsub_rn(z[i], ilo[3 * inst + 2]) : 0.0};
-  const double V[3] = {vx[i], vy[i], dim == 3 ? vz[i] : 0.0};
-  float xh[3], xl[3], vh[3], vl[3];
-#pragma unroll
-  for (int ax = 0; ax < 3; ++ax) {
-    to_f32_split_scaled(X[ax], kL, U->invL, xh[ax], xl[ax]);
-    to_f32_split_scaled(V[ax], kV, U->invV, vh[ax], vl[ax]);
-  }
-  const float hf = to_f32_scaled(h[i], kL, U->invL), mf = to_f32_scaled(m[i], kM, U->invM);
-  const float rf = to_f32_scaled(rho[i], kR, U->invrho);
-  pk.px(i) = make_float4(xh[0], xh[1], xh[2], hf);
-  pk.pxl(i) = make_float4(xl[0], xl[1], xl[2], mf);
-  pk.pv(i) = make_float4(vh[0], vh[1], vh[2], rf);
-  pk.pvl(i) = make_float4(vl[0], vl[1], vl[2], __fdiv_rn(mf, rf));
+  pack_particle(pk, i, dim, x[i], y[i], dim == 3 ? z[i] : 0.0, vx[i], vy[i], dim == 3 ? vz[i] : 0.0, h[i], m[i],
+                rho[i], ilo + 3 * inst, U);
 }
 
 // ---------------------------------------------------------------------------
