@@ -381,7 +381,11 @@ sph_status sph_fragments(sph_ctx *ctx, const sph_state *state, const double *h0,
  * FP64; SPH_MIXED evaluates the forward pass in mixed precision and the pair
  * terms of the derivative in FP32 (in the power-of-two code units of the
  * forward pass, on hi/lo position and velocity differences, compensated sums),
- * the constitutive reverse in FP64 (within ~1e-6 of the FP64 form). */
+ * and the constitutive reverse in FP32: the forward pass A's own sums, the
+ * equation of state differentiated exactly by one dual-number evaluation, the
+ * rest in SI units with each particle's cotangents scaled by a power of two
+ * (within ~3e-6 of the FP64 form, which takes the derivatives of c_s and of
+ * the bulk scale by central differences). */
 sph_status sph_rhs_adjoint(sph_ctx *ctx, sph_state *state, const sph_material *mats, int32_t nmat,
                            const sph_params *params, const sph_derivs *dbar, sph_state *state_bar, double *param_bar,
                            void *stream);
