@@ -171,13 +171,20 @@ typedef struct sph_ctx sph_ctx;
  * the friends-of-friends union by 2^24 pointer steps; a positive value lowers
  * both bounds to iter_cap.  A walk or find that reaches its bound stops and
  * the call returns SPH_ERR_TIMEOUT; a positive value exists to make that
- * happen on purpose (tests of the timeout report). */
+ * happen on purpose (tests of the timeout report).  plain_forms: 0 (default)
+ * lets the predictor-corrector update write the FP32 views of the state it
+ * produces on a kept tree, and the mixed Barnes-Hut walk read its node's skip,
+ * level and leaf flag packed into one word (while the node capacity fits 26
+ * bits); 1 packs the views in a separate launch at every evaluation and reads
+ * the node records unpacked.  Results are the same bit for bit either way; 1
+ * exists to test that. */
 typedef struct {
   int32_t walk_leaf;
   int32_t walk_blocks_per_sm;
   int32_t pass_threads;
   int32_t walk_every_eval;
   int32_t iter_cap;
+  int32_t plain_forms;
 } sph_tuning;
 
 /* Creates a context for up to max_particles particles in up to

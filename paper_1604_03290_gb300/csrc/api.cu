@@ -86,6 +86,7 @@ sph_status sph_create(sph_ctx **out, int32_t dim, int64_t max_particles, int32_t
   c->tune.pass_threads = 128;
   c->tune.walk_every_eval = 0;
   c->tune.iter_cap = 0;
+  c->tune.plain_forms = 0;
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   if (c->num_sms < 1) c->num_sms = 1;
   const int64_t N = max_particles;
@@ -648,6 +649,7 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
   // the FP32 views hold s already: the last corrector wrote them (the first
   // step of a call packs, as the state may have been changed between calls)
   bool packed = false;
+  const bool fuse = c->tune.plain_forms == 0;  // the update may write the views
   for (int it = 0; it < nsteps; ++it) {
     const bool vh = p->n_des > 0.0;
     if (vh) {  // variable smoothing length from the last step's h (Sect. 4.2)
@@ -681,10 +683,15 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
     timestep_reduce(c, s, *p, d[0], st);
     if (reuse_pred) cudaMemsetAsync(B.dmove, 0, sizeof(unsigned long long), st);
     // on a kept tree the update also writes the predicted state's FP32 views
-    pc_update(c, s, &q, d[0], 0.5, mt, *p, st, reuse_pred ? B.dmove : nullptr, reuse_pred);
+    pc_update(c, s, &q, d[0], 0.5, mt, *p, st, reuse_pred ? B.dmove : nullptr, reuse_pred && fuse);
     if (reuse_pred && !build) bound_add(B.dgrow, B.dbuild, B.dmove, st);
     prof_end(c, st, pr);
     if (reuse_pred) {
+      if (!fuse) {
+        pr = prof_begin(c, st, PH_TREE);
+        pack_f32(c, &q, st);
+        prof_end(c, st, pr);
+      }
       // displacement since the walk whose lists are refined: this step's walk
       // at a build, the build step's walk otherwise
       const unsigned long long *since = build ? B.dmove : B.dgrow;
@@ -696,7 +703,7 @@ sph_status sph_step(sph_ctx *c, sph_state *s, const sph_material *mats, int32_t 
     packed = false;
     if (R > 0) {  // the corrector's displacement joins the bound of the reused tree
       // views of the new state for the next step of this call, if it keeps the tree
-      const bool keep = it + 1 < nsteps && !vh && (age + 1) % R != 0;
+      const bool keep = fuse && it + 1 < nsteps && !vh && (age + 1) % R != 0;
       cudaMemsetAsync(B.dmove, 0, sizeof(unsigned long long), st);
       pc_update(c, s, s, d[1], 1.0, mt, *p, st, B.dmove, keep);
       bound_add(B.dbuild, B.dbuild, B.dmove, st);
@@ -870,7 +877,8 @@ sph_status sph_set_tuning(sph_ctx *c, const sph_tuning *t) {
   if (!c || !t) return SPH_ERR_INVALID;
   const int pt = t->pass_threads;
   if (t->walk_leaf < 8 || t->walk_leaf > 1024 || t->walk_blocks_per_sm < 1 || t->walk_blocks_per_sm > 32 ||
-      !(pt == 64 || pt == 128) || (t->walk_every_eval != 0 && t->walk_every_eval != 1) || t->iter_cap < 0)
+      !(pt == 64 || pt == 128) || (t->walk_every_eval != 0 && t->walk_every_eval != 1) || t->iter_cap < 0 ||
+      (t->plain_forms != 0 && t->plain_forms != 1))
     return fail(c, SPH_ERR_INVALID, "tuning out of range");
   c->tune = *t;
   c->tree.iter_cap = t->iter_cap;

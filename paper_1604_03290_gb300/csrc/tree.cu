@@ -808,7 +808,7 @@ void tree_build(sph_ctx *c, const sph_state *s, int leaf_size, int max_depth, cu
   const int dim = s->dim;
   T.leaf_size = leaf_size;
   T.max_depth = max_depth;
-  T.packed_walk = (T.cap_nodes <= kPackedSkip && max_depth <= 31) ? 1 : 0;
+  T.packed_walk = (c->tune.plain_forms == 0 && T.cap_nodes <= kPackedSkip && max_depth <= 31) ? 1 : 0;
   T.perm_identity = 0;
   T.dim = dim;
   T.ninst = ninst;

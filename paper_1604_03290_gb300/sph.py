@@ -71,7 +71,7 @@ class State(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("walk_leaf", C.c_int32), ("walk_blocks_per_sm", C.c_int32), ("pass_threads", C.c_int32),
-                ("walk_every_eval", C.c_int32), ("iter_cap", C.c_int32)]
+                ("walk_every_eval", C.c_int32), ("iter_cap", C.c_int32), ("plain_forms", C.c_int32)]
 
 
 class Derivs(C.Structure):
@@ -229,13 +229,13 @@ class Context:
         t = Tuning()
         self.check(self._lib.sph_get_tuning(self.h, C.byref(t)), "sph_get_tuning")
         return {"walk_leaf": t.walk_leaf, "walk_blocks_per_sm": t.walk_blocks_per_sm, "pass_threads": t.pass_threads,
-                "walk_every_eval": t.walk_every_eval, "iter_cap": t.iter_cap}
+                "walk_every_eval": t.walk_every_eval, "iter_cap": t.iter_cap, "plain_forms": t.plain_forms}
 
     def set_tuning(self, **kw):
         cur = self.get_tuning()
         cur.update(kw)
         t = Tuning(cur["walk_leaf"], cur["walk_blocks_per_sm"], cur["pass_threads"], int(cur["walk_every_eval"]),
-                   int(cur["iter_cap"]))
+                   int(cur["iter_cap"]), int(cur["plain_forms"]))
         self.check(self._lib.sph_set_tuning(self.h, C.byref(t)), "sph_set_tuning")
 
     def profile(self, on=True):

@@ -93,3 +93,29 @@ def test_autotuner_keeps_results_identical(S, tmp_path):
     # cached
     prm3, best3, _ = autotune.tune(ctx, ds, ps.materials, prm, cache_path=str(tmp_path / "t.json"))
     assert best3 == best
+
+
+@pytest.mark.parametrize("case", ["impact", "cloud", "ceres"])
+def test_plain_forms_equal_fused_forms(S, case):
+    """sph_tuning.plain_forms = 1 packs the FP32 views in a separate launch at
+    every evaluation and reads the gravity walk's node records unpacked; the
+    default writes the views in the update on a kept tree and reads the packed
+    node word.  Steps on a reused tree must give the same states bit for bit."""
+    if case == "impact":
+        ps = flawed(wl.measurement_1m(seed=5, n_side=18))
+        prm = replace(ps.params, precision="mixed", tree_reuse=4)
+    elif case == "cloud":  # variable h: a tree per step, the packed gravity word
+        ps = wl.cloud_collapse(seed=3, n=30_000)
+        prm = replace(ps.params, precision="mixed", tree_reuse=3)
+    else:  # gravity on a kept tree: both forms at once
+        ps = flawed(wl.ceres_pair(seed=4, n_each=15_000))
+        prm = replace(ps.params, precision="mixed", tree_reuse=3)
+    out = []
+    for plain in (0, 1):
+        ctx = S.Context(3, ps.n, max_neighbours=160, leaf_size=ps.params.leaf_size)
+        ctx.set_tuning(plain_forms=plain)
+        assert ctx.get_tuning()["plain_forms"] == plain
+        ds = S.DeviceState(ps)
+        S.step(ctx, ds, ps.materials, prm, 7)
+        out.append(ds.to_numpy())
+    _state_equal(out[0], out[1])
